@@ -1,0 +1,423 @@
+"""CPU oracle for the 32-bit RNS-CKKS key-switch path (Cheddar, arxiv 2407.13055).
+
+TEST INFRASTRUCTURE ONLY. Tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it; the CUDA library never imports it.
+
+The integer arithmetic lives in ``ckks_oracle.cpp`` (plain C++, built with g++
+by :func:`build`); this module wraps it with numpy arrays and adds the
+floating-point encoding (Sec. 2.1: u in C^{N/2} -> <Delta u> in R_Q) and the
+big-integer CRT lift used by decoding, both written plainly in Python.
+
+Parity unpinned: none. Every function is pinned by ``tests/test_oracle_*.py``
+against schoolbook products, big-integer CRT, closed forms or brute force.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ckks_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libckks_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+U32P = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the C++ oracle into a shared library (g++, -O2, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            i, u32, u64, i64 = C.c_int, C.c_uint32, C.c_uint64, C.c_int64
+            sig = {
+                "or_is_prime": (i, [u64]),
+                "or_gen_primes": (i, [i, i, i, U32P, U32P]),
+                "or_find_psi": (u32, [u32, i]),
+                "or_smr": (C.c_int32, [i64, u32]),
+                "or_ntt_naive": (None, [U32P, U32P, i, u32]),
+                "or_intt_naive": (None, [U32P, U32P, i, u32]),
+                "or_ntt": (None, [U32P, i, U32P, i]),
+                "or_intt": (None, [U32P, i, U32P, i]),
+                "or_bconv": (None, [U32P, i, U32P, U32P, i, U32P, i]),
+                "or_automorph_ntt": (None, [U32P, U32P, i, i, u32]),
+                "or_automorph_coeff": (None, [U32P, U32P, i, U32P, i, u32]),
+                "or_tensor": (None, [U32P, U32P, i, U32P, i, U32P]),
+                "or_modup": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P]),
+                "or_keymult": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P, U32P]),
+                "or_moddown": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P]),
+                "or_rescale": (None, [U32P, i, i, U32P, i, U32P]),
+                "or_hmult": (None, [i, i, U32P, i, U32P, i, U32P, U32P, i, U32P, i, U32P]),
+                "or_hrot": (None, [i, i, U32P, i, U32P, i, U32P, i, u32, U32P, U32P]),
+                "or_hadd": (None, [U32P, U32P, i, U32P, i, U32P]),
+                "or_pmult": (None, [U32P, U32P, i, U32P, i, U32P]),
+                "or_small_to_ntt": (None, [I64P, i, U32P, i, U32P]),
+                "or_encrypt": (None, [I64P, U32P, I64P, U32P, i, U32P, i, U32P]),
+                "or_decrypt": (None, [I64P, U32P, i, U32P, i, U32P]),
+                "or_keygen_ks": (None, [i, i, U32P, i, U32P, i, I64P, U32P, U32P, I64P, U32P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Parameters
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Params:
+    """RNS-CKKS parameters: N = 2^log_n, L ciphertext primes q, alpha auxiliary
+    primes p, dnum digits of alpha primes each (Sec. 2.1, Table 1)."""
+    log_n: int
+    q: np.ndarray
+    p: np.ndarray
+    dnum: int
+
+    @property
+    def n(self) -> int:
+        return 1 << self.log_n
+
+    @property
+    def L(self) -> int:
+        return len(self.q)
+
+    @property
+    def alpha(self) -> int:
+        return len(self.p)
+
+    def ext_primes(self, n_q: int) -> np.ndarray:
+        return np.concatenate([self.q[:n_q], self.p]).astype(np.uint32)
+
+    def all_primes(self) -> np.ndarray:
+        return self.ext_primes(self.L)
+
+    def digits(self, n_q: int) -> int:
+        return -(-n_q // self.alpha)
+
+    def args(self):
+        return (self.log_n, self.L, _u32(self.q), self.alpha, _u32(self.p), self.dnum)
+
+
+def gen_primes(log_n: int, n_q: int, n_p: int):
+    q = np.zeros(max(n_q, 1), np.uint32)
+    p = np.zeros(max(n_p, 1), np.uint32)
+    if lib().or_gen_primes(log_n, n_q, n_p, q, p) != 0:
+        raise ValueError("not enough NTT-friendly primes")
+    return q[:n_q].copy(), p[:n_p].copy()
+
+
+def make_params(log_n: int, L: int, dnum: int, alpha: int | None = None) -> Params:
+    """alpha = ceil(L / dnum) auxiliary primes unless given."""
+    if alpha is None:
+        alpha = -(-L // dnum)
+    q, p = gen_primes(log_n, L, alpha)
+    return Params(log_n, q, p, dnum)
+
+
+def is_prime(v: int) -> bool:
+    return bool(lib().or_is_prime(int(v)))
+
+
+def find_psi(q: int, log_n: int) -> int:
+    return int(lib().or_find_psi(int(q), log_n))
+
+
+def smr(x: int, q: int) -> int:
+    return int(lib().or_smr(int(x), int(q)))
+
+
+# ----------------------------------------------------------------------------
+# Polynomial operations (integer; wrappers around the C++ core)
+# ----------------------------------------------------------------------------
+
+def ntt_naive(a, q: int, log_n: int) -> np.ndarray:
+    out = np.zeros(1 << log_n, np.uint32)
+    lib().or_ntt_naive(_u32(a), out, log_n, int(q))
+    return out
+
+
+def intt_naive(a, q: int, log_n: int) -> np.ndarray:
+    out = np.zeros(1 << log_n, np.uint32)
+    lib().or_intt_naive(_u32(a), out, log_n, int(q))
+    return out
+
+
+def ntt(a, primes) -> np.ndarray:
+    a = _u32(a).copy()
+    primes = _u32(primes)
+    log_n = int(a.shape[-1]).bit_length() - 1
+    lib().or_ntt(a, len(primes), primes, log_n)
+    return a
+
+
+def intt(a, primes) -> np.ndarray:
+    a = _u32(a).copy()
+    primes = _u32(primes)
+    log_n = int(a.shape[-1]).bit_length() - 1
+    lib().or_intt(a, len(primes), primes, log_n)
+    return a
+
+
+def bconv(x, src, dst) -> np.ndarray:
+    x = _u32(x)
+    src, dst = _u32(src), _u32(dst)
+    log_n = int(x.shape[-1]).bit_length() - 1
+    out = np.zeros((len(dst), x.shape[-1]), np.uint32)
+    lib().or_bconv(x, len(src), src, out, len(dst), dst, log_n)
+    return out
+
+
+def automorph_ntt(a, k: int) -> np.ndarray:
+    a = _u32(a)
+    log_n = int(a.shape[-1]).bit_length() - 1
+    limbs = a.size >> log_n
+    out = np.zeros_like(a)
+    lib().or_automorph_ntt(a, out, limbs, log_n, int(k))
+    return out
+
+
+def automorph_coeff(a, primes, k: int) -> np.ndarray:
+    a = _u32(a)
+    primes = _u32(primes)
+    log_n = int(a.shape[-1]).bit_length() - 1
+    out = np.zeros_like(a)
+    lib().or_automorph_coeff(a, out, len(primes), primes, log_n, int(k))
+    return out
+
+
+def rot_k(r: int, log_n: int) -> int:
+    """Galois element of a left rotation by r slots: 5^r mod 2N (Eq. 4)."""
+    return pow(5, int(r) % (1 << (log_n - 1)), 2 << log_n)
+
+
+def conj_k(log_n: int) -> int:
+    return (2 << log_n) - 1
+
+
+def tensor(ct1, ct2, q) -> np.ndarray:
+    ct1, ct2, q = _u32(ct1), _u32(ct2), _u32(q)
+    n_q, n = ct1.shape[1], ct1.shape[2]
+    out = np.zeros((3, n_q, n), np.uint32)
+    lib().or_tensor(ct1, ct2, n_q, q, n.bit_length() - 1, out)
+    return out
+
+
+def modup(P: Params, d, n_q: int) -> np.ndarray:
+    d = _u32(d)
+    out = np.zeros((P.digits(n_q), n_q + P.alpha, P.n), np.uint32)
+    lib().or_modup(*P.args(), d, n_q, out)
+    return out
+
+
+def keymult(P: Params, up, n_q: int, evk) -> np.ndarray:
+    out = np.zeros((2, n_q + P.alpha, P.n), np.uint32)
+    lib().or_keymult(*P.args(), _u32(up), n_q, _u32(evk), out)
+    return out
+
+
+def moddown(P: Params, acc, n_q: int) -> np.ndarray:
+    out = np.zeros((2, n_q, P.n), np.uint32)
+    lib().or_moddown(*P.args(), _u32(acc), n_q, out)
+    return out
+
+
+def rescale(ct, q) -> np.ndarray:
+    ct, q = _u32(ct), _u32(q)
+    polys, n_q, n = ct.shape
+    out = np.zeros((polys, n_q - 1, n), np.uint32)
+    lib().or_rescale(ct, polys, n_q, q, n.bit_length() - 1, out)
+    return out
+
+
+def hmult(P: Params, ct1, ct2, evk, rescale: bool = True) -> np.ndarray:
+    ct1, ct2 = _u32(ct1), _u32(ct2)
+    n_q = ct1.shape[1]
+    out = np.zeros((2, n_q - (1 if rescale else 0), P.n), np.uint32)
+    lib().or_hmult(*P.args(), ct1, ct2, n_q, _u32(evk), int(bool(rescale)), out)
+    return out
+
+
+def hrot(P: Params, ct, k: int, evk) -> np.ndarray:
+    ct = _u32(ct)
+    n_q = ct.shape[1]
+    out = np.zeros((2, n_q, P.n), np.uint32)
+    lib().or_hrot(*P.args(), ct, n_q, int(k), _u32(evk), out)
+    return out
+
+
+def hadd(x, y, q) -> np.ndarray:
+    x, y = _u32(x), _u32(y)
+    out = np.zeros_like(x)
+    lib().or_hadd(x, y, x.shape[1], _u32(q), x.shape[2].bit_length() - 1, out)
+    return out
+
+
+def pmult(x, pt, q) -> np.ndarray:
+    x, pt = _u32(x), _u32(pt)
+    out = np.zeros_like(x)
+    lib().or_pmult(x, pt, x.shape[1], _u32(q), x.shape[2].bit_length() - 1, out)
+    return out
+
+
+def small_to_ntt(v, primes, log_n: int) -> np.ndarray:
+    primes = _u32(primes)
+    out = np.zeros((len(primes), 1 << log_n), np.uint32)
+    lib().or_small_to_ntt(_i64(v), len(primes), primes, log_n, out)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Keys and encryption (Eq. 1); random inputs come from the input generators
+# ----------------------------------------------------------------------------
+
+def encrypt(P: Params, s, pt, a, e) -> np.ndarray:
+    pt = _u32(pt)
+    n_q = pt.shape[0]
+    out = np.zeros((2, n_q, P.n), np.uint32)
+    lib().or_encrypt(_i64(s), _u32(a), _i64(e), pt, n_q, _u32(P.q[:n_q]), P.log_n, out)
+    return out
+
+
+def decrypt(P: Params, s, ct) -> np.ndarray:
+    ct = _u32(ct)
+    n_q = ct.shape[1]
+    out = np.zeros((n_q, P.n), np.uint32)
+    lib().or_decrypt(_i64(s), ct, n_q, _u32(P.q[:n_q]), P.log_n, out)
+    return out
+
+
+def keygen_ks(P: Params, s, s_from_ntt, a, e) -> np.ndarray:
+    """Key-switching key [dnum][2][L+alpha][N] from s_from (NTT domain) to s."""
+    out = np.zeros((P.dnum, 2, P.L + P.alpha, P.n), np.uint32)
+    lib().or_keygen_ks(*P.args(), _i64(s), _u32(s_from_ntt), _u32(a), _i64(e), out)
+    return out
+
+
+def keygen_relin(P: Params, s, a, e) -> np.ndarray:
+    sh = small_to_ntt(s, P.all_primes(), P.log_n)
+    s2 = ((sh.astype(np.uint64) * sh) % P.all_primes()[:, None].astype(np.uint64)).astype(np.uint32)
+    return keygen_ks(P, s, s2, a, e)
+
+
+def keygen_auto(P: Params, s, k: int, a, e) -> np.ndarray:
+    """Key for phi_k(s) -> s (rotation k = 5^r, conjugation k = 2N-1)."""
+    sh = small_to_ntt(s, P.all_primes(), P.log_n)
+    return keygen_ks(P, s, automorph_ntt(sh, k), a, e)
+
+
+# ----------------------------------------------------------------------------
+# Encoding (Sec. 2.1): slot j <-> zeta^(5^j mod 2N), zeta = exp(i pi / N)
+# ----------------------------------------------------------------------------
+
+def _slot_exponents(log_n: int) -> np.ndarray:
+    n = 1 << log_n
+    e = np.empty(n // 2, dtype=np.int64)
+    v = 1
+    for j in range(n // 2):
+        e[j] = v
+        v = v * 5 % (2 * n)
+    return e
+
+
+def encode_coeffs(u, scale: float, log_n: int) -> np.ndarray:
+    """round(Delta * sigma^-1(u)) as int64 coefficients (half away from zero).
+
+    sigma^-1: the real polynomial m with m(zeta^(5^j)) = u_j and
+    m(zeta^(-5^j)) = conj(u_j); m_k = (1/N) sum_{o odd} z_o zeta^(-o k),
+    i.e. zeta^-k (1/N) sum_j z_(2j+1) exp(-2 pi i j k / N): a length-N forward
+    FFT (numpy) followed by the twist zeta^-k.
+    """
+    n = 1 << log_n
+    e = _slot_exponents(log_n)
+    z = np.zeros(2 * n, dtype=np.complex128)
+    z[e] = u
+    z[(2 * n - e) % (2 * n)] = np.conj(u)
+    zo = z[1::2]                              # z at zeta^(2j+1)
+    k = np.arange(n)
+    m = np.exp(-1j * np.pi * k / n) * np.fft.fft(zo) / n
+    v = np.real(m) * scale
+    return (np.sign(v) * np.floor(np.abs(v) + 0.5)).astype(np.int64)
+
+
+def decode_coeffs(m, scale: float, log_n: int) -> np.ndarray:
+    """Slots u_j = m(zeta^(5^j)) / Delta from real coefficients m."""
+    n = 1 << log_n
+    k = np.arange(n)
+    tw = np.asarray(m, dtype=np.float64) * np.exp(1j * np.pi * k / n)
+    zo = np.fft.ifft(tw) * n                  # z_(2j+1) = sum_k m_k zeta^((2j+1)k)
+    e = _slot_exponents(log_n)
+    return zo[(e - 1) // 2] / scale
+
+
+def encode_coeffs_naive(u, scale: float, log_n: int) -> np.ndarray:
+    """O(N^2) definition of encode_coeffs (small N only)."""
+    n = 1 << log_n
+    e = _slot_exponents(log_n)
+    zeta = np.exp(1j * np.pi / n)
+    m = np.zeros(n)
+    for k in range(n):
+        s = 0j
+        for j in range(n // 2):
+            s += u[j] * zeta ** (-(int(e[j]) * k)) + np.conj(u[j]) * zeta ** (int(e[j]) * k)
+        m[k] = (s / n).real * scale
+    return (np.sign(m) * np.floor(np.abs(m) + 0.5)).astype(np.int64)
+
+
+def crt_centered(res, primes) -> list:
+    """Centered CRT lift of residues [n][N] to Python integers in (-Q/2, Q/2]."""
+    primes = [int(v) for v in primes]
+    Q = 1
+    for v in primes:
+        Q *= v
+    out = [0] * res.shape[1]
+    for i, qi in enumerate(primes):
+        qh = Q // qi
+        c = qh * pow(qh % qi, -1, qi)
+        col = res[i].astype(object)
+        out = [o + int(x) * c for o, x in zip(out, col)]
+    half = Q // 2
+    return [(o % Q) - Q if (o % Q) > half else o % Q for o in out]
+
+
+def encode(P: Params, u, scale: float, n_q: int) -> np.ndarray:
+    """Plaintext in the NTT domain [n_q][N]."""
+    m = encode_coeffs(u, scale, P.log_n)
+    return small_to_ntt(m, P.q[:n_q], P.log_n)
+
+
+def decode(P: Params, pt, scale: float) -> np.ndarray:
+    pt = _u32(pt)
+    n_q = pt.shape[0]
+    coef = intt(pt, P.q[:n_q])
+    big = crt_centered(coef, P.q[:n_q])
+    return decode_coeffs(np.array([float(b) for b in big]), scale, P.log_n)
