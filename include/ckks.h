@@ -1,0 +1,202 @@
+/*
+ * ckks.h -- C ABI of the GB300 RNS-CKKS key-switch library (libckks_gb300.so).
+ *
+ * The library implements the data-parallel hot path of the 32-bit-word
+ * RNS-CKKS scheme described in "Cheddar: A Swift Fully Homomorphic Encryption
+ * Library Designed for GPU Architectures" (arxiv 2407.13055): homomorphic
+ * multiplication and rotation with hybrid key switching, i.e. the negacyclic
+ * NTT/iNTT (Sec. 2.2, Eq. 3), fast basis conversion (Eq. 2), ModUp/ModDown
+ * (Sec. 2.3, Alg. 1), the evaluation-key inner product, tensor and
+ * relinearization, automorphism (Eq. 4) and rescaling (Sec. 2.1).
+ * Every step runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Status: every function returning int returns CKKS_OK (0) or a negative
+ *    CKKS_E* code; ckks_last_error() gives a message for the last failure on
+ *    that context.
+ *  - Ownership: handles are opaque and created through a context. Free each
+ *    with ckks_free() before ckks_ctx_destroy(). A ciphertext made by
+ *    ckks_ct_wrap_device() borrows the caller's device buffer and never frees
+ *    it.
+ *  - Ordering: all operations are enqueued on the context's CUDA stream and
+ *    are asynchronous unless stated; host buffers are read/written before the
+ *    call returns (those calls synchronize the stream). Outputs may alias
+ *    inputs only where stated.
+ *  - Residues: a polynomial at level l has n = l + 1 limbs, limb i modulo
+ *    q_i. Host ("canonical") layout is [limb][N] uint32 residues in [0, q_i)
+ *    with the NTT domain in natural order: A[i] = sum_k a_k psi^((2i+1)k) with
+ *    psi the smallest x in [2, q) with x^N = -1 mod q. A ciphertext is
+ *    [2][n][N] (b then a, Eq. 1). Device buffers use the library's internal
+ *    layout (NTT domain in bit-reversed order); only the import/export and
+ *    ckks_step_* calls see the canonical layout.
+ *  - Auxiliary limbs: an extended polynomial over PQ stores the n ciphertext
+ *    limbs followed by the alpha auxiliary limbs p_0 .. p_{alpha-1}.
+ *    Digit j of the key-switching gadget is q_{j*alpha} .. q_{j*alpha+alpha-1}.
+ *  - Prime ids (ckks_step_*): 0 .. n_q-1 name q_0 .. q_{n_q-1},
+ *    n_q .. n_q+n_p-1 name p_0 .. p_{n_p-1}.
+ */
+#ifndef CKKS_GB300_H
+#define CKKS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKKS_OK 0
+#define CKKS_EINVAL (-1)   /* bad argument, shape or parameter */
+#define CKKS_ELEVEL (-2)   /* level mismatch, or rescale at level 0 */
+#define CKKS_ESCALE (-3)   /* scales differ by more than a relative 2^-20 */
+#define CKKS_ENOKEY (-4)   /* missing or wrong kind of evaluation key */
+#define CKKS_ENOMEM (-5)   /* device or host allocation failed */
+#define CKKS_ECUDA (-6)    /* a CUDA call failed (message in ckks_last_error) */
+#define CKKS_ETIMEOUT (-7) /* a bounded device-side wait expired */
+#define CKKS_EBUSY (-8)    /* admission refused (memory footprint) */
+
+#define CKKS_RESCALE 1     /* ckks_hmult flag: rescale the product (Sec. 2.1) */
+
+typedef struct ckks_ctx ckks_ctx;
+typedef struct ckks_ct ckks_ct;
+typedef struct ckks_pt ckks_pt;
+typedef struct ckks_sk ckks_sk;
+typedef struct ckks_evk ckks_evk;
+
+/* Scheme parameters (Table 1 of the paper): N = 2^log_n; n_q ciphertext
+ * primes q_0..q_{n_q-1}; n_p = alpha auxiliary primes; dnum digits with
+ * dnum * alpha >= n_q. Every prime must satisfy q = 1 mod 2N (Eq. 3) and
+ * q < 2^31 (Sec. 3). log_n must be 8, 12 or 16. scale is the default
+ * encoding scale Delta; secret_hw is the Hamming weight of the ternary secret
+ * drawn by ckks_keygen_secret (0 = uniform ternary); sigma is the error
+ * standard deviation (3.2); seed seeds the library's own sampler. */
+typedef struct {
+  int log_n;
+  int n_q;
+  const uint32_t* q;
+  int n_p;
+  const uint32_t* p;
+  int dnum;
+  double scale;
+  int secret_hw;
+  double sigma;
+  uint64_t seed;
+} ckks_params;
+
+/* Library's prime rule (Eq. 3 with q < 2^31): q_0 is the largest prime below
+ * 2^31 with q = 1 mod 2N, q_1..q_{n_q-1} the largest such primes below 2^30 in
+ * decreasing order, p_0..p_{n_p-1} the next largest such primes below 2^31.
+ * Host only. Returns CKKS_EINVAL if not enough primes exist. */
+int ckks_gen_primes(int log_n, int n_q, int n_p, uint32_t* q_out, uint32_t* p_out);
+
+/* Context: validates the parameters, builds and uploads the per-prime tables
+ * (twiddles, Montgomery/Shoup constants, BConv matrices for every level) and
+ * allocates the key-switching scratch. cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream) on the current device, which must be an sm_103 GPU. */
+int ckks_ctx_create(const ckks_params* params, void* cuda_stream, ckks_ctx** out);
+void ckks_ctx_destroy(ckks_ctx* ctx);
+const char* ckks_last_error(ckks_ctx* ctx);
+int ckks_sync(ckks_ctx* ctx);            /* cudaStreamSynchronize on the context stream */
+void ckks_free(void* handle);            /* any ckks_ct / ckks_pt / ckks_sk / ckks_evk */
+/* Device bytes held by the context's tables and scratch (admission control). */
+size_t ckks_ctx_device_bytes(ckks_ctx* ctx);
+
+/* --- keys (Sec. 2.1; hybrid key switching after Han-Ki, cited by the paper) --- */
+/* Ternary secret drawn with the library's sampler (SplitMix64 stream). */
+int ckks_keygen_secret(ckks_ctx* ctx, uint64_t seed, ckks_sk** out);
+/* Secret from N signed coefficients in {-1, 0, 1} (host). */
+int ckks_sk_import(ckks_ctx* ctx, const int64_t* coeffs, ckks_sk** out);
+/* Relinearization key (s^2 -> s), rotation key (phi_{5^r}(s) -> s) and
+ * conjugation key (phi_{2N-1}(s) -> s); dnum digit pairs over all n_q + n_p
+ * primes, drawn with the library's sampler. */
+int ckks_keygen_relin(ckks_ctx* ctx, const ckks_sk* sk, uint64_t seed, ckks_evk** out);
+int ckks_keygen_rot(ckks_ctx* ctx, const ckks_sk* sk, int r, uint64_t seed, ckks_evk** out);
+int ckks_keygen_conj(ckks_ctx* ctx, const ckks_sk* sk, uint64_t seed, ckks_evk** out);
+/* Key from host residues [dnum][2][n_q + n_p][N] (canonical layout; pair j is
+ * (b_j, a_j)). galois = 0 for a relinearization key, else the Galois element
+ * k of phi_k (5^r mod 2N for a rotation by r, 2N - 1 for conjugation). */
+int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_evk** out);
+
+/* --- encoding and encryption --- */
+/* Encode N/2 complex slots (interleaved re, im) at `level` with `scale`:
+ * round(scale * sigma^-1(u)) (Sec. 2.1; slot j <-> zeta^(5^j), zeta =
+ * exp(i pi / N)), then NTT on the device. */
+int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out);
+/* Decode: iNTT on the device, centered CRT lift and FFT on the host; writes
+ * N/2 interleaved complex slots. Synchronizes. */
+int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out);
+/* Eq. 1: (b, a) = (-a s + m + e, a) with a uniform and e Gaussian from the
+ * library's sampler. */
+int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t seed, ckks_ct** out);
+/* m = b + a s. */
+int ckks_decrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_ct* ct, ckks_pt** out);
+
+/* --- ciphertext and plaintext objects --- */
+/* New ciphertext with room for `capacity_level` (capacity_level+1 limbs per
+ * polynomial); its level and scale are set by the operation that writes it. */
+int ckks_ct_create(ckks_ctx* ctx, int capacity_level, ckks_ct** out);
+int ckks_ct_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_ct** out);
+/* Copies [2][level+1][N] canonical residues to `host` (`words` = its size in
+ * uint32). Synchronizes. */
+int ckks_ct_export(ckks_ctx* ctx, const ckks_ct* ct, uint32_t* host, size_t words, int* level,
+                   double* scale);
+/* Re-import host residues into an existing ciphertext (no allocation). */
+int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* ct, const uint32_t* host, int level, double scale);
+/* Borrow a device buffer of [2][level+1][N] uint32 in the internal layout. */
+int ckks_ct_wrap_device(ckks_ctx* ctx, uint32_t* dev_ptr, int level, double scale, ckks_ct** out);
+int ckks_ct_info(const ckks_ct* ct, int* level, double* scale, uint32_t** dev_ptr);
+int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out);
+int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* pt, uint32_t* host, size_t words, int* level,
+                   double* scale);
+
+/* --- homomorphic operations (Sec. 2.1), all asynchronous on the context stream --- */
+/* HAdd: limb-wise addition; levels must match, scales within 2^-20. out may
+ * alias a or b. */
+int ckks_hadd(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
+/* PMult: ciphertext times plaintext in the NTT domain; scale multiplies. out
+ * may alias a. */
+int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
+/* HMult: tensor (d0, d1, d2), relinearize d2 with evk (ModUp, KeyMult,
+ * ModDown; Sec. 2.3) and, with CKKS_RESCALE, rescale by q_l. out must not
+ * alias a or b. */
+int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags,
+               ckks_ct* out);
+/* Rescale (single rescaling): c'_i = (c_i - [c_l]_centered) * q_l^-1, scale /= q_l.
+ * out must not alias in. */
+int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out);
+/* HRot by r slots to the left (Eq. 4 with k = 5^r mod 2N) with evk from
+ * ckks_keygen_rot(r) or ckks_evk_import(galois = k). out must not alias ct. */
+int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks_ct* out);
+/* HConj (k = 2N - 1). out must not alias ct. */
+int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
+
+/* --- step-level entry points on host buffers (canonical layout; synchronous).
+ * They run the same kernels as the operations above and exist so that each
+ * step of the path can be compared with a reference on its own. --- */
+/* Alg. 2 (signed Montgomery reduction) on n inputs x in [-q 2^31, q 2^31). */
+int ckks_step_smr(ckks_ctx* ctx, const int64_t* x, int n, int prime_id, int32_t* y);
+/* NTT (inverse = 0) or iNTT (inverse = 1) of `limbs` limbs in place;
+ * prime_ids[i] names the prime of limb i. */
+int ckks_step_ntt(ckks_ctx* ctx, uint32_t* data, int limbs, const int* prime_ids, int inverse);
+/* Eq. 2 on coefficient-domain limbs: in [k][N] modulo src primes ->
+ * out [m][N] modulo dst primes. variant 0 = CUDA-core lazy-SMR GEMM,
+ * 1 = byte-split INT8 tensor-core GEMM (mma.sync, INT32 accumulation). */
+int ckks_step_bconv(ckks_ctx* ctx, const uint32_t* in, int k, const int* src_ids, uint32_t* out,
+                    int m, const int* dst_ids, int variant);
+/* Tensor: ct1, ct2 [2][n_q][N] -> out [3][n_q][N] (d0, d1, d2). */
+int ckks_step_tensor(ckks_ctx* ctx, const uint32_t* ct1, const uint32_t* ct2, int n_q, uint32_t* out);
+/* NTT-domain automorphism out[j] = in[((2j+1)k mod 2N - 1)/2] (Eq. 4) on
+ * `limbs` limbs. */
+int ckks_step_automorph(ckks_ctx* ctx, const uint32_t* in, int limbs, uint32_t galois, uint32_t* out);
+/* ModUp of d [n_q][N] (NTT domain): out [digits][n_q + n_p][N]. */
+int ckks_step_modup(ckks_ctx* ctx, const uint32_t* d, int n_q, uint32_t* out);
+/* ModUp fused with KeyMult+MAC: acc [2][n_q + n_p][N] = sum_j ModUp_j(d) * evk_j. */
+int ckks_step_keyswitch_acc(ckks_ctx* ctx, const uint32_t* d, int n_q, const ckks_evk* evk, uint32_t* acc);
+/* ModDown of acc [2][n_q + n_p][N] -> out [2][n_q][N]. */
+int ckks_step_moddown(ckks_ctx* ctx, const uint32_t* acc, int n_q, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKKS_GB300_H */

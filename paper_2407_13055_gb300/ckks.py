@@ -1,0 +1,360 @@
+"""Python binding of libckks_gb300.so (the C ABI in include/ckks.h).
+
+Argument marshalling only: every step of the key-switch path runs in the
+library's CUDA kernels. Importing this module loads the in-tree shared
+library and raises if it has not been built (``__graft_entry__.build()``);
+there is no fallback implementation.
+
+Functions keep the C names. Handles are ``ctypes.c_void_p`` values; numpy
+arrays are passed as host buffers in the canonical layout documented in the
+header.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libckks_gb300.so")
+
+CKKS_OK = 0
+CKKS_EINVAL = -1
+CKKS_ELEVEL = -2
+CKKS_ESCALE = -3
+CKKS_ENOKEY = -4
+CKKS_ENOMEM = -5
+CKKS_ECUDA = -6
+CKKS_ETIMEOUT = -7
+CKKS_EBUSY = -8
+CKKS_RESCALE = 1
+
+
+class CkksError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ckks error {code}: {msg}")
+        self.code = code
+
+
+class ckks_params(C.Structure):
+    _fields_ = [
+        ("log_n", C.c_int),
+        ("n_q", C.c_int),
+        ("q", C.POINTER(C.c_uint32)),
+        ("n_p", C.c_int),
+        ("p", C.POINTER(C.c_uint32)),
+        ("dnum", C.c_int),
+        ("scale", C.c_double),
+        ("secret_hw", C.c_int),
+        ("sigma", C.c_double),
+        ("seed", C.c_uint64),
+    ]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
+
+lib = C.CDLL(LIB_PATH)
+
+_vp, _i, _u32, _u64, _d, _sz = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double, C.c_size_t
+_P = C.POINTER
+_SIGS = {
+    "ckks_gen_primes": (_i, [_i, _i, _i, _vp, _vp]),
+    "ckks_ctx_create": (_i, [_P(ckks_params), _vp, _P(_vp)]),
+    "ckks_ctx_destroy": (None, [_vp]),
+    "ckks_last_error": (C.c_char_p, [_vp]),
+    "ckks_sync": (_i, [_vp]),
+    "ckks_free": (None, [_vp]),
+    "ckks_ctx_device_bytes": (_sz, [_vp]),
+    "ckks_keygen_secret": (_i, [_vp, _u64, _P(_vp)]),
+    "ckks_sk_import": (_i, [_vp, _vp, _P(_vp)]),
+    "ckks_keygen_relin": (_i, [_vp, _vp, _u64, _P(_vp)]),
+    "ckks_keygen_rot": (_i, [_vp, _vp, _i, _u64, _P(_vp)]),
+    "ckks_keygen_conj": (_i, [_vp, _vp, _u64, _P(_vp)]),
+    "ckks_evk_import": (_i, [_vp, _vp, _u32, _P(_vp)]),
+    "ckks_encode": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
+    "ckks_decode": (_i, [_vp, _vp, _vp]),
+    "ckks_encrypt": (_i, [_vp, _vp, _vp, _u64, _P(_vp)]),
+    "ckks_decrypt": (_i, [_vp, _vp, _vp, _P(_vp)]),
+    "ckks_ct_create": (_i, [_vp, _i, _P(_vp)]),
+    "ckks_ct_import": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
+    "ckks_ct_export": (_i, [_vp, _vp, _vp, _sz, _P(_i), _P(_d)]),
+    "ckks_ct_upload": (_i, [_vp, _vp, _vp, _i, _d]),
+    "ckks_ct_wrap_device": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
+    "ckks_ct_info": (_i, [_vp, _P(_i), _P(_d), _P(_vp)]),
+    "ckks_pt_import": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
+    "ckks_pt_export": (_i, [_vp, _vp, _vp, _sz, _P(_i), _P(_d)]),
+    "ckks_hadd": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_pmult": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_hmult": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "ckks_rescale": (_i, [_vp, _vp, _vp]),
+    "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_step_smr": (_i, [_vp, _vp, _i, _i, _vp]),
+    "ckks_step_ntt": (_i, [_vp, _vp, _i, _vp, _i]),
+    "ckks_step_bconv": (_i, [_vp, _vp, _i, _vp, _vp, _i, _vp, _i]),
+    "ckks_step_tensor": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "ckks_step_automorph": (_i, [_vp, _vp, _i, _u32, _vp]),
+    "ckks_step_modup": (_i, [_vp, _vp, _i, _vp]),
+    "ckks_step_keyswitch_acc": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "ckks_step_moddown": (_i, [_vp, _vp, _i, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def check(ctx, rc: int):
+    if rc != CKKS_OK:
+        msg = lib.ckks_last_error(ctx).decode() if ctx else ""
+        raise CkksError(rc, msg)
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers (same names as the C functions)
+# ---------------------------------------------------------------------------
+
+def ckks_gen_primes(log_n: int, n_q: int, n_p: int):
+    q = np.zeros(n_q, np.uint32)
+    p = np.zeros(max(n_p, 1), np.uint32)
+    check(None, lib.ckks_gen_primes(log_n, n_q, n_p, _ptr(q), _ptr(p)))
+    return q, p[:n_p].copy()
+
+
+def ckks_ctx_create(log_n: int, q, p, dnum: int, scale: float = 2.0**30, secret_hw: int = 0,
+                    sigma: float = 3.2, seed: int = 0, stream: int | None = None):
+    q, p = _u32(q), _u32(p)
+    prm = ckks_params(log_n, len(q), q.ctypes.data_as(_P(C.c_uint32)), len(p), p.ctypes.data_as(_P(C.c_uint32)),
+                      dnum, scale, secret_hw, sigma, seed)
+    out = _vp()
+    rc = lib.ckks_ctx_create(C.byref(prm), stream, C.byref(out))
+    check(None, rc)
+    return out
+
+
+def ckks_ctx_destroy(ctx):
+    lib.ckks_ctx_destroy(ctx)
+
+
+def ckks_free(h):
+    lib.ckks_free(h)
+
+
+def ckks_sync(ctx):
+    check(ctx, lib.ckks_sync(ctx))
+
+
+def ckks_keygen_secret(ctx, seed: int):
+    out = _vp()
+    check(ctx, lib.ckks_keygen_secret(ctx, seed, C.byref(out)))
+    return out
+
+
+def ckks_sk_import(ctx, coeffs):
+    c = np.ascontiguousarray(coeffs, dtype=np.int64)
+    out = _vp()
+    check(ctx, lib.ckks_sk_import(ctx, _ptr(c), C.byref(out)))
+    return out
+
+
+def ckks_keygen_relin(ctx, sk, seed: int):
+    out = _vp()
+    check(ctx, lib.ckks_keygen_relin(ctx, sk, seed, C.byref(out)))
+    return out
+
+
+def ckks_keygen_rot(ctx, sk, r: int, seed: int):
+    out = _vp()
+    check(ctx, lib.ckks_keygen_rot(ctx, sk, r, seed, C.byref(out)))
+    return out
+
+
+def ckks_keygen_conj(ctx, sk, seed: int):
+    out = _vp()
+    check(ctx, lib.ckks_keygen_conj(ctx, sk, seed, C.byref(out)))
+    return out
+
+
+def ckks_evk_import(ctx, evk, galois: int):
+    e = _u32(evk)
+    out = _vp()
+    check(ctx, lib.ckks_evk_import(ctx, _ptr(e), galois, C.byref(out)))
+    return out
+
+
+def ckks_encode(ctx, u, level: int, scale: float):
+    u = np.asarray(u, dtype=np.complex128)
+    ri = np.ascontiguousarray(np.stack([u.real, u.imag], axis=1).reshape(-1))
+    out = _vp()
+    check(ctx, lib.ckks_encode(ctx, _ptr(ri), level, scale, C.byref(out)))
+    return out
+
+
+def ckks_decode(ctx, pt, n_slots: int) -> np.ndarray:
+    ri = np.zeros(2 * n_slots, np.float64)
+    check(ctx, lib.ckks_decode(ctx, pt, _ptr(ri)))
+    return ri[0::2] + 1j * ri[1::2]
+
+
+def ckks_encrypt(ctx, sk, pt, seed: int):
+    out = _vp()
+    check(ctx, lib.ckks_encrypt(ctx, sk, pt, seed, C.byref(out)))
+    return out
+
+
+def ckks_decrypt(ctx, sk, ct):
+    out = _vp()
+    check(ctx, lib.ckks_decrypt(ctx, sk, ct, C.byref(out)))
+    return out
+
+
+def ckks_ct_create(ctx, capacity_level: int):
+    out = _vp()
+    check(ctx, lib.ckks_ct_create(ctx, capacity_level, C.byref(out)))
+    return out
+
+
+def ckks_ct_import(ctx, host, level: int, scale: float):
+    h = _u32(host)
+    out = _vp()
+    check(ctx, lib.ckks_ct_import(ctx, _ptr(h), level, scale, C.byref(out)))
+    return out
+
+
+def ckks_ct_upload(ctx, ct, host, level: int, scale: float):
+    h = _u32(host)
+    check(ctx, lib.ckks_ct_upload(ctx, ct, _ptr(h), level, scale))
+
+
+def ckks_ct_info(ct):
+    lv, sc, dp = C.c_int(), C.c_double(), _vp()
+    check(None, lib.ckks_ct_info(ct, C.byref(lv), C.byref(sc), C.byref(dp)))
+    return lv.value, sc.value, dp.value
+
+
+def ckks_ct_export(ctx, ct, n: int, out: np.ndarray | None = None):
+    lv, sc = C.c_int(), C.c_double()
+    level, _, _ = ckks_ct_info(ct)
+    if out is None:
+        out = np.zeros((2, level + 1, n), np.uint32)
+    check(ctx, lib.ckks_ct_export(ctx, ct, _ptr(out), out.size, C.byref(lv), C.byref(sc)))
+    return out, lv.value, sc.value
+
+
+def ckks_ct_wrap_device(ctx, dev_ptr: int, level: int, scale: float):
+    out = _vp()
+    check(ctx, lib.ckks_ct_wrap_device(ctx, dev_ptr, level, scale, C.byref(out)))
+    return out
+
+
+def ckks_pt_import(ctx, host, level: int, scale: float):
+    h = _u32(host)
+    out = _vp()
+    check(ctx, lib.ckks_pt_import(ctx, _ptr(h), level, scale, C.byref(out)))
+    return out
+
+
+def ckks_pt_export(ctx, pt, level: int, n: int):
+    out = np.zeros((level + 1, n), np.uint32)
+    lv, sc = C.c_int(), C.c_double()
+    check(ctx, lib.ckks_pt_export(ctx, pt, _ptr(out), out.size, C.byref(lv), C.byref(sc)))
+    return out, lv.value, sc.value
+
+
+def ckks_hadd(ctx, a, b, out):
+    check(ctx, lib.ckks_hadd(ctx, a, b, out))
+
+
+def ckks_pmult(ctx, a, pt, out):
+    check(ctx, lib.ckks_pmult(ctx, a, pt, out))
+
+
+def ckks_hmult(ctx, a, b, evk, flags: int, out):
+    check(ctx, lib.ckks_hmult(ctx, a, b, evk, flags, out))
+
+
+def ckks_rescale(ctx, a, out):
+    check(ctx, lib.ckks_rescale(ctx, a, out))
+
+
+def ckks_hrot(ctx, a, r: int, evk, out):
+    check(ctx, lib.ckks_hrot(ctx, a, r, evk, out))
+
+
+def ckks_hconj(ctx, a, evk, out):
+    check(ctx, lib.ckks_hconj(ctx, a, evk, out))
+
+
+def ckks_step_smr(ctx, x, prime_id: int) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.int64)
+    y = np.zeros(x.size, np.int32)
+    check(ctx, lib.ckks_step_smr(ctx, _ptr(x), x.size, prime_id, _ptr(y)))
+    return y
+
+
+def ckks_step_ntt(ctx, data, prime_ids, inverse: bool) -> np.ndarray:
+    d = _u32(data).copy()
+    ids = np.ascontiguousarray(prime_ids, dtype=np.int32)
+    check(ctx, lib.ckks_step_ntt(ctx, _ptr(d), len(ids), _ptr(ids), int(inverse)))
+    return d
+
+
+def ckks_step_bconv(ctx, x, src_ids, dst_ids, variant: int = 0) -> np.ndarray:
+    x = _u32(x)
+    s = np.ascontiguousarray(src_ids, dtype=np.int32)
+    d = np.ascontiguousarray(dst_ids, dtype=np.int32)
+    out = np.zeros((len(d), x.shape[-1]), np.uint32)
+    check(ctx, lib.ckks_step_bconv(ctx, _ptr(x), len(s), _ptr(s), _ptr(out), len(d), _ptr(d), variant))
+    return out
+
+
+def ckks_step_tensor(ctx, ct1, ct2) -> np.ndarray:
+    c1, c2 = _u32(ct1), _u32(ct2)
+    out = np.zeros((3,) + c1.shape[1:], np.uint32)
+    check(ctx, lib.ckks_step_tensor(ctx, _ptr(c1), _ptr(c2), c1.shape[1], _ptr(out)))
+    return out
+
+
+def ckks_step_automorph(ctx, x, galois: int) -> np.ndarray:
+    x = _u32(x)
+    out = np.zeros_like(x)
+    limbs = x.size // x.shape[-1]
+    check(ctx, lib.ckks_step_automorph(ctx, _ptr(x), limbs, galois, _ptr(out)))
+    return out
+
+
+def ckks_step_modup(ctx, d, alpha: int) -> np.ndarray:
+    d = _u32(d)
+    n_q, n = d.shape
+    digits = -(-n_q // alpha)
+    out = np.zeros((digits, n_q + alpha, n), np.uint32)
+    check(ctx, lib.ckks_step_modup(ctx, _ptr(d), n_q, _ptr(out)))
+    return out
+
+
+def ckks_step_keyswitch_acc(ctx, d, evk, alpha: int) -> np.ndarray:
+    d = _u32(d)
+    n_q, n = d.shape
+    out = np.zeros((2, n_q + alpha, n), np.uint32)
+    check(ctx, lib.ckks_step_keyswitch_acc(ctx, _ptr(d), n_q, evk, _ptr(out)))
+    return out
+
+
+def ckks_step_moddown(ctx, acc, n_q: int) -> np.ndarray:
+    a = _u32(acc)
+    out = np.zeros((2, n_q, a.shape[-1]), np.uint32)
+    check(ctx, lib.ckks_step_moddown(ctx, _ptr(a), n_q, _ptr(out)))
+    return out

@@ -1,0 +1,452 @@
+// Host-side number theory, table construction, sampling and encoding.
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "internal.h"
+
+namespace ckks {
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+uint32_t mulm(uint32_t a, uint32_t b, uint32_t q) { return (uint32_t)((uint64_t)a * b % q); }
+
+uint32_t powm(uint32_t b, uint64_t e, uint32_t q) {
+  uint64_t r = 1, x = b % q;
+  for (; e; e >>= 1) {
+    if (e & 1) r = r * x % q;
+    x = x * x % q;
+  }
+  return (uint32_t)(r % q);
+}
+
+// Inverse by the extended Euclidean algorithm (a and q coprime).
+uint32_t invm(uint32_t a, uint32_t q) {
+  int64_t t = 0, nt = 1, r = q, nr = a % q;
+  while (nr) {
+    int64_t k = r / nr;
+    int64_t tmp = t - k * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - k * nr;
+    r = nr;
+    nr = tmp;
+  }
+  if (t < 0) t += q;
+  return (uint32_t)t;
+}
+
+uint32_t shoup_of(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+uint2 shoup_pair(uint32_t w, uint32_t q) { return make_uint2(w, shoup_of(w, q)); }
+int32_t centered_h(uint32_t x, uint32_t q) { return x > q / 2 ? (int32_t)((int64_t)x - q) : (int32_t)x; }
+
+uint32_t brev(uint32_t v, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i, v >>= 1) r = (r << 1) | (v & 1);
+  return r;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// Miller-Rabin with bases 2, 3, 5, 7, 11, 13, 17: deterministic below 3.4e14.
+bool host_is_prime(uint64_t n) {
+  if (n < 2) return false;
+  static const uint64_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (uint64_t s : small) {
+    if (n == s) return true;
+    if (n % s == 0) return false;
+  }
+  uint64_t d = n - 1;
+  int r = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++r;
+  }
+  for (uint64_t a : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull}) {
+    u128 x = 1, base = a % n;
+    for (uint64_t e = d; e; e >>= 1) {
+      if (e & 1) x = x * base % n;
+      base = base * base % n;
+    }
+    if (x == 1 || x == n - 1) continue;
+    bool witness = true;
+    for (int i = 1; i < r && witness; ++i) {
+      x = x * x % n;
+      if (x == n - 1) witness = false;
+    }
+    if (witness) return false;
+  }
+  return true;
+}
+
+uint32_t host_find_psi(uint32_t q, int log_n) {
+  const uint64_t n = 1ull << log_n;
+  for (uint32_t x = 2; x < q; ++x)
+    if (powm(x, n, q) == q - 1) return x;
+  return 0;
+}
+
+int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p) {
+  const uint64_t step = 2ull << log_n;
+  // Candidates 1 mod 2N below a bound, scanned downwards.
+  auto scan = [&](uint64_t bound, uint32_t* out, int count, uint32_t skip) {
+    uint64_t c = (bound - 1) / step * step + 1;
+    int got = 0;
+    while (got < count) {
+      if (c <= step || c < (bound >> 2)) return false;
+      if (c != skip && host_is_prime(c)) out[got++] = (uint32_t)c;
+      c -= step;
+    }
+    return true;
+  };
+  if (n_q < 1 || n_p < 0) return CKKS_EINVAL;
+  std::vector<uint32_t> top(1 + n_p);
+  if (!scan(1ull << 31, top.data(), 1 + n_p, 0)) return CKKS_EINVAL;
+  q[0] = top[0];
+  for (int i = 0; i < n_p; ++i) p[i] = top[1 + i];
+  if (n_q > 1 && !scan(1ull << 30, q + 1, n_q - 1, 0)) return CKKS_EINVAL;
+  return CKKS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sampler (SplitMix64, Steele-Lea-Flood 2014)
+// ---------------------------------------------------------------------------
+uint32_t Sampler::uniform(uint32_t q) {
+  uint32_t mask = 1;
+  while (mask < q - 1) mask = (mask << 1) | 1;
+  for (;;) {
+    uint32_t v = (uint32_t)(next() >> 32) & mask;
+    if (v < q) return v;
+  }
+}
+
+// Discrete Gaussian on [-bound, bound] by inversion of its cumulative table.
+int64_t Sampler::gaussian(double sigma, int bound) {
+  static double cached_sigma = -1;
+  static int cached_bound = -1;
+  static std::vector<double> cdf;
+  if (sigma != cached_sigma || bound != cached_bound) {
+    cdf.assign(2 * bound + 1, 0.0);
+    double tot = 0;
+    for (int v = -bound; v <= bound; ++v) tot += std::exp(-(double)v * v / (2 * sigma * sigma));
+    double run = 0;
+    for (int v = -bound; v <= bound; ++v) {
+      run += std::exp(-(double)v * v / (2 * sigma * sigma)) / tot;
+      cdf[v + bound] = run;
+    }
+    cached_sigma = sigma;
+    cached_bound = bound;
+  }
+  const double u = (double)(next() >> 11) * (1.0 / 9007199254740992.0);
+  for (int i = 0; i < 2 * bound; ++i)
+    if (u < cdf[i]) return i - bound;
+  return bound;
+}
+
+void Sampler::ternary(int64_t* s, int n, int hw) {
+  if (hw <= 0) {
+    for (int i = 0; i < n; ++i) {
+      uint32_t v;
+      do v = (uint32_t)(next() >> 62);
+      while (v == 3);
+      s[i] = (int64_t)v - 1;
+    }
+    return;
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  for (int i = 0; i < n; ++i) s[i] = 0;
+  for (int i = 0; i < hw && i < n; ++i) {
+    int j = i + (int)(next() % (uint64_t)(n - i));
+    std::swap(idx[i], idx[j]);
+    s[idx[i]] = (next() >> 63) ? 1 : -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Encoding: slot j <-> zeta^(5^j mod 2N), zeta = exp(i pi / N)
+// ---------------------------------------------------------------------------
+namespace {
+typedef std::complex<double> cd;
+
+// In-place radix-2 FFT: A[k] = sum_j a[j] exp(sign 2 pi i jk / n).
+void fft(std::vector<cd>& a, int sign) {
+  const int n = (int)a.size();
+  for (int i = 1, j = 0; i < n; ++i) {
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (int len = 2; len <= n; len <<= 1) {
+    const double ang = sign * 2 * M_PI / len;
+    for (int i = 0; i < n; i += len)
+      for (int k = 0; k < len / 2; ++k) {
+        const cd w(std::cos(ang * k), std::sin(ang * k));
+        const cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+}  // namespace
+
+void host_encode(const double* re_im, int log_n, double scale, std::vector<int64_t>& coeffs) {
+  const int n = 1 << log_n;
+  std::vector<cd> zo(n, 0.0);  // z at zeta^(2j+1), j < N
+  uint64_t e = 1;
+  for (int j = 0; j < n / 2; ++j) {
+    const cd u(re_im[2 * j], re_im[2 * j + 1]);
+    zo[(e - 1) / 2] = u;
+    zo[(2 * n - e - 1) / 2] = std::conj(u);
+    e = e * 5 % (2 * n);
+  }
+  fft(zo, -1);  // sum_j z_(2j+1) exp(-2 pi i jk / N)
+  coeffs.resize(n);
+  for (int k = 0; k < n; ++k) {
+    const cd tw(std::cos(-M_PI * k / n), std::sin(-M_PI * k / n));
+    const double v = (zo[k] * tw).real() / n * scale;
+    coeffs[k] = (int64_t)(v < 0 ? -std::floor(-v + 0.5) : std::floor(v + 0.5));
+  }
+}
+
+void host_decode(const uint32_t* res, int nl, const uint32_t* q, int log_n, double scale, double* re_im) {
+  const int n = 1 << log_n;
+  // Garner mixed-radix digits; inv[i][j] = q_j^-1 mod q_i.
+  std::vector<uint32_t> inv((size_t)nl * nl);
+  for (int i = 0; i < nl; ++i)
+    for (int j = 0; j < i; ++j) inv[(size_t)i * nl + j] = invm(q[j] % q[i], q[i]);
+  std::vector<double> wt(nl);
+  double w = 1;
+  for (int i = 0; i < nl; ++i) {
+    wt[i] = w;
+    w *= (double)q[i];
+  }
+  // mixed-radix digits of (Q-1)/2, whose residues are (q_i - 1)/2
+  std::vector<uint32_t> half(nl), v(nl);
+  for (int i = 0; i < nl; ++i) {
+    uint32_t t = (q[i] - 1) / 2;
+    for (int j = 0; j < i; ++j) t = mulm((t + q[i] - half[j] % q[i]) % q[i], inv[(size_t)i * nl + j], q[i]);
+    half[i] = t;
+  }
+  std::vector<cd> m(n);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < nl; ++i) {
+      uint32_t t = res[(size_t)i * n + k];
+      for (int j = 0; j < i; ++j) t = mulm((t + q[i] - v[j] % q[i]) % q[i], inv[(size_t)i * nl + j], q[i]);
+      v[i] = t;
+    }
+    bool neg = false;
+    for (int i = nl - 1; i >= 0; --i) {
+      if (v[i] != half[i]) {
+        neg = v[i] > half[i];
+        break;
+      }
+    }
+    double x = 0;
+    if (!neg) {
+      for (int i = nl - 1; i >= 0; --i) x += (double)v[i] * wt[i];
+    } else {
+      for (int i = nl - 1; i >= 0; --i) x += (double)(q[i] - 1 - v[i]) * wt[i];
+      x = -(x + 1);
+    }
+    const cd tw(std::cos(M_PI * k / n), std::sin(M_PI * k / n));
+    m[k] = x * tw;
+  }
+  fft(m, +1);  // sum_k m_k zeta^k exp(2 pi i jk / N) = value at zeta^(2j+1)
+  uint64_t e = 1;
+  for (int j = 0; j < n / 2; ++j) {
+    const cd z = m[(e - 1) / 2] / scale;
+    re_im[2 * j] = z.real();
+    re_im[2 * j + 1] = z.imag();
+    e = e * 5 % (2 * n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Context tables
+// ---------------------------------------------------------------------------
+int build_context(ckks_ctx* ctx, const ckks_params* prm) {
+  const int log_n = prm->log_n, L = prm->n_q, alpha = prm->n_p, dnum = prm->dnum;
+  const int n = 1 << log_n, np = L + alpha;
+  ctx->N = n;
+  ctx->q.assign(prm->q, prm->q + L);
+  ctx->p.assign(prm->p, prm->p + alpha);
+  std::vector<uint32_t> pr(np);
+  for (int i = 0; i < np; ++i) pr[i] = i < L ? prm->q[i] : prm->p[i - L];
+
+  // per-prime constants
+  ctx->pc_host.resize(np);
+  for (int i = 0; i < np; ++i) {
+    const uint32_t q = pr[i];
+    PrimeConst& c = ctx->pc_host[i];
+    c.q = q;
+    uint32_t m = 1;
+    for (int it = 0; it < 5; ++it) m *= 2u - q * m;  // Newton: q m = 1 mod 2^32
+    c.m = m;
+    const uint32_t r1 = (uint32_t)((1ull << 32) % q);
+    const uint32_t r2 = mulm(r1, r1, q);
+    c.r1c = centered_h(r1, q);
+    c.r2c = centered_h(r2, q);
+    c.ninv = invm((uint32_t)(n % q), q);
+    c.ninv_sh = shoup_of(c.ninv, q);
+    c.mont = r1;
+    c.mont_sh = shoup_of(r1, q);
+  }
+
+  // key-switching constants
+  std::vector<uint2> up_cin;
+  std::vector<int32_t> up_mat;
+  std::vector<int2> up_off((size_t)(L + 1) * dnum, make_int2(0, 0));
+  for (int nl = 1; nl <= L; ++nl) {
+    const int ext = nl + alpha;
+    const int digits = (nl + alpha - 1) / alpha;
+    for (int j = 0; j < digits; ++j) {
+      const int lo = j * alpha, hi = std::min(nl, lo + alpha), K = hi - lo;
+      up_off[(size_t)nl * dnum + j] = make_int2((int)up_cin.size(), (int)up_mat.size());
+      for (int i = lo; i < hi; ++i) {
+        uint32_t hat = 1;  // Q_j / q_i mod q_i
+        for (int i2 = lo; i2 < hi; ++i2)
+          if (i2 != i) hat = mulm(hat, pr[i2] % pr[i], pr[i]);
+        up_cin.push_back(shoup_pair(mulm(invm(hat, pr[i]), ctx->pc_host[i].ninv, pr[i]), pr[i]));
+      }
+      for (int t = 0; t < ext; ++t) {
+        const int id = t < nl ? t : L + (t - nl);
+        const uint32_t d = pr[id];
+        for (int i = lo; i < hi; ++i) {
+          if (t >= lo && t < hi) {
+            up_mat.push_back(0);
+            continue;
+          }
+          uint32_t hat = 1;
+          for (int i2 = lo; i2 < hi; ++i2)
+            if (i2 != i) hat = mulm(hat, pr[i2] % d, d);
+          up_mat.push_back(centered_h(mulm(hat, ctx->pc_host[id].mont, d), d));
+        }
+      }
+      (void)K;
+    }
+  }
+  std::vector<uint2> dn_cin(alpha), dn_pinv(L);
+  std::vector<int32_t> dn_mat((size_t)L * alpha);
+  for (int k = 0; k < alpha; ++k) {
+    const uint32_t pk = pr[L + k];
+    uint32_t hat = 1;
+    for (int k2 = 0; k2 < alpha; ++k2)
+      if (k2 != k) hat = mulm(hat, pr[L + k2] % pk, pk);
+    dn_cin[k] = shoup_pair(mulm(invm(hat, pk), ctx->pc_host[L + k].ninv, pk), pk);
+  }
+  ctx->gadget_p.resize(np);
+  for (int i = 0; i < np; ++i) {
+    uint32_t P = 1;
+    for (int k = 0; k < alpha; ++k) P = mulm(P, pr[L + k] % pr[i], pr[i]);
+    ctx->gadget_p[i] = shoup_pair(P, pr[i]);
+  }
+  for (int i = 0; i < L; ++i) {
+    const uint32_t q = pr[i];
+    dn_pinv[i] = shoup_pair(invm(ctx->gadget_p[i].x, q), q);
+    for (int k = 0; k < alpha; ++k) {
+      uint32_t hat = 1;
+      for (int k2 = 0; k2 < alpha; ++k2)
+        if (k2 != k) hat = mulm(hat, pr[L + k2] % q, q);
+      dn_mat[(size_t)i * alpha + k] = centered_h(mulm(hat, ctx->pc_host[i].mont, q), q);
+    }
+  }
+  std::vector<uint2> rs_qinv((size_t)L * L, make_uint2(0, 0));
+  for (int l = 1; l < L; ++l)
+    for (int i = 0; i < l; ++i) rs_qinv[(size_t)l * L + i] = shoup_pair(invm(pr[l] % pr[i], pr[i]), pr[i]);
+
+  // twiddles: tw[id][k] = psi^brev(k), itw[id][k] = psi^-brev(k)
+  std::vector<uint2> tw((size_t)np * n), itw((size_t)np * n);
+  std::vector<uint32_t> pw(n), ipw(n);
+  for (int i = 0; i < np; ++i) {
+    const uint32_t q = pr[i];
+    const uint32_t psi = host_find_psi(q, log_n);
+    if (!psi) return CKKS_EINVAL;
+    const uint32_t ipsi = invm(psi, q);
+    pw[0] = ipw[0] = 1;
+    for (int k = 1; k < n; ++k) {
+      pw[k] = mulm(pw[k - 1], psi, q);
+      ipw[k] = mulm(ipw[k - 1], ipsi, q);
+    }
+    for (int k = 0; k < n; ++k) {
+      const uint32_t e = brev(k, log_n);
+      tw[(size_t)i * n + k] = shoup_pair(pw[e], q);
+      itw[(size_t)i * n + k] = shoup_pair(ipw[e], q);
+    }
+  }
+
+  // one device allocation for all tables
+  struct Part {
+    const void* src;
+    size_t bytes;
+    size_t off;
+  };
+  std::vector<Part> parts = {
+      {ctx->pc_host.data(), ctx->pc_host.size() * sizeof(PrimeConst), 0},
+      {tw.data(), tw.size() * sizeof(uint2), 0},
+      {itw.data(), itw.size() * sizeof(uint2), 0},
+      {up_cin.data(), up_cin.size() * sizeof(uint2), 0},
+      {up_mat.data(), up_mat.size() * sizeof(int32_t), 0},
+      {up_off.data(), up_off.size() * sizeof(int2), 0},
+      {dn_cin.data(), dn_cin.size() * sizeof(uint2), 0},
+      {dn_mat.data(), dn_mat.size() * sizeof(int32_t), 0},
+      {dn_pinv.data(), dn_pinv.size() * sizeof(uint2), 0},
+      {rs_qinv.data(), rs_qinv.size() * sizeof(uint2), 0},
+  };
+  size_t total = 0;
+  for (auto& p : parts) {
+    p.off = total;
+    total += align_up(std::max<size_t>(p.bytes, 16));
+  }
+  char* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) return CKKS_ENOMEM;
+  for (auto& p : parts)
+    if (p.bytes && cudaMemcpy(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(base);
+      return CKKS_ECUDA;
+    }
+  ctx->d_tables = base;
+  ctx->table_bytes = total;
+  DevParams& dp = ctx->dp;
+  dp.log_n = log_n;
+  dp.L = L;
+  dp.alpha = alpha;
+  dp.dnum = dnum;
+  dp.pc = reinterpret_cast<const PrimeConst*>(base + parts[0].off);
+  dp.tw = reinterpret_cast<const uint2*>(base + parts[1].off);
+  dp.itw = reinterpret_cast<const uint2*>(base + parts[2].off);
+  dp.ks.up_cin = reinterpret_cast<const uint2*>(base + parts[3].off);
+  dp.ks.up_mat = reinterpret_cast<const int32_t*>(base + parts[4].off);
+  dp.ks.up_off = reinterpret_cast<const int2*>(base + parts[5].off);
+  dp.ks.dn_cin = reinterpret_cast<const uint2*>(base + parts[6].off);
+  dp.ks.dn_mat = reinterpret_cast<const int32_t*>(base + parts[7].off);
+  dp.ks.dn_pinv = reinterpret_cast<const uint2*>(base + parts[8].off);
+  dp.ks.rs_qinv = reinterpret_cast<const uint2*>(base + parts[9].off);
+
+  // scratch
+  const size_t limb = (size_t)n;
+  const size_t s_limbs = std::max(L, 2 * alpha);
+  const size_t t_limbs = std::max((size_t)dnum * np, (size_t)2 * L);
+  const size_t a_limbs = 2 * (size_t)L, u_limbs = 2 * (size_t)L;
+  const size_t words = (s_limbs + t_limbs + a_limbs + u_limbs) * limb;
+  uint32_t* sc = nullptr;
+  if (cudaMalloc(&sc, words * sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(base);
+    ctx->d_tables = nullptr;
+    return CKKS_ENOMEM;
+  }
+  ctx->d_scratch = sc;
+  ctx->scratch_bytes = words * sizeof(uint32_t);
+  ctx->sc.S = sc;
+  ctx->sc.T = ctx->sc.S + s_limbs * limb;
+  ctx->sc.A = ctx->sc.T + t_limbs * limb;
+  ctx->sc.U = ctx->sc.A + a_limbs * limb;
+  return CKKS_OK;
+}
+
+}  // namespace ckks

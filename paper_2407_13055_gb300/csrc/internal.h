@@ -1,0 +1,211 @@
+// Host-side structures and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ckks.h"
+#include "arith.cuh"
+
+namespace ckks {
+
+// Key-switching constants on the device (all built by host.cu).
+struct KsTables {
+  // ModUp (Alg. 1 Q_j -> PQ): for the level with n ciphertext limbs and digit
+  // j, up_off[n * dnum + j] = (offset into up_cin, offset into up_mat).
+  // up_cin[off + i]: Shoup pair of N^-1 [(Q_j/q_i)^-1]_{q_i} for the digit's
+  // i-th prime; up_mat[off + t * a_j + i]: [(Q_j/q_i) 2^32]_{prime_t}
+  // centered, t over all n + alpha extended limbs (own-digit rows unused).
+  const uint2* up_cin;
+  const int32_t* up_mat;
+  const int2* up_off;
+  // ModDown (P -> Q): dn_cin[k] = Shoup pair of N^-1 [(P/p_k)^-1]_{p_k};
+  // dn_mat[i * alpha + k] = [(P/p_k) 2^32]_{q_i} centered; dn_pinv[i] = Shoup
+  // pair of [P^-1]_{q_i}.
+  const uint2* dn_cin;
+  const int32_t* dn_mat;
+  const uint2* dn_pinv;
+  // Rescale: rs_qinv[l * L + i] = Shoup pair of [q_l^-1]_{q_i}, i < l.
+  const uint2* rs_qinv;
+};
+
+struct DevParams {
+  int log_n, L, alpha, dnum;
+  const PrimeConst* pc;  // [L + alpha]
+  const uint2* tw;       // [L + alpha][N] forward twiddles (w, Shoup companion)
+  const uint2* itw;      // [L + alpha][N] inverse twiddles
+  KsTables ks;
+};
+
+// Limb -> prime id. Either an explicit device array, or the extended-
+// polynomial rule: limb t (mod per_poly) < n -> q_t, else p_{t - n}.
+struct IdMap {
+  const int* ids;
+  int per_poly, n, L;
+  __host__ __device__ int operator()(int limb) const {
+    if (ids) return ids[limb];
+    int t = limb % per_poly;
+    return t < n ? t : L + (t - n);
+  }
+};
+
+inline IdMap id_ct(int n, int L) { return IdMap{nullptr, n, n, L}; }
+inline IdMap id_ext(int n, int L, int alpha) { return IdMap{nullptr, n + alpha, n, L}; }
+inline IdMap id_arr(const int* d) { return IdMap{d, 1 << 30, 0, 0}; }
+
+// Key-switch input modes (what polynomial is key-switched).
+enum KsMode { KS_PLAIN = 0, KS_TENSOR = 1, KS_AUTO = 2 };
+// What the KeyMult row kernel writes.
+enum KmOut { KM_KEYSWITCH = 0, KM_ACC_ALL = 1, KM_MODUP = 2 };
+
+struct KsArgs {
+  int n;                 // active ciphertext limbs
+  int mode;              // KsMode
+  const uint32_t* x0;    // KS_PLAIN: d [n][N]; KS_TENSOR: ct1; KS_AUTO: ct
+  const uint32_t* x1;    // KS_TENSOR: ct2
+  size_t poly_stride0;   // words between b and a of x0 (ciphertexts)
+  size_t poly_stride1;
+  uint32_t galois;       // KS_AUTO
+  const uint32_t* evk;   // [dnum][2][L + alpha][N], Montgomery form
+  uint32_t* out;         // [2][n][N] (stride out_stride between polys)
+  size_t out_stride;
+  int extra;             // ModDown epilogue: 0 none, 1 HMult (d0, d1), 2 HRot (phi(b), 0)
+};
+
+// Scratch buffers owned by the context.
+struct Scratch {
+  uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
+  uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)
+  uint32_t* A;  // accumulators, Q limbs [2][L][N] (or all limbs [2][L+alpha][N])
+  uint32_t* U;  // HMult result before rescaling [2][L][N]
+};
+
+// ---- launchers (k_basic.cu) ----
+void launch_ntt(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, bool inverse, cudaStream_t st);
+// Row phase of the iNTT only (the column phase is fused into a consumer).
+void launch_rows_inv_only(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, cudaStream_t st);
+void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int limbs, bool to_internal,
+                    cudaStream_t st);
+void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, size_t sa,
+                 size_t sb, size_t so, cudaStream_t st);
+void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+                  size_t so, cudaStream_t st);
+void launch_tensor(const DevParams& dp, const uint32_t* c1, const uint32_t* c2, uint32_t* out, int n,
+                   cudaStream_t st);
+void launch_automorph(const DevParams& dp, const uint32_t* in, uint32_t* out, int limbs, uint32_t galois,
+                      cudaStream_t st);
+void launch_small_to_res(const DevParams& dp, const int64_t* v, uint32_t* out, int limbs, IdMap ids,
+                         cudaStream_t st);
+// out = sign_as * a * s + c + d (mod q), limb-wise; any pointer may be null (term skipped).
+void launch_lincomb(const DevParams& dp, const uint32_t* a, const uint32_t* s, int sign_as, const uint32_t* c,
+                    const uint32_t* d, uint32_t* out, int limbs, IdMap ids, cudaStream_t st);
+// out = a * g_limb + b, with g_limb a per-limb constant (gadget) given as Shoup pairs.
+void launch_add_scaled(const DevParams& dp, const uint32_t* a, const uint2* g, const uint32_t* b, uint32_t* out,
+                       int limbs, IdMap ids, cudaStream_t st);
+void launch_to_mont(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, cudaStream_t st);
+void launch_smr(const DevParams& dp, const int64_t* x, int32_t* y, int n, int prime_id, cudaStream_t st);
+
+// ---- launchers (k_keyswitch.cu) ----
+// Full key switch of one polynomial (mode), result written per a.extra.
+void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
+                      cudaStream_t st);
+// ModDown only: acc [2][n + alpha][N] (internal layout) -> out [2][n][N].
+void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
+                    cudaStream_t st);
+// Rescale: in [2][n][N] (stride sin) -> out [2][n-1][N] (stride sout).
+void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, size_t sin, int n,
+                    uint32_t* out, size_t sout, cudaStream_t st);
+
+// ---- launchers (k_bconv.cu) ----
+// Standalone coefficient-domain BConv, in [k][N] -> out [m][N]; cin: Shoup
+// pairs of [(Qs/s_i)^-1]_{s_i} (k entries), mat: [m][k] centered
+// [(Qs/s_i) 2^32]_{d_t} (variant 0); abytes: [mp][kp] byte planes of the
+// tensor-core variant (variant 1, layout in k_bconv.cu); dst ids per output.
+void launch_bconv(const DevParams& dp, const uint32_t* in, int k, const int* src_ids, const uint2* cin,
+                  const int32_t* mat, uint32_t* out, int m, const int* dst_ids, int variant, const uint8_t* abytes,
+                  int mp, int kp, cudaStream_t st);
+
+}  // namespace ckks
+
+// ---- objects ----
+struct ckks_obj {
+  int kind;  // 1 ct, 2 pt, 3 sk, 4 evk
+  ckks_ctx* ctx;
+};
+
+struct ckks_ctx {
+  ckks::DevParams dp;
+  int N;
+  std::vector<uint32_t> q, p;  // host copies
+  std::vector<ckks::PrimeConst> pc_host;
+  double scale, sigma;
+  int secret_hw;
+  uint64_t seed;
+  cudaStream_t stream;
+  void* d_tables;
+  size_t table_bytes;
+  ckks::Scratch sc;
+  void* d_scratch;
+  size_t scratch_bytes;
+  // host-side key-switching constants needed for keygen (gadget P mod prime)
+  std::vector<uint2> gadget_p;  // [L + alpha] Shoup pair of [P]_{prime}
+  std::string err;
+  int device;
+};
+
+struct ckks_ct {
+  ckks_obj h;
+  uint32_t* d;
+  int level, cap_level;
+  double scale;
+  bool borrowed;
+  size_t poly_stride() const { return (size_t)(cap_level + 1) << h.ctx->dp.log_n; }
+};
+
+struct ckks_pt {
+  ckks_obj h;
+  uint32_t* d;
+  int level;
+  double scale;
+};
+
+struct ckks_sk {
+  ckks_obj h;
+  uint32_t* d_s;  // NTT-domain secret over all L + alpha primes (internal layout)
+  std::vector<int64_t> coeffs;
+};
+
+struct ckks_evk {
+  ckks_obj h;
+  uint32_t* d;  // [dnum][2][L + alpha][N], internal layout, Montgomery form
+  uint32_t galois;
+};
+
+// host.cu
+namespace ckks {
+int build_context(ckks_ctx* ctx, const ckks_params* p);
+bool host_is_prime(uint64_t n);
+uint32_t host_find_psi(uint32_t q, int log_n);
+int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p);
+// Encoding (fp64): N/2 complex slots -> N rounded integer coefficients.
+void host_encode(const double* re_im, int log_n, double scale, std::vector<int64_t>& coeffs);
+// Decoding from canonical residues [n][N] (coefficient domain).
+void host_decode(const uint32_t* res, int n, const uint32_t* q, int log_n, double scale, double* re_im);
+// Sampler (SplitMix64 stream).
+struct Sampler {
+  uint64_t state;
+  explicit Sampler(uint64_t seed) : state(seed) {}
+  uint64_t next() {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  uint32_t uniform(uint32_t q);  // rejection sampling in [0, q)
+  int64_t gaussian(double sigma, int bound);
+  void ternary(int64_t* s, int n, int hw);
+};
+}  // namespace ckks

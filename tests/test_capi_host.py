@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function declared in include/ckks.h, its prime rule
+agrees with the oracle's, and it fails cleanly where a GPU is required."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_2407_13055_gb300 import build
+    build.build()
+    from paper_2407_13055_gb300 import ckks
+    return ckks
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ckks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ckks_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(K):
+    names = _declared()
+    assert len(names) >= 30
+    for name in names:
+        assert hasattr(K.lib, name), name
+    assert set(names) == set(K.EXPORTED)
+
+
+@pytest.mark.parametrize("log_n,n_q,n_p", [(8, 6, 2), (12, 4, 4), (16, 40, 14), (16, 40, 40)])
+def test_prime_rule_matches_oracle(K, O, log_n, n_q, n_p):
+    q, p = K.ckks_gen_primes(log_n, n_q, n_p)
+    oq, op = O.gen_primes(log_n, n_q, n_p)
+    assert np.array_equal(q, oq) and np.array_equal(p, op)
+
+
+def test_ctx_create_rejects_bad_parameters(K, O):
+    q, p = O.gen_primes(12, 4, 1)
+    with pytest.raises(K.CkksError) as e:
+        K.ckks_ctx_create(13, q, p, 4)
+    assert e.value.code == K.CKKS_EINVAL
+    with pytest.raises(K.CkksError) as e:
+        K.ckks_ctx_create(12, q, p, 2)          # dnum must be ceil(n_q / n_p)
+    assert e.value.code == K.CKKS_EINVAL
+    bad = q.copy()
+    bad[1] += 2                                  # not 1 mod 2N
+    with pytest.raises(K.CkksError) as e:
+        K.ckks_ctx_create(12, bad, p, 4)
+    assert e.value.code == K.CKKS_EINVAL
+
+
+def test_ctx_create_without_gpu_fails_cleanly(K, O):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    q, p = O.gen_primes(12, 4, 1)
+    with pytest.raises(K.CkksError) as e:
+        K.ckks_ctx_create(12, q, p, 4)
+    assert e.value.code == K.CKKS_ECUDA

@@ -1,0 +1,379 @@
+"""GPU parity: every step of the key-switch path through the C ABI, compared
+element by element with the CPU oracle on the same seeded inputs. Integer
+path: bit-exact. Decrypted slots: max-abs error <= 1e-3."""
+import numpy as np
+import pytest
+
+from paper_2407_13055_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# name: (log_n, L, dnum, alpha)
+PARAMS = {
+    "tiny": (8, 6, 3, 2),        # ragged digits {0,1} {2,3} {4,5}; N = 2^8
+    "toyT1": (12, 4, 4, 1),      # toy configuration, one auxiliary prime, per-prime digits
+    "toyT2": (12, 4, 1, 4),      # toy configuration, one digit, four auxiliary primes
+    "n16d3": (16, 40, 3, 14),    # single-op configuration at N = 2^16, dnum = 3
+}
+
+_ctx_cache = {}
+
+
+@pytest.fixture(scope="module")
+def K():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2407_13055_gb300 import ckks
+    yield ckks
+    for ctx, _ in _ctx_cache.values():
+        ckks.ckks_ctx_destroy(ctx)
+    _ctx_cache.clear()
+
+
+def get(K, O, name):
+    if name not in _ctx_cache:
+        log_n, L, dnum, alpha = PARAMS[name]
+        P = O.make_params(log_n, L, dnum, alpha)
+        ctx = K.ckks_ctx_create(log_n, P.q, P.p, dnum, scale=2.0**30, secret_hw=192 if log_n == 16 else 0)
+        _ctx_cache[name] = (ctx, P)
+    return _ctx_cache[name]
+
+
+def rand_poly(P, primes, seed, stream=0):
+    return inputs.uniform_residues(seed, primes, P.n, stream)
+
+
+def rand_ct(P, n_q, seed, stream=0):
+    return np.stack([rand_poly(P, P.q[:n_q], seed, stream), rand_poly(P, P.q[:n_q], seed, stream + 1)])
+
+
+def rand_evk(P, seed):
+    allp = P.all_primes()
+    return np.stack([np.stack([rand_poly(P, allp, seed, 10 * j + t) for t in range(2)]) for j in range(P.dnum)])
+
+
+# ---------------------------------------------------------------- a1: SMR ---
+
+def test_smr_matches_oracle(K, O):
+    ctx, P = get(K, O, "toyT1")
+    rng = np.random.default_rng(0)
+    for pid in (0, 1, P.L):
+        q = int(P.all_primes()[pid])
+        lo, hi = -q * 2**31, q * 2**31 - 1
+        x = np.concatenate([[lo, hi, 0, -1, 1], rng.integers(lo, hi, 20000, dtype=np.int64)]).astype(np.int64)
+        y = K.ckks_step_smr(ctx, x, pid)
+        want = np.array([O.smr(int(v), q) for v in x[:2000]], np.int32)
+        assert np.array_equal(y[:2000], want)
+        assert np.all(np.abs(y.astype(np.int64)) < q)
+        assert np.all(((y.astype(object) * 2**32 - x.astype(object)) % q) == 0)
+
+
+# ---------------------------------------------------------------- a2: NTT ---
+
+@pytest.mark.parametrize("name", ["tiny", "toyT1", "n16d3"])
+def test_ntt_matches_oracle(K, O, name):
+    ctx, P = get(K, O, name)
+    ids = [0, 1, P.L - 1, P.L, P.L + P.alpha - 1]
+    primes = P.all_primes()[ids]
+    a = np.stack([inputs.uniform_residues(7, [p], P.n)[0] for p in primes])
+    got = K.ckks_step_ntt(ctx, a, ids, inverse=False)
+    assert np.array_equal(got, O.ntt(a, primes))
+    got_i = K.ckks_step_ntt(ctx, a, ids, inverse=True)
+    assert np.array_equal(got_i, O.intt(a, primes))
+
+
+def test_ntt_edge_values(K, O):
+    ctx, P = get(K, O, "n16d3")
+    ids = [0, 1, P.L]
+    primes = P.all_primes()[ids]
+    a = np.zeros((3, P.n), np.uint32)
+    a[:, 0] = primes - 1
+    a[:, -1] = primes - 1
+    a[1, :] = primes[1] - 1         # every coefficient q - 1
+    for inv in (False, True):
+        want = O.intt(a, primes) if inv else O.ntt(a, primes)
+        assert np.array_equal(K.ckks_step_ntt(ctx, a, ids, inverse=inv), want)
+
+
+# ------------------------------------------------------------- a3: tensor ---
+
+@pytest.mark.parametrize("name,n_q", [("toyT1", 4), ("n16d3", 3)])
+def test_tensor_matches_oracle(K, O, name, n_q):
+    ctx, P = get(K, O, name)
+    c1, c2 = rand_ct(P, n_q, 1), rand_ct(P, n_q, 2)
+    assert np.array_equal(K.ckks_step_tensor(ctx, c1, c2), O.tensor(c1, c2, P.q[:n_q]))
+
+
+# -------------------------------------------------------------- a4: BConv ---
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("k_src,m_dst", [(1, 3), (2, 5), (8, 40), (14, 40), (40, 40)])
+def test_bconv_matches_oracle(K, O, variant, k_src, m_dst):
+    ctx, P = get(K, O, "n16d3")
+    allp = P.all_primes()
+    src = list(range(k_src))
+    dst = list(range(P.L, P.L + P.alpha)) + list(range(k_src, P.L))
+    dst = dst[:m_dst]
+    x = np.stack([inputs.uniform_residues(k_src, [allp[i]], P.n)[0] for i in src])
+    # extreme columns: all (q-1)/2, all (q+1)/2, all 0, all q-1
+    half = ((allp[src] - 1) // 2).astype(np.uint32)
+    x[:, 0], x[:, 1], x[:, 2], x[:, 3] = half, half + 1, 0, allp[src] - 1
+    got = K.ckks_step_bconv(ctx, x, src, dst, variant)
+    assert np.array_equal(got, O.bconv(x, allp[src], allp[dst]))
+
+
+def test_bconv_tensor_core_equals_cuda_core(K, O):
+    ctx, P = get(K, O, "toyT2")
+    allp = P.all_primes()
+    x = np.stack([inputs.uniform_residues(3, [allp[i]], P.n)[0] for i in range(4)])
+    a = K.ckks_step_bconv(ctx, x, [0, 1, 2, 3], [4, 5, 6, 7], 0)
+    b = K.ckks_step_bconv(ctx, x, [0, 1, 2, 3], [4, 5, 6, 7], 1)
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------- a4: ModUp ---
+
+@pytest.mark.parametrize("name,n_q", [("tiny", 6), ("tiny", 5), ("tiny", 1), ("toyT1", 4), ("toyT2", 3),
+                                      ("n16d3", 40), ("n16d3", 21), ("n16d3", 2)])
+def test_modup_matches_oracle(K, O, name, n_q):
+    ctx, P = get(K, O, name)
+    d = rand_poly(P, P.q[:n_q], 11)
+    assert np.array_equal(K.ckks_step_modup(ctx, d, P.alpha), O.modup(P, d, n_q))
+
+
+# -------------------------------------------------- a5: KeyMult + MAC ---
+
+@pytest.mark.parametrize("name,n_q", [("tiny", 6), ("tiny", 3), ("toyT2", 4), ("n16d3", 40), ("n16d3", 15)])
+def test_keyswitch_acc_matches_oracle(K, O, name, n_q):
+    ctx, P = get(K, O, name)
+    d = rand_poly(P, P.q[:n_q], 12)
+    evk = rand_evk(P, 13)
+    ek = K.ckks_evk_import(ctx, evk, 0)
+    try:
+        got = K.ckks_step_keyswitch_acc(ctx, d, ek, P.alpha)
+    finally:
+        K.ckks_free(ek)
+    assert np.array_equal(got, O.keymult(P, O.modup(P, d, n_q), n_q, evk))
+
+
+# ------------------------------------------------------ a6: automorphism ---
+
+@pytest.mark.parametrize("name", ["tiny", "toyT1", "n16d3"])
+def test_automorph_matches_oracle(K, O, name):
+    ctx, P = get(K, O, name)
+    a = rand_poly(P, P.q[:3], 14)
+    for k in (O.rot_k(1, P.log_n), O.rot_k(5, P.log_n), O.rot_k(12345, P.log_n), O.conj_k(P.log_n)):
+        assert np.array_equal(K.ckks_step_automorph(ctx, a, k), O.automorph_ntt(a, k))
+
+
+# ------------------------------------------------------------ a7: ModDown ---
+
+@pytest.mark.parametrize("name,n_q", [("tiny", 6), ("toyT1", 2), ("toyT2", 4), ("n16d3", 40), ("n16d3", 2)])
+def test_moddown_matches_oracle(K, O, name, n_q):
+    ctx, P = get(K, O, name)
+    ext = P.ext_primes(n_q)
+    acc = np.stack([rand_poly(P, ext, 15, t) for t in range(2)])
+    assert np.array_equal(K.ckks_step_moddown(ctx, acc, n_q), O.moddown(P, acc, n_q))
+
+
+# ------------------------------------------------------------ a8: rescale ---
+
+@pytest.mark.parametrize("name,n_q", [("tiny", 6), ("tiny", 2), ("toyT1", 4), ("n16d3", 40), ("n16d3", 2)])
+def test_rescale_matches_oracle(K, O, name, n_q):
+    ctx, P = get(K, O, name)
+    c = rand_ct(P, n_q, 16)
+    ct = K.ckks_ct_import(ctx, c, n_q - 1, 2.0**60)
+    out = K.ckks_ct_create(ctx, n_q - 2)
+    try:
+        K.ckks_rescale(ctx, ct, out)
+        got, level, scale = K.ckks_ct_export(ctx, out, P.n)
+    finally:
+        K.ckks_free(ct)
+        K.ckks_free(out)
+    assert level == n_q - 2 and scale == 2.0**60 / float(P.q[n_q - 1])
+    assert np.array_equal(got, O.rescale(c, P.q[:n_q]))
+
+
+# ----------------------------------------------------- a9: HAdd / PMult ---
+
+def test_hadd_pmult_match_oracle(K, O):
+    ctx, P = get(K, O, "n16d3")
+    n_q = 5
+    x, y = rand_ct(P, n_q, 17), rand_ct(P, n_q, 19)
+    pt = rand_poly(P, P.q[:n_q], 21)
+    cx, cy = K.ckks_ct_import(ctx, x, n_q - 1, 2.0**30), K.ckks_ct_import(ctx, y, n_q - 1, 2.0**30)
+    p = K.ckks_pt_import(ctx, pt, n_q - 1, 2.0**30)
+    out = K.ckks_ct_create(ctx, n_q - 1)
+    try:
+        K.ckks_hadd(ctx, cx, cy, out)
+        assert np.array_equal(K.ckks_ct_export(ctx, out, P.n)[0], O.hadd(x, y, P.q[:n_q]))
+        K.ckks_pmult(ctx, cx, p, out)
+        assert np.array_equal(K.ckks_ct_export(ctx, out, P.n)[0], O.pmult(x, pt, P.q[:n_q]))
+        K.ckks_hadd(ctx, cx, cy, cx)   # in place
+        assert np.array_equal(K.ckks_ct_export(ctx, cx, P.n)[0], O.hadd(x, y, P.q[:n_q]))
+    finally:
+        for h in (cx, cy, p, out):
+            K.ckks_free(h)
+
+
+# -------------------------------------------------- full HMult / HRot ---
+
+def _run_hmult(K, ctx, P, c1, c2, evk, rescale):
+    n_q = c1.shape[1]
+    a = K.ckks_ct_import(ctx, c1, n_q - 1, 2.0**30)
+    b = K.ckks_ct_import(ctx, c2, n_q - 1, 2.0**30)
+    ek = K.ckks_evk_import(ctx, evk, 0)
+    out = K.ckks_ct_create(ctx, n_q - 1)
+    try:
+        K.ckks_hmult(ctx, a, b, ek, K.CKKS_RESCALE if rescale else 0, out)
+        return K.ckks_ct_export(ctx, out, P.n)
+    finally:
+        for h in (a, b, ek, out):
+            K.ckks_free(h)
+
+
+def _run_hrot(K, O, ctx, P, c, evk, r=None):
+    n_q = c.shape[1]
+    k = O.conj_k(P.log_n) if r is None else O.rot_k(r, P.log_n)
+    a = K.ckks_ct_import(ctx, c, n_q - 1, 2.0**30)
+    ek = K.ckks_evk_import(ctx, evk, k)
+    out = K.ckks_ct_create(ctx, n_q - 1)
+    try:
+        if r is None:
+            K.ckks_hconj(ctx, a, ek, out)
+        else:
+            K.ckks_hrot(ctx, a, r, ek, out)
+        return K.ckks_ct_export(ctx, out, P.n)[0], k
+    finally:
+        for h in (a, ek, out):
+            K.ckks_free(h)
+
+
+@pytest.mark.parametrize("name,n_q,rescale", [("tiny", 6, True), ("tiny", 4, False), ("tiny", 1, False),
+                                              ("toyT1", 4, True), ("toyT2", 4, True), ("toyT2", 2, False),
+                                              ("n16d3", 40, True), ("n16d3", 21, True), ("n16d3", 2, True)])
+def test_hmult_matches_oracle(K, O, name, n_q, rescale):
+    ctx, P = get(K, O, name)
+    c1, c2 = rand_ct(P, n_q, 31), rand_ct(P, n_q, 33)
+    evk = rand_evk(P, 35)
+    got, level, _ = _run_hmult(K, ctx, P, c1, c2, evk, rescale)
+    assert level == n_q - 1 - int(rescale)
+    assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=rescale))
+
+
+@pytest.mark.parametrize("name,n_q,r", [("tiny", 6, 1), ("tiny", 1, 3), ("toyT1", 4, 1), ("toyT2", 4, 7),
+                                        ("toyT2", 4, None), ("n16d3", 40, 1), ("n16d3", 21, 5),
+                                        ("n16d3", 2, 12345), ("n16d3", 40, None)])
+def test_hrot_matches_oracle(K, O, name, n_q, r):
+    ctx, P = get(K, O, name)
+    c = rand_ct(P, n_q, 41)
+    evk = rand_evk(P, 43)
+    got, k = _run_hrot(K, O, ctx, P, c, evk, r)
+    assert np.array_equal(got, O.hrot(P, c, k, evk))
+
+
+@pytest.mark.parametrize("dnum", [1, 5])
+def test_hmult_full_size_other_dnum(K, O, dnum):
+    """N = 2^16, 40 primes, top level, dnum in {1, 5}: bit-exact HMult+rescale and HRot."""
+    P = O.make_params(16, 40, dnum)
+    ctx = K.ckks_ctx_create(16, P.q, P.p, dnum, scale=2.0**30)
+    try:
+        c1, c2 = rand_ct(P, 40, 51), rand_ct(P, 40, 53)
+        evk = rand_evk(P, 55)
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
+        assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+        got, k = _run_hrot(K, O, ctx, P, c1, evk, 1)
+        assert np.array_equal(got, O.hrot(P, c1, k, evk))
+    finally:
+        K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------- decryption after operations ---
+
+@pytest.mark.parametrize("name", ["toyT1", "toyT2", "n16d3"])
+def test_library_keys_decrypt_within_tolerance(K, O, name):
+    """Keys, encryption and decoding from the library itself; decrypted slots
+    within 1e-3 of the plaintext result (Sec. 2.1 semantics)."""
+    ctx, P = get(K, O, name)
+    scale = 2.0**28 if P.log_n == 12 else 2.0**30
+    n_q = P.L if P.log_n == 12 else 6
+    slots = P.n // 2
+    u, v = inputs.messages(61, slots), inputs.messages(62, slots)
+    sk = K.ckks_keygen_secret(ctx, 63)
+    rk = K.ckks_keygen_relin(ctx, sk, 64)
+    gk = K.ckks_keygen_rot(ctx, sk, 3, 65)
+    ck = K.ckks_keygen_conj(ctx, sk, 66)
+    hs = [sk, rk, gk, ck]
+    try:
+        pu, pv = K.ckks_encode(ctx, u, n_q - 1, scale), K.ckks_encode(ctx, v, n_q - 1, scale)
+        cu, cv = K.ckks_encrypt(ctx, sk, pu, 67), K.ckks_encrypt(ctx, sk, pv, 68)
+        out = K.ckks_ct_create(ctx, n_q - 1)
+        hs += [pu, pv, cu, cv, out]
+
+        def dec(ct):
+            pt = K.ckks_decrypt(ctx, sk, ct)
+            try:
+                return K.ckks_decode(ctx, pt, slots)
+            finally:
+                K.ckks_free(pt)
+
+        assert np.max(np.abs(dec(cu) - u)) < 1e-3
+        K.ckks_hmult(ctx, cu, cv, rk, K.CKKS_RESCALE, out)
+        assert np.max(np.abs(dec(out) - u * v)) < 1e-3
+        K.ckks_hrot(ctx, cu, 3, gk, out)
+        assert np.max(np.abs(dec(out) - np.roll(u, -3))) < 1e-3
+        K.ckks_hconj(ctx, cu, ck, out)
+        assert np.max(np.abs(dec(out) - np.conj(u))) < 1e-3
+        K.ckks_hadd(ctx, cu, cv, out)
+        assert np.max(np.abs(dec(out) - (u + v))) < 1e-3
+    finally:
+        for h in hs:
+            K.ckks_free(h)
+
+
+def test_oracle_encryptions_decrypt_after_gpu_hmult(K, O):
+    """Oracle keys and encryptions, GPU HMult, oracle decryption."""
+    ctx, P = get(K, O, "toyT1")
+    s = inputs.ternary_secret(71, P.n, None)
+    allp = P.all_primes()
+    a = np.stack([inputs.uniform_residues(71, allp, P.n, 200 + j) for j in range(P.dnum)])
+    e = np.stack([inputs.gaussian_error(71, P.n, 200 + j) for j in range(P.dnum)])
+    evk = O.keygen_relin(P, s, a, e)
+    scale = 2.0**28
+    u, v = inputs.messages(72, P.n // 2), inputs.messages(73, P.n // 2)
+    cts = [O.encrypt(P, s, O.encode(P, m, scale, P.L), inputs.uniform_residues(71, P.q, P.n, 300 + i),
+                     inputs.gaussian_error(71, P.n, 300 + i)) for i, m in enumerate((u, v))]
+    got, level, _ = _run_hmult(K, ctx, P, cts[0], cts[1], evk, True)
+    dec = O.decode(P, O.decrypt(P, s, got), scale * scale / float(P.q[P.L - 1]))
+    assert np.max(np.abs(dec - u * v)) < 1e-3
+
+
+# ------------------------------------------------------------- errors ---
+
+def test_error_codes(K, O):
+    ctx, P = get(K, O, "tiny")
+    c3 = K.ckks_ct_import(ctx, rand_ct(P, 3, 81), 2, 2.0**30)
+    c4 = K.ckks_ct_import(ctx, rand_ct(P, 4, 82), 3, 2.0**30)
+    c0 = K.ckks_ct_import(ctx, rand_ct(P, 1, 83), 0, 2.0**30)
+    out = K.ckks_ct_create(ctx, 5)
+    rk = K.ckks_evk_import(ctx, rand_evk(P, 84), O.rot_k(1, P.log_n))
+    try:
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_hadd(ctx, c3, c4, out)
+        assert e.value.code == K.CKKS_ELEVEL
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_rescale(ctx, c0, out)
+        assert e.value.code == K.CKKS_ELEVEL
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_hmult(ctx, c3, c3, rk, 0, out)     # rotation key given to HMult
+        assert e.value.code == K.CKKS_ENOKEY
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_hrot(ctx, c3, 2, rk, out)          # key is for r = 1
+        assert e.value.code == K.CKKS_ENOKEY
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_hrot(ctx, c3, 1, rk, c3)           # aliasing
+        assert e.value.code == K.CKKS_EINVAL
+    finally:
+        for h in (c3, c4, c0, out, rk):
+            K.ckks_free(h)
