@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: HMult / HRot key-switch operations per second at N = 2^16 on GB300.
+
+Workload (single-op key switching at N = 2^16): 40 ciphertext primes
+(q_0 31-bit, q_1..q_39 30-bit), alpha = 14 auxiliary 31-bit primes, dnum = 3,
+top level (40 limbs), ternary secret of Hamming weight 192, sigma = 3.2,
+scale 2^30. One step = for each of B = 16 resident ciphertexts one HMult
+(tensor + relinearize + rescale) and one HRot by 1 slot, so a step runs every
+stage of the hot path (NTT/iNTT, tensor, ModUp BConv, KeyMult + MAC,
+automorphism, ModDown, rescale). The 16 input ciphertexts (320 MB) and two
+evaluation keys (170 MB) exceed the 129 MB L2, so consecutive operations
+stream cold data (no explicit flush). Inputs are fresh encryptions of
+messages uniform in [-1, 1] made by the library itself; keys are random-free
+outputs of its key generation.
+
+`--impl reference` times the CPU oracle (the only reference there is: the
+paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LOG_N, L, DNUM, ALPHA, HW, SCALE = 16, 40, 3, 14, 192, 2.0**30
+LEVEL = L - 1
+BATCH = 16
+METRIC = "HMult/HRot key-switch ops/sec at N=2^16 (1 GB300)"
+UNIT = "key-switch ops/s"
+LIMB_BYTES = (1 << LOG_N) * 4
+
+
+def workload_config(extra=None):
+    cfg = {
+        "workload": "single-op key switching, N=2^16, 40 primes (28-31 bit), dnum=3 (alpha=14), top level (40 limbs), "
+                    "HMult+relin+rescale and HRot(1) per ciphertext",
+        "N": 1 << LOG_N, "limbs": L, "alpha": ALPHA, "dnum": DNUM, "level": LEVEL, "secret_hw": HW,
+        "batch_ciphertexts": BATCH, "ops_per_step": 2 * BATCH,
+        "l2": "inputs larger than L2 (16 ciphertexts = 335 MB + 2 keys = 170 MB, rotated; no flush)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def algorithmic_bytes(n=L, alpha=ALPHA):
+    """Compulsory HBM bytes per op (inputs + truncated evk + outputs)."""
+    d = -(-n // alpha)
+    hmult = (4 * n + 2 * d * (n + alpha) + 2 * (n - 1)) * LIMB_BYTES
+    hrot = (2 * n + 2 * d * (n + alpha) + 2 * n) * LIMB_BYTES
+    return hmult, hrot
+
+
+def kernel_models(n=L, alpha=ALPHA):
+    """Per-launch algorithmic work of each pipeline kernel: compulsory HBM
+    bytes, and modular multiplications (NTT butterflies + BConv products +
+    element-wise products)."""
+    N = 1 << LOG_N
+    d = -(-n // alpha)
+    ext = n + alpha
+    half = N // 2
+    rows, cols = 10, 6                       # stages per phase at N = 2^16 (W = 1024, H = 64)
+    targets = sum(ext - min(alpha, n - j * alpha) for j in range(d))
+    m = {}
+    # bytes: evk stream dominates keymult; inputs/outputs of the op elsewhere
+    m["keymult_rows"] = dict(bytes=2 * d * ext * LIMB_BYTES,
+                             modmul=targets * half * rows + 2 * d * ext * N)
+    m["modup_cols"] = dict(bytes=0, modmul=d * 0 + n * half * cols + targets * half * cols + targets * N * alpha)
+    m["moddown_cols"] = dict(bytes=0, modmul=2 * alpha * half * cols + 2 * n * half * cols + 2 * n * N * alpha)
+    m["ks_in_rows"] = dict(bytes=2 * n * LIMB_BYTES, modmul=n * half * rows + n * N)
+    m["ks_out_rows"] = dict(bytes=(4 * n + 2 * n) * LIMB_BYTES, modmul=2 * n * half * rows + 2 * n * N * 3)
+    m["rescale_in_rows"] = dict(bytes=2 * LIMB_BYTES, modmul=2 * half * rows)
+    m["rescale_cols"] = dict(bytes=0, modmul=2 * half * cols + 2 * (n - 1) * (half * cols + N))
+    m["rescale_out_rows"] = dict(bytes=4 * (n - 1) * LIMB_BYTES, modmul=2 * (n - 1) * (half * rows + N))
+    return m
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle on a bounded sample
+# ----------------------------------------------------------------------------
+
+def time_oracle(max_pairs: int = 1, budget_s: float = 0.0):
+    """Time the CPU oracle on (HMult+rescale, HRot) pairs of the workload:
+    at least one pair, more while under `budget_s` seconds and `max_pairs`.
+    Returns (ops/s, seconds, pairs, description)."""
+    from oracle import oracle as O
+    from paper_2407_13055_gb300 import inputs
+    O.build()
+    P = O.make_params(LOG_N, L, DNUM, ALPHA)
+    n = P.n
+    allp = P.all_primes()
+    evk = np.stack([np.stack([inputs.uniform_residues(5, allp, n, 10 * j + t) for t in range(2)])
+                    for j in range(DNUM)])
+    ct = [np.stack([inputs.uniform_residues(6, P.q, n, 2 * i + t) for t in range(2)]) for i in range(2)]
+    k = O.rot_k(1, LOG_N)
+    pairs, dt = 0, 0.0
+    while pairs < 1 or (pairs < max_pairs and dt * (pairs + 1) / pairs < budget_s):
+        t0 = time.perf_counter()
+        O.hmult(P, ct[0], ct[1], evk, rescale=True)
+        O.hrot(P, ct[0], k, evk)
+        dt += time.perf_counter() - t0
+        pairs += 1
+    desc = f"{pairs} HMult+rescale and {pairs} HRot(1) of the same workload on 1 host thread"
+    return 2 * pairs / dt, dt, pairs, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ops_per_s, dt, pairs, desc = time_oracle(max_pairs=max(1, args.steps), budget_s=120.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ops_per_s, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": pairs, "warmup": 0, "ms_per_step": 1e3 * dt / pairs, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config({"sample": desc, "step": "one HMult+rescale and one HRot(1)"}),
+        "cpu_baseline": {"value": ops_per_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": ops_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------
+
+def run_native(args, rank, world, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+
+    # CPU baseline first (rank 0 at N = 1 only), before any GPU work.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, _, desc = time_oracle(1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, seed=rank,
+                            stream=stream.cuda_stream)
+    sk = K.ckks_keygen_secret(ctx, 1000 + rank)
+    rk = K.ckks_keygen_relin(ctx, sk, 2000 + rank)
+    gk = K.ckks_keygen_rot(ctx, sk, 1, 3000 + rank)
+    cts = []
+    for i in range(BATCH):
+        pt = K.ckks_encode(ctx, inputs.messages(100 + i, (1 << LOG_N) // 2), LEVEL, SCALE)
+        cts.append(K.ckks_encrypt(ctx, sk, pt, 200 + i))
+        K.ckks_free(pt)
+    outs_m = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2)]
+    outs_r = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2)]
+
+    def step():
+        for i in range(BATCH):
+            K.ckks_hmult(ctx, cts[i], cts[(i + 1) % BATCH], rk, K.CKKS_RESCALE, outs_m[i & 1])
+            K.ckks_hrot(ctx, cts[i], 1, gk, outs_r[i & 1])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    K.ckks_profile(ctx, True)
+    launches0 = K.ckks_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    K.ckks_profile(ctx, False)
+    launches = K.ckks_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    prof = K.ckks_profile_read(ctx)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ops = 2 * BATCH * args.steps * world
+    value = ops / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: per op, upload the
+    # inputs from pinned memory, run it, read the result back.
+    n = 1 << LOG_N
+    host_in = [torch.empty((2, L, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32) for _ in range(BATCH)]
+    for i in range(BATCH):
+        K.ckks_ct_export(ctx, cts[i], n, out=host_in[i])
+    host_out_m = torch.empty((2, L - 1, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    host_out_r = torch.empty((2, L, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    e2e_steps = max(1, args.steps // 10)
+    ct_bytes = 2 * L * n * 4
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i in range(BATCH):
+            j = (i + 1) % BATCH
+            K.ckks_ct_upload(ctx, cts[i], host_in[i], LEVEL, SCALE)
+            K.ckks_ct_upload(ctx, cts[j], host_in[j], LEVEL, SCALE)
+            K.ckks_hmult(ctx, cts[i], cts[j], rk, K.CKKS_RESCALE, outs_m[0])
+            K.ckks_ct_export(ctx, outs_m[0], n, out=host_out_m)
+            K.ckks_ct_upload(ctx, cts[i], host_in[i], LEVEL, SCALE)
+            K.ckks_hrot(ctx, cts[i], 1, gk, outs_r[0])
+            K.ckks_ct_export(ctx, outs_r[0], n, out=host_out_r)
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": 2 * BATCH * e2e_steps * world / e2e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": BATCH * 3 * ct_bytes,
+           "d2h_bytes_per_step": BATCH * (ct_bytes * (L - 1) // L + ct_bytes)}
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    models = kernel_models()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    avg_s = dom_ms / 1e3 / max(dom_n, 1)
+    mdl = models[dom]
+    hm_bytes, hr_bytes = algorithmic_bytes()
+    if mdl["bytes"] > 0:
+        achieved = mdl["bytes"] / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": None}
+    else:
+        # plain ALU: modular multiplications against the int32 multiply peak
+        # (152 SMs x 64 IMAD/clk at the maximum SM clock, 3 IMAD per modmul)
+        imad_peak = 152 * 64 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        achieved = mdl["modmul"] / avg_s / 1e12
+        peak = imad_peak / 3 / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
+                "frac": achieved / peak, "peak_source": "derived: 152 SM x 64 IMAD/clk x sm_max_mhz / 3",
+                "traffic": None}
+    stage = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
+                 "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)} for k, v in prof.items()}
+    per_gpu_gbs = BATCH * (hm_bytes + hr_bytes) * args.steps / (ms / 1e3) / 1e9
+    op_hbm = {"hmult_bytes": hm_bytes, "hrot_bytes": hr_bytes, "achieved_gbs_per_gpu": per_gpu_gbs,
+              "frac_of_hbm": per_gpu_gbs / peaks["hbm_gbs"], "peak_source": f"{peak_kind} hbm_gbs"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions of U[-1,1] messages)",
+        "config": workload_config({"parallelism": f"replicas{world}"}),
+        "roofline": roof, "op_roofline": op_hbm, "stages": stage,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for h in cts + outs_m + outs_r + [sk, rk, gk]:
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_native(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

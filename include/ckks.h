@@ -170,6 +170,23 @@ int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks
 /* HConj (k = 2N - 1). out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
 
+/* --- measurement support --- */
+/* Number of kernel ids reported by ckks_profile_read. */
+#define CKKS_PROF_KERNELS 8
+/* enable = 1: clear and start recording one CUDA event on the context stream
+ * after every kernel of the key-switch and rescale pipelines (ModUp rows and
+ * columns, KeyMult, ModDown columns and rows, three rescale kernels);
+ * enable = 0: stop recording. */
+int ckks_profile(ckks_ctx* ctx, int enable);
+/* Synchronizes, then writes per kernel id the total device milliseconds
+ * between the event before and the event after each launch, and the number
+ * of launches (arrays of CKKS_PROF_KERNELS entries). */
+int ckks_profile_read(ckks_ctx* ctx, double* total_ms, uint64_t* launches);
+/* Name of a kernel id, or NULL when out of range. */
+const char* ckks_profile_name(int id);
+/* Kernels this library has launched in this process. */
+uint64_t ckks_launch_count(void);
+
 /* --- step-level entry points on host buffers (canonical layout; synchronous).
  * They run the same kernels as the operations above and exist so that each
  * step of the path can be compared with a reference on its own. --- */

@@ -91,6 +91,10 @@ _SIGS = {
     "ckks_rescale": (_i, [_vp, _vp, _vp]),
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_profile": (_i, [_vp, _i]),
+    "ckks_profile_read": (_i, [_vp, _vp, _vp]),
+    "ckks_profile_name": (C.c_char_p, [_i]),
+    "ckks_launch_count": (_u64, []),
     "ckks_step_smr": (_i, [_vp, _vp, _i, _i, _vp]),
     "ckks_step_ntt": (_i, [_vp, _vp, _i, _vp, _i]),
     "ckks_step_bconv": (_i, [_vp, _vp, _i, _vp, _vp, _i, _vp, _i]),
@@ -296,6 +300,24 @@ def ckks_hrot(ctx, a, r: int, evk, out):
 
 def ckks_hconj(ctx, a, evk, out):
     check(ctx, lib.ckks_hconj(ctx, a, evk, out))
+
+
+CKKS_PROF_KERNELS = 8
+
+
+def ckks_profile(ctx, enable: bool):
+    check(ctx, lib.ckks_profile(ctx, int(enable)))
+
+
+def ckks_profile_read(ctx) -> dict:
+    ms = np.zeros(CKKS_PROF_KERNELS, np.float64)
+    cnt = np.zeros(CKKS_PROF_KERNELS, np.uint64)
+    check(ctx, lib.ckks_profile_read(ctx, _ptr(ms), _ptr(cnt)))
+    return {lib.ckks_profile_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(CKKS_PROF_KERNELS)}
+
+
+def ckks_launch_count() -> int:
+    return int(lib.ckks_launch_count())
 
 
 def ckks_step_smr(ctx, x, prime_id: int) -> np.ndarray:

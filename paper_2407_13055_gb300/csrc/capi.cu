@@ -128,6 +128,7 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   ctx->seed = prm->seed;
   int rc = build_context(ctx, prm);
   if (rc != CKKS_OK) return bad(fail(ctx, rc, "building tables failed (%d)", rc));
+  ctx->sc.prof = &ctx->prof;
   *out = ctx;
   return CKKS_OK;
 }
@@ -138,8 +139,45 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
   else cudaDeviceSynchronize();
   if (ctx->d_tables) cudaFree(ctx->d_tables);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+  for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
 }
+
+int ckks_profile(ckks_ctx* ctx, int enable) {
+  if (!ctx) return CKKS_EINVAL;
+  if (enable) ctx->prof.used = 0;
+  ctx->prof.on = enable != 0;
+  return CKKS_OK;
+}
+
+int ckks_profile_read(ckks_ctx* ctx, double* total_ms, uint64_t* launches) {
+  if (!ctx || !total_ms || !launches) return CKKS_EINVAL;
+  int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile");
+  if (rc) return rc;
+  for (int i = 0; i < P_COUNT; ++i) {
+    total_ms[i] = 0;
+    launches[i] = 0;
+  }
+  const Prof& p = ctx->prof;
+  for (size_t i = 1; i < p.used; ++i) {
+    const int id = p.ids[i];
+    if (id < 0 || id >= P_COUNT) continue;
+    float ms = 0;
+    rc = cuda_check(ctx, cudaEventElapsedTime(&ms, p.ev[i - 1], p.ev[i]), "profile");
+    if (rc) return rc;
+    total_ms[id] += ms;
+    launches[id] += 1;
+  }
+  return CKKS_OK;
+}
+
+const char* ckks_profile_name(int id) {
+  static const char* names[P_COUNT] = {"ks_in_rows",       "modup_cols",  "keymult_rows", "moddown_cols",
+                                       "ks_out_rows",      "rescale_in_rows", "rescale_cols", "rescale_out_rows"};
+  return id >= 0 && id < P_COUNT ? names[id] : nullptr;
+}
+
+uint64_t ckks_launch_count(void) { return launch_count(); }
 
 const char* ckks_last_error(ckks_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 

@@ -75,13 +75,47 @@ struct KsArgs {
   int extra;             // ModDown epilogue: 0 none, 1 HMult (d0, d1), 2 HRot (phi(b), 0)
 };
 
+// Kernel ids of the key-switch and rescale pipelines (measurement support).
+enum ProfId {
+  P_KS_IN = 0,       // R1: input -> iNTT row phase
+  P_MODUP_COLS,      // C1: iNTT cols, BConv Q_j -> PQ, NTT cols
+  P_KEYMULT,         // R2: NTT rows, KeyMult + MAC, P-limb iNTT rows
+  P_MODDOWN_COLS,    // C2: iNTT cols, BConv P -> Q, NTT cols
+  P_KS_OUT,          // R3: NTT rows, ModDown epilogue
+  P_RS_IN,           // rescale: top limb iNTT rows
+  P_RS_COLS,         // rescale: iNTT cols, reduce, NTT cols
+  P_RS_OUT,          // rescale: NTT rows, (c - r) q_l^-1
+  P_COUNT
+};
+
+// Per-kernel timing with CUDA events recorded on the launching stream:
+// mark(-1) before the first kernel of an operation, mark(id) after each
+// kernel; the time between consecutive marks is charged to the later id.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ids;
+  size_t used = 0;
+  void mark(cudaStream_t st, int id);
+};
+
+// Kernels launched by this library in this process.
+uint64_t launch_count();
+void count_launch(int k);
+
 // Scratch buffers owned by the context.
 struct Scratch {
   uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
   uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)
   uint32_t* A;  // accumulators, Q limbs [2][L][N] (or all limbs [2][L+alpha][N])
   uint32_t* U;  // HMult result before rescaling [2][L][N]
+  Prof* prof;   // optional stage timing (null or off: no events)
 };
+
+inline void prof_mark(const Scratch& sc, cudaStream_t st, int id) {
+  if (id >= 0) count_launch(1);
+  if (sc.prof && sc.prof->on) sc.prof->mark(st, id);
+}
 
 // ---- launchers (k_basic.cu) ----
 void launch_ntt(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, bool inverse, cudaStream_t st);
@@ -148,6 +182,7 @@ struct ckks_ctx {
   void* d_tables;
   size_t table_bytes;
   ckks::Scratch sc;
+  ckks::Prof prof;
   void* d_scratch;
   size_t scratch_bytes;
   // host-side key-switching constants needed for keygen (gadget P mod prime)

@@ -3,7 +3,25 @@
 #include "geo.cuh"
 #include "internal.h"
 
+#include <atomic>
+
 namespace ckks {
+
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launch_count() { return g_launches.load(); }
+void count_launch(int k) { g_launches += (uint64_t)k; }
+
+void Prof::mark(cudaStream_t st, int id) {
+  if (used == ev.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ev.push_back(e);
+    ids.push_back(id);
+  }
+  ids[used] = id;
+  cudaEventRecord(ev[used], st);
+  ++used;
+}
 
 // ---------------------------------------------------------------------------
 // Standalone NTT / iNTT, in place on [limbs][N]
@@ -100,6 +118,7 @@ void launch_ntt(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, bool 
       k_rows_inv<G><<<gr, G::RT, 0, st>>>(dp, data, ids);
       k_cols_inv<G><<<gc, G::CT, 0, st>>>(dp, data, ids);
     }
+    count_launch(2);
   });
 }
 
@@ -107,6 +126,7 @@ void launch_rows_inv_only(const DevParams& dp, uint32_t* data, int limbs, IdMap 
   if (limbs <= 0) return;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     k_rows_inv<G><<<dim3(G::H / G::RPC, limbs), G::RT, 0, st>>>(dp, data, ids);
+    count_launch(1);
   });
 }
 
@@ -232,12 +252,14 @@ void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint
                  size_t sb, size_t so, cudaStream_t st) {
   const int th = 64;
   k_hadd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, b, out, n, sa, sb, so);
+  count_launch(1);
 }
 
 void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
                   size_t so, cudaStream_t st) {
   const int th = 64;
   k_pmult<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, sa, so);
+  count_launch(1);
 }
 
 void launch_tensor(const DevParams& dp, const uint32_t* c1, const uint32_t* c2, uint32_t* out, int n,

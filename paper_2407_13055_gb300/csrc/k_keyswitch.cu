@@ -496,18 +496,24 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
   const int digits = (n + alpha - 1) / alpha;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     const dim3 rows_in(G::H / G::RPC, n), rows_ext(G::H / G::RPC, ext);
+    prof_mark(sc, st, -1);
     k_ks_in<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.S);
+    prof_mark(sc, st, P_KS_IN);
     const int tiles = G::W / G::TC;
     const size_t sm1 = col_smem_bytes<G>(alpha);
     set_col_smem<G>((const void*)k_ks_modup_cols<G>, sm1);
     const int g1 = groups_for(tiles * digits, ext);
     k_ks_modup_cols<G><<<dim3(tiles, digits, g1), G::CT, sm1, st>>>(dp, n, sc.S, sc.T, g1);
+    prof_mark(sc, st, P_MODUP_COLS);
     k_ks_keymult<G><<<rows_ext, G::RT, 0, st>>>(dp, a, sc.T, sc.S, sc.A, km_out, km_dst);
+    prof_mark(sc, st, P_KEYMULT);
     if (km_out == KM_KEYSWITCH) {
       set_col_smem<G>((const void*)k_ks_moddown_cols<G>, sm1);
       const int g2 = groups_for(tiles * 2, n);
       k_ks_moddown_cols<G><<<dim3(tiles, 2, g2), G::CT, sm1, st>>>(dp, n, sc.S, sc.T, g2);
+      prof_mark(sc, st, P_MODDOWN_COLS);
       k_ks_out<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.T, sc.A, (size_t)n << dp.log_n);
+      prof_mark(sc, st, P_KS_OUT);
     }
   });
 }
@@ -532,7 +538,9 @@ void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc,
     set_col_smem<G>((const void*)k_ks_moddown_cols<G>, sm);
     const int g2 = groups_for(tiles * 2, n);
     k_ks_moddown_cols<G><<<dim3(tiles, 2, g2), G::CT, sm, st>>>(dp, n, sc.S, sc.T, g2);
+    count_launch(1);
     k_ks_out<G><<<dim3(G::H / G::RPC, n), G::RT, 0, st>>>(dp, a, sc.T, acc, (size_t)ext * limb);
+    count_launch(1);
   });
 }
 
@@ -541,11 +549,15 @@ void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, 
   const int top = n - 1;
   if (top < 1) return;
   CKKS_DISPATCH_LOGN(dp.log_n, {
+    prof_mark(sc, st, -1);
     k_rs_in<G><<<dim3(G::H / G::RPC, 2), G::RT, 0, st>>>(dp, in, sin, n, sc.S);
+    prof_mark(sc, st, P_RS_IN);
     const int tiles = G::W / G::TC;
     const int g = groups_for(tiles * 2, top);
     k_rs_cols<G><<<dim3(tiles, 2, g), G::CT, 0, st>>>(dp, n, sc.S, sc.T, g);
+    prof_mark(sc, st, P_RS_COLS);
     k_rs_out<G><<<dim3(G::H / G::RPC, 2 * top), G::RT, 0, st>>>(dp, in, sin, n, sc.T, out, sout);
+    prof_mark(sc, st, P_RS_OUT);
   });
 }
 
