@@ -170,6 +170,31 @@ int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks
 /* HConj (k = 2N - 1). out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
 
+/* --- rescale without allocation (the paper has no counterpart to this entry
+ * point; it exists for callers that must not allocate device memory while
+ * they run, such as a serving loop with a latency budget, where cudaMalloc can
+ * synchronize the whole device or fail when memory is tight). --- */
+/* Fixed size, in uint32 words, of the library's static device scratch used by
+ * ckks_rescale_noalloc: 2^21 words = 8 MiB, held on every GPU that loads the
+ * library until the process exits. */
+#define CKKS_NOALLOC_SCRATCH_WORDS (1u << 21)
+/* Same result as ckks_rescale (single rescaling, c'_i = (c_i - [c_l]) q_l^-1)
+ * on caller-owned device buffers, with no allocation of any kind.
+ *  in_dev:  [2][level+1][N] uint32 residues, internal layout (as a ciphertext
+ *           created with capacity `level`; see ckks_ct_info).
+ *  out_dev: [2][level][N] uint32, written in the same layout; must not
+ *           overlap in_dev.
+ * The scratch is a file-scope device array shared by every call: it needs
+ * (2 + 2*level) * N <= CKKS_NOALLOC_SCRATCH_WORDS (at N = 2^16: level <= 15),
+ * larger requests return CKKS_EINVAL with a message and launch nothing.
+ * Calls whose kernels overlap on the GPU (other streams, other threads)
+ * race on that array; calls in order on one stream do not. Every scratch word
+ * is written before it is read in each call, so nothing needs clearing.
+ * The first call on each device looks up the array's device address with
+ * that device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture. Asynchronous on the context stream. */
+int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint32_t* out_dev);
+
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */
 #define CKKS_PROF_KERNELS 8

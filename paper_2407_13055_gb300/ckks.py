@@ -91,6 +91,7 @@ _SIGS = {
     "ckks_rescale": (_i, [_vp, _vp, _vp]),
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_rescale_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -300,6 +301,15 @@ def ckks_hrot(ctx, a, r: int, evk, out):
 
 def ckks_hconj(ctx, a, evk, out):
     check(ctx, lib.ckks_hconj(ctx, a, evk, out))
+
+
+CKKS_NOALLOC_SCRATCH_WORDS = 1 << 21
+
+
+def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
+    """Rescale between caller-owned device buffers with the library's fixed
+    scratch; see include/ckks.h for layout, limit and ordering rules."""
+    check(ctx, lib.ckks_rescale_noalloc(ctx, in_dev, level, out_dev))
 
 
 CKKS_PROF_KERNELS = 8
