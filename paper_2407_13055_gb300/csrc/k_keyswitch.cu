@@ -27,28 +27,31 @@ __device__ __forceinline__ uint32_t addm(uint32_t a, uint32_t b, uint32_t q) { r
 
 __device__ __forceinline__ int prime_of(int t, int n, int L) { return t < n ? t : L + (t - n); }
 
-// Lazy-reduction range fix: (-2^32 p, 2^32 p) -> [-2^31 p, 2^31 p).
-__device__ __forceinline__ int64_t range_fix(int64_t a, int64_t lim, int64_t wrap) {
-  return a >= lim ? a - wrap : (a < -lim ? a + wrap : a);
-}
-
 // BConv of EC coefficient-domain values per thread: out[i] = sum_k y[k][i] *
 // mat[k] reduced modulo p (Eq. 2 with the 2^32 factor folded into mat).
-// y is thread-private in shared memory: y4[(k * EC/4 + i/4) * NT + tid].
+// y is in shared memory: y4[(k * EC/4 + i/4) * NT + pos]. Lazy reduction as
+// in Sec. 4.2: |y|, |mat| < p/2 bound each product by 2^29 p, so eight of
+// them and then four more after each range reduction stay below 2^63. The
+// range reduction folds the high word back with 2^32 = r1c (mod p):
+// acc = lo + hi * r1c, |acc| < 2^30 p + 2^32, which also meets the signed
+// Montgomery reduction's input range [-p 2^31, p 2^31).
+__device__ __forceinline__ int64_t fold(int64_t a, int32_t r1c) {
+  return (int64_t)(uint32_t)a + (int64_t)(int32_t)(a >> 32) * (int64_t)r1c;
+}
+
 template <int EC, int NT>
-__device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, int K,
-                                                 const int32_t* __restrict__ mat, uint32_t p, uint32_t pm,
+__device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, int pos, int K,
+                                                 const int32_t* __restrict__ mat, const PrimeConst& P,
                                                  uint32_t (&out)[EC]) {
   int64_t acc[EC];
 #pragma unroll
   for (int i = 0; i < EC; ++i) acc[i] = 0;
-  const int64_t lim = (int64_t)p << 31, wrap = (int64_t)p << 32;
   int since = 0, batch = 8;
   for (int k = 0; k < K; ++k) {
     const int32_t b = __ldg(mat + k);
 #pragma unroll
     for (int i4 = 0; i4 < EC / 4; ++i4) {
-      const int4 v = y4[(k * (EC / 4) + i4) * NT + threadIdx.x];
+      const int4 v = y4[(k * (EC / 4) + i4) * NT + pos];
       acc[4 * i4 + 0] += (int64_t)v.x * (int64_t)b;
       acc[4 * i4 + 1] += (int64_t)v.y * (int64_t)b;
       acc[4 * i4 + 2] += (int64_t)v.z * (int64_t)b;
@@ -56,13 +59,13 @@ __device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, in
     }
     if (++since == batch) {
 #pragma unroll
-      for (int i = 0; i < EC; ++i) acc[i] = range_fix(acc[i], lim, wrap);
+      for (int i = 0; i < EC; ++i) acc[i] = fold(acc[i], P.r1c);
       since = 0;
       batch = 4;
     }
   }
 #pragma unroll
-  for (int i = 0; i < EC; ++i) out[i] = fix_signed(smr(range_fix(acc[i], lim, wrap), p, pm), p);
+  for (int i = 0; i < EC; ++i) out[i] = fix_signed(smr(fold(acc[i], P.r1c), P.q, P.m), P.q);
 }
 
 }  // namespace
@@ -126,13 +129,25 @@ __global__ void __launch_bounds__(G::RT) k_ks_in(DevParams dp, KsArgs a, uint32_
 // Column kernels
 // ---------------------------------------------------------------------------
 
-// Load K input limbs of a column tile, finish their iNTT (column phase),
-// multiply by cin[k] and keep the centered values in shared memory.
-template <class G>
+// Column kernels. A block covers a tile of TC columns x H rows and is split
+// into GS slices of CT = TC * EC threads; position pos = (jj, c) of a slice
+// owns EC elements of one column. The slices share the coefficient-domain
+// tile: slice s finishes the iNTT of input limbs k = s, s + GS, ..., then
+// (after one block barrier) handles targets m = s, s + GS, ...; each slice
+// synchronizes its own transposes with a named barrier.
+template <class G, int TC>
+struct ColTile {
+  static constexpr int EC = G::EC, H = G::H, W = G::W;
+  static constexpr int CT = TC * EC;
+  static constexpr int BUF = (H + EC) * TC;
+};
+
+template <class G, int TC>
 __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* src, size_t src_stride, int K,
                                            int id0, const uint2* cin, int4* y4, uint32_t* colbuf, int l, int jj,
-                                           int c) {
-  for (int k = 0; k < K; ++k) {
+                                           int c, int pos, int slice, int GS) {
+  using CTL = ColTile<G, TC>;
+  for (int k = slice; k < K; k += GS) {
     const int id = id0 + k;
     const uint32_t q = dp.pc[id].q;
     const uint2* itw = dp.itw + ((size_t)id << dp.log_n);
@@ -140,78 +155,83 @@ __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* 
     uint32_t x[G::EC];
 #pragma unroll
     for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
-    if (q < (1u << 30)) col_inv<G::EC, G::TC, true>(x, colbuf, itw, jj, c, q);
-    else col_inv<G::EC, G::TC, false>(x, colbuf, itw, jj, c, q);
+    if (q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
+    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
     const uint2 w = cin[k];
     int32_t y[G::EC];
 #pragma unroll
     for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], w.x, w.y, q), q), q);
 #pragma unroll
     for (int i4 = 0; i4 < G::EC / 4; ++i4)
-      y4[(k * (G::EC / 4) + i4) * G::CT + threadIdx.x] =
-          make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+      y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
   }
 }
 
-// BConv one target and run its NTT column phase; store B layout (lazy).
-template <class G>
+// BConv one target and run its NTT column phase; store B layout (lazy range).
+template <class G, int TC>
 __device__ __forceinline__ void col_target(const DevParams& dp, const int4* y4, int K, const int32_t* mat_row,
-                                           int id, uint32_t* dst, uint32_t* colbuf, int l, int jj, int c) {
+                                           int id, uint32_t* dst, uint32_t* colbuf, int l, int jj, int c, int pos,
+                                           int slice) {
+  using CTL = ColTile<G, TC>;
   const PrimeConst P = dp.pc[id];
   uint32_t x[G::EC];
-  bconv_accumulate<G::EC, G::CT>(y4, K, mat_row, P.q, P.m, x);
+  bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, mat_row, P, x);
   const uint2* tw = dp.tw + ((size_t)id << dp.log_n);
-  if (P.q < (1u << 30)) col_fwd<G::EC, G::TC, true>(x, colbuf, tw, jj, c, P.q);
-  else col_fwd<G::EC, G::TC, false>(x, colbuf, tw, jj, c, P.q);
+  if (P.q < (1u << 30)) col_fwd<G::EC, TC, true>(x, colbuf, tw, jj, c, P.q, slice + 1, CTL::CT);
+  else col_fwd<G::EC, TC, false>(x, colbuf, tw, jj, c, P.q, slice + 1, CTL::CT);
 #pragma unroll
   for (int i = 0; i < G::EC; ++i) dst[(G::EC * jj + i) * G::W + l] = x[i];
 }
 
-// C1: ModUp column kernel. grid (W/TC, digits, target groups).
-template <class G>
-__global__ void __launch_bounds__(G::CT) k_ks_modup_cols(DevParams dp, int n, const uint32_t* S, uint32_t* T,
-                                                        int groups) {
+constexpr int kSlices = 4;
+
+// C1: ModUp column kernel. grid (W/TC, digits), block kSlices * CT.
+template <class G, int TC>
+__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
+                                                                               const uint32_t* S, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
-  const int c = threadIdx.x % G::TC, jj = threadIdx.x / G::TC;
-  const int l = blockIdx.x * G::TC + c;
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
   const int j = blockIdx.y;
   const int alpha = dp.alpha, L = dp.L, ext = n + alpha;
   const int lo = j * alpha, hi = min(n, lo + alpha), K = hi - lo;
   const int2 off = dp.ks.up_off[n * dp.dnum + j];
   int4* y4 = smem4;
-  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * G::CT);
-  col_inputs<G>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, lo, dp.ks.up_cin + off.x, y4, colbuf,
-                l, jj, c);
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, lo, dp.ks.up_cin + off.x, y4,
+                    colbuf, l, jj, c, pos, slice, kSlices);
+  __syncthreads();
   const int M = ext - K;
-  const int per = (M + groups - 1) / groups;
-  const int m0 = blockIdx.z * per, m1 = min(M, m0 + per);
-  for (int m = m0; m < m1; ++m) {
+  for (int m = slice; m < M; m += kSlices) {
     const int t = m < lo ? m : m + K;  // skip the digit's own limbs
-    const int id = prime_of(t, n, L);
     uint32_t* dst = T + ((size_t)(j * ext + t) << dp.log_n);
-    col_target<G>(dp, y4, K, dp.ks.up_mat + off.y + t * K, id, dst, colbuf, l, jj, c);
+    col_target<G, TC>(dp, y4, K, dp.ks.up_mat + off.y + t * K, prime_of(t, n, L), dst, colbuf, l, jj, c, pos,
+                      slice);
   }
 }
 
-// C2: ModDown column kernel. grid (W/TC, 2 polys, target groups). Input:
-// S [2][alpha][N] (P limbs after the row-phase iNTT); output T [2][n][N].
-template <class G>
-__global__ void __launch_bounds__(G::CT) k_ks_moddown_cols(DevParams dp, int n, const uint32_t* S, uint32_t* T,
-                                                          int groups) {
+// C2: ModDown column kernel. grid (W/TC, 2 polys). Input S [2][alpha][N]
+// (P limbs after the row-phase iNTT); output T [2][n][N].
+template <class G, int TC>
+__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
+                                                                                 const uint32_t* S, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
-  const int c = threadIdx.x % G::TC, jj = threadIdx.x / G::TC;
-  const int l = blockIdx.x * G::TC + c;
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
   const int u = blockIdx.y;
   const int alpha = dp.alpha;
   int4* y4 = smem4;
-  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * G::CT);
-  col_inputs<G>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
-                y4, colbuf, l, jj, c);
-  const int per = (n + groups - 1) / groups;
-  const int m0 = blockIdx.z * per, m1 = min(n, m0 + per);
-  for (int i = m0; i < m1; ++i) {
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
+                    y4, colbuf, l, jj, c, pos, slice, kSlices);
+  __syncthreads();
+  for (int i = slice; i < n; i += kSlices) {
     uint32_t* dst = T + ((size_t)(u * n + i) << dp.log_n);
-    col_target<G>(dp, y4, alpha, dp.ks.dn_mat + i * alpha, i, dst, colbuf, l, jj, c);
+    col_target<G, TC>(dp, y4, alpha, dp.ks.dn_mat + i * alpha, i, dst, colbuf, l, jj, c, pos, slice);
   }
 }
 
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(G::CT) k_ks_moddown_cols(DevParams dp, int n, 
 // R2: KeyMult + MAC (Par. 1: one kernel for all digits and both key halves)
 // ---------------------------------------------------------------------------
 template <class G>
-__global__ void __launch_bounds__(G::RT) k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* S,
+__global__ void __launch_bounds__(G::RT, 3) k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* S,
                                                      uint32_t* A, int km_out, uint32_t* km_dst) {
   __shared__ uint32_t buf[G::RPC * G::ROWBUF];
   const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(G::RT) k_ks_keymult(DevParams dp, KsArgs a, co
 // R3: ModDown epilogue. out_u[i] = (A_u[i] - NTT(T_u[i])) P^-1 + extra_u[i]
 // ---------------------------------------------------------------------------
 template <class G>
-__global__ void __launch_bounds__(G::RT) k_ks_out(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A,
+__global__ void __launch_bounds__(G::RT, 3) k_ks_out(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A,
                                                  size_t a_stride) {
   __shared__ uint32_t buf[G::RPC * G::ROWBUF];
   const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
@@ -342,20 +362,27 @@ __global__ void __launch_bounds__(G::RT) k_ks_out(DevParams dp, KsArgs a, const 
 #pragma unroll
     for (int k = 0; k < G::ER; ++k) z[k] = csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q);
     if (a.extra == 1) {
-      // HMult: d0 = b1 b2, d1 = a1 b2 + a2 b1 recomputed from the inputs.
-      uint32_t b1[G::ER], b2[G::ER];
-      load_vec<G::ER>(b1, a.x0 + rowoff + G::ER * jj);
-      load_vec<G::ER>(b2, a.x1 + rowoff + G::ER * jj);
-      if (u == 0) {
+      // HMult: d0 = b1 b2, d1 = a1 b2 + a2 b1 recomputed from the inputs,
+      // four elements at a time.
+      const uint32_t* pb1 = a.x0 + rowoff + G::ER * jj;
+      const uint32_t* pb2 = a.x1 + rowoff + G::ER * jj;
 #pragma unroll
-        for (int k = 0; k < G::ER; ++k) z[k] = addm(z[k], mulmod(b1[k], b2[k], P), P.q);
-      } else {
-        uint32_t a1[G::ER], a2[G::ER];
-        load_vec<G::ER>(a1, a.x0 + a.poly_stride0 + rowoff + G::ER * jj);
-        load_vec<G::ER>(a2, a.x1 + a.poly_stride1 + rowoff + G::ER * jj);
+      for (int k4 = 0; k4 < G::ER / 4; ++k4) {
+        uint32_t b1[4], b2[4];
+        load_vec<4>(b1, pb1 + 4 * k4);
+        load_vec<4>(b2, pb2 + 4 * k4);
+        if (u == 0) {
 #pragma unroll
-        for (int k = 0; k < G::ER; ++k)
-          z[k] = addm(z[k], addm(mulmod(a1[k], b2[k], P), mulmod(a2[k], b1[k], P), P.q), P.q);
+          for (int v = 0; v < 4; ++v) z[4 * k4 + v] = addm(z[4 * k4 + v], mulmod(b1[v], b2[v], P), P.q);
+        } else {
+          uint32_t a1[4], a2[4];
+          load_vec<4>(a1, pb1 + a.poly_stride0 + 4 * k4);
+          load_vec<4>(a2, pb2 + a.poly_stride1 + 4 * k4);
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            z[4 * k4 + v] =
+                addm(z[4 * k4 + v], addm(mulmod(a1[v], b2[v], P), mulmod(a2[v], b1[v], P), P.q), P.q);
+        }
       }
     } else if (a.extra == 2 && u == 0) {
       // HRot: add phi_k(b).
@@ -480,14 +507,36 @@ static int groups_for(int blocks_per_group, int max_groups) {
   return g < 1 ? 1 : g;
 }
 
-template <class G>
+template <class G, int TC>
 static size_t col_smem_bytes(int K) {
-  return (size_t)K * (G::EC / 4) * G::CT * sizeof(int4) + (size_t)G::COLBUF * sizeof(uint32_t);
+  using CTL = ColTile<G, TC>;
+  return (size_t)K * (G::EC / 4) * CTL::CT * sizeof(int4) + (size_t)kSlices * CTL::BUF * sizeof(uint32_t);
 }
 
-template <class G>
 static void set_col_smem(const void* f, size_t bytes) {
   cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Column-tile width: 8 columns (32-byte row segments) when that already
+// gives two blocks per SM, else 4 to double the block count.
+template <class G, class F8, class F4>
+static void with_tc(int blocks_per_tile_column, F8 f8, F4 f4) {
+  if ((G::W / 8) * blocks_per_tile_column >= 2 * 152 || G::W / 4 < 16) f8();
+  else f4();
+}
+
+template <class G, int TC>
+static void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, cudaStream_t st) {
+  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
+  set_col_smem((const void*)k_ks_modup_cols<G, TC>, sm);
+  k_ks_modup_cols<G, TC><<<dim3(G::W / TC, digits), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
+}
+
+template <class G, int TC>
+static void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, cudaStream_t st) {
+  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
+  set_col_smem((const void*)k_ks_moddown_cols<G, TC>, sm);
+  k_ks_moddown_cols<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
 }
 
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
@@ -499,18 +548,14 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
     prof_mark(sc, st, -1);
     k_ks_in<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.S);
     prof_mark(sc, st, P_KS_IN);
-    const int tiles = G::W / G::TC;
-    const size_t sm1 = col_smem_bytes<G>(alpha);
-    set_col_smem<G>((const void*)k_ks_modup_cols<G>, sm1);
-    const int g1 = groups_for(tiles * digits, ext);
-    k_ks_modup_cols<G><<<dim3(tiles, digits, g1), G::CT, sm1, st>>>(dp, n, sc.S, sc.T, g1);
+    with_tc<G>(digits, [&] { launch_modup_cols<G, 8>(dp, n, digits, sc, st); },
+               [&] { launch_modup_cols<G, 4>(dp, n, digits, sc, st); });
     prof_mark(sc, st, P_MODUP_COLS);
     k_ks_keymult<G><<<rows_ext, G::RT, 0, st>>>(dp, a, sc.T, sc.S, sc.A, km_out, km_dst);
     prof_mark(sc, st, P_KEYMULT);
     if (km_out == KM_KEYSWITCH) {
-      set_col_smem<G>((const void*)k_ks_moddown_cols<G>, sm1);
-      const int g2 = groups_for(tiles * 2, n);
-      k_ks_moddown_cols<G><<<dim3(tiles, 2, g2), G::CT, sm1, st>>>(dp, n, sc.S, sc.T, g2);
+      with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
+                 [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
       prof_mark(sc, st, P_MODDOWN_COLS);
       k_ks_out<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.T, sc.A, (size_t)n << dp.log_n);
       prof_mark(sc, st, P_KS_OUT);
@@ -533,11 +578,8 @@ void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc,
   a.extra = 0;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     launch_rows_inv_only(dp, sc.S, 2 * alpha, IdMap{nullptr, alpha, 0, dp.L}, st);
-    const int tiles = G::W / G::TC;
-    const size_t sm = col_smem_bytes<G>(alpha);
-    set_col_smem<G>((const void*)k_ks_moddown_cols<G>, sm);
-    const int g2 = groups_for(tiles * 2, n);
-    k_ks_moddown_cols<G><<<dim3(tiles, 2, g2), G::CT, sm, st>>>(dp, n, sc.S, sc.T, g2);
+    with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
+               [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
     count_launch(1);
     k_ks_out<G><<<dim3(G::H / G::RPC, n), G::RT, 0, st>>>(dp, a, sc.T, acc, (size_t)ext * limb);
     count_launch(1);

@@ -93,26 +93,35 @@ __device__ __forceinline__ void row_b_to_a(uint32_t (&x)[E], uint32_t* buf, int 
   __syncwarp();
 }
 
+// Barrier over the threads that share a column tile: the whole block
+// (bar == 0) or named barrier `bar` over `nthr` threads (a slice of the block).
+__device__ __forceinline__ void tile_sync(int bar, int nthr) {
+  if (bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
 // Column transpose for a tile of TC columns: buf[(h + h/E) * TC + c].
-// The E threads of a column are spread over several warps: block barrier.
+// The E threads of a column are spread over several warps: tile barrier.
 template <int E, int TC>
-__device__ __forceinline__ void col_a_to_b(uint32_t (&x)[E], uint32_t* buf, int jj, int c) {
+__device__ __forceinline__ void col_a_to_b(uint32_t (&x)[E], uint32_t* buf, int jj, int c, int bar = 0,
+                                           int nthr = 0) {
 #pragma unroll
   for (int i = 0; i < E; ++i) buf[(jj + (E + 1) * i) * TC + c] = x[i];
-  __syncthreads();
+  tile_sync(bar, nthr);
 #pragma unroll
   for (int i = 0; i < E; ++i) x[i] = buf[((E + 1) * jj + i) * TC + c];
-  __syncthreads();
+  tile_sync(bar, nthr);
 }
 
 template <int E, int TC>
-__device__ __forceinline__ void col_b_to_a(uint32_t (&x)[E], uint32_t* buf, int jj, int c) {
+__device__ __forceinline__ void col_b_to_a(uint32_t (&x)[E], uint32_t* buf, int jj, int c, int bar = 0,
+                                           int nthr = 0) {
 #pragma unroll
   for (int i = 0; i < E; ++i) buf[((E + 1) * jj + i) * TC + c] = x[i];
-  __syncthreads();
+  tile_sync(bar, nthr);
 #pragma unroll
   for (int i = 0; i < E; ++i) x[i] = buf[(jj + (E + 1) * i) * TC + c];
-  __syncthreads();
+  tile_sync(bar, nthr);
 }
 
 // Phases. H = EC^2 rows of W = ER^2 words.
@@ -137,18 +146,18 @@ __device__ __forceinline__ void row_inv(uint32_t (&x)[ER], uint32_t* buf, const 
 // Column phase, forward: A layout along h in, B layout out.
 template <int EC, int TC, bool LAZY>
 __device__ __forceinline__ void col_fwd(uint32_t (&x)[EC], uint32_t* buf, const uint2* tw, int jj, int c,
-                                        uint32_t q) {
+                                        uint32_t q, int bar = 0, int nthr = 0) {
   ct_pass<EC, LAZY>(x, tw, 1, q);
-  col_a_to_b<EC, TC>(x, buf, jj, c);
+  col_a_to_b<EC, TC>(x, buf, jj, c, bar, nthr);
   ct_pass<EC, LAZY>(x, tw, EC + jj, q);
 }
 
 // Column phase, inverse: B layout in, A layout out.
 template <int EC, int TC, bool LAZY>
 __device__ __forceinline__ void col_inv(uint32_t (&x)[EC], uint32_t* buf, const uint2* itw, int jj, int c,
-                                        uint32_t q) {
+                                        uint32_t q, int bar = 0, int nthr = 0) {
   gs_pass<EC, LAZY>(x, itw, EC + jj, q);
-  col_b_to_a<EC, TC>(x, buf, jj, c);
+  col_b_to_a<EC, TC>(x, buf, jj, c, bar, nthr);
   gs_pass<EC, LAZY>(x, itw, 1, q);
 }
 
