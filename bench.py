@@ -61,26 +61,31 @@ def algorithmic_bytes(n=L, alpha=ALPHA):
 
 
 def kernel_models(n=L, alpha=ALPHA):
-    """Per-launch algorithmic work of each pipeline kernel: compulsory HBM
-    bytes, and modular multiplications (NTT butterflies + BConv products +
-    element-wise products)."""
+    """Per-launch algorithmic work of each pipeline stage, averaged over one
+    HMult+rescale and one HRot: compulsory HBM bytes (evaluation-key stream,
+    the op's inputs and outputs; scratch is meant to stay in L2) and modular
+    multiplications (NTT butterflies, BConv products, element-wise products)."""
     N = 1 << LOG_N
     d = -(-n // alpha)
     ext = n + alpha
-    half = N // 2
-    rows, cols = 10, 6                       # stages per phase at N = 2^16 (W = 1024, H = 64)
+    row, col = N // 2 * 10, N // 2 * 6      # butterflies per limb: row phase (W=1024), column phase (H=64)
     targets = sum(ext - min(alpha, n - j * alpha) for j in range(d))
-    m = {}
-    # bytes: evk stream dominates keymult; inputs/outputs of the op elsewhere
-    m["keymult_rows"] = dict(bytes=2 * d * ext * LIMB_BYTES,
-                             modmul=targets * half * rows + 2 * d * ext * N)
-    m["modup_cols"] = dict(bytes=0, modmul=d * 0 + n * half * cols + targets * half * cols + targets * N * alpha)
-    m["moddown_cols"] = dict(bytes=0, modmul=2 * alpha * half * cols + 2 * n * half * cols + 2 * n * N * alpha)
-    m["ks_in_rows"] = dict(bytes=2 * n * LIMB_BYTES, modmul=n * half * rows + n * N)
-    m["ks_out_rows"] = dict(bytes=(4 * n + 2 * n) * LIMB_BYTES, modmul=2 * n * half * rows + 2 * n * N * 3)
-    m["rescale_in_rows"] = dict(bytes=2 * LIMB_BYTES, modmul=2 * half * rows)
-    m["rescale_cols"] = dict(bytes=0, modmul=2 * half * cols + 2 * (n - 1) * (half * cols + N))
-    m["rescale_out_rows"] = dict(bytes=4 * (n - 1) * LIMB_BYTES, modmul=2 * (n - 1) * (half * rows + N))
+    lb = LIMB_BYTES
+    m = {
+        "ks_prep": dict(bytes=(2 * n + n) * lb // 2, modmul=n * N // 2),
+        "ks_in_rows": dict(bytes=0, modmul=n * row),
+        "modup_cols": dict(bytes=0, modmul=(n + targets) * col + targets * N * alpha),
+        "modup_rows": dict(bytes=0, modmul=targets * row),
+        "keymult": dict(bytes=2 * d * ext * lb, modmul=2 * d * ext * N),
+        "moddown_in_rows": dict(bytes=0, modmul=2 * alpha * row),
+        "moddown_cols": dict(bytes=0, modmul=2 * (alpha + n) * col + 2 * n * N * alpha),
+        "moddown_rows": dict(bytes=0, modmul=2 * n * row),
+        "ks_epilogue": dict(bytes=2 * n * lb // 2, modmul=2 * n * N * 2),
+        "rescale_in_rows": dict(bytes=0, modmul=2 * row),
+        "rescale_cols": dict(bytes=0, modmul=2 * col + 2 * (n - 1) * (col + N)),
+        "rescale_rows": dict(bytes=0, modmul=2 * (n - 1) * row),
+        "rescale_epilogue": dict(bytes=2 * (n - 1) * lb, modmul=2 * (n - 1) * N),
+    }
     return m
 
 
@@ -216,42 +221,67 @@ def run_native(args, rank, world, local_rank):
         pt = K.ckks_encode(ctx, inputs.messages(100 + i, (1 << LOG_N) // 2), LEVEL, SCALE)
         cts.append(K.ckks_encrypt(ctx, sk, pt, 200 + i))
         K.ckks_free(pt)
-    outs_m = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2)]
-    outs_r = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2)]
+    # execution lanes: lane 0 is the context itself, the others are clones
+    # with their own stream and scratch; lane l takes ciphertexts i = l mod lanes
+    streams = [stream] + [torch.cuda.Stream() for _ in range(args.lanes - 1)]
+    lanes = [ctx] + [K.ckks_ctx_clone(ctx, s_.cuda_stream) for s_ in streams[1:]]
+    outs_m = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
+    outs_r = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
 
-    def step():
+    def step(n_lanes):
         for i in range(BATCH):
-            K.ckks_hmult(ctx, cts[i], cts[(i + 1) % BATCH], rk, K.CKKS_RESCALE, outs_m[i & 1])
-            K.ckks_hrot(ctx, cts[i], 1, gk, outs_r[i & 1])
+            l = i % n_lanes
+            K.ckks_hmult(lanes[l], cts[i], cts[(i + 1) % BATCH], rk, K.CKKS_RESCALE, outs_m[l])
+            K.ckks_hrot(lanes[l], cts[i], 1, gk, outs_r[l])
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    K.ckks_profile(ctx, True)
-    launches0 = K.ckks_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
+    def timed(n_steps, n_lanes):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         ev0.record(stream)
-        for _ in range(args.steps):
-            step()
+        for s_ in streams[1:n_lanes]:
+            s_.wait_event(ev0)
+        for _ in range(n_steps):
+            step(n_lanes)
+        for s_ in streams[1:n_lanes]:
+            e = torch.cuda.Event()
+            e.record(s_)
+            stream.wait_event(e)
         ev1.record(stream)
         barrier()
-    K.ckks_profile(ctx, False)
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        step(args.lanes)
+    barrier()
+    launches0 = K.ckks_launch_count()
+    with ClockSampler(local_rank) as clk:
+        ms = timed(args.steps, args.lanes)
     launches = K.ckks_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
-    prof = K.ckks_profile_read(ctx)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     ops = 2 * BATCH * args.steps * world
     value = ops / (ms / 1e3)
+
+    # one lane, in order: per-kernel CUDA-event times on the launching stream
+    seq_steps = max(3, args.steps // 4)
+    K.ckks_profile(ctx, True)
+    ms_seq = timed(seq_steps, 1)
+    K.ckks_profile(ctx, False)
+    prof = K.ckks_profile_read(ctx)
+    seq_ops_per_s = 2 * BATCH * seq_steps / (ms_seq / 1e3)
+    hm_stages = ("ks_prep", "ks_in_rows", "modup_cols", "modup_rows", "keymult", "moddown_in_rows",
+                 "moddown_cols", "moddown_rows", "ks_epilogue", "rescale_in_rows", "rescale_cols",
+                 "rescale_rows", "rescale_epilogue")
+    per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
+    hmult_us = 1e3 * sum(per_launch[k] for k in hm_stages)
+    hrot_us = 1e3 * sum(per_launch[k] for k in hm_stages[:9])
 
     # end to end through the C ABI with host buffers: per op, upload the
     # inputs from pinned memory, run it, read the result back.
@@ -261,7 +291,7 @@ def run_native(args, rank, world, local_rank):
         K.ckks_ct_export(ctx, cts[i], n, out=host_in[i])
     host_out_m = torch.empty((2, L - 1, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     host_out_r = torch.empty((2, L, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
-    e2e_steps = max(1, args.steps // 10)
+    e2e_steps = max(1, args.steps // 20)
     ct_bytes = 2 * L * n * 4
     barrier()
     t0 = time.perf_counter()
@@ -296,13 +326,14 @@ def run_native(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": None}
     else:
         # plain ALU: modular multiplications against the int32 multiply peak
-        # (152 SMs x 64 IMAD/clk at the maximum SM clock, 3 IMAD per modmul)
-        imad_peak = 152 * 64 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        # (152 SMs x 128 IMAD/clk, measured issue rate, at the maximum SM
+        # clock; 3 IMAD-class instructions per modular product)
+        imad_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
         achieved = mdl["modmul"] / avg_s / 1e12
         peak = imad_peak / 3 / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
-                "frac": achieved / peak, "peak_source": "derived: 152 SM x 64 IMAD/clk x sm_max_mhz / 3",
-                "traffic": None}
+                "frac": achieved / peak, "peak_source": "derived: 152 SM x 128 IMAD/clk x sm_max_mhz / 3",
+                "algorithmic_modmul_per_launch": mdl["modmul"], "traffic": None}
     stage = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
                  "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)} for k, v in prof.items()}
     per_gpu_gbs = BATCH * (hm_bytes + hr_bytes) * args.steps / (ms / 1e3) / 1e9
@@ -312,7 +343,11 @@ def run_native(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions of U[-1,1] messages)",
-        "config": workload_config({"parallelism": f"replicas{world}"}),
+        "config": workload_config({"parallelism": f"replicas{world}",
+                                   "lanes": f"{args.lanes} concurrent CUDA streams (context clones), "
+                                            "independent ciphertexts per lane"}),
+        "one_lane": {"value": seq_ops_per_s, "unit": UNIT, "hmult_rescale_us": hmult_us, "hrot_us": hrot_us,
+                     "note": "same workload issued in order on one stream; stage times from its CUDA events"},
         "roofline": roof, "op_roofline": op_hbm, "stages": stage,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }
@@ -322,6 +357,8 @@ def run_native(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     for h in cts + outs_m + outs_r + [sk, rk, gk]:
         K.ckks_free(h)
+    for c in lanes[1:]:
+        K.ckks_ctx_destroy(c)
     K.ckks_ctx_destroy(ctx)
 
 
@@ -332,6 +369,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -95,6 +95,13 @@ int ckks_gen_primes(int log_n, int n_q, int n_p, uint32_t* q_out, uint32_t* p_ou
  * legacy default stream) on the current device, which must be an sm_103 GPU. */
 int ckks_ctx_create(const ckks_params* params, void* cuda_stream, ckks_ctx** out);
 void ckks_ctx_destroy(ckks_ctx* ctx);
+/* Execution lane: a context that shares `parent`'s parameters and device
+ * tables but has its own CUDA stream and key-switching scratch, so that
+ * operations issued on different lanes can run concurrently on the GPU.
+ * Objects (ciphertexts, keys) of the parent work with the clone; ordering
+ * between lanes is the caller's (CUDA events). Destroy clones before their
+ * parent. */
+int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out);
 const char* ckks_last_error(ckks_ctx* ctx);
 int ckks_sync(ckks_ctx* ctx);            /* cudaStreamSynchronize on the context stream */
 void ckks_free(void* handle);            /* any ckks_ct / ckks_pt / ckks_sk / ckks_evk */
@@ -197,10 +204,11 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
 
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */
-#define CKKS_PROF_KERNELS 8
+#define CKKS_PROF_KERNELS 13
 /* enable = 1: clear and start recording one CUDA event on the context stream
- * after every kernel of the key-switch and rescale pipelines (ModUp rows and
- * columns, KeyMult, ModDown columns and rows, three rescale kernels);
+ * after every stage of the key-switch and rescale pipelines (input prep,
+ * ModUp rows/columns/rows, KeyMult, ModDown rows/columns/rows, epilogue, and
+ * the four rescale stages);
  * enable = 0: stop recording. */
 int ckks_profile(ckks_ctx* ctx, int enable);
 /* Synchronizes, then writes per kernel id the total device milliseconds

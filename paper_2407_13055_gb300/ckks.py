@@ -63,6 +63,7 @@ _SIGS = {
     "ckks_gen_primes": (_i, [_i, _i, _i, _vp, _vp]),
     "ckks_ctx_create": (_i, [_P(ckks_params), _vp, _P(_vp)]),
     "ckks_ctx_destroy": (None, [_vp]),
+    "ckks_ctx_clone": (_i, [_vp, _vp, _P(_vp)]),
     "ckks_last_error": (C.c_char_p, [_vp]),
     "ckks_sync": (_i, [_vp]),
     "ckks_free": (None, [_vp]),
@@ -152,6 +153,12 @@ def ckks_ctx_create(log_n: int, q, p, dnum: int, scale: float = 2.0**30, secret_
 
 def ckks_ctx_destroy(ctx):
     lib.ckks_ctx_destroy(ctx)
+
+
+def ckks_ctx_clone(parent, stream: int | None = None):
+    out = _vp()
+    check(parent, lib.ckks_ctx_clone(parent, stream, C.byref(out)))
+    return out
 
 
 def ckks_free(h):
@@ -312,7 +319,7 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
     check(ctx, lib.ckks_rescale_noalloc(ctx, in_dev, level, out_dev))
 
 
-CKKS_PROF_KERNELS = 8
+CKKS_PROF_KERNELS = 13
 
 
 def ckks_profile(ctx, enable: bool):

@@ -104,6 +104,7 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   if (prm->dnum != (L + alpha - 1) / alpha)
     return bad(fail(ctx, CKKS_EINVAL, "dnum (%d) must equal ceil(n_q / n_p) = %d", prm->dnum,
                     (L + alpha - 1) / alpha));
+  if (prm->dnum > 8) return bad(fail(ctx, CKKS_EINVAL, "dnum %d above the supported maximum of 8", prm->dnum));
   const uint64_t two_n = 2ull << log_n;
   std::vector<uint32_t> all(prm->q, prm->q + L);
   all.insert(all.end(), prm->p, prm->p + alpha);
@@ -133,11 +134,42 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   return CKKS_OK;
 }
 
+int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
+  if (!parent || !out) return CKKS_EINVAL;
+  *out = nullptr;
+  ckks_ctx* c = new (std::nothrow) ckks_ctx();
+  if (!c) return CKKS_ENOMEM;
+  c->dp = parent->dp;
+  c->N = parent->N;
+  c->q = parent->q;
+  c->p = parent->p;
+  c->pc_host = parent->pc_host;
+  c->scale = parent->scale;
+  c->sigma = parent->sigma;
+  c->secret_hw = parent->secret_hw;
+  c->seed = parent->seed;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->d_tables = parent->d_tables;
+  c->table_bytes = 0;
+  c->owns_tables = false;
+  c->gadget_p = parent->gadget_p;
+  c->device = parent->device;
+  c->d_scratch = nullptr;
+  const int rc = alloc_scratch(c);
+  if (rc != CKKS_OK) {
+    delete c;
+    return fail(parent, rc, "clone: scratch allocation failed");
+  }
+  c->sc.prof = &c->prof;
+  *out = c;
+  return CKKS_OK;
+}
+
 void ckks_ctx_destroy(ckks_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
-  if (ctx->d_tables) cudaFree(ctx->d_tables);
+  if (ctx->d_tables && ctx->owns_tables) cudaFree(ctx->d_tables);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
@@ -172,8 +204,10 @@ int ckks_profile_read(ckks_ctx* ctx, double* total_ms, uint64_t* launches) {
 }
 
 const char* ckks_profile_name(int id) {
-  static const char* names[P_COUNT] = {"ks_in_rows",       "modup_cols",  "keymult_rows", "moddown_cols",
-                                       "ks_out_rows",      "rescale_in_rows", "rescale_cols", "rescale_out_rows"};
+  static const char* names[P_COUNT] = {
+      "ks_prep",      "ks_in_rows",       "modup_cols",   "modup_rows",    "keymult",
+      "moddown_in_rows", "moddown_cols",  "moddown_rows", "ks_epilogue",   "rescale_in_rows",
+      "rescale_cols", "rescale_rows",     "rescale_epilogue"};
   return id >= 0 && id < P_COUNT ? names[id] : nullptr;
 }
 

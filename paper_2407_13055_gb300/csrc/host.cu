@@ -331,6 +331,16 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       (void)K;
     }
   }
+  std::vector<int2> up_rows;
+  for (int nl = 1; nl <= L; ++nl) {
+    const int ext = nl + alpha;
+    const int digits = (nl + alpha - 1) / alpha;
+    for (int j = 0; j < digits; ++j) {
+      const int lo = j * alpha, hi = std::min(nl, lo + alpha);
+      for (int t = 0; t < ext; ++t)
+        if (t < lo || t >= hi) up_rows.push_back(make_int2(j * ext + t, t < nl ? t : L + (t - nl)));
+    }
+  }
   std::vector<uint2> dn_cin(alpha), dn_pinv(L);
   std::vector<int32_t> dn_mat((size_t)L * alpha);
   for (int k = 0; k < alpha; ++k) {
@@ -397,6 +407,7 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {dn_mat.data(), dn_mat.size() * sizeof(int32_t), 0},
       {dn_pinv.data(), dn_pinv.size() * sizeof(uint2), 0},
       {rs_qinv.data(), rs_qinv.size() * sizeof(uint2), 0},
+      {up_rows.data(), up_rows.size() * sizeof(int2), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -427,19 +438,30 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   dp.ks.dn_mat = reinterpret_cast<const int32_t*>(base + parts[7].off);
   dp.ks.dn_pinv = reinterpret_cast<const uint2*>(base + parts[8].off);
   dp.ks.rs_qinv = reinterpret_cast<const uint2*>(base + parts[9].off);
+  dp.ks.up_rows = reinterpret_cast<const int2*>(base + parts[10].off);
 
-  // scratch
-  const size_t limb = (size_t)n;
-  const size_t s_limbs = std::max(L, 2 * alpha);
-  const size_t t_limbs = std::max((size_t)dnum * np, (size_t)2 * L);
-  const size_t a_limbs = 2 * (size_t)L, u_limbs = 2 * (size_t)L;
-  const size_t words = (s_limbs + t_limbs + a_limbs + u_limbs) * limb;
-  uint32_t* sc = nullptr;
-  if (cudaMalloc(&sc, words * sizeof(uint32_t)) != cudaSuccess) {
+  ctx->owns_tables = true;
+  const int rc = alloc_scratch(ctx);
+  if (rc != CKKS_OK) {
     cudaFree(base);
     ctx->d_tables = nullptr;
-    return CKKS_ENOMEM;
   }
+  return rc;
+}
+
+// Key-switching scratch of one context (one execution lane): S (row-phase
+// iNTT outputs), T (column-phase outputs), A (accumulators), U (HMult result
+// before rescaling).
+int alloc_scratch(ckks_ctx* ctx) {
+  const DevParams& dp = ctx->dp;
+  const int L = dp.L, np = dp.L + dp.alpha;
+  const size_t limb = (size_t)1 << dp.log_n;
+  const size_t s_limbs = std::max(L, 2 * dp.alpha);
+  const size_t t_limbs = std::max((size_t)dp.dnum * np, (size_t)2 * L);
+  const size_t a_limbs = 2 * (size_t)np, u_limbs = 2 * (size_t)L;
+  const size_t words = (s_limbs + t_limbs + a_limbs + u_limbs) * limb;
+  uint32_t* sc = nullptr;
+  if (cudaMalloc(&sc, words * sizeof(uint32_t)) != cudaSuccess) return CKKS_ENOMEM;
   ctx->d_scratch = sc;
   ctx->scratch_bytes = words * sizeof(uint32_t);
   ctx->sc.S = sc;

@@ -30,6 +30,10 @@ struct KsTables {
   const uint2* dn_pinv;
   // Rescale: rs_qinv[l * L + i] = Shoup pair of [q_l^-1]_{q_i}, i < l.
   const uint2* rs_qinv;
+  // ModUp output limbs that need the NTT row phase, per level n (in order of
+  // n = 1 .. L): (limb index j (n + alpha) + t in the scratch, prime id) for
+  // every digit j and every extended limb t outside the digit.
+  const int2* up_rows;
 };
 
 struct DevParams {
@@ -77,14 +81,19 @@ struct KsArgs {
 
 // Kernel ids of the key-switch and rescale pipelines (measurement support).
 enum ProfId {
-  P_KS_IN = 0,       // R1: input -> iNTT row phase
-  P_MODUP_COLS,      // C1: iNTT cols, BConv Q_j -> PQ, NTT cols
-  P_KEYMULT,         // R2: NTT rows, KeyMult + MAC, P-limb iNTT rows
-  P_MODDOWN_COLS,    // C2: iNTT cols, BConv P -> Q, NTT cols
-  P_KS_OUT,          // R3: NTT rows, ModDown epilogue
-  P_RS_IN,           // rescale: top limb iNTT rows
-  P_RS_COLS,         // rescale: iNTT cols, reduce, NTT cols
-  P_RS_OUT,          // rescale: NTT rows, (c - r) q_l^-1
+  P_KS_PREP = 0,      // input d, a1*a2 or phi(a) (streaming)
+  P_KS_IN_ROWS,       // iNTT row phase of the input
+  P_MODUP_COLS,       // iNTT cols, BConv Q_j -> PQ, NTT cols
+  P_MODUP_ROWS,       // NTT row phase of the ModUp output
+  P_KEYMULT,          // KeyMult + MAC (streaming)
+  P_MODDOWN_IN_ROWS,  // iNTT row phase of the P limbs
+  P_MODDOWN_COLS,     // iNTT cols, BConv P -> Q, NTT cols
+  P_MODDOWN_ROWS,     // NTT row phase of the converted limbs
+  P_KS_EPILOGUE,      // (acc - z) P^-1 + d0/d1 or phi(b) (streaming)
+  P_RS_IN_ROWS,       // rescale: iNTT rows of the top limb
+  P_RS_COLS,          // rescale: iNTT cols, reduce, NTT cols
+  P_RS_ROWS,          // rescale: NTT rows
+  P_RS_EPILOGUE,      // rescale: (c - r) q_l^-1 (streaming)
   P_COUNT
 };
 
@@ -107,13 +116,12 @@ void count_launch(int k);
 struct Scratch {
   uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
   uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)
-  uint32_t* A;  // accumulators, Q limbs [2][L][N] (or all limbs [2][L+alpha][N])
+  uint32_t* A;  // accumulators [2][n + alpha][N]
   uint32_t* U;  // HMult result before rescaling [2][L][N]
   Prof* prof;   // optional stage timing (null or off: no events)
 };
 
 inline void prof_mark(const Scratch& sc, cudaStream_t st, int id) {
-  if (id >= 0) count_launch(1);
   if (sc.prof && sc.prof->on) sc.prof->mark(st, id);
 }
 
@@ -181,6 +189,7 @@ struct ckks_ctx {
   cudaStream_t stream;
   void* d_tables;
   size_t table_bytes;
+  bool owns_tables;  // false for a clone (tables belong to the parent context)
   ckks::Scratch sc;
   ckks::Prof prof;
   void* d_scratch;
@@ -222,6 +231,7 @@ struct ckks_evk {
 // host.cu
 namespace ckks {
 int build_context(ckks_ctx* ctx, const ckks_params* p);
+int alloc_scratch(ckks_ctx* ctx);
 bool host_is_prime(uint64_t n);
 uint32_t host_find_psi(uint32_t q, int log_n);
 int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p);

@@ -1,23 +1,28 @@
-// Fused hybrid key switching (Sec. 2.3: ModUp -> KeyMult -> MAC -> ModDown)
-// and single rescaling (Sec. 2.1), built from alternating row and column
-// kernels so that every ModSwitch (iNTT -> BConv -> NTT, Alg. 1) is split at
-// its coefficient-domain midpoint:
+// Hybrid key switching (Sec. 2.3: ModUp -> KeyMult -> MAC -> ModDown) and
+// single rescaling (Sec. 2.1). Every ModSwitch (iNTT -> BConv -> NTT, Alg. 1)
+// is split at its coefficient-domain midpoint, which only exists between the
+// two column phases, so the pipeline alternates:
 //
-//   R1 (rows)  : input (d, a1*a2 or phi_k(a)) -> iNTT row phase          -> S
-//   C1 (cols)  : iNTT col phase, * N^-1 (Q_j/q_i)^-1, BConv Eq. 2 to every
-//                prime outside digit j, NTT col phase                    -> T
-//   R2 (rows)  : NTT row phase, KeyMult + MAC over the digits with evk;
-//                Q limbs -> A, P limbs -> iNTT row phase                 -> S
-//   C2 (cols)  : iNTT col phase, * N^-1 (P/p_k)^-1, BConv P -> Q, NTT col -> T
-//   R3 (rows)  : NTT row phase, (acc - z) P^-1 + (d0, d1) or (phi(b), 0)  -> out
+//   prep    (stream): input d, a1*a2 (tensor) or phi_k(a) (automorphism)    -> S
+//   rows^-1 (rows)  : iNTT row phase of S, in place
+//   C1      (cols)  : iNTT col phase, * N^-1 (Q_j/q_i)^-1, BConv (Eq. 2) to
+//                     every prime outside digit j, NTT col phase            -> T
+//   rows    (rows)  : NTT row phase of every T limb, in place
+//   KeyMult (stream): acc_u = sum_j ModUp_j * evk_j[u] (Par. 1)            -> A
+//   rows^-1 (rows)  : iNTT row phase of the P limbs of A                     -> S
+//   C2      (cols)  : iNTT col phase, * N^-1 (P/p_k)^-1, BConv P -> Q, NTT col -> T
+//   rows    (rows)  : NTT row phase of T, in place
+//   epilogue(stream): (acc - z) P^-1 + (d0, d1) or (phi(b), 0)              -> out
 //
-// Constants are folded as in the paper's Seq. 2 (N^-1 into the BConv
-// constant, 2^32 into the BConv matrix so that the signed Montgomery
-// reduction of the lazily accumulated sum needs no correction). The BConv
-// matrix product uses the paper's lazy reduction (Sec. 4.2): centered inputs
-// and entries, eight 64-bit products, then +-2^32 p range fixes every four.
+// Row kernels (rows.cuh) hold W-word rows in registers with their twiddles
+// loaded up front; column kernels hold a tile of TC columns; streaming kernels
+// do the NTT-domain element-wise work with 128-bit accesses at full
+// occupancy. Constants are folded as in the paper's Seq. 2 (N^-1 into the
+// BConv constant, 2^32 into the BConv matrix). The BConv product uses the
+// paper's lazy reduction (Sec. 4.2).
 #include "geo.cuh"
 #include "internal.h"
+#include "rows.cuh"
 
 namespace ckks {
 
@@ -69,61 +74,6 @@ __device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, in
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// R1: key-switch input -> iNTT row phase -> S [n][N] (A layout stores)
-// ---------------------------------------------------------------------------
-template <class G>
-__device__ __forceinline__ void load_ks_input_row(const DevParams& dp, const KsArgs& a, int i, int h, int jj,
-                                                  uint32_t* b, uint32_t (&x)[G::ER]) {
-  const size_t rowoff = ((size_t)i << dp.log_n) + (size_t)h * G::W;
-  if (a.mode == KS_PLAIN) {
-    load_vec<G::ER>(x, a.x0 + rowoff + G::ER * jj);
-  } else if (a.mode == KS_TENSOR) {
-    const PrimeConst P = dp.pc[i];
-    uint32_t a1[G::ER], a2[G::ER];
-    load_vec<G::ER>(a1, a.x0 + a.poly_stride0 + rowoff + G::ER * jj);
-    load_vec<G::ER>(a2, a.x1 + a.poly_stride1 + rowoff + G::ER * jj);
-#pragma unroll
-    for (int r = 0; r < G::ER; ++r) x[r] = mulmod(a1[r], a2[r], P);
-  } else {
-    // phi_k(a): destination row h reads one source row (Eq. 4 keeps the high
-    // bits of the bit-reversed position together); stage it in shared memory.
-    const uint32_t src_row = auto_src((uint32_t)h * G::W, a.galois, dp.log_n) / G::W;
-    const uint32_t* s = a.x0 + a.poly_stride0 + ((size_t)i << dp.log_n) + (size_t)src_row * G::W;
-#pragma unroll
-    for (int r = 0; r < G::ER; ++r) {
-      const int l = jj + G::ER * r;
-      b[l + l / G::ER] = s[l];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < G::ER; ++r) {
-      const uint32_t l = G::ER * jj + r;
-      const uint32_t ls = auto_src((uint32_t)h * G::W + l, a.galois, dp.log_n) % G::W;
-      x[r] = b[ls + ls / G::ER];
-    }
-    __syncwarp();
-  }
-}
-
-template <class G>
-__global__ void __launch_bounds__(G::RT) k_ks_in(DevParams dp, KsArgs a, uint32_t* S) {
-  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
-  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
-  const int h = blockIdx.x * G::RPC + r;
-  const int i = blockIdx.y;
-  uint32_t* b = buf + r * G::ROWBUF;
-  uint32_t x[G::ER];
-  load_ks_input_row<G>(dp, a, i, h, jj, b, x);
-  const uint32_t q = dp.pc[i].q;
-  const uint2* itw = dp.itw + ((size_t)i << dp.log_n);
-  if (q < (1u << 30)) row_inv<G::ER, G::H, true>(x, b, itw, h, jj, q);
-  else row_inv<G::ER, G::H, false>(x, b, itw, h, jj, q);
-  uint32_t* o = S + ((size_t)i << dp.log_n) + (size_t)h * G::W;
-#pragma unroll
-  for (int k = 0; k < G::ER; ++k) o[jj + G::ER * k] = x[k];
-}
 
 // ---------------------------------------------------------------------------
 // Column kernels
@@ -236,199 +186,9 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols
 }
 
 // ---------------------------------------------------------------------------
-// R2: KeyMult + MAC (Par. 1: one kernel for all digits and both key halves)
+// Rescale column kernel: iNTT cols of the top limb, centered, reduced into
+// every lower prime, NTT cols.
 // ---------------------------------------------------------------------------
-template <class G>
-__global__ void __launch_bounds__(G::RT, 3) k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* S,
-                                                     uint32_t* A, int km_out, uint32_t* km_dst) {
-  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
-  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
-  const int h = blockIdx.x * G::RPC + r;
-  const int t = blockIdx.y;
-  const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
-  const int id = prime_of(t, n, L);
-  const int key_limb = t < n ? t : L + (t - n);
-  const PrimeConst P = dp.pc[id];
-  const bool lazy = P.q < (1u << 30);
-  const uint2* tw = dp.tw + ((size_t)id << dp.log_n);
-  uint32_t* b = buf + r * G::ROWBUF;
-  const size_t rowoff = (size_t)h * G::W;
-  const int digits = (n + alpha - 1) / alpha;
-  uint32_t acc0[G::ER], acc1[G::ER];
-#pragma unroll
-  for (int i = 0; i < G::ER; ++i) acc0[i] = acc1[i] = 0;
-  for (int j = 0; j < digits; ++j) {
-    const int lo = j * alpha, hi = min(n, lo + alpha);
-    uint32_t x[G::ER];
-    if (t >= lo && t < hi) {
-      load_ks_input_row<G>(dp, a, t, h, jj, b, x);  // the digit's own limb: ModUp copies it
-    } else {
-      const uint32_t* s = T + ((size_t)(j * ext + t) << dp.log_n) + rowoff;
-#pragma unroll
-      for (int i = 0; i < G::ER; ++i) x[i] = s[jj + G::ER * i];
-      if (lazy) {
-        row_fwd<G::ER, G::H, true>(x, b, tw, h, jj, P.q);
-#pragma unroll
-        for (int i = 0; i < G::ER; ++i) x[i] = csub(x[i], 2 * P.q);  // [0, 2q) < 2^31
-      } else {
-        row_fwd<G::ER, G::H, false>(x, b, tw, h, jj, P.q);
-#pragma unroll
-        for (int i = 0; i < G::ER; ++i) x[i] = csub(x[i], P.q);      // [0, q)
-      }
-    }
-    if (km_out == KM_MODUP) {
-#pragma unroll
-      for (int i = 0; i < G::ER; ++i) x[i] = csub(x[i], P.q);
-      store_vec<G::ER>(km_dst + ((size_t)(j * ext + t) << dp.log_n) + rowoff + G::ER * jj, x);
-      continue;
-    }
-    const uint32_t* e0 = a.evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + rowoff + G::ER * jj;
-    const uint32_t* e1 = a.evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + rowoff + G::ER * jj;
-#pragma unroll
-    for (int i4 = 0; i4 < G::ER / 4; ++i4) {
-      uint32_t k0[4], k1[4];
-      load_vec_stream<4>(k0, e0 + 4 * i4);
-      load_vec_stream<4>(k1, e1 + 4 * i4);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = 4 * i4 + v;
-        acc0[i] = addm(acc0[i], fix_signed(mont_mul(x[i], k0[v], P.q, P.m), P.q), P.q);
-        acc1[i] = addm(acc1[i], fix_signed(mont_mul(x[i], k1[v], P.q, P.m), P.q), P.q);
-      }
-    }
-  }
-  if (km_out == KM_MODUP) return;
-  if (km_out == KM_ACC_ALL) {
-    store_vec<G::ER>(km_dst + ((size_t)t << dp.log_n) + rowoff + G::ER * jj, acc0);
-    store_vec<G::ER>(km_dst + ((size_t)(ext + t) << dp.log_n) + rowoff + G::ER * jj, acc1);
-    return;
-  }
-  if (t < n) {
-    store_vec<G::ER>(A + ((size_t)t << dp.log_n) + rowoff + G::ER * jj, acc0);
-    store_vec<G::ER>(A + ((size_t)(n + t) << dp.log_n) + rowoff + G::ER * jj, acc1);
-  } else {
-    const int k = t - n;
-    const uint2* itw = dp.itw + ((size_t)id << dp.log_n);
-    if (lazy) {
-      row_inv<G::ER, G::H, true>(acc0, b, itw, h, jj, P.q);
-      row_inv<G::ER, G::H, true>(acc1, b, itw, h, jj, P.q);
-    } else {
-      row_inv<G::ER, G::H, false>(acc0, b, itw, h, jj, P.q);
-      row_inv<G::ER, G::H, false>(acc1, b, itw, h, jj, P.q);
-    }
-    uint32_t* o0 = S + ((size_t)k << dp.log_n) + rowoff;
-    uint32_t* o1 = S + ((size_t)(alpha + k) << dp.log_n) + rowoff;
-#pragma unroll
-    for (int i = 0; i < G::ER; ++i) {
-      o0[jj + G::ER * i] = acc0[i];
-      o1[jj + G::ER * i] = acc1[i];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// R3: ModDown epilogue. out_u[i] = (A_u[i] - NTT(T_u[i])) P^-1 + extra_u[i]
-// ---------------------------------------------------------------------------
-template <class G>
-__global__ void __launch_bounds__(G::RT, 3) k_ks_out(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A,
-                                                 size_t a_stride) {
-  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
-  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
-  const int h = blockIdx.x * G::RPC + r;
-  const int i = blockIdx.y;
-  const int n = a.n;
-  const PrimeConst P = dp.pc[i];
-  const bool lazy = P.q < (1u << 30);
-  const uint2* tw = dp.tw + ((size_t)i << dp.log_n);
-  const uint2 pinv = dp.ks.dn_pinv[i];
-  uint32_t* b = buf + r * G::ROWBUF;
-  const size_t rowoff = ((size_t)i << dp.log_n) + (size_t)h * G::W;
-  for (int u = 0; u < 2; ++u) {
-    uint32_t z[G::ER];
-    const uint32_t* s = T + ((size_t)(u * n + i) << dp.log_n) + (size_t)h * G::W;
-#pragma unroll
-    for (int k = 0; k < G::ER; ++k) z[k] = s[jj + G::ER * k];
-    if (lazy) {
-      row_fwd<G::ER, G::H, true>(z, b, tw, h, jj, P.q);
-#pragma unroll
-      for (int k = 0; k < G::ER; ++k) z[k] = normalize<true>(z[k], P.q);
-    } else {
-      row_fwd<G::ER, G::H, false>(z, b, tw, h, jj, P.q);
-#pragma unroll
-      for (int k = 0; k < G::ER; ++k) z[k] = normalize<false>(z[k], P.q);
-    }
-    uint32_t acc[G::ER];
-    load_vec<G::ER>(acc, A + u * a_stride + rowoff + G::ER * jj);
-#pragma unroll
-    for (int k = 0; k < G::ER; ++k) z[k] = csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q);
-    if (a.extra == 1) {
-      // HMult: d0 = b1 b2, d1 = a1 b2 + a2 b1 recomputed from the inputs,
-      // four elements at a time.
-      const uint32_t* pb1 = a.x0 + rowoff + G::ER * jj;
-      const uint32_t* pb2 = a.x1 + rowoff + G::ER * jj;
-#pragma unroll
-      for (int k4 = 0; k4 < G::ER / 4; ++k4) {
-        uint32_t b1[4], b2[4];
-        load_vec<4>(b1, pb1 + 4 * k4);
-        load_vec<4>(b2, pb2 + 4 * k4);
-        if (u == 0) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) z[4 * k4 + v] = addm(z[4 * k4 + v], mulmod(b1[v], b2[v], P), P.q);
-        } else {
-          uint32_t a1[4], a2[4];
-          load_vec<4>(a1, pb1 + a.poly_stride0 + 4 * k4);
-          load_vec<4>(a2, pb2 + a.poly_stride1 + 4 * k4);
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-            z[4 * k4 + v] =
-                addm(z[4 * k4 + v], addm(mulmod(a1[v], b2[v], P), mulmod(a2[v], b1[v], P), P.q), P.q);
-        }
-      }
-    } else if (a.extra == 2 && u == 0) {
-      // HRot: add phi_k(b).
-      const uint32_t src_row = auto_src((uint32_t)h * G::W, a.galois, dp.log_n) / G::W;
-      const uint32_t* sb = a.x0 + ((size_t)i << dp.log_n) + (size_t)src_row * G::W;
-#pragma unroll
-      for (int k = 0; k < G::ER; ++k) {
-        const int l = jj + G::ER * k;
-        b[l + l / G::ER] = sb[l];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < G::ER; ++k) {
-        const uint32_t l = G::ER * jj + k;
-        const uint32_t ls = auto_src((uint32_t)h * G::W + l, a.galois, dp.log_n) % G::W;
-        z[k] = addm(z[k], b[ls + ls / G::ER], P.q);
-      }
-      __syncwarp();
-    }
-    store_vec<G::ER>(a.out + u * a.out_stride + rowoff + G::ER * jj, z);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Rescale (single rescaling): iNTT of the top limb, centered, reduced into
-// every lower prime, NTT, then (c_i - r_i) q_l^-1.
-// ---------------------------------------------------------------------------
-template <class G>
-__global__ void __launch_bounds__(G::RT) k_rs_in(DevParams dp, const uint32_t* in, size_t sin, int n,
-                                                uint32_t* S) {
-  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
-  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
-  const int h = blockIdx.x * G::RPC + r;
-  const int u = blockIdx.y, l = n - 1;
-  const uint32_t q = dp.pc[l].q;
-  const uint2* itw = dp.itw + ((size_t)l << dp.log_n);
-  uint32_t* b = buf + r * G::ROWBUF;
-  uint32_t x[G::ER];
-  load_vec<G::ER>(x, in + u * sin + ((size_t)l << dp.log_n) + (size_t)h * G::W + G::ER * jj);
-  if (q < (1u << 30)) row_inv<G::ER, G::H, true>(x, b, itw, h, jj, q);
-  else row_inv<G::ER, G::H, false>(x, b, itw, h, jj, q);
-  uint32_t* o = S + ((size_t)u << dp.log_n) + (size_t)h * G::W;
-#pragma unroll
-  for (int k = 0; k < G::ER; ++k) o[jj + G::ER * k] = x[k];
-}
-
 template <class G>
 __global__ void __launch_bounds__(G::CT) k_rs_cols(DevParams dp, int n, const uint32_t* S, uint32_t* T,
                                                   int groups) {
@@ -463,37 +223,149 @@ __global__ void __launch_bounds__(G::CT) k_rs_cols(DevParams dp, int n, const ui
   }
 }
 
-template <class G>
-__global__ void __launch_bounds__(G::RT) k_rs_out(DevParams dp, const uint32_t* in, size_t sin, int n,
-                                                 const uint32_t* T, uint32_t* out, size_t sout) {
-  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
-  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
-  const int h = blockIdx.x * G::RPC + r;
+
+// ---------------------------------------------------------------------------
+// Streaming kernels: grid (N / (4 * threads), limbs), four consecutive
+// positions per thread.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t stream_pos() { return 4 * (blockIdx.x * blockDim.x + threadIdx.x); }
+
+// Four NTT-domain values of the key-switched polynomial at limb i.
+__device__ __forceinline__ void ks_input4(const DevParams& dp, const KsArgs& a, int i, uint32_t p0,
+                                          uint32_t (&v)[4]) {
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  if (a.mode == KS_PLAIN) {
+    load_vec<4>(v, a.x0 + off);
+  } else if (a.mode == KS_TENSOR) {
+    const PrimeConst P = dp.pc[i];
+    uint32_t a1[4], a2[4];
+    load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
+    load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = mulmod(a1[k], a2[k], P);
+  } else {
+    const uint32_t* s = a.x0 + a.poly_stride0 + ((size_t)i << dp.log_n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldg(s + auto_src(p0 + k, a.galois, dp.log_n));
+  }
+}
+
+__global__ void k_ks_prep(DevParams dp, KsArgs a, uint32_t* S) {
+  const int i = blockIdx.y;
+  const uint32_t p0 = stream_pos();
+  uint32_t v[4];
+  ks_input4(dp, a, i, p0, v);
+  store_vec<4>(S + ((size_t)i << dp.log_n) + p0, v);
+}
+
+// KeyMult + MAC over the D digits for extended limb t (Par. 1): the digit's
+// own limbs are the input itself (ModUp copies them), the others come from
+// the NTT'd ModUp output T[j][t]. All loads of a thread are issued before any
+// product so that one memory latency covers the whole sum. A = [2][n + alpha][N].
+template <int D>
+__global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* A, int km_out,
+                             uint32_t* km_dst) {
+  const int t = blockIdx.y;
+  const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
+  const int id = prime_of(t, n, L);
+  const int key_limb = t < n ? t : L + (t - n);
+  const PrimeConst P = dp.pc[id];
+  const uint32_t p0 = stream_pos();
+  uint32_t x[D][4], e0[D][4], e1[D][4];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const int lo = j * alpha, hi = min(n, lo + alpha);
+    if (t >= lo && t < hi) ks_input4(dp, a, t, p0, x[j]);
+    else load_vec<4>(x[j], T + ((size_t)(j * ext + t) << dp.log_n) + p0);
+  }
+  if (km_out == KM_MODUP) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) store_vec<4>(km_dst + ((size_t)(j * ext + t) << dp.log_n) + p0, x[j]);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    load_vec_stream<4>(e0[j], a.evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+    load_vec_stream<4>(e1[j], a.evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
+  }
+  uint32_t acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc0[k] = addm(acc0[k], fix_signed(mont_mul(x[j][k], e0[j][k], P.q, P.m), P.q), P.q);
+      acc1[k] = addm(acc1[k], fix_signed(mont_mul(x[j][k], e1[j][k], P.q, P.m), P.q), P.q);
+    }
+  uint32_t* dst = km_out == KM_ACC_ALL ? km_dst : A;
+  store_vec<4>(dst + ((size_t)t << dp.log_n) + p0, acc0);
+  store_vec<4>(dst + ((size_t)(ext + t) << dp.log_n) + p0, acc1);
+}
+
+static void launch_keymult(int digits, dim3 g, int th, cudaStream_t st, const DevParams& dp, const KsArgs& a,
+                           const uint32_t* T, uint32_t* A, int km_out, uint32_t* km_dst) {
+  switch (digits) {
+#define CKKS_KM(D) \
+  case D: k_ks_keymult<D><<<g, th, 0, st>>>(dp, a, T, A, km_out, km_dst); break;
+    CKKS_KM(1) CKKS_KM(2) CKKS_KM(3) CKKS_KM(4) CKKS_KM(5) CKKS_KM(6) CKKS_KM(7) CKKS_KM(8)
+#undef CKKS_KM
+    default:
+      break;
+  }
+}
+
+// ModDown epilogue: out_u[i] = (A_u[i] - T_u[i]) P^-1 + extra_u[i], with
+// extra = (d0, d1) recomputed from the inputs (HMult) or (phi_k(b), 0) (HRot).
+__global__ void k_ks_epilogue(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
+  const int n = a.n;
+  const int u = blockIdx.y / n, i = blockIdx.y % n;
+  const PrimeConst P = dp.pc[i];
+  const uint2 pinv = dp.ks.dn_pinv[i];
+  const uint32_t p0 = stream_pos();
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  uint32_t z[4], acc[4];
+  load_vec<4>(z, T + ((size_t)(u * n + i) << dp.log_n) + p0);
+  load_vec<4>(acc, A + u * a_stride + off);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) z[k] = csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q);
+  if (a.extra == 1) {
+    uint32_t b1[4], b2[4];
+    load_vec<4>(b1, a.x0 + off);
+    load_vec<4>(b2, a.x1 + off);
+    if (u == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z[k] = addm(z[k], mulmod(b1[k], b2[k], P), P.q);
+    } else {
+      uint32_t a1[4], a2[4];
+      load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
+      load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z[k] = addm(z[k], addm(mulmod(a1[k], b2[k], P), mulmod(a2[k], b1[k], P), P.q), P.q);
+    }
+  } else if (a.extra == 2 && u == 0) {
+    const uint32_t* sb = a.x0 + ((size_t)i << dp.log_n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = addm(z[k], __ldg(sb + auto_src(p0 + k, a.galois, dp.log_n)), P.q);
+  }
+  store_vec<4>(a.out + u * a.out_stride + off, z);
+}
+
+// Rescale epilogue: out_u[i] = (c_u[i] - r_u[i]) q_l^-1, r = NTT of the
+// centered top limb reduced modulo q_i.
+__global__ void k_rs_epilogue(DevParams dp, const uint32_t* in, size_t sin, int n, const uint32_t* T,
+                              uint32_t* out, size_t sout) {
   const int top = n - 1;
   const int u = blockIdx.y / top, i = blockIdx.y % top;
   const PrimeConst P = dp.pc[i];
   const uint2 qinv = dp.ks.rs_qinv[top * dp.L + i];
-  const uint2* tw = dp.tw + ((size_t)i << dp.log_n);
-  uint32_t* b = buf + r * G::ROWBUF;
-  uint32_t z[G::ER];
-  const uint32_t* s = T + ((size_t)(u * top + i) << dp.log_n) + (size_t)h * G::W;
+  const uint32_t p0 = stream_pos();
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  uint32_t z[4], c[4];
+  load_vec<4>(z, T + ((size_t)(u * top + i) << dp.log_n) + p0);
+  load_vec<4>(c, in + u * sin + off);
 #pragma unroll
-  for (int k = 0; k < G::ER; ++k) z[k] = s[jj + G::ER * k];
-  if (P.q < (1u << 30)) {
-    row_fwd<G::ER, G::H, true>(z, b, tw, h, jj, P.q);
-#pragma unroll
-    for (int k = 0; k < G::ER; ++k) z[k] = normalize<true>(z[k], P.q);
-  } else {
-    row_fwd<G::ER, G::H, false>(z, b, tw, h, jj, P.q);
-#pragma unroll
-    for (int k = 0; k < G::ER; ++k) z[k] = normalize<false>(z[k], P.q);
-  }
-  const size_t rowoff = ((size_t)i << dp.log_n) + (size_t)h * G::W + G::ER * jj;
-  uint32_t cv[G::ER];
-  load_vec<G::ER>(cv, in + u * sin + rowoff);
-#pragma unroll
-  for (int k = 0; k < G::ER; ++k) z[k] = csub(shoup(cv[k] - z[k] + P.q, qinv.x, qinv.y, P.q), P.q);
-  store_vec<G::ER>(out + u * sout + rowoff, z);
+  for (int k = 0; k < 4; ++k) z[k] = csub(shoup(c[k] - z[k] + P.q, qinv.x, qinv.y, P.q), P.q);
+  store_vec<4>(out + u * sout + off, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,11 +397,13 @@ static void with_tc(int blocks_per_tile_column, F8 f8, F4 f4) {
   else f4();
 }
 
+
 template <class G, int TC>
 static void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, cudaStream_t st) {
   const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
   set_col_smem((const void*)k_ks_modup_cols<G, TC>, sm);
   k_ks_modup_cols<G, TC><<<dim3(G::W / TC, digits), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
+    count_launch(1);
 }
 
 template <class G, int TC>
@@ -537,52 +411,89 @@ static void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, c
   const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
   set_col_smem((const void*)k_ks_moddown_cols<G, TC>, sm);
   k_ks_moddown_cols<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
+    count_launch(1);
+}
+
+// Streaming grid: four positions per thread.
+static void stream_grid(int log_n, int limbs, dim3& grid, int& threads) {
+  const int quads = (1 << log_n) / 4;
+  threads = quads < 256 ? quads : 256;
+  grid = dim3(quads / threads, limbs);
+}
+
+// Offset and count of the level's entries in the ModUp limb table (the
+// NTT'd ModUp limbs (j, t), t outside digit j).
+static void modup_rows_range(int n, int alpha, int& off, int& cnt) {
+  auto count = [&](int m) { return ((m + alpha - 1) / alpha) * (m + alpha) - m; };
+  off = 0;
+  for (int m = 1; m < n; ++m) off += count(m);
+  cnt = count(n);
+}
+
+// ModDown from the accumulators A = [2][n + alpha][N] (a_stride between
+// polys): P-limb iNTT rows (into S), C2, NTT rows, epilogue.
+template <class G>
+static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
+                         size_t a_stride, cudaStream_t st) {
+  const int n = a.n, alpha = dp.alpha;
+  const size_t limb = (size_t)1 << dp.log_n;
+  // P limbs n .. n+alpha-1 of both accumulators -> S [2][alpha] (compact)
+  launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
+                   LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
+  prof_mark(sc, st, P_MODDOWN_IN_ROWS);
+  with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
+             [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
+  prof_mark(sc, st, P_MODDOWN_COLS);
+  launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+  prof_mark(sc, st, P_MODDOWN_ROWS);
+  dim3 g;
+  int th;
+  stream_grid(dp.log_n, 2 * n, g, th);
+  k_ks_epilogue<<<g, th, 0, st>>>(dp, a, sc.T, A, a_stride);
+    count_launch(1);
+  prof_mark(sc, st, P_KS_EPILOGUE);
 }
 
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st) {
   const int n = a.n, alpha = dp.alpha, ext = n + alpha;
   const int digits = (n + alpha - 1) / alpha;
+  const size_t limb = (size_t)1 << dp.log_n;
+  dim3 g;
+  int th;
   CKKS_DISPATCH_LOGN(dp.log_n, {
-    const dim3 rows_in(G::H / G::RPC, n), rows_ext(G::H / G::RPC, ext);
     prof_mark(sc, st, -1);
-    k_ks_in<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.S);
-    prof_mark(sc, st, P_KS_IN);
+    stream_grid(dp.log_n, n, g, th);
+    k_ks_prep<<<g, th, 0, st>>>(dp, a, sc.S);
+    count_launch(1);
+    prof_mark(sc, st, P_KS_PREP);
+    launch_rows_g<G>(dp, true, sc.S, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+    prof_mark(sc, st, P_KS_IN_ROWS);
     with_tc<G>(digits, [&] { launch_modup_cols<G, 8>(dp, n, digits, sc, st); },
                [&] { launch_modup_cols<G, 4>(dp, n, digits, sc, st); });
     prof_mark(sc, st, P_MODUP_COLS);
-    k_ks_keymult<G><<<rows_ext, G::RT, 0, st>>>(dp, a, sc.T, sc.S, sc.A, km_out, km_dst);
+    int off, cnt;
+    modup_rows_range(n, alpha, off, cnt);
+    launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+    prof_mark(sc, st, P_MODUP_ROWS);
+    stream_grid(dp.log_n, ext, g, th);
+    launch_keymult(digits, g, th, st, dp, a, sc.T, sc.A, km_out, km_dst);
+    count_launch(1);
     prof_mark(sc, st, P_KEYMULT);
-    if (km_out == KM_KEYSWITCH) {
-      with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
-                 [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
-      prof_mark(sc, st, P_MODDOWN_COLS);
-      k_ks_out<G><<<rows_in, G::RT, 0, st>>>(dp, a, sc.T, sc.A, (size_t)n << dp.log_n);
-      prof_mark(sc, st, P_KS_OUT);
-    }
+    if (km_out == KM_KEYSWITCH) moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
   });
 }
 
 void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
                     cudaStream_t st) {
-  const int alpha = dp.alpha, ext = n + alpha;
-  const size_t limb = (size_t)1 << dp.log_n;
-  // S <- P limbs of both polynomials, then their row-phase iNTT in place.
-  for (int u = 0; u < 2; ++u)
-    cudaMemcpyAsync(sc.S + (size_t)u * alpha * limb, acc + ((size_t)u * ext + n) * limb,
-                    (size_t)alpha * limb * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
   KsArgs a{};
   a.n = n;
   a.out = out;
-  a.out_stride = (size_t)n * limb;
+  a.out_stride = (size_t)n << dp.log_n;
   a.extra = 0;
   CKKS_DISPATCH_LOGN(dp.log_n, {
-    launch_rows_inv_only(dp, sc.S, 2 * alpha, IdMap{nullptr, alpha, 0, dp.L}, st);
-    with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
-               [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
-    count_launch(1);
-    k_ks_out<G><<<dim3(G::H / G::RPC, n), G::RT, 0, st>>>(dp, a, sc.T, acc, (size_t)ext * limb);
-    count_launch(1);
+    prof_mark(sc, st, -1);
+    moddown_tail<G>(dp, sc, a, acc, (size_t)(n + dp.alpha) << dp.log_n, st);
   });
 }
 
@@ -592,14 +503,22 @@ void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, 
   if (top < 1) return;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
-    k_rs_in<G><<<dim3(G::H / G::RPC, 2), G::RT, 0, st>>>(dp, in, sin, n, sc.S);
-    prof_mark(sc, st, P_RS_IN);
+    // top limb of both polynomials -> S [2] (compact)
+    launch_rows_g<G>(dp, true, in, sc.S, 2, LimbMap{nullptr, top, n, n, dp.L, 1, (int)(sin >> dp.log_n)}, true, st);
+    prof_mark(sc, st, P_RS_IN_ROWS);
     const int tiles = G::W / G::TC;
-    const int g = groups_for(tiles * 2, top);
-    k_rs_cols<G><<<dim3(tiles, 2, g), G::CT, 0, st>>>(dp, n, sc.S, sc.T, g);
+    const int gr = groups_for(tiles * 2, top);
+    k_rs_cols<G><<<dim3(tiles, 2, gr), G::CT, 0, st>>>(dp, n, sc.S, sc.T, gr);
+    count_launch(1);
     prof_mark(sc, st, P_RS_COLS);
-    k_rs_out<G><<<dim3(G::H / G::RPC, 2 * top), G::RT, 0, st>>>(dp, in, sin, n, sc.T, out, sout);
-    prof_mark(sc, st, P_RS_OUT);
+    launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
+    prof_mark(sc, st, P_RS_ROWS);
+    dim3 g;
+    int th;
+    stream_grid(dp.log_n, 2 * top, g, th);
+    k_rs_epilogue<<<g, th, 0, st>>>(dp, in, sin, n, sc.T, out, sout);
+    count_launch(1);
+    prof_mark(sc, st, P_RS_EPILOGUE);
   });
 }
 

@@ -1,0 +1,222 @@
+// Row phase of the NTT / iNTT as standalone kernels over a list of limbs.
+//
+// Each warp-group of ER threads owns one row of W = ER^2 words. All global
+// loads a thread needs (its row elements and the twiddles of its second
+// register pass, which are specific to the thread) are issued before the
+// first butterfly, so a warp waits for memory once instead of once per stage.
+#pragma once
+#include "geo.cuh"
+#include "internal.h"
+
+namespace ckks {
+
+// Limb list of a row launch: launch index y -> (data limb index, prime id).
+// Rule (no table): y = u * pl + r selects limb first + r of polynomial u,
+// whose limbs start at data limb u * ps; that limb's extended index
+// t = (first + r) % per is q_t for t < n, else p_(t - n).
+struct LimbMap {
+  const int2* tab;  // explicit table, or null for the rule
+  int first;
+  int per, n, L;
+  int pl = 1 << 30, ps = 0;
+  __device__ __forceinline__ int2 operator()(int y) const {
+    if (tab) return tab[y];
+    const int u = y / pl, r = y % pl;
+    const int t = (first + r) % per;
+    return make_int2(u * ps + first + r, t < n ? t : L + (t - n));
+  }
+};
+
+// Register-resident twiddles of one pass: tw[(1 << s) - 1 + b] for local
+// stage s and block b (2^s blocks).
+template <int E, bool LAZY>
+__device__ __forceinline__ void ct_pass_reg(uint32_t (&x)[E], const uint2 (&tw)[E - 1], uint32_t q) {
+  constexpr int e = Log2<E>::v;
+#pragma unroll
+  for (int s = 0; s < e; ++s) {
+    const int half = E >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w = tw[(1 << s) - 1 + b];
+#pragma unroll
+      for (int r = 0; r < half; ++r) {
+        const int i0 = b * 2 * half + r;
+        ct_bfly<LAZY>(x[i0], x[i0 + half], w.x, w.y, q);
+      }
+    }
+  }
+}
+
+template <int E, bool LAZY>
+__device__ __forceinline__ void gs_pass_reg(uint32_t (&x)[E], const uint2 (&tw)[E - 1], uint32_t q) {
+  constexpr int e = Log2<E>::v;
+#pragma unroll
+  for (int s = e - 1; s >= 0; --s) {
+    const int half = E >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w = tw[(1 << s) - 1 + b];
+#pragma unroll
+      for (int r = 0; r < half; ++r) {
+        const int i0 = b * 2 * half + r;
+        gs_bfly<LAZY>(x[i0], x[i0 + half], w.x, w.y, q);
+      }
+    }
+  }
+}
+
+// First-pass twiddles of the block's RPC rows h0 .. h0+RPC-1 (the same for
+// every thread of a row): stage s needs indices (H + h) 2^s + b, contiguous
+// over the block's rows; staged in shared memory at
+// (2^s - 1) RPC + r 2^s + b.
+template <int E, int H, int RPC>
+__device__ __forceinline__ void stage_pass_a_twiddles(uint2* sm, const uint2* __restrict__ t, int h0) {
+  constexpr int e = Log2<E>::v;
+#pragma unroll
+  for (int s = 0; s < e; ++s) {
+    const int cnt = RPC << s;
+    const uint2* src = t + ((uint32_t)(H + h0) << s);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sm[((1 << s) - 1) * RPC + i] = __ldg(src + i);
+  }
+}
+
+template <int E, int RPC, bool LAZY>
+__device__ __forceinline__ void ct_pass_sm(uint32_t (&x)[E], const uint2* sm, int r, uint32_t q) {
+  constexpr int e = Log2<E>::v;
+#pragma unroll
+  for (int s = 0; s < e; ++s) {
+    const int half = E >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w = sm[((1 << s) - 1) * RPC + (r << s) + b];
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        ct_bfly<LAZY>(x[i0], x[i0 + half], w.x, w.y, q);
+      }
+    }
+  }
+}
+
+template <int E, int RPC, bool LAZY>
+__device__ __forceinline__ void gs_pass_sm(uint32_t (&x)[E], const uint2* sm, int r, uint32_t q) {
+  constexpr int e = Log2<E>::v;
+#pragma unroll
+  for (int s = e - 1; s >= 0; --s) {
+    const int half = E >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w = sm[((1 << s) - 1) * RPC + (r << s) + b];
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        gs_bfly<LAZY>(x[i0], x[i0 + half], w.x, w.y, q);
+      }
+    }
+  }
+}
+
+// Second-pass twiddles of thread jj in row h: indices ((H + h) E + jj) 2^s + b,
+// contiguous for each stage, so stages s >= 1 load with 16-byte vectors.
+template <int E, int H>
+__device__ __forceinline__ void load_pass_b_twiddles(uint2 (&tw)[E - 1], const uint2* __restrict__ t, int h,
+                                                     int jj) {
+  constexpr int e = Log2<E>::v;
+  const uint32_t base = (uint32_t)(H + h) * E + jj;
+  tw[0] = __ldg(t + base);
+#pragma unroll
+  for (int s = 1; s < e; ++s) {
+    const uint4* p = reinterpret_cast<const uint4*>(t + (base << s));
+#pragma unroll
+    for (int b2 = 0; b2 < (1 << (s - 1)); ++b2) {
+      const uint4 v = __ldg(p + b2);
+      tw[(1 << s) - 1 + 2 * b2] = make_uint2(v.x, v.y);
+      tw[(1 << s) + 2 * b2] = make_uint2(v.z, v.w);
+    }
+  }
+}
+
+// Forward row phase: src in A layout (column-phase output, natural
+// positions), dst in B layout, values normalized to [0, q). dst_compact:
+// write limb y at dst + y N instead of at the source limb index.
+template <class G>
+__global__ void __launch_bounds__(G::RT) k_rows_fwd_g(DevParams dp, const uint32_t* src, uint32_t* dst,
+                                                      LimbMap map, int dst_compact) {
+  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
+  __shared__ uint2 twa[G::RPC * (G::ER - 1)];
+  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
+  const int h = blockIdx.x * G::RPC + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  const uint2* tw = dp.tw + ((size_t)lm.y << dp.log_n);
+  uint2 twb[G::ER - 1];
+  load_pass_b_twiddles<G::ER, G::H>(twb, tw, h, jj);
+  const uint32_t* s = src + ((size_t)lm.x << dp.log_n) + (size_t)h * G::W;
+  uint32_t x[G::ER];
+#pragma unroll
+  for (int i = 0; i < G::ER; ++i) x[i] = s[jj + G::ER * i];
+  stage_pass_a_twiddles<G::ER, G::H, G::RPC>(twa, tw, blockIdx.x * G::RPC);
+  __syncthreads();
+  uint32_t* b = buf + r * G::ROWBUF;
+  if (q < (1u << 30)) {
+    ct_pass_sm<G::ER, G::RPC, true>(x, twa, r, q);
+    row_a_to_b<G::ER>(x, b, jj);
+    ct_pass_reg<G::ER, true>(x, twb, q);
+#pragma unroll
+    for (int i = 0; i < G::ER; ++i) x[i] = normalize<true>(x[i], q);
+  } else {
+    ct_pass_sm<G::ER, G::RPC, false>(x, twa, r, q);
+    row_a_to_b<G::ER>(x, b, jj);
+    ct_pass_reg<G::ER, false>(x, twb, q);
+#pragma unroll
+    for (int i = 0; i < G::ER; ++i) x[i] = normalize<false>(x[i], q);
+  }
+  const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
+  store_vec<G::ER>(dst + (dl << dp.log_n) + (size_t)h * G::W + G::ER * jj, x);
+}
+
+// Inverse row phase: src in B layout (NTT domain), dst in A layout, lazy
+// range [0, 2q) (the column phase that follows accepts it).
+template <class G>
+__global__ void __launch_bounds__(G::RT) k_rows_inv_g(DevParams dp, const uint32_t* src, uint32_t* dst,
+                                                      LimbMap map, int dst_compact) {
+  __shared__ uint32_t buf[G::RPC * G::ROWBUF];
+  __shared__ uint2 twa[G::RPC * (G::ER - 1)];
+  const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
+  const int h = blockIdx.x * G::RPC + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  const uint2* itw = dp.itw + ((size_t)lm.y << dp.log_n);
+  uint2 twb[G::ER - 1];
+  load_pass_b_twiddles<G::ER, G::H>(twb, itw, h, jj);
+  uint32_t x[G::ER];
+  load_vec<G::ER>(x, src + ((size_t)lm.x << dp.log_n) + (size_t)h * G::W + G::ER * jj);
+  stage_pass_a_twiddles<G::ER, G::H, G::RPC>(twa, itw, blockIdx.x * G::RPC);
+  __syncthreads();
+  uint32_t* b = buf + r * G::ROWBUF;
+  if (q < (1u << 30)) {
+    gs_pass_reg<G::ER, true>(x, twb, q);
+    row_b_to_a<G::ER>(x, b, jj);
+    gs_pass_sm<G::ER, G::RPC, true>(x, twa, r, q);
+  } else {
+    gs_pass_reg<G::ER, false>(x, twb, q);
+    row_b_to_a<G::ER>(x, b, jj);
+    gs_pass_sm<G::ER, G::RPC, false>(x, twa, r, q);
+  }
+  const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
+  uint32_t* o = dst + (dl << dp.log_n) + (size_t)h * G::W;
+#pragma unroll
+  for (int i = 0; i < G::ER; ++i) o[jj + G::ER * i] = x[i];
+}
+
+template <class G>
+inline void launch_rows_g(const DevParams& dp, bool inverse, const uint32_t* src, uint32_t* dst, int limbs,
+                          LimbMap map, bool dst_compact, cudaStream_t st) {
+  if (limbs <= 0) return;
+  const dim3 grid(G::H / G::RPC, limbs);
+  if (inverse) k_rows_inv_g<G><<<grid, G::RT, 0, st>>>(dp, src, dst, map, dst_compact ? 1 : 0);
+  else k_rows_fwd_g<G><<<grid, G::RT, 0, st>>>(dp, src, dst, map, dst_compact ? 1 : 0);
+  count_launch(1);
+}
+
+}  // namespace ckks

@@ -377,3 +377,38 @@ def test_error_codes(K, O):
     finally:
         for h in (c3, c4, c0, out, rk):
             K.ckks_free(h)
+
+
+# ------------------------------------------------- execution lanes (clones) ---
+
+def test_lanes_give_identical_results_concurrently(K, O):
+    """Operations on clone contexts (own stream and scratch) running at the
+    same time give the same residues as the oracle for each input."""
+    import torch
+    ctx, P = get(K, O, "n16d3")
+    n_q = 12
+    evk = rand_evk(P, 91)
+    ek = K.ckks_evk_import(ctx, evk, 0)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    lanes = [K.ckks_ctx_clone(ctx, s.cuda_stream) for s in streams]
+    hosts = [(rand_ct(P, n_q, 92 + 2 * i), rand_ct(P, n_q, 93 + 2 * i)) for i in range(3)]
+    cts = [(K.ckks_ct_import(ctx, a, n_q - 1, 2.0**30), K.ckks_ct_import(ctx, b, n_q - 1, 2.0**30)) for a, b in hosts]
+    outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in lanes]
+    try:
+        torch.cuda.synchronize()
+        for _ in range(3):   # several rounds so that the lanes overlap
+            for lane, (a, b), out in zip(lanes, cts, outs):
+                K.ckks_hmult(lane, a, b, ek, K.CKKS_RESCALE, out)
+        for lane in lanes:
+            K.ckks_sync(lane)
+        for (a, b), out in zip(hosts, outs):
+            got = K.ckks_ct_export(ctx, out, P.n)[0]
+            assert np.array_equal(got, O.hmult(P, a, b, evk, rescale=True))
+    finally:
+        for a, b in cts:
+            K.ckks_free(a)
+            K.ckks_free(b)
+        for h in outs + [ek]:
+            K.ckks_free(h)
+        for lane in lanes:
+            K.ckks_ctx_destroy(lane)
