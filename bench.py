@@ -362,6 +362,154 @@ def run_native(args, rank, world, local_rank):
     K.ckks_ctx_destroy(ctx)
 
 
+# ----------------------------------------------------------------------------
+# batched form: independent operations at mixed levels (one op per launch vs
+# lanes vs lanes captured into one CUDA graph)
+# ----------------------------------------------------------------------------
+
+def run_batched(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    sk = K.ckks_keygen_secret(ctx, 11)
+    rk = K.ckks_keygen_relin(ctx, sk, 12)
+    gk = K.ckks_keygen_rot(ctx, sk, 1, 13)
+    count = 64
+    levels = inputs.level_list(7, count, L - 1)
+    kinds = ["hmult", "hrot", "pmult", "rescale"]
+    kind_ix = np.random.default_rng(8).integers(0, 4, count)
+    handles, ops = [], []
+    for i in range(count):
+        lv, kind = int(levels[i]), kinds[int(kind_ix[i])]
+        enc = lambda seed: K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(seed, (1 << LOG_N) // 2), lv,
+                                                                   SCALE), seed)
+        a = enc(1000 + i)
+        out = K.ckks_ct_create(ctx, lv)
+        handles += [a, out]
+        if kind == "hmult":
+            b = enc(2000 + i)
+            handles.append(b)
+            ops.append(dict(op=K.CKKS_OP_HMULT, a=a, b=b, evk=rk, flags=K.CKKS_RESCALE, out=out))
+        elif kind == "hrot":
+            ops.append(dict(op=K.CKKS_OP_HROT, a=a, r=1, evk=gk, out=out))
+        elif kind == "pmult":
+            pt = K.ckks_encode(ctx, inputs.messages(3000 + i, (1 << LOG_N) // 2), lv, SCALE)
+            handles.append(pt)
+            ops.append(dict(op=K.CKKS_OP_PMULT, a=a, pt=pt, out=out))
+        else:
+            ops.append(dict(op=K.CKKS_OP_RESCALE, a=a, out=out))
+    results = {}
+    for name, lanes, graph in (("one_op_per_launch", 1, False), ("lanes4", 4, False), ("lanes4_graph", 4, True)):
+        batch = K.ckks_batch_create(ctx, ops, lanes, graph)
+        for _ in range(args.warmup):
+            K.ckks_batch_run(ctx, batch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = K.ckks_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            K.ckks_batch_run(ctx, batch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        results[name] = {"ops_s": count * args.steps / (ms / 1e3), "ms_per_batch": ms / args.steps,
+                         "kernel_launches_per_batch": (K.ckks_launch_count() - l0) / args.steps}
+        K.ckks_batch_destroy(batch)
+    line = {"metric": "batched mixed-level ops/sec at N=2^16 (1 GB300)", "value": results["lanes4_graph"]["ops_s"],
+            "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": results["lanes4_graph"]["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions)",
+            "config": {"workload": "64 ciphertexts, levels U{1..39}, ops uniform over HMult+rescale / HRot / PMult / "
+                                   "rescale, independent", "N": 1 << LOG_N, "limbs_top": L, "dnum": DNUM},
+            "modes": results}
+    print(json.dumps(line), flush=True)
+    for h in handles + [sk, rk, gk]:
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
+# served form: Poisson arrivals, continuous batching over lanes
+# ----------------------------------------------------------------------------
+
+def run_serve(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    from paper_2407_13055_gb300.serve import Request, Server, latency_stats, poisson_arrivals
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    sk = K.ckks_keygen_secret(ctx, 21)
+    rk = K.ckks_keygen_relin(ctx, sk, 22)
+    n_keys = 64
+    rots = sorted(set(int(r) for r in inputs.rotation_list(23, 4 * n_keys, (1 << LOG_N) // 2)))[:n_keys]
+    gks = {r: K.ckks_keygen_rot(ctx, sk, r, 100 + r) for r in rots}
+    pool = {}
+    for lv in range(1, L):
+        pool[lv] = [K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(500 + 2 * lv + t, (1 << LOG_N) // 2),
+                                                           lv, SCALE), 900 + 2 * lv + t) for t in range(2)]
+    count = args.requests
+    rng = np.random.default_rng(31)
+    levels = inputs.level_list(32, count, L - 1)
+    ops = ["hmult" if v < 0.5 else "hrot" for v in rng.random(count)]
+    rot_ix = rng.integers(0, len(rots), count)
+    reqs = [Request(i, ops[i], int(levels[i]), rots[int(rot_ix[i])] if ops[i] == "hrot" else 0) for i in range(count)]
+    outs = {}
+
+    def out_for(req, lane):
+        if lane not in outs:
+            outs[lane] = K.ckks_ct_create(ctx, L - 1)
+        return outs[lane]
+
+    inputs_for = lambda r: (pool[r.level][0], pool[r.level][1])
+    key_for = lambda r: rk if r.op == "hmult" else gks[r.rot]
+    # capacity: the whole request list back to back on one stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in reqs:
+        a, b = inputs_for(r)
+        if r.op == "hmult":
+            K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, out_for(r, -1))
+        else:
+            K.ckks_hrot(ctx, a, r.rot, gks[r.rot], out_for(r, -1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    capacity = count / (e0.elapsed_time(e1) / 1e3)
+    budget = 4 << 30
+    results = {}
+    for frac in (0.5, 0.8, 0.95):
+        arr = poisson_arrivals(np.random.default_rng(int(frac * 100)), count, frac * capacity)
+        for r, t in zip(reqs, arr):
+            r.arrival = t
+        for name, lanes in (("one_op_per_launch", 1), ("continuous_batching_4_lanes", 4)):
+            srv = Server(K, ctx, lanes, budget, 1 << LOG_N)
+            try:
+                done = srv.run(reqs, inputs_for, key_for, out_for)
+            finally:
+                srv.close()
+            results[f"{name}@{frac}"] = latency_stats(done)
+    best = results["continuous_batching_4_lanes@0.95"]
+    line = {"metric": "served HMult/HRot requests at N=2^16 (1 GB300): throughput and p50/p99 latency",
+            "value": best["throughput_ops_s"], "unit": "requests/s", "n_gpus": 1, "steps": count, "warmup": 0,
+            "ms_per_step": best["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (fresh encryptions)",
+            "config": {"workload": f"{count} Poisson requests, HMult+rescale / HRot 50:50, levels U{{1..39}}, "
+                                   f"{len(rots)} resident rotation keys, arrival rate = 0.5/0.8/0.95 x one-stream "
+                                   "capacity", "capacity_ops_s": capacity, "admission_budget_bytes": budget},
+            "runs": results}
+    print(json.dumps(line), flush=True)
+    for h in list(outs.values()) + [c for v in pool.values() for c in v] + list(gks.values()) + [sk, rk]:
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,12 +518,20 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
+    ap.add_argument("--workload", choices=["single", "batched", "serve"], default="single")
+    ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, local_rank)
+        return
+    if args.workload == "serve":
+        run_serve(args, local_rank)
         return
     if world > 1:
         import torch

@@ -177,6 +177,37 @@ int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks
 /* HConj (k = 2N - 1). out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
 
+/* --- batched form (SURVEY configs: many ciphertexts at mixed levels) ---
+ * A batch is a list of independent operations (no operation's output may be
+ * an input or output of another one in the same batch) issued across `lanes`
+ * execution lanes (ckks_ctx_clone) that fork from and join into the context
+ * stream; with use_graph != 0 the whole list is captured once into a CUDA
+ * graph and each ckks_batch_run is a single graph launch. Operations follow
+ * the single-operation entry points (same checks, same results). */
+#define CKKS_OP_HMULT 1   /* ckks_hmult(a, b, evk, flags, out) */
+#define CKKS_OP_HROT 2    /* ckks_hrot(a, r, evk, out) */
+#define CKKS_OP_HCONJ 3   /* ckks_hconj(a, evk, out) */
+#define CKKS_OP_PMULT 4   /* ckks_pmult(a, pt, out) */
+#define CKKS_OP_RESCALE 5 /* ckks_rescale(a, out) */
+#define CKKS_OP_HADD 6    /* ckks_hadd(a, b, out) */
+typedef struct {
+  int op;
+  int flags;
+  int r;
+  const ckks_ct* a;
+  const ckks_ct* b;
+  const ckks_pt* pt;
+  const ckks_evk* evk;
+  ckks_ct* out;
+} ckks_op;
+typedef struct ckks_batch ckks_batch;
+/* Validates the list by running it once (synchronizes), then captures it if
+ * use_graph. The batch references (does not own) the operands. */
+int ckks_batch_create(ckks_ctx* ctx, const ckks_op* ops, int count, int lanes, int use_graph, ckks_batch** out);
+/* Enqueue the whole list on the context stream (asynchronous). */
+int ckks_batch_run(ckks_batch* batch);
+void ckks_batch_destroy(ckks_batch* batch);
+
 /* --- rescale without allocation (the paper has no counterpart to this entry
  * point; it exists for callers that must not allocate device memory while
  * they run, such as a serving loop with a latency budget, where cudaMalloc can

@@ -52,6 +52,22 @@ class ckks_params(C.Structure):
     ]
 
 
+class ckks_op(C.Structure):
+    _fields_ = [
+        ("op", C.c_int),
+        ("flags", C.c_int),
+        ("r", C.c_int),
+        ("a", C.c_void_p),
+        ("b", C.c_void_p),
+        ("pt", C.c_void_p),
+        ("evk", C.c_void_p),
+        ("out", C.c_void_p),
+    ]
+
+
+CKKS_OP_HMULT, CKKS_OP_HROT, CKKS_OP_HCONJ, CKKS_OP_PMULT, CKKS_OP_RESCALE, CKKS_OP_HADD = 1, 2, 3, 4, 5, 6
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
 
@@ -93,6 +109,9 @@ _SIGS = {
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
     "ckks_rescale_noalloc": (_i, [_vp, _vp, _i, _vp]),
+    "ckks_batch_create": (_i, [_vp, _vp, _i, _i, _i, _P(_vp)]),
+    "ckks_batch_run": (_i, [_vp]),
+    "ckks_batch_destroy": (None, [_vp]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -308,6 +327,25 @@ def ckks_hrot(ctx, a, r: int, evk, out):
 
 def ckks_hconj(ctx, a, evk, out):
     check(ctx, lib.ckks_hconj(ctx, a, evk, out))
+
+
+def ckks_batch_create(ctx, ops, lanes: int, use_graph: bool):
+    """ops: list of dicts with keys op, flags, r, a, b, pt, evk, out (handles)."""
+    arr = (ckks_op * len(ops))()
+    for i, o in enumerate(ops):
+        arr[i] = ckks_op(o["op"], o.get("flags", 0), o.get("r", 0), o.get("a"), o.get("b"), o.get("pt"),
+                         o.get("evk"), o["out"])
+    out = _vp()
+    check(ctx, lib.ckks_batch_create(ctx, arr, len(ops), lanes, int(use_graph), C.byref(out)))
+    return out
+
+
+def ckks_batch_run(ctx, batch):
+    check(ctx, lib.ckks_batch_run(batch))
+
+
+def ckks_batch_destroy(batch):
+    lib.ckks_batch_destroy(batch)
 
 
 CKKS_NOALLOC_SCRATCH_WORDS = 1 << 21

@@ -709,15 +709,11 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   k.poly_stride1 = b->poly_stride();
   k.evk = evk->d;
   k.extra = 1;
-  if (rs) {
-    k.out = ctx->sc.U;
-    k.out_stride = (size_t)n * lw;
-  } else {
-    k.out = out->d;
-    k.out_stride = out->poly_stride();
-  }
+  k.rescale = rs ? 1 : 0;  // rescaling fused into ModDown
+  k.out = out->d;
+  k.out_stride = out->poly_stride();
+  (void)lw;
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
-  if (rs) launch_rescale(ctx->dp, ctx->sc, ctx->sc.U, (size_t)n * lw, n, out->d, out->poly_stride(), ctx->stream);
   out->level = rs ? a->level - 1 : a->level;
   out->scale = a->scale * b->scale / (rs ? (double)ctx->q[a->level] : 1.0);
   return launched(ctx, "hmult");

@@ -366,6 +366,16 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       dn_mat[(size_t)i * alpha + k] = centered_h(mulm(hat, ctx->pc_host[i].mont, q), q);
     }
   }
+  std::vector<int32_t> rs_mat((size_t)L * (alpha + 1));
+  for (int i = 0; i < L; ++i) {
+    for (int k = 0; k < alpha; ++k) rs_mat[(size_t)i * (alpha + 1) + k] = dn_mat[(size_t)i * alpha + k];
+    rs_mat[(size_t)i * (alpha + 1) + alpha] =
+        centered_h(mulm(ctx->gadget_p[i].x, ctx->pc_host[i].mont, pr[i]), pr[i]);
+  }
+  std::vector<uint2> dn_pqinv((size_t)L * L, make_uint2(0, 0));
+  for (int l = 1; l < L; ++l)
+    for (int i = 0; i < l; ++i)
+      dn_pqinv[(size_t)l * L + i] = shoup_pair(invm(mulm(ctx->gadget_p[i].x, pr[l] % pr[i], pr[i]), pr[i]), pr[i]);
   std::vector<uint2> rs_qinv((size_t)L * L, make_uint2(0, 0));
   for (int l = 1; l < L; ++l)
     for (int i = 0; i < l; ++i) rs_qinv[(size_t)l * L + i] = shoup_pair(invm(pr[l] % pr[i], pr[i]), pr[i]);
@@ -408,6 +418,8 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {dn_pinv.data(), dn_pinv.size() * sizeof(uint2), 0},
       {rs_qinv.data(), rs_qinv.size() * sizeof(uint2), 0},
       {up_rows.data(), up_rows.size() * sizeof(int2), 0},
+      {rs_mat.data(), rs_mat.size() * sizeof(int32_t), 0},
+      {dn_pqinv.data(), dn_pqinv.size() * sizeof(uint2), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -439,6 +451,8 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   dp.ks.dn_pinv = reinterpret_cast<const uint2*>(base + parts[8].off);
   dp.ks.rs_qinv = reinterpret_cast<const uint2*>(base + parts[9].off);
   dp.ks.up_rows = reinterpret_cast<const int2*>(base + parts[10].off);
+  dp.ks.rs_mat = reinterpret_cast<const int32_t*>(base + parts[11].off);
+  dp.ks.dn_pqinv = reinterpret_cast<const uint2*>(base + parts[12].off);
 
   ctx->owns_tables = true;
   const int rc = alloc_scratch(ctx);
@@ -457,7 +471,7 @@ int alloc_scratch(ckks_ctx* ctx) {
   const int L = dp.L, np = dp.L + dp.alpha;
   const size_t limb = (size_t)1 << dp.log_n;
   const size_t s_limbs = std::max(L, 2 * dp.alpha);
-  const size_t t_limbs = std::max((size_t)dp.dnum * np, (size_t)2 * L);
+  const size_t t_limbs = std::max((size_t)dp.dnum * np, (size_t)2 * L + 4);
   const size_t a_limbs = 2 * (size_t)np, u_limbs = 2 * (size_t)L;
   const size_t words = (s_limbs + t_limbs + a_limbs + u_limbs) * limb;
   uint32_t* sc = nullptr;

@@ -34,6 +34,11 @@ struct KsTables {
   // n = 1 .. L): (limb index j (n + alpha) + t in the scratch, prime id) for
   // every digit j and every extended limb t outside the digit.
   const int2* up_rows;
+  // ModDown fused with rescaling: rs_mat[i * (alpha + 1) + k] = dn_mat row i
+  // followed by [P 2^32]_{q_i} (centered); dn_pqinv[l * L + i] = Shoup pair of
+  // [(P q_l)^-1]_{q_i}, i < l.
+  const int32_t* rs_mat;
+  const uint2* dn_pqinv;
 };
 
 struct DevParams {
@@ -74,8 +79,9 @@ struct KsArgs {
   size_t poly_stride1;
   uint32_t galois;       // KS_AUTO
   const uint32_t* evk;   // [dnum][2][L + alpha][N], Montgomery form
-  uint32_t* out;         // [2][n][N] (stride out_stride between polys)
+  uint32_t* out;         // [2][n][N] (stride out_stride between polys); [2][n-1][N] with rescale
   size_t out_stride;
+  int rescale;           // 1: ModDown fused with rescaling by q_(n-1) (HMult)
   int extra;             // ModDown epilogue: 0 none, 1 HMult (d0, d1), 2 HRot (phi(b), 0)
 };
 

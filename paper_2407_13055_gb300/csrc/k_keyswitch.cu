@@ -21,6 +21,9 @@
 // BConv constant, 2^32 into the BConv matrix). The BConv product uses the
 // paper's lazy reduction (Sec. 4.2).
 #include "geo.cuh"
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 #include "rows.cuh"
 
@@ -45,30 +48,40 @@ __device__ __forceinline__ int64_t fold(int64_t a, int32_t r1c) {
 }
 
 template <int EC, int NT>
+__device__ __forceinline__ void mac4(int64_t (&acc)[EC], const int4* __restrict__ y4, int pos, int k, int64_t b) {
+#pragma unroll
+  for (int i4 = 0; i4 < EC / 4; ++i4) {
+    const int4 v = y4[(k * (EC / 4) + i4) * NT + pos];
+    acc[4 * i4 + 0] += (int64_t)v.x * b;
+    acc[4 * i4 + 1] += (int64_t)v.y * b;
+    acc[4 * i4 + 2] += (int64_t)v.z * b;
+    acc[4 * i4 + 3] += (int64_t)v.w * b;
+  }
+}
+
+// Chunks of four products, unrolled: the bound 2^29 p per product allows
+// eight before the first range reduction and four after each one, so the
+// fold runs after every chunk but the first, and once at the end.
+template <int EC, int NT>
 __device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, int pos, int K,
                                                  const int32_t* __restrict__ mat, const PrimeConst& P,
                                                  uint32_t (&out)[EC]) {
   int64_t acc[EC];
 #pragma unroll
   for (int i = 0; i < EC; ++i) acc[i] = 0;
-  int since = 0, batch = 8;
-  for (int k = 0; k < K; ++k) {
-    const int32_t b = __ldg(mat + k);
-#pragma unroll
-    for (int i4 = 0; i4 < EC / 4; ++i4) {
-      const int4 v = y4[(k * (EC / 4) + i4) * NT + pos];
-      acc[4 * i4 + 0] += (int64_t)v.x * (int64_t)b;
-      acc[4 * i4 + 1] += (int64_t)v.y * (int64_t)b;
-      acc[4 * i4 + 2] += (int64_t)v.z * (int64_t)b;
-      acc[4 * i4 + 3] += (int64_t)v.w * (int64_t)b;
-    }
-    if (++since == batch) {
+  int k = 0;
+  for (; k + 4 <= K; k += 4) {
+    const int64_t b0 = __ldg(mat + k), b1 = __ldg(mat + k + 1), b2 = __ldg(mat + k + 2), b3 = __ldg(mat + k + 3);
+    mac4<EC, NT>(acc, y4, pos, k, b0);
+    mac4<EC, NT>(acc, y4, pos, k + 1, b1);
+    mac4<EC, NT>(acc, y4, pos, k + 2, b2);
+    mac4<EC, NT>(acc, y4, pos, k + 3, b3);
+    if (k >= 4) {
 #pragma unroll
       for (int i = 0; i < EC; ++i) acc[i] = fold(acc[i], P.r1c);
-      since = 0;
-      batch = 4;
     }
   }
+  for (; k < K; ++k) mac4<EC, NT>(acc, y4, pos, k, (int64_t)__ldg(mat + k));
 #pragma unroll
   for (int i = 0; i < EC; ++i) out[i] = fix_signed(smr(fold(acc[i], P.r1c), P.q, P.m), P.q);
 }
@@ -95,7 +108,7 @@ struct ColTile {
 template <class G, int TC>
 __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* src, size_t src_stride, int K,
                                            int id0, const uint2* cin, int4* y4, uint32_t* colbuf, int l, int jj,
-                                           int c, int pos, int slice, int GS) {
+                                           int c, int pos, int slice, int GS, uint32_t* ycopy = nullptr) {
   using CTL = ColTile<G, TC>;
   for (int k = slice; k < K; k += GS) {
     const int id = id0 + k;
@@ -114,23 +127,44 @@ __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* 
 #pragma unroll
     for (int i4 = 0; i4 < G::EC / 4; ++i4)
       y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+    if (ycopy) {
+      uint32_t* yc = ycopy + ((size_t)k << dp.log_n);
+#pragma unroll
+      for (int i = 0; i < G::EC; ++i) yc[(jj + G::EC * i) * G::W + l] = (uint32_t)y[i];
+    }
   }
 }
 
-// BConv one target and run its NTT column phase; store B layout (lazy range).
+// NTT column phase of one converted target; store B layout (lazy range).
 template <class G, int TC>
-__device__ __forceinline__ void col_target(const DevParams& dp, const int4* y4, int K, const int32_t* mat_row,
-                                           int id, uint32_t* dst, uint32_t* colbuf, int l, int jj, int c, int pos,
-                                           int slice) {
+__device__ __forceinline__ void col_ntt_store(const DevParams& dp, uint32_t (&x)[G::EC], int id, uint32_t* dst,
+                                              uint32_t* colbuf, int l, int jj, int c, int slice) {
   using CTL = ColTile<G, TC>;
-  const PrimeConst P = dp.pc[id];
-  uint32_t x[G::EC];
-  bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, mat_row, P, x);
+  const uint32_t q = dp.pc[id].q;
   const uint2* tw = dp.tw + ((size_t)id << dp.log_n);
-  if (P.q < (1u << 30)) col_fwd<G::EC, TC, true>(x, colbuf, tw, jj, c, P.q, slice + 1, CTL::CT);
-  else col_fwd<G::EC, TC, false>(x, colbuf, tw, jj, c, P.q, slice + 1, CTL::CT);
+  if (q < (1u << 30)) col_fwd<G::EC, TC, true>(x, colbuf, tw, jj, c, q, slice + 1, CTL::CT);
+  else col_fwd<G::EC, TC, false>(x, colbuf, tw, jj, c, q, slice + 1, CTL::CT);
 #pragma unroll
   for (int i = 0; i < G::EC; ++i) dst[(G::EC * jj + i) * G::W + l] = x[i];
+}
+
+// BConv each target m of this slice (mat row, prime id, destination from
+// tgt), then its NTT column phase.
+template <class G, int TC, class Target>
+__device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4, int K, int M, int slice,
+                                            int slices, Target tgt, uint32_t* colbuf, int l, int jj, int c,
+                                            int pos) {
+  using CTL = ColTile<G, TC>;
+  for (int m = slice; m < M; m += slices) {
+    const int32_t* row;
+    int id;
+    uint32_t* dst;
+    tgt(m, row, id, dst);
+    const PrimeConst P = dp.pc[id];
+    uint32_t x[G::EC];
+    bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, row, P, x);
+    col_ntt_store<G, TC>(dp, x, id, dst, colbuf, l, jj, c, slice);
+  }
 }
 
 constexpr int kSlices = 4;
@@ -154,12 +188,13 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_modup_cols(D
                     colbuf, l, jj, c, pos, slice, kSlices);
   __syncthreads();
   const int M = ext - K;
-  for (int m = slice; m < M; m += kSlices) {
+  auto tgt = [&](int m, const int32_t*& row, int& id, uint32_t*& dst) {
     const int t = m < lo ? m : m + K;  // skip the digit's own limbs
-    uint32_t* dst = T + ((size_t)(j * ext + t) << dp.log_n);
-    col_target<G, TC>(dp, y4, K, dp.ks.up_mat + off.y + t * K, prime_of(t, n, L), dst, colbuf, l, jj, c, pos,
-                      slice);
-  }
+    row = dp.ks.up_mat + off.y + t * K;
+    id = prime_of(t, n, L);
+    dst = T + ((size_t)(j * ext + t) << dp.log_n);
+  };
+  col_targets<G, TC>(dp, y4, K, M, slice, kSlices, tgt, colbuf, l, jj, c, pos);
 }
 
 // C2: ModDown column kernel. grid (W/TC, 2 polys). Input S [2][alpha][N]
@@ -179,12 +214,96 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols
   col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
                     y4, colbuf, l, jj, c, pos, slice, kSlices);
   __syncthreads();
-  for (int i = slice; i < n; i += kSlices) {
-    uint32_t* dst = T + ((size_t)(u * n + i) << dp.log_n);
-    col_target<G, TC>(dp, y4, alpha, dp.ks.dn_mat + i * alpha, i, dst, colbuf, l, jj, c, pos, slice);
-  }
+  auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.dn_mat + i * alpha;
+    id = i;
+    dst = T + ((size_t)(u * n + i) << dp.log_n);
+  };
+  col_targets<G, TC>(dp, y4, alpha, n, slice, kSlices, tgt, colbuf, l, jj, c, pos);
 }
 
+
+// ModDown fused with rescaling, first column kernel: the P limbs' iNTT
+// columns give the centered coefficients y (kept in Y for the second
+// kernel); only the top limb q_l is converted here (its ModDown output is
+// needed in the coefficient domain before the others). grid (W/TC, 2 polys).
+template <class G, int TC>
+__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
+                                                                                        const uint32_t* S,
+                                                                                        uint32_t* T, uint32_t* Y) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  const int alpha = dp.alpha, top = n - 1;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
+                    y4, colbuf, l, jj, c, pos, slice, kSlices, Y + ((size_t)(u * alpha) << dp.log_n));
+  __syncthreads();
+  auto tgt = [&](int, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.dn_mat + top * alpha;
+    id = top;
+    dst = T + ((size_t)u << dp.log_n);
+  };
+  col_targets<G, TC>(dp, y4, alpha, 1, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+}
+
+// ModDown fused with rescaling, second column kernel: iNTT columns of the top
+// limb's ModDown output (row phase already applied) give c_l, centered; with
+// the stored y it forms K = alpha + 1 inputs whose conversion to q_i (matrix
+// rs_mat: the ModDown row plus [P]_{q_i}) is w_i = z_i + P [c_l]_{q_i}; then
+// the NTT columns. grid (W/TC, 2 polys); targets i < l.
+template <class G, int TC>
+__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
+                                                                                  const uint32_t* V,
+                                                                                  const uint32_t* Y, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  const int alpha = dp.alpha, top = n - 1, K = alpha + 1;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  // stored centered P-limb coefficients, A layout along h
+  for (int k = slice; k < alpha; k += kSlices) {
+    const uint32_t* yk = Y + ((size_t)(u * alpha + k) << dp.log_n);
+    int32_t y[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) y[i] = (int32_t)yk[(jj + G::EC * i) * G::W + l];
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+  }
+  if (slice == kSlices - 1) {
+    const PrimeConst Pt = dp.pc[top];
+    const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
+    const uint32_t* s = V + ((size_t)u << dp.log_n);
+    uint32_t x[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
+    if (Pt.q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    int32_t y[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], Pt.ninv, Pt.ninv_sh, Pt.q), Pt.q), Pt.q);
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos] =
+          make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+  }
+  __syncthreads();
+  auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.rs_mat + i * K;
+    id = i;
+    dst = T + ((size_t)(u * top + i) << dp.log_n);
+  };
+  col_targets<G, TC>(dp, y4, K, top, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+}
 // ---------------------------------------------------------------------------
 // Rescale column kernel: iNTT cols of the top limb, centered, reduced into
 // every lower prime, NTT cols.
@@ -350,6 +469,68 @@ __global__ void k_ks_epilogue(DevParams dp, KsArgs a, const uint32_t* T, const u
   store_vec<4>(a.out + u * a.out_stride + off, z);
 }
 
+
+// Extra term of the ModDown output at limb i (HMult: d0 or d1; HRot: phi(b)).
+__device__ __forceinline__ void ks_extra4(const DevParams& dp, const KsArgs& a, int u, int i, uint32_t p0,
+                                          const PrimeConst& P, uint32_t (&e)[4]) {
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[k] = 0;
+  if (a.extra == 1) {
+    uint32_t b1[4], b2[4];
+    load_vec<4>(b1, a.x0 + off);
+    load_vec<4>(b2, a.x1 + off);
+    if (u == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) e[k] = mulmod(b1[k], b2[k], P);
+    } else {
+      uint32_t a1[4], a2[4];
+      load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
+      load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) e[k] = addm(mulmod(a1[k], b2[k], P), mulmod(a2[k], b1[k], P), P.q);
+    }
+  } else if (a.extra == 2 && u == 0) {
+    const uint32_t* sb = a.x0 + ((size_t)i << dp.log_n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = __ldg(sb + auto_src(p0 + k, a.galois, dp.log_n));
+  }
+}
+
+// ModDown output of the top limb l only (both polys): V_u = (A_u[l] - T_u) P^-1 + extra_u[l].
+__global__ void k_ks_epilogue_top(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride,
+                                  uint32_t* V) {
+  const int u = blockIdx.y, top = a.n - 1;
+  const PrimeConst P = dp.pc[top];
+  const uint2 pinv = dp.ks.dn_pinv[top];
+  const uint32_t p0 = stream_pos();
+  uint32_t z[4], acc[4], e[4];
+  load_vec<4>(z, T + ((size_t)u << dp.log_n) + p0);
+  load_vec<4>(acc, A + u * a_stride + ((size_t)top << dp.log_n) + p0);
+  ks_extra4(dp, a, u, top, p0, P, e);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) z[k] = addm(csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
+  store_vec<4>(V + ((size_t)u << dp.log_n) + p0, z);
+}
+
+// Rescaled ModDown output, limbs i < l: (A_u[i] - w_u[i]) (P q_l)^-1 + extra_u[i] q_l^-1.
+__global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
+  const int top = a.n - 1;
+  const int u = blockIdx.y / top, i = blockIdx.y % top;
+  const PrimeConst P = dp.pc[i];
+  const uint2 pq = dp.ks.dn_pqinv[top * dp.L + i], qi = dp.ks.rs_qinv[top * dp.L + i];
+  const uint32_t p0 = stream_pos();
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  uint32_t w[4], acc[4], e[4];
+  load_vec<4>(w, T + ((size_t)(u * top + i) << dp.log_n) + p0);
+  load_vec<4>(acc, A + u * a_stride + off);
+  ks_extra4(dp, a, u, i, p0, P, e);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    w[k] = addm(csub(shoup(acc[k] - w[k] + P.q, pq.x, pq.y, P.q), P.q), csub(shoup(e[k], qi.x, qi.y, P.q), P.q), P.q);
+  store_vec<4>(a.out + u * a.out_stride + off, w);
+}
+
 // Rescale epilogue: out_u[i] = (c_u[i] - r_u[i]) q_l^-1, r = NTT of the
 // centered top limb reduced modulo q_i.
 __global__ void k_rs_epilogue(DevParams dp, const uint32_t* in, size_t sin, int n, const uint32_t* T,
@@ -385,8 +566,18 @@ static size_t col_smem_bytes(int K) {
   return (size_t)K * (G::EC / 4) * CTL::CT * sizeof(int4) + (size_t)kSlices * CTL::BUF * sizeof(uint32_t);
 }
 
+// Raise a kernel's dynamic shared-memory limit once per process (and only
+// when a larger size is needed), so that steady-state launches and graph
+// captures issue no attribute calls.
 static void set_col_smem(const void* f, size_t bytes) {
-  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = done[f];
+  if (bytes > cur) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
 }
 
 // Column-tile width: 8 columns (32-byte row segments) when that already
@@ -432,6 +623,62 @@ static void modup_rows_range(int n, int alpha, int& off, int& cnt) {
 
 // ModDown from the accumulators A = [2][n + alpha][N] (a_stride between
 // polys): P-limb iNTT rows (into S), C2, NTT rows, epilogue.
+template <class G, int TC>
+static void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint32_t* Y, cudaStream_t st) {
+  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
+  set_col_smem((const void*)k_ks_moddown_cols_top<G, TC>, sm);
+  k_ks_moddown_cols_top<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T, Y);
+  count_launch(1);
+}
+
+template <class G, int TC>
+static void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
+                                 cudaStream_t st) {
+  const size_t sm = col_smem_bytes<G, TC>(dp.alpha + 1);
+  set_col_smem((const void*)k_rs_cols_fused<G, TC>, sm);
+  k_rs_cols_fused<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, V, Y, T3);
+  count_launch(1);
+}
+
+// ModDown fused with rescaling by q_l (l = n - 1): out gets n - 1 limbs.
+template <class G>
+static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
+                                 size_t a_stride, cudaStream_t st) {
+  const int n = a.n, alpha = dp.alpha, top = n - 1;
+  const size_t limb = (size_t)1 << dp.log_n;
+  uint32_t* T2 = sc.T;              // [2] converted top limb (NTT cols, then rows)
+  uint32_t* V = sc.T + 2 * limb;    // [2] ModDown output of the top limb
+  uint32_t* T3 = sc.T + 4 * limb;   // [2][top] fused conversions
+  uint32_t* Y = sc.U;               // [2][alpha] centered P-limb coefficients
+  launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
+                   LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
+  prof_mark(sc, st, P_MODDOWN_IN_ROWS);
+  with_tc<G>(2, [&] { launch_moddown_cols_top<G, 8>(dp, n, sc, Y, st); },
+             [&] { launch_moddown_cols_top<G, 4>(dp, n, sc, Y, st); });
+  prof_mark(sc, st, P_MODDOWN_COLS);
+  LimbMap top_map{nullptr, 0, 1, 1, dp.L};
+  top_map.fixed = top;
+  launch_rows_g<G>(dp, false, T2, T2, 2, top_map, false, st);
+  prof_mark(sc, st, P_MODDOWN_ROWS);
+  dim3 g;
+  int th;
+  stream_grid(dp.log_n, 2, g, th);
+  k_ks_epilogue_top<<<g, th, 0, st>>>(dp, a, T2, A, a_stride, V);
+  count_launch(1);
+  prof_mark(sc, st, P_KS_EPILOGUE);
+  launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
+  prof_mark(sc, st, P_RS_IN_ROWS);
+  with_tc<G>(2, [&] { launch_rs_cols_fused<G, 8>(dp, n, V, Y, T3, st); },
+             [&] { launch_rs_cols_fused<G, 4>(dp, n, V, Y, T3, st); });
+  prof_mark(sc, st, P_RS_COLS);
+  launch_rows_g<G>(dp, false, T3, T3, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
+  prof_mark(sc, st, P_RS_ROWS);
+  stream_grid(dp.log_n, 2 * top, g, th);
+  k_ks_epilogue_rs<<<g, th, 0, st>>>(dp, a, T3, A, a_stride);
+  count_launch(1);
+  prof_mark(sc, st, P_RS_EPILOGUE);
+}
+
 template <class G>
 static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
                          size_t a_stride, cudaStream_t st) {
@@ -480,7 +727,10 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
     launch_keymult(digits, g, th, st, dp, a, sc.T, sc.A, km_out, km_dst);
     count_launch(1);
     prof_mark(sc, st, P_KEYMULT);
-    if (km_out == KM_KEYSWITCH) moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+    if (km_out == KM_KEYSWITCH) {
+      if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+      else moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+    }
   });
 }
 

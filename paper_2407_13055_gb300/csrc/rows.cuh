@@ -19,11 +19,12 @@ struct LimbMap {
   int first;
   int per, n, L;
   int pl = 1 << 30, ps = 0;
+  int fixed = -1;   // >= 0: every limb uses this prime id
   __device__ __forceinline__ int2 operator()(int y) const {
     if (tab) return tab[y];
     const int u = y / pl, r = y % pl;
     const int t = (first + r) % per;
-    return make_int2(u * ps + first + r, t < n ? t : L + (t - n));
+    return make_int2(u * ps + first + r, fixed >= 0 ? fixed : (t < n ? t : L + (t - n)));
   }
 };
 
@@ -65,30 +66,29 @@ __device__ __forceinline__ void gs_pass_reg(uint32_t (&x)[E], const uint2 (&tw)[
   }
 }
 
-// First-pass twiddles of the block's RPC rows h0 .. h0+RPC-1 (the same for
-// every thread of a row): stage s needs indices (H + h) 2^s + b, contiguous
-// over the block's rows; staged in shared memory at
-// (2^s - 1) RPC + r 2^s + b.
-template <int E, int H, int RPC>
-__device__ __forceinline__ void stage_pass_a_twiddles(uint2* sm, const uint2* __restrict__ t, int h0) {
-  constexpr int e = Log2<E>::v;
-#pragma unroll
-  for (int s = 0; s < e; ++s) {
-    const int cnt = RPC << s;
-    const uint2* src = t + ((uint32_t)(H + h0) << s);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sm[((1 << s) - 1) * RPC + i] = __ldg(src + i);
+// First-pass twiddles of row h (the same for every thread of the row):
+// local stage s, block b uses index (H + h) 2^s + b; the row's ER threads
+// stage them in the row's own shared slice at (2^s - 1) + b and sync with a
+// warp barrier (a row never spans two warps).
+template <int E, int H>
+__device__ __forceinline__ void stage_row_twiddles(uint2* sm, const uint2* __restrict__ t, int h, int jj) {
+  for (int idx = jj; idx < E - 1; idx += E) {
+    const int s = 31 - __clz(idx + 1);
+    const int b = idx + 1 - (1 << s);
+    sm[idx] = __ldg(t + ((uint32_t)(H + h) << s) + b);
   }
+  __syncwarp();
 }
 
-template <int E, int RPC, bool LAZY>
-__device__ __forceinline__ void ct_pass_sm(uint32_t (&x)[E], const uint2* sm, int r, uint32_t q) {
+template <int E, bool LAZY>
+__device__ __forceinline__ void ct_pass_sm(uint32_t (&x)[E], const uint2* sm, uint32_t q) {
   constexpr int e = Log2<E>::v;
 #pragma unroll
   for (int s = 0; s < e; ++s) {
     const int half = E >> (s + 1);
 #pragma unroll
     for (int b = 0; b < (1 << s); ++b) {
-      const uint2 w = sm[((1 << s) - 1) * RPC + (r << s) + b];
+      const uint2 w = sm[(1 << s) - 1 + b];
 #pragma unroll
       for (int k = 0; k < half; ++k) {
         const int i0 = b * 2 * half + k;
@@ -98,15 +98,15 @@ __device__ __forceinline__ void ct_pass_sm(uint32_t (&x)[E], const uint2* sm, in
   }
 }
 
-template <int E, int RPC, bool LAZY>
-__device__ __forceinline__ void gs_pass_sm(uint32_t (&x)[E], const uint2* sm, int r, uint32_t q) {
+template <int E, bool LAZY>
+__device__ __forceinline__ void gs_pass_sm(uint32_t (&x)[E], const uint2* sm, uint32_t q) {
   constexpr int e = Log2<E>::v;
 #pragma unroll
   for (int s = e - 1; s >= 0; --s) {
     const int half = E >> (s + 1);
 #pragma unroll
     for (int b = 0; b < (1 << s); ++b) {
-      const uint2 w = sm[((1 << s) - 1) * RPC + (r << s) + b];
+      const uint2 w = sm[(1 << s) - 1 + b];
 #pragma unroll
       for (int k = 0; k < half; ++k) {
         const int i0 = b * 2 * half + k;
@@ -155,17 +155,17 @@ __global__ void __launch_bounds__(G::RT) k_rows_fwd_g(DevParams dp, const uint32
   uint32_t x[G::ER];
 #pragma unroll
   for (int i = 0; i < G::ER; ++i) x[i] = s[jj + G::ER * i];
-  stage_pass_a_twiddles<G::ER, G::H, G::RPC>(twa, tw, blockIdx.x * G::RPC);
-  __syncthreads();
+  uint2* tr = twa + r * (G::ER - 1);
+  stage_row_twiddles<G::ER, G::H>(tr, tw, h, jj);
   uint32_t* b = buf + r * G::ROWBUF;
   if (q < (1u << 30)) {
-    ct_pass_sm<G::ER, G::RPC, true>(x, twa, r, q);
+    ct_pass_sm<G::ER, true>(x, tr, q);
     row_a_to_b<G::ER>(x, b, jj);
     ct_pass_reg<G::ER, true>(x, twb, q);
 #pragma unroll
     for (int i = 0; i < G::ER; ++i) x[i] = normalize<true>(x[i], q);
   } else {
-    ct_pass_sm<G::ER, G::RPC, false>(x, twa, r, q);
+    ct_pass_sm<G::ER, false>(x, tr, q);
     row_a_to_b<G::ER>(x, b, jj);
     ct_pass_reg<G::ER, false>(x, twb, q);
 #pragma unroll
@@ -191,17 +191,17 @@ __global__ void __launch_bounds__(G::RT) k_rows_inv_g(DevParams dp, const uint32
   load_pass_b_twiddles<G::ER, G::H>(twb, itw, h, jj);
   uint32_t x[G::ER];
   load_vec<G::ER>(x, src + ((size_t)lm.x << dp.log_n) + (size_t)h * G::W + G::ER * jj);
-  stage_pass_a_twiddles<G::ER, G::H, G::RPC>(twa, itw, blockIdx.x * G::RPC);
-  __syncthreads();
+  uint2* tr = twa + r * (G::ER - 1);
+  stage_row_twiddles<G::ER, G::H>(tr, itw, h, jj);
   uint32_t* b = buf + r * G::ROWBUF;
   if (q < (1u << 30)) {
     gs_pass_reg<G::ER, true>(x, twb, q);
     row_b_to_a<G::ER>(x, b, jj);
-    gs_pass_sm<G::ER, G::RPC, true>(x, twa, r, q);
+    gs_pass_sm<G::ER, true>(x, tr, q);
   } else {
     gs_pass_reg<G::ER, false>(x, twb, q);
     row_b_to_a<G::ER>(x, b, jj);
-    gs_pass_sm<G::ER, G::RPC, false>(x, twa, r, q);
+    gs_pass_sm<G::ER, false>(x, tr, q);
   }
   const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
   uint32_t* o = dst + (dl << dp.log_n) + (size_t)h * G::W;

@@ -412,3 +412,76 @@ def test_lanes_give_identical_results_concurrently(K, O):
             K.ckks_free(h)
         for lane in lanes:
             K.ckks_ctx_destroy(lane)
+
+
+# ------------------------------------------------------------ batched form ---
+
+@pytest.mark.parametrize("lanes,use_graph", [(1, False), (3, False), (3, True)])
+def test_batch_mixed_levels_matches_oracle(K, O, lanes, use_graph):
+    """Independent operations at mixed levels in one batch (direct or one CUDA
+    graph launch, replayed twice): every output equals the oracle's."""
+    ctx, P = get(K, O, "n16d3")
+    rng = np.random.default_rng(101)
+    relin = rand_evk(P, 102)
+    rotk = rand_evk(P, 103)
+    k1 = O.rot_k(1, P.log_n)
+    ek_r = K.ckks_evk_import(ctx, relin, 0)
+    ek_g = K.ckks_evk_import(ctx, rotk, k1)
+    kinds = ["hmult_rs", "hrot", "pmult", "rescale", "hmult", "hadd"]
+    handles, ops, want = [], [], []
+    for i in range(8):
+        kind = kinds[i % len(kinds)]
+        n_q = int(rng.integers(2, 9))
+        a = rand_ct(P, n_q, 200 + i)
+        ha = K.ckks_ct_import(ctx, a, n_q - 1, 2.0**30)
+        out = K.ckks_ct_create(ctx, n_q - 1)
+        handles += [ha, out]
+        if kind in ("hmult_rs", "hmult", "hadd"):
+            b = rand_ct(P, n_q, 300 + i)
+            hb = K.ckks_ct_import(ctx, b, n_q - 1, 2.0**30)
+            handles.append(hb)
+            if kind == "hadd":
+                ops.append(dict(op=K.CKKS_OP_HADD, a=ha, b=hb, out=out))
+                want.append(O.hadd(a, b, P.q[:n_q]))
+            else:
+                rs = kind == "hmult_rs"
+                ops.append(dict(op=K.CKKS_OP_HMULT, a=ha, b=hb, evk=ek_r, flags=K.CKKS_RESCALE if rs else 0, out=out))
+                want.append(O.hmult(P, a, b, relin, rescale=rs))
+        elif kind == "hrot":
+            ops.append(dict(op=K.CKKS_OP_HROT, a=ha, r=1, evk=ek_g, out=out))
+            want.append(O.hrot(P, a, k1, rotk))
+        elif kind == "pmult":
+            pt = rand_poly(P, P.q[:n_q], 400 + i)
+            hp = K.ckks_pt_import(ctx, pt, n_q - 1, 2.0**30)
+            handles.append(hp)
+            ops.append(dict(op=K.CKKS_OP_PMULT, a=ha, pt=hp, out=out))
+            want.append(O.pmult(a, pt, P.q[:n_q]))
+        else:
+            ops.append(dict(op=K.CKKS_OP_RESCALE, a=ha, out=out))
+            want.append(O.rescale(a, P.q[:n_q]))
+    batch = K.ckks_batch_create(ctx, ops, lanes, use_graph)
+    try:
+        for _ in range(2):
+            K.ckks_batch_run(ctx, batch)
+            K.ckks_sync(ctx)
+            for o, w in zip(ops, want):
+                assert np.array_equal(K.ckks_ct_export(ctx, o["out"], P.n)[0], w)
+    finally:
+        K.ckks_batch_destroy(batch)
+        for h in handles + [ek_r, ek_g]:
+            K.ckks_free(h)
+
+
+def test_batch_rejects_dependent_operations(K, O):
+    ctx, P = get(K, O, "tiny")
+    a = K.ckks_ct_import(ctx, rand_ct(P, 3, 501), 2, 2.0**30)
+    b = K.ckks_ct_import(ctx, rand_ct(P, 3, 502), 2, 2.0**30)
+    out = K.ckks_ct_create(ctx, 2)
+    try:
+        ops = [dict(op=K.CKKS_OP_HADD, a=a, b=b, out=out), dict(op=K.CKKS_OP_HADD, a=out, b=b, out=a)]
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_batch_create(ctx, ops, 2, True)
+        assert e.value.code == K.CKKS_EINVAL
+    finally:
+        for h in (a, b, out):
+            K.ckks_free(h)
