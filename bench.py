@@ -89,6 +89,35 @@ def kernel_models(n=L, alpha=ALPHA):
     return m
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# one-lane pipeline's kernels from one `ncu --set full` capture (cold cache;
+# command in profiles/keyswitch_n16_l40_dnum3_top.md), keyed by stage. They
+# describe the kernel sources they were taken on: when the SHA-1 of csrc/
+# differs, the figures are stale and the bench reports null.
+NCU_TRAFFIC = {
+    "sources_sha1": "07a22a9cb52d4129139b3b63b3962d92a86ce547",
+    "bytes_per_launch": {"modup_cols": 10.63e6, "keymult": 143.79e6, "modup_rows": 60.92e6,
+                         "rescale_cols": 7.92e6, "rescale_rows": 40.93e6},
+}
+
+
+def csrc_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2407_13055_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(stage):
+    if csrc_sha1() != NCU_TRAFFIC["sources_sha1"]:
+        return None
+    return NCU_TRAFFIC["bytes_per_launch"].get(stage)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -200,7 +229,7 @@ def run_reference(args, rank, world):
 def run_native(args, rank, world, local_rank):
     import torch
     from paper_2407_13055_gb300 import ckks as K
-    from paper_2407_13055_gb300 import inputs
+    from paper_2407_13055_gb300 import inputs, replicas
 
     # CPU baseline first (rank 0 at N = 1 only), before any GPU work.
     cpu = None
@@ -235,8 +264,7 @@ def run_native(args, rank, world, local_rank):
             K.ckks_hrot(lanes[l], cts[i], 1, gk, outs_r[l])
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     def timed(n_steps, n_lanes):
@@ -262,12 +290,9 @@ def run_native(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         ms = timed(args.steps, args.lanes)
     launches = K.ckks_launch_count() - launches0
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms)
     ops = 2 * BATCH * args.steps * world
-    value = ops / (ms / 1e3)
+    value = replicas.job_throughput(2 * BATCH * args.steps, ms, world)
 
     # one lane, in order: per-kernel CUDA-event times on the launching stream
     seq_steps = max(3, args.steps // 4)
@@ -323,7 +348,7 @@ def run_native(args, rank, world, local_rank):
         achieved = mdl["bytes"] / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": None}
+                "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": ncu_traffic(dom)}
     else:
         # plain ALU: modular multiplications against the int32 multiply peak
         # (152 SMs x 128 IMAD/clk, measured issue rate, at the maximum SM
@@ -333,7 +358,7 @@ def run_native(args, rank, world, local_rank):
         peak = imad_peak / 3 / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
                 "frac": achieved / peak, "peak_source": "derived: 152 SM x 128 IMAD/clk x sm_max_mhz / 3",
-                "algorithmic_modmul_per_launch": mdl["modmul"], "traffic": None}
+                "algorithmic_modmul_per_launch": mdl["modmul"], "traffic": ncu_traffic(dom)}
     stage = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
                  "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)} for k, v in prof.items()}
     per_gpu_gbs = BATCH * (hm_bytes + hr_bytes) * args.steps / (ms / 1e3) / 1e9

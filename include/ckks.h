@@ -177,7 +177,7 @@ int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks
 /* HConj (k = 2N - 1). out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
 
-/* --- batched form (SURVEY configs: many ciphertexts at mixed levels) ---
+/* --- batched form: many independent ciphertext operations at mixed levels ---
  * A batch is a list of independent operations (no operation's output may be
  * an input or output of another one in the same batch) issued across `lanes`
  * execution lanes (ckks_ctx_clone) that fork from and join into the context
