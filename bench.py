@@ -118,6 +118,19 @@ def ncu_traffic(stage):
     return NCU_TRAFFIC["bytes_per_launch"].get(stage)
 
 
+def tune_levels(K, ctx, levels, enabled, reps=3):
+    """Run the column-kernel fine-tuner at each level (outside any timed
+    region) and return the chosen shapes {level: {kernel: (tc, sl, z, us)}}."""
+    if not enabled:
+        return None
+    names = {K.CKKS_COL_MODUP: "modup_cols", K.CKKS_COL_MODDOWN: "moddown_cols", K.CKKS_COL_RS_FUSED: "rescale_cols"}
+    out = {}
+    for lv in sorted(set(int(x) for x in levels)):
+        K.ckks_tune(ctx, lv, reps)
+        out[lv] = {nm: K.ckks_tune_get(ctx, k, lv) for k, nm in names.items()}
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -256,6 +269,7 @@ def run_native(args, rank, world, local_rank):
     lanes = [ctx] + [K.ckks_ctx_clone(ctx, s_.cuda_stream) for s_ in streams[1:]]
     outs_m = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
     outs_r = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
+    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune)
 
     def step(n_lanes):
         for i in range(BATCH):
@@ -370,7 +384,9 @@ def run_native(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions of U[-1,1] messages)",
         "config": workload_config({"parallelism": f"replicas{world}",
                                    "lanes": f"{args.lanes} concurrent CUDA streams (context clones), "
-                                            "independent ciphertexts per lane"}),
+                                            "independent ciphertexts per lane",
+                                   "column_shapes": ({k: list(v) for k, v in tuned[LEVEL].items()} if tuned
+                                                     else "default rule")}),
         "one_lane": {"value": seq_ops_per_s, "unit": UNIT, "hmult_rescale_us": hmult_us, "hrot_us": hrot_us,
                      "note": "same workload issued in order on one stream; stage times from its CUDA events"},
         "roofline": roof, "op_roofline": op_hbm, "stages": stage,
@@ -427,6 +443,7 @@ def run_batched(args, local_rank):
             ops.append(dict(op=K.CKKS_OP_PMULT, a=a, pt=pt, out=out))
         else:
             ops.append(dict(op=K.CKKS_OP_RESCALE, a=a, out=out))
+    tuned = tune_levels(K, ctx, levels, not args.no_tune, reps=2)
     results = {}
     for name, lanes, graph in (("one_op_per_launch", 1, False), ("lanes4", 4, False), ("lanes4_graph", 4, True)):
         batch = K.ckks_batch_create(ctx, ops, lanes, graph)
@@ -449,10 +466,68 @@ def run_batched(args, local_rank):
             "ms_per_step": results["lanes4_graph"]["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions)",
             "config": {"workload": "64 ciphertexts, levels U{1..39}, ops uniform over HMult+rescale / HRot / PMult / "
-                                   "rescale, independent", "N": 1 << LOG_N, "limbs_top": L, "dnum": DNUM},
+                                   "rescale, independent", "N": 1 << LOG_N, "limbs_top": L, "dnum": DNUM,
+                       "column_shapes": "tuned per level" if tuned else "default rule"},
             "modes": results}
     print(json.dumps(line), flush=True)
     for h in handles + [sk, rk, gk]:
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
+# hoisted rotations: one ModUp shared by many rotations of one ciphertext
+# ----------------------------------------------------------------------------
+
+def run_hoisted(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    sk = K.ckks_keygen_secret(ctx, 41)
+    rots = list(range(1, 33))
+    gks = [K.ckks_keygen_rot(ctx, sk, r, 500 + r) for r in rots]
+    cts = [K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(600 + i, (1 << LOG_N) // 2), LEVEL, SCALE),
+                          700 + i) for i in range(4)]
+    outs = [K.ckks_ct_create(ctx, LEVEL) for _ in rots]
+    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune)
+
+    def hoisted(c):
+        K.ckks_hrot_hoisted(ctx, c, rots, gks, outs)
+
+    def separate(c):
+        for r, g, o in zip(rots, gks, outs):
+            K.ckks_hrot(ctx, c, r, g, o)
+
+    res = {}
+    for name, fn in (("separate_hrot", separate), ("hoisted", hoisted)):
+        for _ in range(args.warmup):
+            fn(cts[0])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = K.ckks_launch_count()
+        e0.record(stream)
+        for i in range(args.steps):
+            fn(cts[i % len(cts)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"rotations_s": len(rots) * args.steps / (ms / 1e3), "us_per_rotation": 1e3 * ms / args.steps /
+                     len(rots), "launches_per_step": (K.ckks_launch_count() - l0) / args.steps}
+    line = {"metric": "hoisted HRot throughput at N=2^16 (1 GB300): 32 rotations of one ciphertext",
+            "value": res["hoisted"]["rotations_s"], "unit": "rotations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": len(rots) * res["hoisted"]["us_per_rotation"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (fresh encryptions)",
+            "config": {"workload": "32 rotations (r = 1..32) of one top-level ciphertext per step, one shared ModUp",
+                       "N": 1 << LOG_N, "limbs": L, "dnum": DNUM,
+                       "column_shapes": "tuned" if tuned else "default rule"},
+            "modes": res, "speedup_vs_separate": res["hoisted"]["rotations_s"] / res["separate_hrot"]["rotations_s"]}
+    print(json.dumps(line), flush=True)
+    for h in outs + cts + gks + [sk]:
         K.ckks_free(h)
     K.ckks_ctx_destroy(ctx)
 
@@ -494,6 +569,7 @@ def run_serve(args, local_rank):
 
     inputs_for = lambda r: (pool[r.level][0], pool[r.level][1])
     key_for = lambda r: rk if r.op == "hmult" else gks[r.rot]
+    tuned = tune_levels(K, ctx, range(1, L), not args.no_tune, reps=2)
     # capacity: the whole request list back to back on one stream
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -527,7 +603,8 @@ def run_serve(args, local_rank):
             "dtype": "u32", "data": "synthetic (fresh encryptions)",
             "config": {"workload": f"{count} Poisson requests, HMult+rescale / HRot 50:50, levels U{{1..39}}, "
                                    f"{len(rots)} resident rotation keys, arrival rate = 0.5/0.8/0.95 x one-stream "
-                                   "capacity", "capacity_ops_s": capacity, "admission_budget_bytes": budget},
+                                   "capacity", "capacity_ops_s": capacity, "admission_budget_bytes": budget,
+                       "column_shapes": "tuned per level" if tuned else "default rule"},
             "runs": results}
     print(json.dumps(line), flush=True)
     for h in list(outs.values()) + [c for v in pool.values() for c in v] + list(gks.values()) + [sk, rk]:
@@ -543,8 +620,9 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
-    ap.add_argument("--workload", choices=["single", "batched", "serve"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
+    ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -557,6 +635,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, local_rank)
+        return
+    if args.workload == "hoisted":
+        run_hoisted(args, local_rank)
         return
     if world > 1:
         import torch

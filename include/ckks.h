@@ -176,6 +176,15 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out);
 int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks_ct* out);
 /* HConj (k = 2N - 1). out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
+/* Hoisted rotations (Par. 5, Fig. 5): outs[i] = HRot(ct, r[i]) under evks[i]
+ * for i < count, sharing one ModUp of ct's a part. Because the BConv of the
+ * ModUp is centered (odd), ModUp commutes with the automorphism exactly and
+ * every output is bit-identical to a separate ckks_hrot. Each ModDown reads
+ * the automorphism of the shared ModUp limbs while multiplying by the key.
+ * Outputs must be distinct, must not alias ct and need capacity >= ct's
+ * level. Asynchronous on the context stream; count = 0 does nothing. */
+int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* ct, int count, const int* r, const ckks_evk* const* evks,
+                      ckks_ct* const* outs);
 
 /* --- batched form: many independent ciphertext operations at mixed levels ---
  * A batch is a list of independent operations (no operation's output may be
@@ -232,6 +241,31 @@ void ckks_batch_destroy(ckks_batch* batch);
  * that device current (cudaGetSymbolAddress); make that first call before any
  * stream capture. Asynchronous on the context stream. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint32_t* out_dev);
+
+/* --- launch-shape fine-tuning (Sec. 4.2, "Fine-tuning"; Sec. 6) ---
+ * The three BConv column kernels (ModUp conversion, ModDown conversion,
+ * fused ModDown + rescale conversion) can run in several launch shapes
+ * (tc, sl, z): column-tile width tc in {4, 8} columns, sl in {2, 4, 8}
+ * thread slices per block sharing the tile, and z in 1..4 blocks per tile
+ * splitting the conversion targets. Every shape computes identical values;
+ * only time changes. A context and its clones share one table of shapes per
+ * (kernel, level); levels without an entry use a fixed rule. */
+#define CKKS_COL_MODUP 0
+#define CKKS_COL_MODDOWN 1
+#define CKKS_COL_RS_FUSED 2
+/* Times every candidate shape of the three kernels at `level` (reps launches
+ * each, CUDA events on the context stream, on the context's scratch) and
+ * records the fastest. Synchronizes the stream: do not call it while the
+ * stream is being captured. level in [0, n_q - 1] (the fused rescale kernel
+ * is tuned for level >= 1). */
+int ckks_tune(ckks_ctx* ctx, int level, int reps);
+/* Tuned shape of `kernel` at `level` and its mean launch time in
+ * microseconds; *tc = 0 when the level has no entry. */
+int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, float* us);
+/* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4; at N = 2^8
+ * only tc = 8, since a slice must be whole warps), or clears the entry with
+ * tc = 0. Changes no value any operation computes. */
+int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z);
 
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */

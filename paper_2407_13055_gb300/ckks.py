@@ -108,10 +108,14 @@ _SIGS = {
     "ckks_rescale": (_i, [_vp, _vp, _vp]),
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_hrot_hoisted": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "ckks_rescale_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "ckks_batch_create": (_i, [_vp, _vp, _i, _i, _i, _P(_vp)]),
     "ckks_batch_run": (_i, [_vp]),
     "ckks_batch_destroy": (None, [_vp]),
+    "ckks_tune": (_i, [_vp, _i, _i]),
+    "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
+    "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -329,6 +333,17 @@ def ckks_hconj(ctx, a, evk, out):
     check(ctx, lib.ckks_hconj(ctx, a, evk, out))
 
 
+def ckks_hrot_hoisted(ctx, a, rs, evks, outs):
+    """outs[i] = HRot(a, rs[i]) with evks[i], sharing one ModUp."""
+    cnt = len(rs)
+    if len(evks) != cnt or len(outs) != cnt:
+        raise ValueError("rs, evks and outs must have the same length")
+    r_arr = (C.c_int * max(cnt, 1))(*[int(x) for x in rs])
+    e_arr = (C.c_void_p * max(cnt, 1))(*evks)
+    o_arr = (C.c_void_p * max(cnt, 1))(*outs)
+    check(ctx, lib.ckks_hrot_hoisted(ctx, a, cnt, r_arr, e_arr, o_arr))
+
+
 def ckks_batch_create(ctx, ops, lanes: int, use_graph: bool):
     """ops: list of dicts with keys op, flags, r, a, b, pt, evk, out (handles)."""
     arr = (ckks_op * len(ops))()
@@ -355,6 +370,24 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
     """Rescale between caller-owned device buffers with the library's fixed
     scratch; see include/ckks.h for layout, limit and ordering rules."""
     check(ctx, lib.ckks_rescale_noalloc(ctx, in_dev, level, out_dev))
+
+
+CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED = 0, 1, 2
+
+
+def ckks_tune(ctx, level: int, reps: int = 5):
+    check(ctx, lib.ckks_tune(ctx, level, reps))
+
+
+def ckks_tune_get(ctx, kernel: int, level: int):
+    """(tc, sl, z, microseconds) of the tuned shape; tc = 0 when untuned."""
+    tc, sl, z, us = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+    check(ctx, lib.ckks_tune_get(ctx, kernel, level, C.byref(tc), C.byref(sl), C.byref(z), C.byref(us)))
+    return tc.value, sl.value, z.value, us.value
+
+
+def ckks_tune_set(ctx, kernel: int, level: int, tc: int, sl: int = 4, z: int = 1):
+    check(ctx, lib.ckks_tune_set(ctx, kernel, level, tc, sl, z))
 
 
 CKKS_PROF_KERNELS = 13

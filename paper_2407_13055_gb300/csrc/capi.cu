@@ -130,6 +130,8 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   int rc = build_context(ctx, prm);
   if (rc != CKKS_OK) return bad(fail(ctx, rc, "building tables failed (%d)", rc));
   ctx->sc.prof = &ctx->prof;
+  ctx->tune = std::make_shared<ckks::Tuning>(L);
+  ctx->sc.tune = ctx->tune.get();
   *out = ctx;
   return CKKS_OK;
 }
@@ -161,6 +163,8 @@ int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
     return fail(parent, rc, "clone: scratch allocation failed");
   }
   c->sc.prof = &c->prof;
+  c->tune = parent->tune;
+  c->sc.tune = c->tune.get();
   *out = c;
   return CKKS_OK;
 }
@@ -173,6 +177,44 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
+}
+
+int ckks_tune(ckks_ctx* ctx, int level, int reps) {
+  if (!ctx || !ctx->tune) return CKKS_EINVAL;
+  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  if (reps < 1 || reps > 1000) return fail(ctx, CKKS_EINVAL, "tune: reps %d out of [1, 1000]", reps);
+  const int rc = ckks::tune_columns(ctx->dp, ctx->sc, *ctx->tune, level + 1, reps, ctx->stream);
+  if (rc != CKKS_OK) return fail(ctx, rc, "tune: %s", cudaGetErrorString(cudaGetLastError()));
+  return CKKS_OK;
+}
+
+int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, float* us) {
+  if (!ctx || !ctx->tune || !tc || !sl || !z || !us) return CKKS_EINVAL;
+  if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
+  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  const ckks::ColShape s = ctx->tune->get(kernel, level + 1);
+  *tc = s.tc;
+  *sl = s.sl;
+  *z = s.z;
+  *us = ctx->tune->time_us(kernel, level + 1);
+  return CKKS_OK;
+}
+
+int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z) {
+  if (!ctx || !ctx->tune) return CKKS_EINVAL;
+  if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
+  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  ckks::ColShape s;
+  if (tc != 0) {
+    if (!ckks::col_shape_supported(ctx->dp.log_n, tc, sl, z))
+      return fail(ctx, CKKS_EINVAL, "tune: shape (%d, %d, %d) not supported at N = 2^%d", tc, sl, z,
+                  ctx->dp.log_n);
+    s.tc = tc;
+    s.sl = sl;
+    s.z = z;
+  }
+  ctx->tune->set(kernel, level + 1, s, 0.f);
+  return CKKS_OK;
 }
 
 int ckks_profile(ckks_ctx* ctx, int enable) {
@@ -747,6 +789,43 @@ int ckks_hrot(ckks_ctx* ctx, const ckks_ct* c, int r, const ckks_evk* evk, ckks_
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* c, const ckks_evk* evk, ckks_ct* out) {
   if (!ctx || !c || !evk || !out) return CKKS_EINVAL;
   return hauto(ctx, c, (2u << ctx->dp.log_n) - 1, evk, out);
+}
+
+int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* c, int count, const int* r, const ckks_evk* const* evks,
+                      ckks_ct* const* outs) {
+  if (!ctx || !c || count < 0 || (count > 0 && (!r || !evks || !outs))) return CKKS_EINVAL;
+  if (count == 0) return CKKS_OK;
+  std::vector<KsArgs> ks((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    const ckks_evk* evk = evks[i];
+    ckks_ct* out = outs[i];
+    if (!evk || !out) return fail(ctx, CKKS_EINVAL, "hoisted rotation %d: missing key or output", i);
+    const uint32_t galois = galois_rot(r[i], ctx->dp.log_n);
+    if (evk->galois != galois)
+      return fail(ctx, CKKS_ENOKEY, "hoisted rotation %d: key is for galois element %u, need %u", i, evk->galois,
+                  galois);
+    if (out == c || out->d == c->d) return fail(ctx, CKKS_EINVAL, "hoisted rotation %d: output aliases the input", i);
+    if (out->cap_level < c->level) return fail(ctx, CKKS_ELEVEL, "hoisted rotation %d: output capacity too small", i);
+    for (int j = 0; j < i; ++j)
+      if (outs[j]->d == out->d) return fail(ctx, CKKS_EINVAL, "hoisted rotations %d and %d share an output", j, i);
+    KsArgs& k = ks[(size_t)i];
+    k.n = c->level + 1;
+    k.mode = KS_AUTO;
+    k.x0 = c->d;
+    k.poly_stride0 = c->poly_stride();
+    k.galois = galois;
+    k.evk = evk->d;
+    k.out = out->d;
+    k.out_stride = out->poly_stride();
+    k.extra = 2;
+    k.hoisted = 1;
+  }
+  launch_hoisted_rotations(ctx->dp, ctx->sc, ks.data(), count, ctx->stream);
+  for (int i = 0; i < count; ++i) {
+    outs[i]->level = c->level;
+    outs[i]->scale = c->scale;
+  }
+  return launched(ctx, "hrot_hoisted");
 }
 
 // ---------------------------------------------------------------------------

@@ -3,7 +3,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -83,6 +85,8 @@ struct KsArgs {
   size_t out_stride;
   int rescale;           // 1: ModDown fused with rescaling by q_(n-1) (HMult)
   int extra;             // ModDown epilogue: 0 none, 1 HMult (d0, d1), 2 HRot (phi(b), 0)
+  int hoisted;           // 1: the ModUp limbs in scratch are of a itself (hoisted rotations), so
+                         //    KeyMult applies the automorphism phi_galois while loading them
 };
 
 // Kernel ids of the key-switch and rescale pipelines (measurement support).
@@ -119,12 +123,59 @@ uint64_t launch_count();
 void count_launch(int k);
 
 // Scratch buffers owned by the context.
+// Column kernels with a tunable launch shape, and the table of tuned shapes
+// (one per context, shared with its clones). A shape is (tc, sl, z): column
+// tile width, slices per block, blocks per tile. Entries are atomics so that
+// lanes on other host threads may read while ckks_tune writes.
+enum ColKernel { CK_MODUP = 0, CK_MODDOWN = 1, CK_RS_FUSED = 2, CK_COUNT = 3 };
+
+struct ColShape {
+  int tc = 0, sl = 0, z = 0;
+  bool valid() const { return tc > 0; }
+};
+
+struct Tuning {
+  explicit Tuning(int max_n)
+      : max_n(max_n),
+        packed(new std::atomic<uint32_t>[CK_COUNT * (max_n + 1)]),
+        us(new std::atomic<float>[CK_COUNT * (max_n + 1)]) {
+    for (int i = 0; i < CK_COUNT * (max_n + 1); ++i) {
+      packed[i].store(0);
+      us[i].store(0.f);
+    }
+  }
+  ColShape get(int k, int n) const {
+    ColShape s;
+    if (k < 0 || k >= CK_COUNT || n < 1 || n > max_n) return s;
+    const uint32_t v = packed[k * (max_n + 1) + n].load(std::memory_order_relaxed);
+    if (v) {
+      s.tc = (int)(v & 0xff);
+      s.sl = (int)((v >> 8) & 0xff);
+      s.z = (int)((v >> 16) & 0xff);
+    }
+    return s;
+  }
+  float time_us(int k, int n) const {
+    return (k < 0 || k >= CK_COUNT || n < 1 || n > max_n) ? 0.f : us[k * (max_n + 1) + n].load();
+  }
+  void set(int k, int n, const ColShape& s, float t_us) {
+    if (k < 0 || k >= CK_COUNT || n < 1 || n > max_n) return;
+    const uint32_t v = s.valid() ? (uint32_t)s.tc | ((uint32_t)s.sl << 8) | ((uint32_t)s.z << 16) : 0u;
+    packed[k * (max_n + 1) + n].store(v, std::memory_order_relaxed);
+    us[k * (max_n + 1) + n].store(t_us);
+  }
+  const int max_n;
+  std::unique_ptr<std::atomic<uint32_t>[]> packed;
+  std::unique_ptr<std::atomic<float>[]> us;
+};
+
 struct Scratch {
   uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
   uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)
   uint32_t* A;  // accumulators [2][n + alpha][N]
-  uint32_t* U;  // HMult result before rescaling [2][L][N]
+  uint32_t* U;  // centered P-limb coefficients of the fused ModDown + rescale [2][alpha][N]
   Prof* prof;   // optional stage timing (null or off: no events)
+  const Tuning* tune = nullptr;  // tuned column-kernel shapes (null: default rule)
 };
 
 inline void prof_mark(const Scratch& sc, cudaStream_t st, int id) {
@@ -158,9 +209,13 @@ void launch_smr(const DevParams& dp, const int64_t* x, int32_t* y, int n, int pr
 
 // ---- launchers (k_keyswitch.cu) ----
 // Full key switch of one polynomial (mode), result written per a.extra.
+bool col_shape_supported(int log_n, int tc, int sl, int z);
+int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int reps, cudaStream_t st);
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st);
 // ModDown only: acc [2][n + alpha][N] (internal layout) -> out [2][n][N].
+void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsArgs* rots, int count,
+                              cudaStream_t st);
 void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
                     cudaStream_t st);
 // Rescale: in [2][n][N] (stride sin) -> out [2][n-1][N] (stride sout).
@@ -198,6 +253,7 @@ struct ckks_ctx {
   bool owns_tables;  // false for a clone (tables belong to the parent context)
   ckks::Scratch sc;
   ckks::Prof prof;
+  std::shared_ptr<ckks::Tuning> tune;  // shared with clones
   void* d_scratch;
   size_t scratch_bytes;
   // host-side key-switching constants needed for keygen (gadget P mod prime)

@@ -21,8 +21,10 @@
 // BConv constant, 2^32 into the BConv matrix). The BConv product uses the
 // paper's lazy reduction (Sec. 4.2).
 #include "geo.cuh"
+#include <functional>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "rows.cuh"
@@ -148,14 +150,14 @@ __device__ __forceinline__ void col_ntt_store(const DevParams& dp, uint32_t (&x)
   for (int i = 0; i < G::EC; ++i) dst[(G::EC * jj + i) * G::W + l] = x[i];
 }
 
-// BConv each target m of this slice (mat row, prime id, destination from
-// tgt), then its NTT column phase.
+// BConv each target m = m0, m0 + step, ... (mat row, prime id, destination
+// from tgt), then its NTT column phase.
 template <class G, int TC, class Target>
-__device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4, int K, int M, int slice,
-                                            int slices, Target tgt, uint32_t* colbuf, int l, int jj, int c,
-                                            int pos) {
+__device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4, int K, int M, int m0, int step,
+                                            Target tgt, uint32_t* colbuf, int l, int jj, int c, int pos,
+                                            int slice) {
   using CTL = ColTile<G, TC>;
-  for (int m = slice; m < M; m += slices) {
+  for (int m = m0; m < M; m += step) {
     const int32_t* row;
     int id;
     uint32_t* dst;
@@ -167,11 +169,13 @@ __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4,
   }
 }
 
-constexpr int kSlices = 4;
+// Launch shape (section "Launch shapes" below): SL slices per block; blockIdx.z
+// of gridDim.z blocks per column tile takes targets m = slice + SL z (mod
+// SL gridDim.z), all of them recomputing the shared input iNTT columns.
 
-// C1: ModUp column kernel. grid (W/TC, digits), block kSlices * CT.
-template <class G, int TC>
-__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
+// C1: ModUp column kernel. grid (W/TC, digits, Z), block SL * CT.
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
                                                                                const uint32_t* S, uint32_t* T) {
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_modup_cols(D
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
   col_inputs<G, TC>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, lo, dp.ks.up_cin + off.x, y4,
-                    colbuf, l, jj, c, pos, slice, kSlices);
+                    colbuf, l, jj, c, pos, slice, SL);
   __syncthreads();
   const int M = ext - K;
   auto tgt = [&](int m, const int32_t*& row, int& id, uint32_t*& dst) {
@@ -194,13 +198,13 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_modup_cols(D
     id = prime_of(t, n, L);
     dst = T + ((size_t)(j * ext + t) << dp.log_n);
   };
-  col_targets<G, TC>(dp, y4, K, M, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+  col_targets<G, TC>(dp, y4, K, M, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
 }
 
-// C2: ModDown column kernel. grid (W/TC, 2 polys). Input S [2][alpha][N]
+// C2: ModDown column kernel. grid (W/TC, 2 polys, Z). Input S [2][alpha][N]
 // (P limbs after the row-phase iNTT); output T [2][n][N].
-template <class G, int TC>
-__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
                                                                                  const uint32_t* S, uint32_t* T) {
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
@@ -212,14 +216,15 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
   col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
-                    y4, colbuf, l, jj, c, pos, slice, kSlices);
+                    y4, colbuf, l, jj, c, pos, slice, SL);
   __syncthreads();
   auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
     row = dp.ks.dn_mat + i * alpha;
     id = i;
     dst = T + ((size_t)(u * n + i) << dp.log_n);
   };
-  col_targets<G, TC>(dp, y4, alpha, n, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+  col_targets<G, TC>(dp, y4, alpha, n, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
+                     slice);
 }
 
 
@@ -227,8 +232,8 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols
 // columns give the centered coefficients y (kept in Y for the second
 // kernel); only the top limb q_l is converted here (its ModDown output is
 // needed in the coefficient domain before the others). grid (W/TC, 2 polys).
-template <class G, int TC>
-__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
                                                                                         const uint32_t* S,
                                                                                         uint32_t* T, uint32_t* Y) {
   using CTL = ColTile<G, TC>;
@@ -241,23 +246,23 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_ks_moddown_cols
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
   col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
-                    y4, colbuf, l, jj, c, pos, slice, kSlices, Y + ((size_t)(u * alpha) << dp.log_n));
+                    y4, colbuf, l, jj, c, pos, slice, SL, Y + ((size_t)(u * alpha) << dp.log_n));
   __syncthreads();
   auto tgt = [&](int, const int32_t*& row, int& id, uint32_t*& dst) {
     row = dp.ks.dn_mat + top * alpha;
     id = top;
     dst = T + ((size_t)u << dp.log_n);
   };
-  col_targets<G, TC>(dp, y4, alpha, 1, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+  col_targets<G, TC>(dp, y4, alpha, 1, slice, SL, tgt, colbuf, l, jj, c, pos, slice);
 }
 
 // ModDown fused with rescaling, second column kernel: iNTT columns of the top
 // limb's ModDown output (row phase already applied) give c_l, centered; with
 // the stored y it forms K = alpha + 1 inputs whose conversion to q_i (matrix
 // rs_mat: the ModDown row plus [P]_{q_i}) is w_i = z_i + P [c_l]_{q_i}; then
-// the NTT columns. grid (W/TC, 2 polys); targets i < l.
-template <class G, int TC>
-__global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
+// the NTT columns. grid (W/TC, 2 polys, Z); targets i < l.
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
                                                                                   const uint32_t* V,
                                                                                   const uint32_t* Y, uint32_t* T) {
   using CTL = ColTile<G, TC>;
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_rs_cols_fused(D
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
   // stored centered P-limb coefficients, A layout along h
-  for (int k = slice; k < alpha; k += kSlices) {
+  for (int k = slice; k < alpha; k += SL) {
     const uint32_t* yk = Y + ((size_t)(u * alpha + k) << dp.log_n);
     int32_t y[G::EC];
 #pragma unroll
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_rs_cols_fused(D
     for (int i4 = 0; i4 < G::EC / 4; ++i4)
       y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
   }
-  if (slice == kSlices - 1) {
+  if (slice == SL - 1) {
     const PrimeConst Pt = dp.pc[top];
     const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
     const uint32_t* s = V + ((size_t)u << dp.log_n);
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kSlices* ColTile<G, TC>::CT) k_rs_cols_fused(D
     id = i;
     dst = T + ((size_t)(u * top + i) << dp.log_n);
   };
-  col_targets<G, TC>(dp, y4, K, top, slice, kSlices, tgt, colbuf, l, jj, c, pos);
+  col_targets<G, TC>(dp, y4, K, top, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
 }
 // ---------------------------------------------------------------------------
 // Rescale column kernel: iNTT cols of the top limb, centered, reduced into
@@ -395,8 +400,17 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const int lo = j * alpha, hi = min(n, lo + alpha);
-    if (t >= lo && t < hi) ks_input4(dp, a, t, p0, x[j]);
-    else load_vec<4>(x[j], T + ((size_t)(j * ext + t) << dp.log_n) + p0);
+    const uint32_t* tj = T + ((size_t)(j * ext + t) << dp.log_n);
+    if (t >= lo && t < hi) {
+      ks_input4(dp, a, t, p0, x[j]);
+    } else if (a.hoisted) {
+      // ModUp commutes with the automorphism exactly (centered BConv), so
+      // phi(ModUp(a)) is a gather from the ModUp limbs of a
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[j][k] = __ldg(tj + auto_src(p0 + k, a.galois, dp.log_n));
+    } else {
+      load_vec<4>(x[j], tj + p0);
+    }
   }
   if (km_out == KM_MODUP) {
 #pragma unroll
@@ -560,10 +574,10 @@ static int groups_for(int blocks_per_group, int max_groups) {
   return g < 1 ? 1 : g;
 }
 
-template <class G, int TC>
+template <class G, int TC, int SL>
 static size_t col_smem_bytes(int K) {
   using CTL = ColTile<G, TC>;
-  return (size_t)K * (G::EC / 4) * CTL::CT * sizeof(int4) + (size_t)kSlices * CTL::BUF * sizeof(uint32_t);
+  return (size_t)K * (G::EC / 4) * CTL::CT * sizeof(int4) + (size_t)SL * CTL::BUF * sizeof(uint32_t);
 }
 
 // Raise a kernel's dynamic shared-memory limit once per process (and only
@@ -580,29 +594,117 @@ static void set_col_smem(const void* f, size_t bytes) {
   }
 }
 
-// Column-tile width: 8 columns (32-byte row segments) when that already
-// gives two blocks per SM, else 4 to double the block count.
-template <class G, class F8, class F4>
-static void with_tc(int blocks_per_tile_column, F8 f8, F4 f4) {
-  if ((G::W / 8) * blocks_per_tile_column >= 2 * 152 || G::W / 4 < 16) f8();
-  else f4();
+// ---------------------------------------------------------------------------
+// Launch shapes of the column kernels
+//
+// A shape is (tc, sl, z): column-tile width, slices per block and blocks per
+// tile. Every shape computes the same values (only the division of targets
+// among threads changes), so the choice affects time alone. The default
+// follows a fixed rule; ckks_tune times every candidate at a level and
+// records the fastest in the context's tuning table, which launches read.
+// ---------------------------------------------------------------------------
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// Calls f(IC<TC>, IC<SL>) for a shape's compile-time parameters.
+template <class F>
+static bool with_shape(const ColShape& s, F f) {
+  switch (s.tc * 16 + s.sl) {
+    case 8 * 16 + 2: f(IC<8>{}, IC<2>{}); return true;
+    case 8 * 16 + 4: f(IC<8>{}, IC<4>{}); return true;
+    case 8 * 16 + 8: f(IC<8>{}, IC<8>{}); return true;
+    case 4 * 16 + 2: f(IC<4>{}, IC<2>{}); return true;
+    case 4 * 16 + 4: f(IC<4>{}, IC<4>{}); return true;
+    case 4 * 16 + 8: f(IC<4>{}, IC<8>{}); return true;
+    default: return false;
+  }
 }
 
-
-template <class G, int TC>
-static void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, cudaStream_t st) {
-  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
-  set_col_smem((const void*)k_ks_modup_cols<G, TC>, sm);
-  k_ks_modup_cols<G, TC><<<dim3(G::W / TC, digits), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
-    count_launch(1);
+// Default shape: 8 columns (32-byte row segments) when that already gives
+// two blocks per SM, else 4 to double the block count; four slices; no split.
+template <class G>
+static ColShape default_shape(int blocks_per_tile_column) {
+  ColShape s;
+  s.tc = ((G::W / 8) * blocks_per_tile_column >= 2 * 152 || G::W / 4 < 16) ? 8 : 4;
+  s.sl = 4;
+  s.z = 1;
+  return s;
 }
 
-template <class G, int TC>
-static void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, cudaStream_t st) {
-  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
-  set_col_smem((const void*)k_ks_moddown_cols<G, TC>, sm);
-  k_ks_moddown_cols<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
+// A shape is launchable when the tile width divides the row, a slice is a
+// whole number of warps (each slice synchronizes its transposes with a named
+// barrier, whose thread count must be a multiple of the warp size) and the
+// parameters are among the compiled ones.
+template <class G>
+static bool shape_ok(const ColShape& s) {
+  return (s.tc == 4 || s.tc == 8) && G::W % s.tc == 0 && (s.tc * G::EC) % 32 == 0 &&
+         (s.sl == 2 || s.sl == 4 || s.sl == 8) && s.z >= 1 && s.z <= 4;
+}
+
+template <class G>
+static ColShape pick_shape(const Scratch& sc, ColKernel k, int n, const ColShape& def) {
+  if (sc.tune) {
+    const ColShape s = sc.tune->get(k, n);
+    if (s.valid() && shape_ok<G>(s)) return s;
+  }
+  return def;
+}
+
+bool col_shape_supported(int log_n, int tc, int sl, int z) {
+  const ColShape s{tc, sl, z};
+  bool ok = false;
+  CKKS_DISPATCH_LOGN(log_n, { ok = shape_ok<G>(s); });
+  return ok;
+}
+
+template <class G>
+static void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, const ColShape& s,
+                              cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_modup_cols<G, TC, SL>, sm);
+    k_ks_modup_cols<G, TC, SL><<<dim3(G::W / TC, digits, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S,
+                                                                                                  sc.T);
     count_launch(1);
+  });
+}
+
+template <class G>
+static void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, const ColShape& s, cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_moddown_cols<G, TC, SL>, sm);
+    k_ks_moddown_cols<G, TC, SL><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T);
+    count_launch(1);
+  });
+}
+
+template <class G>
+static void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint32_t* Y, cudaStream_t st) {
+  ColShape s = default_shape<G>(2);
+  with_shape(s, [&](auto tc, auto sl) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_moddown_cols_top<G, TC, SL>, sm);
+    k_ks_moddown_cols_top<G, TC, SL><<<dim3(G::W / TC, 2), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T,
+                                                                                             Y);
+    count_launch(1);
+  });
+}
+
+template <class G>
+static void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
+                                 const ColShape& s, cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
+    set_col_smem((const void*)k_rs_cols_fused<G, TC, SL>, sm);
+    k_rs_cols_fused<G, TC, SL><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, V, Y, T3);
+    count_launch(1);
+  });
 }
 
 // Streaming grid: four positions per thread.
@@ -621,25 +723,6 @@ static void modup_rows_range(int n, int alpha, int& off, int& cnt) {
   cnt = count(n);
 }
 
-// ModDown from the accumulators A = [2][n + alpha][N] (a_stride between
-// polys): P-limb iNTT rows (into S), C2, NTT rows, epilogue.
-template <class G, int TC>
-static void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint32_t* Y, cudaStream_t st) {
-  const size_t sm = col_smem_bytes<G, TC>(dp.alpha);
-  set_col_smem((const void*)k_ks_moddown_cols_top<G, TC>, sm);
-  k_ks_moddown_cols_top<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T, Y);
-  count_launch(1);
-}
-
-template <class G, int TC>
-static void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
-                                 cudaStream_t st) {
-  const size_t sm = col_smem_bytes<G, TC>(dp.alpha + 1);
-  set_col_smem((const void*)k_rs_cols_fused<G, TC>, sm);
-  k_rs_cols_fused<G, TC><<<dim3(G::W / TC, 2), kSlices * ColTile<G, TC>::CT, sm, st>>>(dp, n, V, Y, T3);
-  count_launch(1);
-}
-
 // ModDown fused with rescaling by q_l (l = n - 1): out gets n - 1 limbs.
 template <class G>
 static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
@@ -653,8 +736,7 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
                    LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  with_tc<G>(2, [&] { launch_moddown_cols_top<G, 8>(dp, n, sc, Y, st); },
-             [&] { launch_moddown_cols_top<G, 4>(dp, n, sc, Y, st); });
+  launch_moddown_cols_top<G>(dp, n, sc, Y, st);
   prof_mark(sc, st, P_MODDOWN_COLS);
   LimbMap top_map{nullptr, 0, 1, 1, dp.L};
   top_map.fixed = top;
@@ -668,8 +750,7 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_KS_EPILOGUE);
   launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
   prof_mark(sc, st, P_RS_IN_ROWS);
-  with_tc<G>(2, [&] { launch_rs_cols_fused<G, 8>(dp, n, V, Y, T3, st); },
-             [&] { launch_rs_cols_fused<G, 4>(dp, n, V, Y, T3, st); });
+  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, n, default_shape<G>(2)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_g<G>(dp, false, T3, T3, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
   prof_mark(sc, st, P_RS_ROWS);
@@ -688,8 +769,7 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
                    LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  with_tc<G>(2, [&] { launch_moddown_cols<G, 8>(dp, n, sc, st); },
-             [&] { launch_moddown_cols<G, 4>(dp, n, sc, st); });
+  launch_moddown_cols<G>(dp, n, sc, pick_shape<G>(sc, CK_MODDOWN, n, default_shape<G>(2)), st);
   prof_mark(sc, st, P_MODDOWN_COLS);
   launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
@@ -716,8 +796,7 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
     prof_mark(sc, st, P_KS_PREP);
     launch_rows_g<G>(dp, true, sc.S, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
-    with_tc<G>(digits, [&] { launch_modup_cols<G, 8>(dp, n, digits, sc, st); },
-               [&] { launch_modup_cols<G, 4>(dp, n, digits, sc, st); });
+    launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
     prof_mark(sc, st, P_MODUP_COLS);
     int off, cnt;
     modup_rows_range(n, alpha, off, cnt);
@@ -730,6 +809,128 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
     if (km_out == KM_KEYSWITCH) {
       if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
       else moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Software fine-tuner for the column kernels (Sec. 4.2, "Fine-tuning"): for
+// the level with n limbs, time every candidate shape of each kernel (reps
+// launches per shape, CUDA events on st) and record the fastest. The kernels
+// run on the lane's scratch exactly as inside an operation; they read what
+// the scratch holds (their time does not depend on the values) and write
+// only scratch.
+// ---------------------------------------------------------------------------
+
+template <class G>
+static std::vector<ColShape> shape_candidates(int targets, const ColShape& def) {
+  std::vector<ColShape> v;
+  for (int tc : {8, 4}) {
+    if (G::W % tc != 0) continue;
+    for (int sl : {2, 4, 8})
+      for (int z = 1; z <= 4; ++z) {
+        const ColShape c{tc, sl, z};
+        const bool is_def = tc == def.tc && sl == def.sl && z == def.z;
+        if (!shape_ok<G>(c)) continue;
+        if (sl * z > targets && !is_def) continue;  // some slices would have no target
+        v.push_back(c);
+      }
+  }
+  return v;
+}
+
+int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int reps, cudaStream_t st) {
+  if (n < 1 || n > dp.L || reps < 1) return CKKS_EINVAL;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return CKKS_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CKKS_ECUDA;
+  }
+  int rc = CKKS_OK;
+  const size_t limb = (size_t)1 << dp.log_n;
+  const int alpha = dp.alpha, digits = (n + alpha - 1) / alpha;
+  CKKS_DISPATCH_LOGN(dp.log_n, {
+    for (int k = 0; k < CK_COUNT && rc == CKKS_OK; ++k) {
+      if (k == CK_RS_FUSED && n < 2) continue;
+      ColShape def;
+      int targets;
+      std::function<void(const ColShape&)> run;
+      if (k == CK_MODUP) {
+        def = default_shape<G>(digits);
+        targets = n;  // fewest targets of a digit: n + alpha - (digit size)
+        run = [&](const ColShape& s) { launch_modup_cols<G>(dp, n, digits, sc, s, st); };
+      } else if (k == CK_MODDOWN) {
+        def = default_shape<G>(2);
+        targets = n;
+        run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, sc, s, st); };
+      } else {
+        def = default_shape<G>(2);
+        targets = n - 1;
+        run = [&](const ColShape& s) {
+          launch_rs_cols_fused<G>(dp, n, sc.T + 2 * limb, sc.U, sc.T + 4 * limb, s, st);
+        };
+      }
+      ColShape best = def;
+      float best_ms = -1.f;
+      for (const ColShape& s : shape_candidates<G>(targets, def)) {
+        run(s);  // first launch: attributes, instruction cache
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r) run(s);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = CKKS_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+          best_ms = ms;
+          best = s;
+        }
+      }
+      if (rc == CKKS_OK) tu.set(k, n, best, 1e3f * best_ms / reps);
+    }
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == CKKS_OK && cudaGetLastError() != cudaSuccess) rc = CKKS_ECUDA;
+  return rc;
+}
+
+// Hoisted rotations of one ciphertext (Par. 5): ModUp of its a part once
+// (iNTT rows straight from the ciphertext, ModUp columns, NTT rows), then for
+// each rotation KeyMult with phi_k applied while loading the ModUp limbs,
+// ModDown and the epilogue adding phi_k(b). The ModDown conversions use the
+// scratch after the ModUp limbs so that those stay intact for the next
+// rotation. Bit-identical to one full key switch per rotation.
+void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsArgs* rots, int count,
+                              cudaStream_t st) {
+  if (count < 1) return;
+  const KsArgs& a0 = rots[0];
+  const int n = a0.n, alpha = dp.alpha, ext = n + alpha;
+  const int digits = (n + alpha - 1) / alpha;
+  const size_t limb = (size_t)1 << dp.log_n;
+  Scratch down = sc;
+  down.T = sc.T + (size_t)digits * ext * limb;
+  dim3 g;
+  int th;
+  CKKS_DISPATCH_LOGN(dp.log_n, {
+    prof_mark(sc, st, -1);
+    launch_rows_g<G>(dp, true, a0.x0 + a0.poly_stride0, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
+    prof_mark(sc, st, P_KS_IN_ROWS);
+    launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
+    prof_mark(sc, st, P_MODUP_COLS);
+    int off, cnt;
+    modup_rows_range(n, alpha, off, cnt);
+    launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+    prof_mark(sc, st, P_MODUP_ROWS);
+    for (int i = 0; i < count; ++i) {
+      stream_grid(dp.log_n, ext, g, th);
+      launch_keymult(digits, g, th, st, dp, rots[i], sc.T, sc.A, KM_KEYSWITCH, nullptr);
+      count_launch(1);
+      prof_mark(sc, st, P_KEYMULT);
+      moddown_tail<G>(dp, down, rots[i], sc.A, (size_t)ext * limb, st);
     }
   });
 }

@@ -289,6 +289,141 @@ def test_hmult_full_size_other_dnum(K, O, dnum):
         K.ckks_ctx_destroy(ctx)
 
 
+def test_more_auxiliary_than_ciphertext_primes(K, O):
+    """alpha > L (one digit, five auxiliary primes, three ciphertext primes):
+    HMult with rescaling and HRot stay bit-exact."""
+    P = O.make_params(12, 3, 1, 5)
+    ctx = K.ckks_ctx_create(12, P.q, P.p, 1, scale=2.0**30)
+    try:
+        c1, c2 = rand_ct(P, 3, 57), rand_ct(P, 3, 59)
+        evk = rand_evk(P, 61)
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
+        assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+        got, k = _run_hrot(K, O, ctx, P, c1, evk, 3)
+        assert np.array_equal(got, O.hrot(P, c1, k, evk))
+    finally:
+        K.ckks_ctx_destroy(ctx)
+
+
+# ------------------------------------------------- hoisted rotations ---
+
+@pytest.mark.parametrize("name,n_q,rs", [("tiny", 6, [1, 2, 5]), ("tiny", 1, [3]), ("toyT1", 4, [1, 7, 100]),
+                                         ("toyT2", 3, [2, 9]), ("n16d3", 40, [1, 2, 3, 17]),
+                                         ("n16d3", 21, [5, 12345]), ("n16d3", 2, [1, 4])])
+def test_hrot_hoisted_matches_oracle(K, O, name, n_q, rs):
+    """One ModUp shared by several rotations (Par. 5): every output equals the
+    oracle's separate HRot bit for bit."""
+    ctx, P = get(K, O, name)
+    c = rand_ct(P, n_q, 91)
+    evks = [rand_evk(P, 93 + i) for i in range(len(rs))]
+    a = K.ckks_ct_import(ctx, c, n_q - 1, 2.0**30)
+    eks = [K.ckks_evk_import(ctx, e, O.rot_k(r, P.log_n)) for e, r in zip(evks, rs)]
+    outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in rs]
+    try:
+        K.ckks_hrot_hoisted(ctx, a, rs, eks, outs)
+        for r, e, o in zip(rs, evks, outs):
+            got, level, _ = K.ckks_ct_export(ctx, o, P.n)
+            assert level == n_q - 1
+            assert np.array_equal(got, O.hrot(P, c, O.rot_k(r, P.log_n), e)), r
+    finally:
+        for h in [a] + eks + outs:
+            K.ckks_free(h)
+
+
+def test_hrot_hoisted_rejects_bad_calls(K, O):
+    ctx, P = get(K, O, "tiny")
+    c = rand_ct(P, 4, 97)
+    a = K.ckks_ct_import(ctx, c, 3, 2.0**30)
+    e1 = K.ckks_evk_import(ctx, rand_evk(P, 98), O.rot_k(1, P.log_n))
+    o1, o2 = K.ckks_ct_create(ctx, 3), K.ckks_ct_create(ctx, 1)
+    try:
+        K.ckks_hrot_hoisted(ctx, a, [], [], [])                  # nothing to do
+        with pytest.raises(RuntimeError):
+            K.ckks_hrot_hoisted(ctx, a, [2], [e1], [o1])         # key for another rotation
+        with pytest.raises(RuntimeError):
+            K.ckks_hrot_hoisted(ctx, a, [1], [e1], [a])          # output aliases the input
+        with pytest.raises(RuntimeError):
+            K.ckks_hrot_hoisted(ctx, a, [1, 1], [e1, e1], [o1, o1])  # shared output
+        with pytest.raises(RuntimeError):
+            K.ckks_hrot_hoisted(ctx, a, [1], [e1], [o2])         # capacity too small
+    finally:
+        for h in (a, e1, o1, o2):
+            K.ckks_free(h)
+
+
+# --------------------------------------------- launch-shape fine-tuning ---
+
+SHAPES = [(tc, sl, z) for tc in (8, 4) for sl in (2, 4, 8) for z in (1, 2, 3, 4)]
+
+
+def _set_all(K, ctx, level, shape):
+    for kern in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
+        K.ckks_tune_set(ctx, kern, level, *shape)
+
+
+@pytest.mark.parametrize("name,n_q", [("n16d3", 40), ("n16d3", 3), ("toyT2", 4), ("tiny", 6)])
+def test_every_column_shape_gives_identical_results(K, O, name, n_q):
+    """Each launch shape of the three column kernels (tile width, slices,
+    target split; some with idle slices at small levels) reproduces the
+    oracle's HMult+rescale and HRot bit for bit."""
+    ctx, P = get(K, O, name)
+    c1, c2 = rand_ct(P, n_q, 71), rand_ct(P, n_q, 73)
+    evk = rand_evk(P, 75)
+    want_m = O.hmult(P, c1, c2, evk, rescale=n_q > 1)
+    k = O.rot_k(1, P.log_n)
+    want_r = O.hrot(P, c1, k, evk)
+    try:
+        for shape in SHAPES:
+            if P.log_n == 8 and shape[0] == 4:
+                # 4 columns x 4 rows per thread is half a warp per slice: refused
+                with pytest.raises(RuntimeError):
+                    K.ckks_tune_set(ctx, K.CKKS_COL_MODUP, n_q - 1, *shape)
+                continue
+            _set_all(K, ctx, n_q - 1, shape)
+            got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, n_q > 1)
+            assert np.array_equal(got, want_m), shape
+            got, _ = _run_hrot(K, O, ctx, P, c1, evk, 1)
+            assert np.array_equal(got, want_r), shape
+    finally:
+        _set_all(K, ctx, n_q - 1, (0, 4, 1))
+
+
+def test_tune_records_a_shape_and_keeps_results(K, O):
+    ctx, P = get(K, O, "n16d3")
+    n_q = 21
+    K.ckks_tune(ctx, n_q - 1, 2)
+    try:
+        for kern in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
+            tc, sl, z, us = K.ckks_tune_get(ctx, kern, n_q - 1)
+            assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and us > 0
+        # a clone shares the table
+        import torch
+        s = torch.cuda.Stream()
+        lane = K.ckks_ctx_clone(ctx, s.cuda_stream)
+        try:
+            assert K.ckks_tune_get(lane, K.CKKS_COL_MODUP, n_q - 1) == K.ckks_tune_get(ctx, K.CKKS_COL_MODUP, n_q - 1)
+        finally:
+            K.ckks_ctx_destroy(lane)
+        c1, c2 = rand_ct(P, n_q, 81), rand_ct(P, n_q, 83)
+        evk = rand_evk(P, 85)
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
+        assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+    finally:
+        _set_all(K, ctx, n_q - 1, (0, 4, 1))
+
+
+def test_tune_rejects_bad_arguments(K, O):
+    ctx, P = get(K, O, "tiny")
+    with pytest.raises(RuntimeError):
+        K.ckks_tune_set(ctx, 0, 0, 16, 4, 1)
+    with pytest.raises(RuntimeError):
+        K.ckks_tune_set(ctx, 3, 0, 8, 4, 1)
+    with pytest.raises(RuntimeError):
+        K.ckks_tune_set(ctx, 0, P.L, 8, 4, 1)
+    with pytest.raises(RuntimeError):
+        K.ckks_tune(ctx, 0, 0)
+
+
 # ----------------------------------------- decryption after operations ---
 
 @pytest.mark.parametrize("name", ["toyT1", "toyT2", "n16d3"])
