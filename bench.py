@@ -494,6 +494,13 @@ def run_hoisted(args, local_rank):
                           700 + i) for i in range(4)]
     outs = [K.ckks_ct_create(ctx, LEVEL) for _ in rots]
     tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune)
+    # linear transform sum_{r=0..32} d_r (.) HRot(ct, r): extended diagonals
+    lt_rots = [0] + rots
+    lt_keys = [None] + gks
+    diags = [K.ckks_encode_ext(ctx, inputs.messages(800 + i, (1 << LOG_N) // 2), LEVEL, SCALE)
+             for i in range(len(lt_rots))]
+    acc = K.ckks_ct_create(ctx, LEVEL)
+    tmp = K.ckks_ct_create(ctx, LEVEL)
 
     def hoisted(c):
         K.ckks_hrot_hoisted(ctx, c, rots, gks, outs)
@@ -502,8 +509,20 @@ def run_hoisted(args, local_rank):
         for r, g, o in zip(rots, gks, outs):
             K.ckks_hrot(ctx, c, r, g, o)
 
+    def lt_fused(c):
+        K.ckks_linear_transform(ctx, c, lt_rots, lt_keys, diags, acc)
+
+    def lt_composed(c):
+        # the same sum from hoisted rotations, PMult and HAdd (one ModDown per rotation)
+        K.ckks_hrot_hoisted(ctx, c, rots, gks, outs)
+        K.ckks_pmult(ctx, c, diags[0], acc)
+        for o, d in zip(outs, diags[1:]):
+            K.ckks_pmult(ctx, o, d, tmp)
+            K.ckks_hadd(ctx, acc, tmp, acc)
+
     res = {}
-    for name, fn in (("separate_hrot", separate), ("hoisted", hoisted)):
+    for name, fn in (("separate_hrot", separate), ("hoisted", hoisted), ("lt_composed", lt_composed),
+                     ("lt_fused", lt_fused)):
         for _ in range(args.warmup):
             fn(cts[0])
         torch.cuda.synchronize()
@@ -525,9 +544,12 @@ def run_hoisted(args, local_rank):
             "config": {"workload": "32 rotations (r = 1..32) of one top-level ciphertext per step, one shared ModUp",
                        "N": 1 << LOG_N, "limbs": L, "dnum": DNUM,
                        "column_shapes": "tuned" if tuned else "default rule"},
-            "modes": res, "speedup_vs_separate": res["hoisted"]["rotations_s"] / res["separate_hrot"]["rotations_s"]}
+            "modes": res, "speedup_vs_separate": res["hoisted"]["rotations_s"] / res["separate_hrot"]["rotations_s"],
+            "linear_transform": {"terms": len(lt_rots), "fused_ms": 32e-3 * res["lt_fused"]["us_per_rotation"],
+                                 "composed_ms": 32e-3 * res["lt_composed"]["us_per_rotation"],
+                                 "speedup": res["lt_fused"]["rotations_s"] / res["lt_composed"]["rotations_s"]}}
     print(json.dumps(line), flush=True)
-    for h in outs + cts + gks + [sk]:
+    for h in outs + cts + gks + diags + [sk, acc, tmp]:
         K.ckks_free(h)
     K.ckks_ctx_destroy(ctx)
 

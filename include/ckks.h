@@ -129,6 +129,11 @@ int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_e
  * round(scale * sigma^-1(u)) (Sec. 2.1; slot j <-> zeta^(5^j), zeta =
  * exp(i pi / N)), then NTT on the device. */
 int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out);
+/* Extended plaintext for ckks_linear_transform: the same integer
+ * coefficients reduced modulo the level + 1 ciphertext primes and the n_p
+ * auxiliary primes, stored [level + 1 Q limbs][n_p P limbs]. ckks_pmult and
+ * ckks_pt_export use its Q limbs. */
+int ckks_encode_ext(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out);
 /* Decode: iNTT on the device, centered CRT lift and FFT on the host; writes
  * N/2 interleaved complex slots. Synchronizes. */
 int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out);
@@ -153,6 +158,9 @@ int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* ct, const uint32_t* host, int level, 
 int ckks_ct_wrap_device(ckks_ctx* ctx, uint32_t* dev_ptr, int level, double scale, ckks_ct** out);
 int ckks_ct_info(const ckks_ct* ct, int* level, double* scale, uint32_t** dev_ptr);
 int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out);
+/* Extended plaintext from canonical residues [level + 1 + n_p][N] (Q limbs,
+ * then P limbs). Synchronizes. */
+int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out);
 int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* pt, uint32_t* host, size_t words, int* level,
                    double* scale);
 
@@ -185,6 +193,19 @@ int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* o
  * level. Asynchronous on the context stream; count = 0 does nothing. */
 int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* ct, int count, const int* r, const ckks_evk* const* evks,
                       ckks_ct* const* outs);
+/* Linear transform (Par. 4, Par. 5): out = sum_{i < count} pts[i] (.) HRot(ct, r[i])
+ * (r[i] = 0: pts[i] (.) ct, no key needed; evks[i] may be NULL there).
+ * The rotated terms share one ModUp of ct's a part; their KeyMult + MAC,
+ * each multiplied by its plaintext in the extended basis Q_l P, accumulate
+ * in one kernel, and ONE ModDown of that sum follows (so the key-switch
+ * rounding differs from summing separate HRot + PMult results, within the
+ * same noise bound); the b parts enter as one accumulated sum of
+ * plaintext-weighted automorphisms. pts[i]: extended plaintexts
+ * (ckks_encode_ext / ckks_pt_import_ext) at a level >= ct's, all of one
+ * scale. 1 <= count <= 64. out: level of ct, scale ct.scale * pt scale;
+ * it must not alias ct. Asynchronous on the context stream. */
+int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* ct, int count, const int* r, const ckks_evk* const* evks,
+                          const ckks_pt* const* pts, ckks_ct* out);
 
 /* --- batched form: many independent ciphertext operations at mixed levels ---
  * A batch is a list of independent operations (no operation's output may be

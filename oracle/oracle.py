@@ -275,6 +275,52 @@ def hrot(P: Params, ct, k: int, evk) -> np.ndarray:
     return out
 
 
+def encode_ext(P: Params, u, scale: float, n_q: int) -> np.ndarray:
+    """Extended plaintext: the encoding's integer coefficients reduced modulo
+    q_0..q_{n_q-1} and then p_0..p_{alpha-1}, NTT domain [n_q + alpha][N]."""
+    m = encode_coeffs(u, scale, P.log_n)
+    return small_to_ntt(m, list(P.q[:n_q]) + list(P.p), P.log_n)
+
+
+def linear_transform(P: Params, ct, rots, evks, pts_ext) -> np.ndarray:
+    """Linear transform sum_i pt_i (.) HRot_{r_i}(ct) with a shared ModUp and
+    one ModDown (Par. 4, Par. 5; the hoisting of the cited linear-transform
+    method). With M_j = ModUp_j(a) (Alg. 1) and phi_i the automorphism of r_i
+    (Eq. 4), over the terms with r_i != 0:
+        acc_u = sum_i pt_i (.) sum_j phi_i(M_j) (.) evk_i[j][u]   in basis Q_l P
+        out_0 = ModDown(acc)_0 + sum_i pt_i (.) phi_i(b)           (all terms)
+        out_1 = ModDown(acc)_1 + sum_{i: r_i = 0} pt_i (.) a
+    pts_ext[i]: [n_q + alpha][N] NTT-domain residues (Q limbs, then P limbs);
+    evks[i] is ignored for r_i = 0."""
+    ct = _u32(ct)
+    n_q = ct.shape[1]
+    qcol = np.array(P.q[:n_q], np.uint64)[:, None]
+    ecol = np.array(list(P.q[:n_q]) + list(P.p), np.uint64)[:, None]
+    b, a = ct[0].astype(np.uint64), ct[1].astype(np.uint64)
+    out = np.zeros((2, n_q, P.n), np.uint64)
+    acc = np.zeros((2, n_q + P.alpha, P.n), np.uint64)
+    up = None
+    rotated = False
+    for r, evk, pt in zip(rots, evks, pts_ext):
+        pt = np.asarray(pt, np.uint64)
+        k = rot_k(r, P.log_n)
+        if k == 1:
+            out[0] = (out[0] + pt[:n_q] * b) % qcol
+            out[1] = (out[1] + pt[:n_q] * a) % qcol
+            continue
+        if up is None:
+            up = modup(P, ct[1], n_q)
+        rotated = True
+        upk = np.stack([automorph_ntt(up[j], k) for j in range(up.shape[0])])
+        km = keymult(P, upk, n_q, evk).astype(np.uint64)
+        acc = (acc + km * pt[None]) % ecol[None]
+        bk = automorph_ntt(ct[0], k).astype(np.uint64)
+        out[0] = (out[0] + pt[:n_q] * bk) % qcol
+    if rotated:
+        out = (out + moddown(P, acc.astype(np.uint32), n_q).astype(np.uint64)) % qcol[None]
+    return out.astype(np.uint32)
+
+
 def hadd(x, y, q) -> np.ndarray:
     x, y = _u32(x), _u32(y)
     out = np.zeros_like(x)

@@ -109,6 +109,9 @@ _SIGS = {
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_hconj": (_i, [_vp, _vp, _vp, _vp]),
     "ckks_hrot_hoisted": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "ckks_linear_transform": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "ckks_encode_ext": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
+    "ckks_pt_import_ext": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
     "ckks_rescale_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "ckks_batch_create": (_i, [_vp, _vp, _i, _i, _i, _P(_vp)]),
     "ckks_batch_run": (_i, [_vp]),
@@ -238,6 +241,14 @@ def ckks_encode(ctx, u, level: int, scale: float):
     return out
 
 
+def ckks_encode_ext(ctx, u, level: int, scale: float):
+    u = np.asarray(u, dtype=np.complex128)
+    ri = np.ascontiguousarray(np.stack([u.real, u.imag], axis=1).reshape(-1))
+    out = _vp()
+    check(ctx, lib.ckks_encode_ext(ctx, _ptr(ri), level, scale, C.byref(out)))
+    return out
+
+
 def ckks_decode(ctx, pt, n_slots: int) -> np.ndarray:
     ri = np.zeros(2 * n_slots, np.float64)
     check(ctx, lib.ckks_decode(ctx, pt, _ptr(ri)))
@@ -302,6 +313,13 @@ def ckks_pt_import(ctx, host, level: int, scale: float):
     return out
 
 
+def ckks_pt_import_ext(ctx, host, level: int, scale: float):
+    h = _u32(host)
+    out = _vp()
+    check(ctx, lib.ckks_pt_import_ext(ctx, _ptr(h), level, scale, C.byref(out)))
+    return out
+
+
 def ckks_pt_export(ctx, pt, level: int, n: int):
     out = np.zeros((level + 1, n), np.uint32)
     lv, sc = C.c_int(), C.c_double()
@@ -331,6 +349,17 @@ def ckks_hrot(ctx, a, r: int, evk, out):
 
 def ckks_hconj(ctx, a, evk, out):
     check(ctx, lib.ckks_hconj(ctx, a, evk, out))
+
+
+def ckks_linear_transform(ctx, a, rs, evks, pts, out):
+    """out = sum_i pts[i] (.) HRot(a, rs[i]) with one shared ModUp and one ModDown."""
+    cnt = len(rs)
+    if len(evks) != cnt or len(pts) != cnt:
+        raise ValueError("rs, evks and pts must have the same length")
+    r_arr = (C.c_int * max(cnt, 1))(*[int(x) for x in rs])
+    e_arr = (C.c_void_p * max(cnt, 1))(*[e if e is not None else None for e in evks])
+    p_arr = (C.c_void_p * max(cnt, 1))(*pts)
+    check(ctx, lib.ckks_linear_transform(ctx, a, cnt, r_arr, e_arr, p_arr, out))
 
 
 def ckks_hrot_hoisted(ctx, a, rs, evks, outs):

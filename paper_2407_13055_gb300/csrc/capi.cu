@@ -387,12 +387,13 @@ int ckks_ct_info(const ckks_ct* c, int* level, double* scale, uint32_t** dev_ptr
   return CKKS_OK;
 }
 
-static int pt_alloc(ckks_ctx* ctx, int level, double scale, ckks_pt** out) {
+static int pt_alloc(ckks_ctx* ctx, int level, double scale, ckks_pt** out, int ext = 0) {
   ckks_pt* p = new_obj<ckks_pt>(ctx, K_PT);
   if (!p) return CKKS_ENOMEM;
   p->level = level;
   p->scale = scale;
-  if (cudaMalloc(&p->d, (size_t)(level + 1) * limb_words(ctx) * 4) != cudaSuccess) {
+  p->ext = ext;
+  if (cudaMalloc(&p->d, (size_t)(level + 1 + ext) * limb_words(ctx) * 4) != cudaSuccess) {
     delete p;
     return fail(ctx, CKKS_ENOMEM, "plaintext allocation failed");
   }
@@ -406,6 +407,28 @@ int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
   int rc = pt_alloc(ctx, level, scale, out);
   if (rc) return rc;
   const int n = level + 1;
+  const size_t lw = limb_words(ctx);
+  rc = cuda_check(ctx, cudaMemcpyAsync(ctx->sc.A, host, (size_t)n * lw * 4, cudaMemcpyHostToDevice, ctx->stream),
+                  "upload");
+  if (!rc) {
+    launch_permute(ctx->dp, ctx->sc.A, (*out)->d, n, true, ctx->stream);
+    rc = launched(ctx, "permute");
+  }
+  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload");
+  if (rc) {
+    ckks_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out) {
+  if (!ctx || !host || !out) return CKKS_EINVAL;
+  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  const int alpha = ctx->dp.alpha;
+  int rc = pt_alloc(ctx, level, scale, out, alpha);
+  if (rc) return rc;
+  const int n = level + 1 + alpha;
   const size_t lw = limb_words(ctx);
   rc = cuda_check(ctx, cudaMemcpyAsync(ctx->sc.A, host, (size_t)n * lw * 4, cudaMemcpyHostToDevice, ctx->stream),
                   "upload");
@@ -626,6 +649,31 @@ int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckk
   return rc;
 }
 
+int ckks_encode_ext(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out) {
+  if (!ctx || !re_im || !out) return CKKS_EINVAL;
+  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  std::vector<int64_t> m;
+  host_encode(re_im, ctx->dp.log_n, scale, m);
+  const int alpha = ctx->dp.alpha, n = level + 1;
+  int rc = pt_alloc(ctx, level, scale, out, alpha);
+  if (rc) return rc;
+  DevBuf tmp;
+  rc = tmp.alloc(m.size() * 8) ? fail(ctx, CKKS_ENOMEM, "encode scratch") : CKKS_OK;
+  if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(tmp.p, m.data(), m.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "upload");
+  if (!rc) {
+    const IdMap ids = id_ext(n, ctx->dp.L, alpha);
+    launch_small_to_res(ctx->dp, tmp.as<int64_t>(), (*out)->d, n + alpha, ids, ctx->stream);
+    launch_ntt(ctx->dp, (*out)->d, n + alpha, ids, false, ctx->stream);
+    rc = launched(ctx, "encode");
+  }
+  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encode");
+  if (rc) {
+    ckks_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
 int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out) {
   if (!ctx || !pt || !re_im_out) return CKKS_EINVAL;
   const int n = pt->level + 1;
@@ -826,6 +874,52 @@ int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* c, int count, const int* r, 
     outs[i]->scale = c->scale;
   }
   return launched(ctx, "hrot_hoisted");
+}
+
+int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* c, int count, const int* r, const ckks_evk* const* evks,
+                          const ckks_pt* const* pts, ckks_ct* out) {
+  if (!ctx || !c || !out || count < 1 || !r || !pts || !evks) return CKKS_EINVAL;
+  if (count > ckks::kLtMax) return fail(ctx, CKKS_EINVAL, "linear transform: at most %d terms", ckks::kLtMax);
+  if (out == c || out->d == c->d) return fail(ctx, CKKS_EINVAL, "linear transform: output aliases the input");
+  if (out->cap_level < c->level) return fail(ctx, CKKS_ELEVEL, "linear transform: output capacity too small");
+  ckks::LtArgs lt{};
+  lt.count = count;
+  const double pscale = pts[0] ? pts[0]->scale : 0.0;
+  for (int i = 0; i < count; ++i) {
+    const ckks_pt* pt = pts[i];
+    if (!pt) return fail(ctx, CKKS_EINVAL, "linear transform: term %d has no plaintext", i);
+    if (pt->ext != ctx->dp.alpha)
+      return fail(ctx, CKKS_EINVAL, "linear transform: term %d needs an extended plaintext (ckks_encode_ext)", i);
+    if (pt->level < c->level) return fail(ctx, CKKS_ELEVEL, "linear transform: term %d plaintext level too low", i);
+    if (std::fabs(pt->scale - pscale) > 1e-9 * pscale)
+      return fail(ctx, CKKS_ESCALE, "linear transform: term %d plaintext scale differs", i);
+    lt.pt[i] = pt->d;
+    lt.pt_p[i] = pt->level + 1;
+    const uint32_t galois = galois_rot(r[i], ctx->dp.log_n);
+    if (galois == 1) {
+      lt.galois[i] = 1;
+      lt.evk[i] = nullptr;
+      continue;
+    }
+    const ckks_evk* evk = evks[i];
+    if (!evk) return fail(ctx, CKKS_ENOKEY, "linear transform: term %d has no key", i);
+    if (evk->galois != galois)
+      return fail(ctx, CKKS_ENOKEY, "linear transform: term %d key is for galois element %u, need %u", i,
+                  evk->galois, galois);
+    lt.galois[i] = galois;
+    lt.evk[i] = evk->d;
+    ++lt.rotated;
+  }
+  KsArgs k{};
+  k.n = c->level + 1;
+  k.x0 = c->d;
+  k.poly_stride0 = c->poly_stride();
+  k.out = out->d;
+  k.out_stride = out->poly_stride();
+  launch_linear_transform(ctx->dp, ctx->sc, k, lt, ctx->stream);
+  out->level = c->level;
+  out->scale = c->scale * pscale;
+  return launched(ctx, "linear_transform");
 }
 
 // ---------------------------------------------------------------------------

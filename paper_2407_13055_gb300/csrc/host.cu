@@ -220,12 +220,6 @@ void host_decode(const uint32_t* res, int nl, const uint32_t* q, int log_n, doub
   std::vector<uint32_t> inv((size_t)nl * nl);
   for (int i = 0; i < nl; ++i)
     for (int j = 0; j < i; ++j) inv[(size_t)i * nl + j] = invm(q[j] % q[i], q[i]);
-  std::vector<double> wt(nl);
-  double w = 1;
-  for (int i = 0; i < nl; ++i) {
-    wt[i] = w;
-    w *= (double)q[i];
-  }
   // mixed-radix digits of (Q-1)/2, whose residues are (q_i - 1)/2
   std::vector<uint32_t> half(nl), v(nl);
   for (int i = 0; i < nl; ++i) {
@@ -247,11 +241,14 @@ void host_decode(const uint32_t* res, int nl, const uint32_t* q, int log_n, doub
         break;
       }
     }
+    // value = d_0 + q_0 (d_1 + q_1 (d_2 + ...)), evaluated from the top digit
+    // (Horner): the leading digits of a small value are 0 (or q_i - 1 for a
+    // negative one), so nothing overflows however many limbs there are.
     double x = 0;
     if (!neg) {
-      for (int i = nl - 1; i >= 0; --i) x += (double)v[i] * wt[i];
+      for (int i = nl - 1; i >= 0; --i) x = x * (double)q[i] + (double)v[i];
     } else {
-      for (int i = nl - 1; i >= 0; --i) x += (double)(q[i] - 1 - v[i]) * wt[i];
+      for (int i = nl - 1; i >= 0; --i) x = x * (double)q[i] + (double)(q[i] - 1 - v[i]);
       x = -(x + 1);
     }
     const cd tw(std::cos(M_PI * k / n), std::sin(M_PI * k / n));

@@ -89,6 +89,21 @@ struct KsArgs {
                          //    KeyMult applies the automorphism phi_galois while loading them
 };
 
+// Terms of a linear transform sum_i pt_i (.) HRot_{r_i}(ct) (Par. 4, Par. 5),
+// passed to the kernels by value. Term i: automorphism galois[i] (1 for
+// r = 0), key evk[i] (null for r = 0: the term is pt_i (.) ct itself) and the
+// extended plaintext pt[i] = [pt_level + 1 Q limbs][alpha P limbs], whose
+// first P limb is at limb index pt_p[i].
+constexpr int kLtMax = 64;
+struct LtArgs {
+  int count;      // number of terms
+  int rotated;    // number of terms with a key
+  uint32_t galois[kLtMax];
+  const uint32_t* evk[kLtMax];
+  const uint32_t* pt[kLtMax];
+  int pt_p[kLtMax];
+};
+
 // Kernel ids of the key-switch and rescale pipelines (measurement support).
 enum ProfId {
   P_KS_PREP = 0,      // input d, a1*a2 or phi(a) (streaming)
@@ -216,6 +231,8 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
 // ModDown only: acc [2][n + alpha][N] (internal layout) -> out [2][n][N].
 void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsArgs* rots, int count,
                               cudaStream_t st);
+void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
+                             cudaStream_t st);
 void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
                     cudaStream_t st);
 // Rescale: in [2][n][N] (stride sin) -> out [2][n-1][N] (stride sout).
@@ -276,6 +293,7 @@ struct ckks_pt {
   uint32_t* d;
   int level;
   double scale;
+  int ext = 0;  // auxiliary (P) limbs stored after the level + 1 Q limbs (extended plaintexts)
 };
 
 struct ckks_sk {

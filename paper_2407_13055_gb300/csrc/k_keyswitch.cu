@@ -484,6 +484,106 @@ __global__ void k_ks_epilogue(DevParams dp, KsArgs a, const uint32_t* T, const u
 }
 
 
+// Linear transform, KeyMult + MAC of every rotated term in one kernel
+// (Par. 5): for extended limb t,
+//   acc_u[t] = sum_i pt_i[t] (.) sum_j phi_i(ModUp_j(a))[t] (.) evk_i[j][u][t],
+// the automorphism read as a gather from the shared ModUp limbs of a (own
+// digit limbs: from a itself). The plaintexts are in the extended basis, so
+// the sum stays in Q_l P until one ModDown. A = [2][n + alpha][N].
+template <int D>
+__global__ void k_lt_keymult(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* T, uint32_t* A) {
+  const int t = blockIdx.y;
+  const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
+  const int id = prime_of(t, n, L);
+  const int key_limb = t < n ? t : L + (t - n);
+  const PrimeConst P = dp.pc[id];
+  const uint32_t p0 = stream_pos();
+  const uint32_t* ain = a.x0 + a.poly_stride0 + ((size_t)t << dp.log_n);
+  uint32_t acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+  for (int i = 0; i < lt.count; ++i) {
+    const uint32_t* evk = lt.evk[i];
+    if (!evk) continue;
+    const uint32_t g = lt.galois[i];
+    uint32_t x[D][4], e0[D][4], e1[D][4], w[4];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int lo = j * alpha, hi = min(n, lo + alpha);
+      const uint32_t* src = (t >= lo && t < hi) ? ain : T + ((size_t)(j * ext + t) << dp.log_n);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[j][k] = __ldg(src + auto_src(p0 + k, g, dp.log_n));
+      load_vec_stream<4>(e0[j], evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e1[j], evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
+    }
+    const int pl = t < n ? t : lt.pt_p[i] + (t - n);
+    load_vec<4>(w, lt.pt[i] + ((size_t)pl << dp.log_n) + p0);
+    uint32_t s0[4] = {0, 0, 0, 0}, s1[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        s0[k] = addm(s0[k], fix_signed(mont_mul(x[j][k], e0[j][k], P.q, P.m), P.q), P.q);
+        s1[k] = addm(s1[k], fix_signed(mont_mul(x[j][k], e1[j][k], P.q, P.m), P.q), P.q);
+      }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc0[k] = addm(acc0[k], mulmod(s0[k], w[k], P), P.q);
+      acc1[k] = addm(acc1[k], mulmod(s1[k], w[k], P), P.q);
+    }
+  }
+  store_vec<4>(A + ((size_t)t << dp.log_n) + p0, acc0);
+  store_vec<4>(A + ((size_t)(ext + t) << dp.log_n) + p0, acc1);
+}
+
+static void launch_lt_keymult(int digits, dim3 g, int th, cudaStream_t st, const DevParams& dp, const KsArgs& a,
+                              const LtArgs& lt, const uint32_t* T, uint32_t* A) {
+  switch (digits) {
+#define CKKS_LT(D) \
+  case D: k_lt_keymult<D><<<g, th, 0, st>>>(dp, a, lt, T, A); break;
+    CKKS_LT(1) CKKS_LT(2) CKKS_LT(3) CKKS_LT(4) CKKS_LT(5) CKKS_LT(6) CKKS_LT(7) CKKS_LT(8)
+#undef CKKS_LT
+    default:
+      break;
+  }
+}
+
+// Linear transform epilogue, limb i of output poly u:
+//   out_0 = (A_0 - Z_0) P^-1 + sum_i pt_i (.) phi_i(b)      (accumulated automorphisms, Par. 4)
+//   out_1 = (A_1 - Z_1) P^-1 + sum_{i: r_i = 0} pt_i (.) a
+// ks = 0 (no rotated term): the key-switch part is zero and A, Z are not read.
+__global__ void k_lt_epilogue(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* Z, const uint32_t* A,
+                              size_t a_stride, int ks) {
+  const int n = a.n;
+  const int u = blockIdx.y / n, i = blockIdx.y % n;
+  const PrimeConst P = dp.pc[i];
+  const uint32_t p0 = stream_pos();
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  uint32_t z[4] = {0, 0, 0, 0};
+  if (ks) {
+    const uint2 pinv = dp.ks.dn_pinv[i];
+    uint32_t acc[4];
+    load_vec<4>(z, Z + ((size_t)(u * n + i) << dp.log_n) + p0);
+    load_vec<4>(acc, A + u * a_stride + off);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q);
+  }
+  const uint32_t* src = a.x0 + u * a.poly_stride0 + ((size_t)i << dp.log_n);
+  for (int t = 0; t < lt.count; ++t) {
+    const bool plain = lt.evk[t] == nullptr;
+    if (u == 1 && !plain) continue;
+    uint32_t w[4], v[4];
+    load_vec<4>(w, lt.pt[t] + off);
+    if (plain) {
+      load_vec<4>(v, src + p0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __ldg(src + auto_src(p0 + k, lt.galois[t], dp.log_n));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = addm(z[k], mulmod(w[k], v[k], P), P.q);
+  }
+  store_vec<4>(a.out + u * a.out_stride + off, z);
+}
+
 // Extra term of the ModDown output at limb i (HMult: d0 or d1; HRot: phi(b)).
 __device__ __forceinline__ void ks_extra4(const DevParams& dp, const KsArgs& a, int u, int i, uint32_t p0,
                                           const PrimeConst& P, uint32_t (&e)[4]) {
@@ -932,6 +1032,50 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
       prof_mark(sc, st, P_KEYMULT);
       moddown_tail<G>(dp, down, rots[i], sc.A, (size_t)ext * limb, st);
     }
+  });
+}
+
+// Linear transform (Par. 5): ModUp of a once, KeyMult + MAC of all rotated
+// terms with their extended plaintexts in one kernel, one ModDown of the
+// sum, and the epilogue adding the plaintext-weighted automorphisms of b
+// (and pt (.) a for unrotated terms).
+void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
+                             cudaStream_t st) {
+  const int n = a.n, alpha = dp.alpha, ext = n + alpha;
+  const int digits = (n + alpha - 1) / alpha;
+  const size_t limb = (size_t)1 << dp.log_n;
+  Scratch down = sc;
+  down.T = sc.T + (size_t)digits * ext * limb;
+  dim3 g;
+  int th;
+  CKKS_DISPATCH_LOGN(dp.log_n, {
+    prof_mark(sc, st, -1);
+    if (lt.rotated > 0) {
+      launch_rows_g<G>(dp, true, a.x0 + a.poly_stride0, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
+      prof_mark(sc, st, P_KS_IN_ROWS);
+      launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
+      prof_mark(sc, st, P_MODUP_COLS);
+      int off, cnt;
+      modup_rows_range(n, alpha, off, cnt);
+      launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+      prof_mark(sc, st, P_MODUP_ROWS);
+      stream_grid(dp.log_n, ext, g, th);
+      launch_lt_keymult(digits, g, th, st, dp, a, lt, sc.T, sc.A);
+      count_launch(1);
+      prof_mark(sc, st, P_KEYMULT);
+      const size_t a_stride = (size_t)ext * limb;
+      launch_rows_g<G>(dp, true, sc.A, down.S, 2 * alpha,
+                       LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
+      prof_mark(sc, st, P_MODDOWN_IN_ROWS);
+      launch_moddown_cols<G>(dp, n, down, pick_shape<G>(sc, CK_MODDOWN, n, default_shape<G>(2)), st);
+      prof_mark(sc, st, P_MODDOWN_COLS);
+      launch_rows_g<G>(dp, false, down.T, down.T, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+      prof_mark(sc, st, P_MODDOWN_ROWS);
+    }
+    stream_grid(dp.log_n, 2 * n, g, th);
+    k_lt_epilogue<<<g, th, 0, st>>>(dp, a, lt, down.T, sc.A, (size_t)ext * limb, lt.rotated > 0 ? 1 : 0);
+    count_launch(1);
+    prof_mark(sc, st, P_KS_EPILOGUE);
   });
 }
 

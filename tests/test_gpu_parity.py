@@ -351,6 +351,92 @@ def test_hrot_hoisted_rejects_bad_calls(K, O):
             K.ckks_free(h)
 
 
+# ------------------------------------------------ linear transform ---
+
+def _rand_ext_pt(P, n_q, seed):
+    return inputs.uniform_residues(seed, list(P.q[:n_q]) + list(P.p), P.n, 7)
+
+
+@pytest.mark.parametrize("name,n_q,rs", [("tiny", 6, [0, 1, 2, 5]), ("tiny", 1, [3, 0]), ("toyT1", 4, [1, 7, 1]),
+                                         ("toyT2", 3, [0, 2]), ("n16d3", 40, [0, 1, 2, 3, 17]),
+                                         ("n16d3", 21, [5, 12345]), ("n16d3", 2, [1]), ("n16d3", 40, [0])])
+def test_linear_transform_matches_oracle(K, O, name, n_q, rs):
+    ctx, P = get(K, O, name)
+    c = rand_ct(P, n_q, 101)
+    evks = [rand_evk(P, 103 + i) if r else None for i, r in enumerate(rs)]
+    pts = [_rand_ext_pt(P, n_q, 111 + i) for i in range(len(rs))]
+    a = K.ckks_ct_import(ctx, c, n_q - 1, 2.0**30)
+    eks = [K.ckks_evk_import(ctx, e, O.rot_k(r, P.log_n)) if r else None for e, r in zip(evks, rs)]
+    dps = [K.ckks_pt_import_ext(ctx, pt, n_q - 1, 2.0**20) for pt in pts]
+    out = K.ckks_ct_create(ctx, n_q - 1)
+    try:
+        K.ckks_linear_transform(ctx, a, rs, eks, dps, out)
+        got, level, scale = K.ckks_ct_export(ctx, out, P.n)
+        assert level == n_q - 1 and scale == 2.0**50
+        assert np.array_equal(got, O.linear_transform(P, c, rs, evks, pts))
+    finally:
+        for h in [a, out] + [e for e in eks if e] + dps:
+            K.ckks_free(h)
+
+
+def test_linear_transform_decrypts_with_library_keys(K, O):
+    """N = 2^16, top level: library encryption, keys and extended encodings;
+    the decryption is the weighted sum of rotations within 1e-3."""
+    ctx, P = get(K, O, "n16d3")
+    lv = 39
+    sk = K.ckks_keygen_secret(ctx, 7)
+    u = inputs.messages(7, P.n // 2)
+    rs = [0, 1, 2, 3, 4, 8]
+    diags = [inputs.messages(70 + i, P.n // 2) for i in range(len(rs))]
+    handles = [sk]
+    try:
+        pt = K.ckks_encode(ctx, u, lv, 2.0**30)
+        ct = K.ckks_encrypt(ctx, sk, pt, 8)
+        handles += [pt, ct]
+        eks = [K.ckks_keygen_rot(ctx, sk, r, 200 + r) if r else None for r in rs]
+        dps = [K.ckks_encode_ext(ctx, d, lv, 2.0**30) for d in diags]
+        handles += [e for e in eks if e] + dps
+        out = K.ckks_ct_create(ctx, lv)
+        handles.append(out)
+        K.ckks_linear_transform(ctx, ct, rs, eks, dps, out)
+        res = K.ckks_ct_create(ctx, lv - 1)
+        handles.append(res)
+        K.ckks_rescale(ctx, out, res)
+        dec = K.ckks_decrypt(ctx, sk, res)
+        handles.append(dec)
+        got = K.ckks_decode(ctx, dec, P.n // 2)
+        want = sum(d * np.roll(u, -r) for d, r in zip(diags, rs))
+        assert np.max(np.abs(got - want)) < 1e-3
+    finally:
+        for h in handles:
+            K.ckks_free(h)
+
+
+def test_linear_transform_rejects_bad_calls(K, O):
+    ctx, P = get(K, O, "tiny")
+    c = rand_ct(P, 4, 121)
+    a = K.ckks_ct_import(ctx, c, 3, 2.0**30)
+    e1 = K.ckks_evk_import(ctx, rand_evk(P, 122), O.rot_k(1, P.log_n))
+    plain = K.ckks_pt_import(ctx, rand_ct(P, 4, 123)[0], 3, 1.0)
+    ext = K.ckks_pt_import_ext(ctx, _rand_ext_pt(P, 4, 124), 3, 1.0)
+    ext2 = K.ckks_pt_import_ext(ctx, _rand_ext_pt(P, 4, 125), 3, 2.0)
+    out = K.ckks_ct_create(ctx, 3)
+    try:
+        with pytest.raises(RuntimeError):
+            K.ckks_linear_transform(ctx, a, [1], [e1], [plain], out)       # not an extended plaintext
+        with pytest.raises(RuntimeError):
+            K.ckks_linear_transform(ctx, a, [2], [e1], [ext], out)         # key for another rotation
+        with pytest.raises(RuntimeError):
+            K.ckks_linear_transform(ctx, a, [1, 0], [e1, None], [ext, ext2], out)  # scales differ
+        with pytest.raises(RuntimeError):
+            K.ckks_linear_transform(ctx, a, [1], [e1], [ext], a)           # output aliases the input
+        with pytest.raises(RuntimeError):
+            K.ckks_linear_transform(ctx, a, [0] * 65, [None] * 65, [ext] * 65, out)  # too many terms
+    finally:
+        for h in (a, e1, plain, ext, ext2, out):
+            K.ckks_free(h)
+
+
 # --------------------------------------------- launch-shape fine-tuning ---
 
 SHAPES = [(tc, sl, z) for tc in (8, 4) for sl in (2, 4, 8) for z in (1, 2, 3, 4)]
@@ -464,6 +550,24 @@ def test_library_keys_decrypt_within_tolerance(K, O, name):
         assert np.max(np.abs(dec(out) - (u + v))) < 1e-3
     finally:
         for h in hs:
+            K.ckks_free(h)
+
+
+@pytest.mark.parametrize("level", [39, 34, 33])
+def test_library_decode_at_high_levels(K, O, level):
+    """Encode -> encrypt -> decrypt -> decode at levels whose modulus exceeds
+    the double range (more than 33 primes)."""
+    ctx, P = get(K, O, "n16d3")
+    u = inputs.messages(64, P.n // 2)
+    sk = K.ckks_keygen_secret(ctx, 65)
+    pt = K.ckks_encode(ctx, u, level, 2.0**30)
+    ct = K.ckks_encrypt(ctx, sk, pt, 66)
+    dec = K.ckks_decrypt(ctx, sk, ct)
+    try:
+        assert np.max(np.abs(K.ckks_decode(ctx, dec, P.n // 2) - u)) < 1e-3
+        assert np.max(np.abs(K.ckks_decode(ctx, pt, P.n // 2) - u)) < 1e-6
+    finally:
+        for h in (sk, pt, ct, dec):
             K.ckks_free(h)
 
 

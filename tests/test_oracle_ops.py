@@ -369,3 +369,50 @@ def test_config_n16_low_level_decrypt(O, dnum):
     rot = O.hrot(P, ct1, k, O.keygen_auto(P, s, k, a, e))
     err = np.max(np.abs(O.decode(P, O.decrypt(P, s, rot), scale) - np.roll(u, -5)))
     assert err < 1e-3, err
+
+
+@pytest.mark.parametrize("name,log_n,L,dnum,alpha", TOY)
+def test_linear_transform_decrypts_to_weighted_rotation_sum(O, name, log_n, L, dnum, alpha):
+    """Par. 5 with one ModDown: decrypting sum_i d_i (.) HRot_{r_i}(ct) gives
+    the slot-wise sum of d_i times u rotated left by r_i."""
+    P = O.make_params(log_n, L, dnum, alpha)
+    seed = 5
+    s, ks = _keys(O, P, seed, None)
+    scale = 2.0**28
+    u = inputs.messages(seed, P.n // 2)
+    ct = _enc(O, P, s, u, scale, L, seed, 1)
+    rots = [0, 1, 3, 1]
+    diags = [inputs.messages(50 + i, P.n // 2) for i in range(len(rots))]
+    pts = [O.encode_ext(P, d, scale, L) for d in diags]
+    evks = []
+    for i, r in enumerate(rots):
+        a, e = ks(10 + i)
+        evks.append(O.keygen_auto(P, s, O.rot_k(r, log_n), a, e) if r else None)
+    out = O.linear_transform(P, ct, rots, evks, pts)
+    want = sum(d * np.roll(u, -r) for d, r in zip(diags, rots))
+    err = np.max(np.abs(O.decode(P, O.decrypt(P, s, out), scale * scale) - want))
+    assert err < 1e-3, err
+
+
+def test_linear_transform_single_rotation_is_pmult_of_hrot_up_to_moddown(O):
+    """One rotated term: ModDown(pt (.) KeyMult) and pt (.) ModDown(KeyMult)
+    are both exact divisions by P of values congruent modulo Q_l, so they
+    differ by a small integer polynomial only: the coefficient-domain
+    difference is bounded (here by N * max|pt| / P-scale, far below q)."""
+    P = O.make_params(8, 4, 2)
+    rng = np.random.default_rng(3)
+    n_q = 4
+    ct = np.stack([np.stack([rng.integers(0, int(v), P.n) for v in P.q[:n_q]]) for _ in range(2)]).astype(np.uint32)
+    evk = np.stack([np.stack([np.stack([rng.integers(0, int(v), P.n) for v in P.all_primes()]) for _ in range(2)])
+                    for _ in range(P.dnum)]).astype(np.uint32)
+    k = O.rot_k(1, P.log_n)
+    m = rng.integers(-3, 4, P.n)                     # small plaintext coefficients
+    pt_ext = O.small_to_ntt(m, list(P.q[:n_q]) + list(P.p), P.log_n)
+    got = O.linear_transform(P, ct, [1], [evk], [pt_ext])
+    ref = O.pmult(O.hrot(P, ct, k, evk), pt_ext[:n_q], P.q[:n_q])
+    diff = (got.astype(np.int64) - ref.astype(np.int64)) % np.array(P.q[:n_q], np.int64)[None, :, None]
+    coeff = O.intt(diff.reshape(2 * n_q, P.n).astype(np.uint32), list(P.q[:n_q]) * 2).reshape(2, n_q, P.n)
+    for u_ in range(2):
+        big = O.crt_centered(coeff[u_], P.q[:n_q])
+        # |pt (.) rounding| <= N * max|m| * (alpha + 1) / 2 per coefficient (rounding in [-K/2, K/2] per limb)
+        assert max(abs(int(x)) for x in big) <= P.n * 3 * (P.alpha + 2)
