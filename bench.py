@@ -555,6 +555,65 @@ def run_hoisted(args, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# bootstrap-shaped trace: linear transforms, polynomial, linear transforms
+# ----------------------------------------------------------------------------
+
+def run_bootstrap(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    from paper_2407_13055_gb300.trace import Trace, TraceSpec, expected
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    sk = K.ckks_keygen_secret(ctx, 51)
+    spec = TraceSpec()
+    slots = (1 << LOG_N) // 2
+    u = inputs.messages(52, slots)
+    pt = K.ckks_encode(ctx, u, LEVEL, SCALE)
+    ct = K.ckks_encrypt(ctx, sk, pt, 53)
+    tuned = tune_levels(K, ctx, range(LEVEL - spec.levels_used(), LEVEL + 1), not args.no_tune, reps=2)
+    tr = Trace(K, ctx, spec, LEVEL, q, slots, sk=sk)
+    want = expected(spec, u)
+    res = {}
+    for name, fused in (("one_op_at_a_time", False), ("fused", True)):
+        out, level = tr.run(ct, fused)           # first run: plaintexts, pooled ciphertexts
+        dec = K.ckks_decrypt(ctx, sk, out)
+        err = float(np.max(np.abs(K.ckks_decode(ctx, dec, slots) - want)))
+        K.ckks_free(dec)
+        for _ in range(args.warmup):
+            tr.run(ct, fused)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = K.ckks_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            tr.run(ct, fused)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms_per_trace": ms, "traces_s": 1e3 / ms, "max_abs_error": err, "final_level": level,
+                     "launches_per_trace": (K.ckks_launch_count() - l0) / args.steps}
+    tr.close()
+    line = {"metric": "bootstrap-shaped trace at N=2^16 (1 GB300)", "value": res["fused"]["traces_s"],
+            "unit": "traces/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fused"]["ms_per_trace"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryption of U[-1,1] slots)",
+            "config": {"workload": f"CoeffToSlot-like {spec.lt_levels} BSGS linear transforms ({spec.n1} baby x "
+                                   f"{spec.n2} giant steps, random diagonals), degree-{1 << spec.depth} polynomial "
+                                   f"(product tree of HMult+rescale, depth {spec.depth}), SlotToCoeff-like "
+                                   f"{spec.lt_levels} transforms; start level {LEVEL}",
+                       "N": 1 << LOG_N, "limbs": L, "dnum": DNUM,
+                       "column_shapes": "tuned per level" if tuned else "default rule"},
+            "modes": res, "speedup_vs_one_op": res["one_op_at_a_time"]["ms_per_trace"] / res["fused"]["ms_per_trace"]}
+    print(json.dumps(line), flush=True)
+    for h in (pt, ct, sk):
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
 # served form: Poisson arrivals, continuous batching over lanes
 # ----------------------------------------------------------------------------
 
@@ -642,7 +701,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
     args = ap.parse_args()
@@ -660,6 +719,9 @@ def main():
         return
     if args.workload == "hoisted":
         run_hoisted(args, local_rank)
+        return
+    if args.workload == "bootstrap":
+        run_bootstrap(args, local_rank)
         return
     if world > 1:
         import torch

@@ -168,6 +168,9 @@ int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* pt, uint32_t* host, size_t word
 /* HAdd: limb-wise addition; levels must match, scales within 2^-20. out may
  * alias a or b. */
 int ckks_hadd(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
+/* PAdd: (b + pt, a) limb-wise; the plaintext's level must be >= the
+ * ciphertext's and its scale equal within 2^-20. out may alias a. */
+int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
 /* PMult: ciphertext times plaintext in the NTT domain; scale multiplies. out
  * may alias a. */
 int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
@@ -220,6 +223,7 @@ int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* ct, int count, const int
 #define CKKS_OP_PMULT 4   /* ckks_pmult(a, pt, out) */
 #define CKKS_OP_RESCALE 5 /* ckks_rescale(a, out) */
 #define CKKS_OP_HADD 6    /* ckks_hadd(a, b, out) */
+#define CKKS_OP_PADD 7    /* ckks_padd(a, pt, out) */
 typedef struct {
   int op;
   int flags;

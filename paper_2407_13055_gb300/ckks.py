@@ -65,7 +65,7 @@ class ckks_op(C.Structure):
     ]
 
 
-CKKS_OP_HMULT, CKKS_OP_HROT, CKKS_OP_HCONJ, CKKS_OP_PMULT, CKKS_OP_RESCALE, CKKS_OP_HADD = 1, 2, 3, 4, 5, 6
+CKKS_OP_HMULT, CKKS_OP_HROT, CKKS_OP_HCONJ, CKKS_OP_PMULT, CKKS_OP_RESCALE, CKKS_OP_HADD, CKKS_OP_PADD = 1, 2, 3, 4, 5, 6, 7
 
 
 if not os.path.exists(LIB_PATH):
@@ -104,6 +104,7 @@ _SIGS = {
     "ckks_pt_export": (_i, [_vp, _vp, _vp, _sz, _P(_i), _P(_d)]),
     "ckks_hadd": (_i, [_vp, _vp, _vp, _vp]),
     "ckks_pmult": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_padd": (_i, [_vp, _vp, _vp, _vp]),
     "ckks_hmult": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "ckks_rescale": (_i, [_vp, _vp, _vp]),
     "ckks_hrot": (_i, [_vp, _vp, _i, _vp, _vp]),
@@ -345,6 +346,10 @@ def ckks_rescale(ctx, a, out):
 
 def ckks_hrot(ctx, a, r: int, evk, out):
     check(ctx, lib.ckks_hrot(ctx, a, r, evk, out))
+
+
+def ckks_padd(ctx, a, pt, out):
+    check(ctx, lib.ckks_padd(ctx, a, pt, out))
 
 
 def ckks_hconj(ctx, a, evk, out):

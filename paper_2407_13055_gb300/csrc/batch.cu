@@ -33,6 +33,8 @@ int issue_one(ckks_ctx* lane, const ckks_op& o) {
       return ckks_rescale(lane, o.a, o.out);
     case CKKS_OP_HADD:
       return ckks_hadd(lane, o.a, o.b, o.out);
+    case CKKS_OP_PADD:
+      return ckks_padd(lane, o.a, o.pt, o.out);
     default:
       return CKKS_EINVAL;
   }

@@ -769,6 +769,17 @@ int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out)
   return launched(ctx, "pmult");
 }
 
+int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out) {
+  if (!ctx || !a || !pt || !out) return CKKS_EINVAL;
+  if (pt->level < a->level) return fail(ctx, CKKS_ELEVEL, "padd: plaintext level %d below %d", pt->level, a->level);
+  if (!scales_match(a->scale, pt->scale)) return fail(ctx, CKKS_ESCALE, "padd: scales differ");
+  if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "padd: output capacity too small");
+  launch_padd(ctx->dp, a->d, pt->d, out->d, a->level + 1, a->poly_stride(), out->poly_stride(), ctx->stream);
+  out->level = a->level;
+  out->scale = a->scale;
+  return launched(ctx, "padd");
+}
+
 int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out) {
   if (!ctx || !in || !out) return CKKS_EINVAL;
   if (in->level < 1) return fail(ctx, CKKS_ELEVEL, "rescale at level 0");

@@ -205,6 +205,8 @@ void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int 
                     cudaStream_t st);
 void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, size_t sa,
                  size_t sb, size_t so, cudaStream_t st);
+void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+                 size_t so, cudaStream_t st);
 void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
                   size_t so, cudaStream_t st);
 void launch_tensor(const DevParams& dp, const uint32_t* c1, const uint32_t* c2, uint32_t* out, int n,

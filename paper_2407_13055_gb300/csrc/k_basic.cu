@@ -169,6 +169,20 @@ __global__ void k_hadd(DevParams dp, const uint32_t* a, const uint32_t* b, uint3
       make_uint4(addmod(x.x, y.x, q), addmod(x.y, y.y, q), addmod(x.z, y.z, q), addmod(x.w, y.w, q));
 }
 
+// PAdd: (b + pt, a) limb by limb.
+__global__ void k_padd(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+                       size_t so) {
+  const int t = blockIdx.y / n, i = blockIdx.y % n;
+  const uint32_t q = dp.pc[i].q;
+  const size_t off = ((size_t)i << dp.log_n) + 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  uint4 x = *reinterpret_cast<const uint4*>(a + t * sa + off);
+  if (t == 0) {
+    const uint4 y = *reinterpret_cast<const uint4*>(pt + off);
+    x = make_uint4(addmod(x.x, y.x, q), addmod(x.y, y.y, q), addmod(x.z, y.z, q), addmod(x.w, y.w, q));
+  }
+  *reinterpret_cast<uint4*>(out + t * so + off) = x;
+}
+
 __global__ void k_pmult(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
                         size_t so) {
   const int t = blockIdx.y / n, i = blockIdx.y % n;
@@ -252,6 +266,13 @@ void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint
                  size_t sb, size_t so, cudaStream_t st) {
   const int th = 64;
   k_hadd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, b, out, n, sa, sb, so);
+  count_launch(1);
+}
+
+void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+                 size_t so, cudaStream_t st) {
+  const int th = 64;
+  k_padd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, sa, so);
   count_launch(1);
 }
 

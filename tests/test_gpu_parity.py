@@ -197,7 +197,7 @@ def test_rescale_matches_oracle(K, O, name, n_q):
 
 # ----------------------------------------------------- a9: HAdd / PMult ---
 
-def test_hadd_pmult_match_oracle(K, O):
+def test_hadd_pmult_padd_match_oracle(K, O):
     ctx, P = get(K, O, "n16d3")
     n_q = 5
     x, y = rand_ct(P, n_q, 17), rand_ct(P, n_q, 19)
@@ -210,6 +210,9 @@ def test_hadd_pmult_match_oracle(K, O):
         assert np.array_equal(K.ckks_ct_export(ctx, out, P.n)[0], O.hadd(x, y, P.q[:n_q]))
         K.ckks_pmult(ctx, cx, p, out)
         assert np.array_equal(K.ckks_ct_export(ctx, out, P.n)[0], O.pmult(x, pt, P.q[:n_q]))
+        K.ckks_padd(ctx, cx, p, out)
+        zero = np.zeros_like(pt)
+        assert np.array_equal(K.ckks_ct_export(ctx, out, P.n)[0], O.hadd(x, np.stack([pt, zero]), P.q[:n_q]))
         K.ckks_hadd(ctx, cx, cy, cx)   # in place
         assert np.array_equal(K.ckks_ct_export(ctx, cx, P.n)[0], O.hadd(x, y, P.q[:n_q]))
     finally:
