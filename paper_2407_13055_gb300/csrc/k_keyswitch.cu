@@ -3,21 +3,23 @@
 // is split at its coefficient-domain midpoint, which only exists between the
 // two column phases, so the pipeline alternates:
 //
-//   prep    (stream): input d, a1*a2 (tensor) or phi_k(a) (automorphism)    -> S
-//   rows^-1 (rows)  : iNTT row phase of S, in place
+//   rows^-1 (rows)  : input d, a1*a2 (tensor) or phi_k(a) (automorphism)
+//                     formed while loading, iNTT row phase                  -> S
 //   C1      (cols)  : iNTT col phase, * N^-1 (Q_j/q_i)^-1, BConv (Eq. 2) to
 //                     every prime outside digit j, NTT col phase            -> T
 //   rows    (rows)  : NTT row phase of every T limb, in place
 //   KeyMult (stream): acc_u = sum_j ModUp_j * evk_j[u] (Par. 1)            -> A
 //   rows^-1 (rows)  : iNTT row phase of the P limbs of A                     -> S
 //   C2      (cols)  : iNTT col phase, * N^-1 (P/p_k)^-1, BConv P -> Q, NTT col -> T
-//   rows    (rows)  : NTT row phase of T, in place
-//   epilogue(stream): (acc - z) P^-1 + (d0, d1) or (phi(b), 0)              -> out
+//   rows    (rows)  : NTT row phase of T, then the epilogue
+//                     (acc - z) P^-1 + (d0, d1) or (phi(b), 0)               -> out
 //
 // Row kernels (rows.cuh) hold W-word rows in registers with their twiddles
-// loaded up front; column kernels hold a tile of TC columns; streaming kernels
-// do the NTT-domain element-wise work with 128-bit accesses at full
-// occupancy. Constants are folded as in the paper's Seq. 2 (N^-1 into the
+// loaded up front, and take the element-wise step before (input preparation)
+// or after (ModDown and rescale epilogues) the transform as a functor, so
+// those values never make a round trip through memory; column kernels hold a
+// tile of TC columns; the KeyMult kernel streams the evaluation key with
+// 128-bit accesses at full occupancy. Constants are folded as in the paper's Seq. 2 (N^-1 into the
 // BConv constant, 2^32 into the BConv matrix). The BConv product uses the
 // paper's lazy reduction (Sec. 4.2).
 #include "geo.cuh"
@@ -375,14 +377,6 @@ __device__ __forceinline__ void ks_input4(const DevParams& dp, const KsArgs& a, 
   }
 }
 
-__global__ void k_ks_prep(DevParams dp, KsArgs a, uint32_t* S) {
-  const int i = blockIdx.y;
-  const uint32_t p0 = stream_pos();
-  uint32_t v[4];
-  ks_input4(dp, a, i, p0, v);
-  store_vec<4>(S + ((size_t)i << dp.log_n) + p0, v);
-}
-
 // KeyMult + MAC over the D digits for extended limb t (Par. 1): the digit's
 // own limbs are the input itself (ModUp copies them), the others come from
 // the NTT'd ModUp output T[j][t]. All loads of a thread are issued before any
@@ -446,43 +440,6 @@ static void launch_keymult(int digits, dim3 g, int th, cudaStream_t st, const De
       break;
   }
 }
-
-// ModDown epilogue: out_u[i] = (A_u[i] - T_u[i]) P^-1 + extra_u[i], with
-// extra = (d0, d1) recomputed from the inputs (HMult) or (phi_k(b), 0) (HRot).
-__global__ void k_ks_epilogue(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
-  const int n = a.n;
-  const int u = blockIdx.y / n, i = blockIdx.y % n;
-  const PrimeConst P = dp.pc[i];
-  const uint2 pinv = dp.ks.dn_pinv[i];
-  const uint32_t p0 = stream_pos();
-  const size_t off = ((size_t)i << dp.log_n) + p0;
-  uint32_t z[4], acc[4];
-  load_vec<4>(z, T + ((size_t)(u * n + i) << dp.log_n) + p0);
-  load_vec<4>(acc, A + u * a_stride + off);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q);
-  if (a.extra == 1) {
-    uint32_t b1[4], b2[4];
-    load_vec<4>(b1, a.x0 + off);
-    load_vec<4>(b2, a.x1 + off);
-    if (u == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) z[k] = addm(z[k], mulmod(b1[k], b2[k], P), P.q);
-    } else {
-      uint32_t a1[4], a2[4];
-      load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
-      load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) z[k] = addm(z[k], addm(mulmod(a1[k], b2[k], P), mulmod(a2[k], b1[k], P), P.q), P.q);
-    }
-  } else if (a.extra == 2 && u == 0) {
-    const uint32_t* sb = a.x0 + ((size_t)i << dp.log_n);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) z[k] = addm(z[k], __ldg(sb + auto_src(p0 + k, a.galois, dp.log_n)), P.q);
-  }
-  store_vec<4>(a.out + u * a.out_stride + off, z);
-}
-
 
 // Linear transform, KeyMult + MAC of every rotated term in one kernel
 // (Par. 5): for extended limb t,
@@ -611,22 +568,9 @@ __device__ __forceinline__ void ks_extra4(const DevParams& dp, const KsArgs& a, 
   }
 }
 
-// ModDown output of the top limb l only (both polys): V_u = (A_u[l] - T_u) P^-1 + extra_u[l].
-__global__ void k_ks_epilogue_top(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride,
-                                  uint32_t* V) {
-  const int u = blockIdx.y, top = a.n - 1;
-  const PrimeConst P = dp.pc[top];
-  const uint2 pinv = dp.ks.dn_pinv[top];
-  const uint32_t p0 = stream_pos();
-  uint32_t z[4], acc[4], e[4];
-  load_vec<4>(z, T + ((size_t)u << dp.log_n) + p0);
-  load_vec<4>(acc, A + u * a_stride + ((size_t)top << dp.log_n) + p0);
-  ks_extra4(dp, a, u, top, p0, P, e);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = addm(csub(shoup(acc[k] - z[k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
-  store_vec<4>(V + ((size_t)u << dp.log_n) + p0, z);
-}
-
+// The rescaled ModDown epilogue stays a streaming kernel: it re-forms d0/d1
+// from four input limbs, whose loads a row kernel at its occupancy cannot
+// hide (fused into the NTT rows it measured 60 us against 24 + 21 us apart).
 // Rescaled ModDown output, limbs i < l: (A_u[i] - w_u[i]) (P q_l)^-1 + extra_u[i] q_l^-1.
 __global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
   const int top = a.n - 1;
@@ -645,23 +589,108 @@ __global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, cons
   store_vec<4>(a.out + u * a.out_stride + off, w);
 }
 
-// Rescale epilogue: out_u[i] = (c_u[i] - r_u[i]) q_l^-1, r = NTT of the
-// centered top limb reduced modulo q_i.
-__global__ void k_rs_epilogue(DevParams dp, const uint32_t* in, size_t sin, int n, const uint32_t* T,
-                              uint32_t* out, size_t sout) {
-  const int top = n - 1;
-  const int u = blockIdx.y / top, i = blockIdx.y % top;
-  const PrimeConst P = dp.pc[i];
-  const uint2 qinv = dp.ks.rs_qinv[top * dp.L + i];
-  const uint32_t p0 = stream_pos();
-  const size_t off = ((size_t)i << dp.log_n) + p0;
-  uint32_t z[4], c[4];
-  load_vec<4>(z, T + ((size_t)(u * top + i) << dp.log_n) + p0);
-  load_vec<4>(c, in + u * sin + off);
+// ---------------------------------------------------------------------------
+// Row-kernel sources and epilogues (the streaming steps fused into the row
+// phases): a thread handles positions pos0 .. pos0 + E - 1 of launch limb y,
+// four at a time.
+// ---------------------------------------------------------------------------
+
+// Key-switch input before the iNTT rows: d, a1 a2 or phi_k(a) at limb y.
+struct SrcKsInput {
+  KsArgs a;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = csub(shoup(c[k] - z[k] + P.q, qinv.x, qinv.y, P.q), P.q);
-  store_vec<4>(out + u * sout + off, z);
-}
+    for (int c = 0; c < E / 4; ++c) {
+      uint32_t v[4];
+      ks_input4(dp, a, y, pos0 + 4 * c, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[4 * c + k] = v[k];
+    }
+  }
+};
+
+// ModDown epilogue after the NTT rows of z (launch limb y = u n + i):
+// out_u[i] = (A_u[i] - z) P^-1 + extra_u[i].
+struct EpiModDown {
+  KsArgs a;
+  const uint32_t* A;
+  size_t a_stride;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int n = a.n, u = y / n, i = y % n;
+    const PrimeConst P = dp.pc[i];
+    const uint2 pinv = dp.ks.dn_pinv[i];
+    const size_t limb = (size_t)i << dp.log_n;
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      const uint32_t p = pos0 + 4 * c;
+      uint32_t acc[4], e[4], z[4];
+      load_vec<4>(acc, A + u * a_stride + limb + p);
+      ks_extra4(dp, a, u, i, p, P, e);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
+      store_vec<4>(a.out + u * a.out_stride + limb + p, z);
+    }
+  }
+};
+
+// Top limb of the fused ModDown + rescale (launch limb y = u):
+// V_u = (A_u[l] - z) P^-1 + extra_u[l].
+struct EpiModDownTop {
+  KsArgs a;
+  const uint32_t* A;
+  size_t a_stride;
+  uint32_t* V;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int u = y, top = a.n - 1;
+    const PrimeConst P = dp.pc[top];
+    const uint2 pinv = dp.ks.dn_pinv[top];
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      const uint32_t p = pos0 + 4 * c;
+      uint32_t acc[4], e[4], z[4];
+      load_vec<4>(acc, A + u * a_stride + ((size_t)top << dp.log_n) + p);
+      ks_extra4(dp, a, u, top, p, P, e);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
+      store_vec<4>(V + ((size_t)u << dp.log_n) + p, z);
+    }
+  }
+};
+
+// Rescale after the NTT rows of r (launch limb y = u top + i):
+// out_u[i] = (c_u[i] - r) q_l^-1.
+struct EpiRescale {
+  const uint32_t* in;
+  size_t sin;
+  int top;
+  uint32_t* out;
+  size_t sout;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int u = y / top, i = y % top;
+    const PrimeConst P = dp.pc[i];
+    const uint2 qinv = dp.ks.rs_qinv[top * dp.L + i];
+    const size_t limb = (size_t)i << dp.log_n;
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      const uint32_t p = pos0 + 4 * c;
+      uint32_t cv[4], z[4];
+      load_vec<4>(cv, in + u * sin + limb + p);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z[k] = csub(shoup(cv[k] - x[4 * c + k] + P.q, qinv.x, qinv.y, P.q), P.q);
+      store_vec<4>(out + u * sout + limb + p, z);
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Launchers
@@ -840,20 +869,16 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_MODDOWN_COLS);
   LimbMap top_map{nullptr, 0, 1, 1, dp.L};
   top_map.fixed = top;
-  launch_rows_g<G>(dp, false, T2, T2, 2, top_map, false, st);
+  launch_rows_fwd<G>(dp, T2, EpiModDownTop{a, A, a_stride, V}, 2, top_map, st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
-  dim3 g;
-  int th;
-  stream_grid(dp.log_n, 2, g, th);
-  k_ks_epilogue_top<<<g, th, 0, st>>>(dp, a, T2, A, a_stride, V);
-  count_launch(1);
-  prof_mark(sc, st, P_KS_EPILOGUE);
   launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
   prof_mark(sc, st, P_RS_IN_ROWS);
   launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, n, default_shape<G>(2)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_g<G>(dp, false, T3, T3, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
   prof_mark(sc, st, P_RS_ROWS);
+  dim3 g;
+  int th;
   stream_grid(dp.log_n, 2 * top, g, th);
   k_ks_epilogue_rs<<<g, th, 0, st>>>(dp, a, T3, A, a_stride);
   count_launch(1);
@@ -871,14 +896,8 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
   launch_moddown_cols<G>(dp, n, sc, pick_shape<G>(sc, CK_MODDOWN, n, default_shape<G>(2)), st);
   prof_mark(sc, st, P_MODDOWN_COLS);
-  launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+  launch_rows_fwd<G>(dp, sc.T, EpiModDown{a, A, a_stride}, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
-  dim3 g;
-  int th;
-  stream_grid(dp.log_n, 2 * n, g, th);
-  k_ks_epilogue<<<g, th, 0, st>>>(dp, a, sc.T, A, a_stride);
-    count_launch(1);
-  prof_mark(sc, st, P_KS_EPILOGUE);
 }
 
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
@@ -890,11 +909,7 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
   int th;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
-    stream_grid(dp.log_n, n, g, th);
-    k_ks_prep<<<g, th, 0, st>>>(dp, a, sc.S);
-    count_launch(1);
-    prof_mark(sc, st, P_KS_PREP);
-    launch_rows_g<G>(dp, true, sc.S, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+    launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
     launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
     prof_mark(sc, st, P_MODUP_COLS);
@@ -1106,14 +1121,9 @@ void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, 
     k_rs_cols<G><<<dim3(tiles, 2, gr), G::CT, 0, st>>>(dp, n, sc.S, sc.T, gr);
     count_launch(1);
     prof_mark(sc, st, P_RS_COLS);
-    launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
+    launch_rows_fwd<G>(dp, sc.T, EpiRescale{in, sin, top, out, sout}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L},
+                       st);
     prof_mark(sc, st, P_RS_ROWS);
-    dim3 g;
-    int th;
-    stream_grid(dp.log_n, 2 * top, g, th);
-    k_rs_epilogue<<<g, th, 0, st>>>(dp, in, sin, n, sc.T, out, sout);
-    count_launch(1);
-    prof_mark(sc, st, P_RS_EPILOGUE);
   });
 }
 

@@ -136,12 +136,37 @@ __device__ __forceinline__ void load_pass_b_twiddles(uint2 (&tw)[E - 1], const u
   }
 }
 
+// Where a forward row phase puts its results, and where an inverse row phase
+// gets its inputs. A thread holds the E consecutive device positions
+// pos0 .. pos0 + E - 1 of its row (B layout: pos0 = h W + E jj) of launch
+// limb y, whose data limb and prime are lm = map(y). The plain forms store to
+// / load from a limb array; the key-switch kernels supply fused ones (input
+// preparation before the iNTT, ModDown and rescale epilogues after the NTT).
+struct RowStore {
+  uint32_t* dst;
+  int compact;  // write launch limb y at dst + y N instead of at data limb lm.x
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2 lm,
+                                             uint32_t pos0) const {
+    const size_t dl = compact ? (size_t)y : (size_t)lm.x;
+    store_vec<E>(dst + (dl << dp.log_n) + pos0, x);
+  }
+};
+
+struct RowLoad {
+  const uint32_t* src;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int, int2 lm,
+                                             uint32_t pos0) const {
+    load_vec<E>(x, src + ((size_t)lm.x << dp.log_n) + pos0);
+  }
+};
+
 // Forward row phase: src in A layout (column-phase output, natural
-// positions), dst in B layout, values normalized to [0, q). dst_compact:
-// write limb y at dst + y N instead of at the source limb index.
-template <class G>
-__global__ void __launch_bounds__(G::RT) k_rows_fwd_g(DevParams dp, const uint32_t* src, uint32_t* dst,
-                                                      LimbMap map, int dst_compact) {
+// positions); the epilogue receives the B-layout results normalized to
+// [0, q).
+template <class G, class Epi>
+__global__ void __launch_bounds__(G::RT) k_rows_fwd_t(DevParams dp, const uint32_t* src, Epi epi, LimbMap map) {
   __shared__ uint32_t buf[G::RPC * G::ROWBUF];
   __shared__ uint2 twa[G::RPC * (G::ER - 1)];
   const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
@@ -171,15 +196,15 @@ __global__ void __launch_bounds__(G::RT) k_rows_fwd_g(DevParams dp, const uint32
 #pragma unroll
     for (int i = 0; i < G::ER; ++i) x[i] = normalize<false>(x[i], q);
   }
-  const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
-  store_vec<G::ER>(dst + (dl << dp.log_n) + (size_t)h * G::W + G::ER * jj, x);
+  epi(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * G::W + G::ER * jj));
 }
 
-// Inverse row phase: src in B layout (NTT domain), dst in A layout, lazy
-// range [0, 2q) (the column phase that follows accepts it).
-template <class G>
-__global__ void __launch_bounds__(G::RT) k_rows_inv_g(DevParams dp, const uint32_t* src, uint32_t* dst,
-                                                      LimbMap map, int dst_compact) {
+// Inverse row phase: the source gives B-layout values in [0, q) (NTT domain);
+// dst in A layout, lazy range [0, 2q) (the column phase that follows accepts
+// it). dst_compact: write limb y at dst + y N instead of at data limb lm.x.
+template <class G, class Src>
+__global__ void __launch_bounds__(G::RT) k_rows_inv_t(DevParams dp, Src src, uint32_t* dst, LimbMap map,
+                                                      int dst_compact) {
   __shared__ uint32_t buf[G::RPC * G::ROWBUF];
   __shared__ uint2 twa[G::RPC * (G::ER - 1)];
   const int r = threadIdx.x / G::ER, jj = threadIdx.x % G::ER;
@@ -190,7 +215,7 @@ __global__ void __launch_bounds__(G::RT) k_rows_inv_g(DevParams dp, const uint32
   uint2 twb[G::ER - 1];
   load_pass_b_twiddles<G::ER, G::H>(twb, itw, h, jj);
   uint32_t x[G::ER];
-  load_vec<G::ER>(x, src + ((size_t)lm.x << dp.log_n) + (size_t)h * G::W + G::ER * jj);
+  src(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * G::W + G::ER * jj));
   uint2* tr = twa + r * (G::ER - 1);
   stage_row_twiddles<G::ER, G::H>(tr, itw, h, jj);
   uint32_t* b = buf + r * G::ROWBUF;
@@ -209,14 +234,27 @@ __global__ void __launch_bounds__(G::RT) k_rows_inv_g(DevParams dp, const uint32
   for (int i = 0; i < G::ER; ++i) o[jj + G::ER * i] = x[i];
 }
 
+template <class G, class Epi>
+inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi& epi, int limbs, LimbMap map,
+                            cudaStream_t st) {
+  if (limbs <= 0) return;
+  k_rows_fwd_t<G, Epi><<<dim3(G::H / G::RPC, limbs), G::RT, 0, st>>>(dp, src, epi, map);
+  count_launch(1);
+}
+
+template <class G, class Src>
+inline void launch_rows_inv(const DevParams& dp, const Src& srcf, uint32_t* dst, int limbs, LimbMap map,
+                            bool dst_compact, cudaStream_t st) {
+  if (limbs <= 0) return;
+  k_rows_inv_t<G, Src><<<dim3(G::H / G::RPC, limbs), G::RT, 0, st>>>(dp, srcf, dst, map, dst_compact ? 1 : 0);
+  count_launch(1);
+}
+
 template <class G>
 inline void launch_rows_g(const DevParams& dp, bool inverse, const uint32_t* src, uint32_t* dst, int limbs,
                           LimbMap map, bool dst_compact, cudaStream_t st) {
-  if (limbs <= 0) return;
-  const dim3 grid(G::H / G::RPC, limbs);
-  if (inverse) k_rows_inv_g<G><<<grid, G::RT, 0, st>>>(dp, src, dst, map, dst_compact ? 1 : 0);
-  else k_rows_fwd_g<G><<<grid, G::RT, 0, st>>>(dp, src, dst, map, dst_compact ? 1 : 0);
-  count_launch(1);
+  if (inverse) launch_rows_inv<G>(dp, RowLoad{src}, dst, limbs, map, dst_compact, st);
+  else launch_rows_fwd<G>(dp, src, RowStore{dst, dst_compact ? 1 : 0}, limbs, map, st);
 }
 
 }  // namespace ckks
