@@ -270,9 +270,10 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
 /* --- launch-shape fine-tuning (Sec. 4.2, "Fine-tuning"; Sec. 6) ---
  * The three BConv column kernels (ModUp conversion, ModDown conversion,
  * fused ModDown + rescale conversion) can run in several launch shapes
- * (tc, sl, z): column-tile width tc in {4, 8} columns, sl in {2, 4, 8}
- * thread slices per block sharing the tile, and z in 1..4 blocks per tile
- * splitting the conversion targets. Every shape computes identical values;
+ * (tc, sl, z, tp): column-tile width tc in {4, 8} columns, sl in {2, 4, 8}
+ * thread slices per block sharing the tile, z in 1..4 blocks per tile
+ * splitting the conversion targets, and tp in {1, 2} targets converted per
+ * pass over the shared inputs. Every shape computes identical values;
  * only time changes. A context and its clones share one table of shapes per
  * (kernel, level); levels without an entry use a fixed rule. */
 #define CKKS_COL_MODUP 0
@@ -286,11 +287,11 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
 int ckks_tune(ckks_ctx* ctx, int level, int reps);
 /* Tuned shape of `kernel` at `level` and its mean launch time in
  * microseconds; *tc = 0 when the level has no entry. */
-int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, float* us);
-/* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4; at N = 2^8
- * only tc = 8, since a slice must be whole warps), or clears the entry with
- * tc = 0. Changes no value any operation computes. */
-int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z);
+int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us);
+/* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4, tp in
+ * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps), or
+ * clears the entry with tc = 0. Changes no value any operation computes. */
+int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp);
 
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */

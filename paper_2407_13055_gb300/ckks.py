@@ -118,8 +118,8 @@ _SIGS = {
     "ckks_batch_run": (_i, [_vp]),
     "ckks_batch_destroy": (None, [_vp]),
     "ckks_tune": (_i, [_vp, _i, _i]),
-    "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
-    "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i]),
+    "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
+    "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -414,14 +414,15 @@ def ckks_tune(ctx, level: int, reps: int = 5):
 
 
 def ckks_tune_get(ctx, kernel: int, level: int):
-    """(tc, sl, z, microseconds) of the tuned shape; tc = 0 when untuned."""
-    tc, sl, z, us = C.c_int(), C.c_int(), C.c_int(), C.c_float()
-    check(ctx, lib.ckks_tune_get(ctx, kernel, level, C.byref(tc), C.byref(sl), C.byref(z), C.byref(us)))
-    return tc.value, sl.value, z.value, us.value
+    """(tc, sl, z, tp, microseconds) of the tuned shape; tc = 0 when untuned."""
+    tc, sl, z, tp, us = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_float()
+    check(ctx, lib.ckks_tune_get(ctx, kernel, level, C.byref(tc), C.byref(sl), C.byref(z), C.byref(tp),
+                                 C.byref(us)))
+    return tc.value, sl.value, z.value, tp.value, us.value
 
 
-def ckks_tune_set(ctx, kernel: int, level: int, tc: int, sl: int = 4, z: int = 1):
-    check(ctx, lib.ckks_tune_set(ctx, kernel, level, tc, sl, z))
+def ckks_tune_set(ctx, kernel: int, level: int, tc: int, sl: int = 4, z: int = 1, tp: int = 1):
+    check(ctx, lib.ckks_tune_set(ctx, kernel, level, tc, sl, z, tp))
 
 
 CKKS_PROF_KERNELS = 13

@@ -188,30 +188,32 @@ int ckks_tune(ckks_ctx* ctx, int level, int reps) {
   return CKKS_OK;
 }
 
-int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, float* us) {
-  if (!ctx || !ctx->tune || !tc || !sl || !z || !us) return CKKS_EINVAL;
+int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us) {
+  if (!ctx || !ctx->tune || !tc || !sl || !z || !tp || !us) return CKKS_EINVAL;
   if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
   if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   const ckks::ColShape s = ctx->tune->get(kernel, level + 1);
   *tc = s.tc;
   *sl = s.sl;
   *z = s.z;
+  *tp = s.tp;
   *us = ctx->tune->time_us(kernel, level + 1);
   return CKKS_OK;
 }
 
-int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z) {
+int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp) {
   if (!ctx || !ctx->tune) return CKKS_EINVAL;
   if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
   if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   ckks::ColShape s;
   if (tc != 0) {
-    if (!ckks::col_shape_supported(ctx->dp.log_n, tc, sl, z))
-      return fail(ctx, CKKS_EINVAL, "tune: shape (%d, %d, %d) not supported at N = 2^%d", tc, sl, z,
+    if (!ckks::col_shape_supported(ctx->dp.log_n, tc, sl, z, tp))
+      return fail(ctx, CKKS_EINVAL, "tune: shape (%d, %d, %d, %d) not supported at N = 2^%d", tc, sl, z, tp,
                   ctx->dp.log_n);
     s.tc = tc;
     s.sl = sl;
     s.z = z;
+    s.tp = tp;
   }
   ctx->tune->set(kernel, level + 1, s, 0.f);
   return CKKS_OK;

@@ -1,0 +1,496 @@
+// Column phase of the key switch: every ModSwitch (iNTT -> BConv -> NTT,
+// Alg. 1) runs its coefficient-domain middle inside one column kernel. A block
+// holds a tile of TC columns x H rows; its slices of TC * EC threads share the
+// tile's centered inputs in shared memory and convert the targets between
+// them. Launch shapes (tile width, slices, target split, targets per pass)
+// are chosen at run time; the launchers are instantiated per geometry in
+// separate translation units (k_cols_*.cu) so that the variants compile in
+// parallel.
+#pragma once
+#include <map>
+#include <mutex>
+#include <type_traits>
+
+#include "geo.cuh"
+#include "internal.h"
+
+namespace ckks {
+
+namespace {
+
+__device__ __forceinline__ uint32_t addm(uint32_t a, uint32_t b, uint32_t q) { return csub(a + b, q); }
+
+__device__ __forceinline__ int prime_of(int t, int n, int L) { return t < n ? t : L + (t - n); }
+
+// BConv of EC coefficient-domain values per thread: out[i] = sum_k y[k][i] *
+// mat[k] reduced modulo p (Eq. 2 with the 2^32 factor folded into mat).
+// y is in shared memory: y4[(k * EC/4 + i/4) * NT + pos]. Lazy reduction as
+// in Sec. 4.2: |y|, |mat| < p/2 bound each product by 2^29 p, so eight of
+// them and then four more after each range reduction stay below 2^63. The
+// range reduction folds the high word back with 2^32 = r1c (mod p):
+// acc = lo + hi * r1c, |acc| < 2^30 p + 2^32, which also meets the signed
+// Montgomery reduction's input range [-p 2^31, p 2^31).
+__device__ __forceinline__ int64_t fold(int64_t a, int32_t r1c) {
+  return (int64_t)(uint32_t)a + (int64_t)(int32_t)(a >> 32) * (int64_t)r1c;
+}
+
+template <int EC, int NT>
+__device__ __forceinline__ void mac4(int64_t (&acc)[EC], const int4* __restrict__ y4, int pos, int k, int64_t b) {
+#pragma unroll
+  for (int i4 = 0; i4 < EC / 4; ++i4) {
+    const int4 v = y4[(k * (EC / 4) + i4) * NT + pos];
+    acc[4 * i4 + 0] += (int64_t)v.x * b;
+    acc[4 * i4 + 1] += (int64_t)v.y * b;
+    acc[4 * i4 + 2] += (int64_t)v.z * b;
+    acc[4 * i4 + 3] += (int64_t)v.w * b;
+  }
+}
+
+// Chunks of four products, unrolled: the bound 2^29 p per product allows
+// eight before the first range reduction and four after each one, so the
+// fold runs after every chunk but the first, and once at the end.
+template <int EC, int NT>
+__device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, int pos, int K,
+                                                 const int32_t* __restrict__ mat, const PrimeConst& P,
+                                                 uint32_t (&out)[EC]) {
+  int64_t acc[EC];
+#pragma unroll
+  for (int i = 0; i < EC; ++i) acc[i] = 0;
+  int k = 0;
+  for (; k + 4 <= K; k += 4) {
+    const int64_t b0 = __ldg(mat + k), b1 = __ldg(mat + k + 1), b2 = __ldg(mat + k + 2), b3 = __ldg(mat + k + 3);
+    mac4<EC, NT>(acc, y4, pos, k, b0);
+    mac4<EC, NT>(acc, y4, pos, k + 1, b1);
+    mac4<EC, NT>(acc, y4, pos, k + 2, b2);
+    mac4<EC, NT>(acc, y4, pos, k + 3, b3);
+    if (k >= 4) {
+#pragma unroll
+      for (int i = 0; i < EC; ++i) acc[i] = fold(acc[i], P.r1c);
+    }
+  }
+  for (; k < K; ++k) mac4<EC, NT>(acc, y4, pos, k, (int64_t)__ldg(mat + k));
+#pragma unroll
+  for (int i = 0; i < EC; ++i) out[i] = fix_signed(smr(fold(acc[i], P.r1c), P.q, P.m), P.q);
+}
+
+// Two targets per pass: each shared-memory read of y feeds both sums, which
+// halves the shared-memory traffic of the conversion at the cost of a second
+// set of accumulators.
+template <int EC, int NT>
+__device__ __forceinline__ void mac4x2(int64_t (&a0)[EC], int64_t (&a1)[EC], const int4* __restrict__ y4, int pos,
+                                       int k, int64_t b0, int64_t b1) {
+#pragma unroll
+  for (int i4 = 0; i4 < EC / 4; ++i4) {
+    const int4 v = y4[(k * (EC / 4) + i4) * NT + pos];
+    a0[4 * i4 + 0] += (int64_t)v.x * b0;
+    a0[4 * i4 + 1] += (int64_t)v.y * b0;
+    a0[4 * i4 + 2] += (int64_t)v.z * b0;
+    a0[4 * i4 + 3] += (int64_t)v.w * b0;
+    a1[4 * i4 + 0] += (int64_t)v.x * b1;
+    a1[4 * i4 + 1] += (int64_t)v.y * b1;
+    a1[4 * i4 + 2] += (int64_t)v.z * b1;
+    a1[4 * i4 + 3] += (int64_t)v.w * b1;
+  }
+}
+
+template <int EC, int NT>
+__device__ __forceinline__ void bconv_accumulate2(const int4* __restrict__ y4, int pos, int K,
+                                                  const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
+                                                  const PrimeConst& P0, const PrimeConst& P1, uint32_t (&o0)[EC],
+                                                  uint32_t (&o1)[EC]) {
+  int64_t a0[EC], a1[EC];
+#pragma unroll
+  for (int i = 0; i < EC; ++i) a0[i] = a1[i] = 0;
+  int k = 0;
+  for (; k + 4 <= K; k += 4) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      mac4x2<EC, NT>(a0, a1, y4, pos, k + kk, (int64_t)__ldg(m0 + k + kk), (int64_t)__ldg(m1 + k + kk));
+    if (k >= 4) {
+#pragma unroll
+      for (int i = 0; i < EC; ++i) {
+        a0[i] = fold(a0[i], P0.r1c);
+        a1[i] = fold(a1[i], P1.r1c);
+      }
+    }
+  }
+  for (; k < K; ++k) mac4x2<EC, NT>(a0, a1, y4, pos, k, (int64_t)__ldg(m0 + k), (int64_t)__ldg(m1 + k));
+#pragma unroll
+  for (int i = 0; i < EC; ++i) {
+    o0[i] = fix_signed(smr(fold(a0[i], P0.r1c), P0.q, P0.m), P0.q);
+    o1[i] = fix_signed(smr(fold(a1[i], P1.r1c), P1.q, P1.m), P1.q);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Column kernels
+// ---------------------------------------------------------------------------
+
+// Column kernels. A block covers a tile of TC columns x H rows and is split
+// into GS slices of CT = TC * EC threads; position pos = (jj, c) of a slice
+// owns EC elements of one column. The slices share the coefficient-domain
+// tile: slice s finishes the iNTT of input limbs k = s, s + GS, ..., then
+// (after one block barrier) handles targets m = s, s + GS, ...; each slice
+// synchronizes its own transposes with a named barrier.
+template <class G, int TC>
+struct ColTile {
+  static constexpr int EC = G::EC, H = G::H, W = G::W;
+  static constexpr int CT = TC * EC;
+  static constexpr int BUF = (H + EC) * TC;
+};
+
+template <class G, int TC>
+__device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* src, size_t src_stride, int K,
+                                           int id0, const uint2* cin, int4* y4, uint32_t* colbuf, int l, int jj,
+                                           int c, int pos, int slice, int GS, uint32_t* ycopy = nullptr) {
+  using CTL = ColTile<G, TC>;
+  for (int k = slice; k < K; k += GS) {
+    const int id = id0 + k;
+    const uint32_t q = dp.pc[id].q;
+    const uint2* itw = dp.itw + ((size_t)id << dp.log_n);
+    const uint32_t* s = src + k * src_stride;
+    uint32_t x[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
+    if (q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
+    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
+    const uint2 w = cin[k];
+    int32_t y[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], w.x, w.y, q), q), q);
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+    if (ycopy) {
+      uint32_t* yc = ycopy + ((size_t)k << dp.log_n);
+#pragma unroll
+      for (int i = 0; i < G::EC; ++i) yc[(jj + G::EC * i) * G::W + l] = (uint32_t)y[i];
+    }
+  }
+}
+
+// NTT column phase of one converted target; store B layout (lazy range).
+template <class G, int TC>
+__device__ __forceinline__ void col_ntt_store(const DevParams& dp, uint32_t (&x)[G::EC], int id, uint32_t* dst,
+                                              uint32_t* colbuf, int l, int jj, int c, int slice) {
+  using CTL = ColTile<G, TC>;
+  const uint32_t q = dp.pc[id].q;
+  const uint2* tw = dp.tw + ((size_t)id << dp.log_n);
+  if (q < (1u << 30)) col_fwd<G::EC, TC, true>(x, colbuf, tw, jj, c, q, slice + 1, CTL::CT);
+  else col_fwd<G::EC, TC, false>(x, colbuf, tw, jj, c, q, slice + 1, CTL::CT);
+#pragma unroll
+  for (int i = 0; i < G::EC; ++i) dst[(G::EC * jj + i) * G::W + l] = x[i];
+}
+
+// BConv each target m = m0, m0 + step, ... (mat row, prime id, destination
+// from tgt), then its NTT column phase; TP = 2 converts targets in pairs.
+template <class G, int TC, int TP, class Target>
+__device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4, int K, int M, int m0, int step,
+                                            Target tgt, uint32_t* colbuf, int l, int jj, int c, int pos,
+                                            int slice) {
+  using CTL = ColTile<G, TC>;
+  int m = m0;
+  if (TP == 2) {
+    for (; m + step < M; m += 2 * step) {
+      const int32_t *r0, *r1;
+      int i0, i1;
+      uint32_t *d0, *d1;
+      tgt(m, r0, i0, d0);
+      tgt(m + step, r1, i1, d1);
+      const PrimeConst P0 = dp.pc[i0], P1 = dp.pc[i1];
+      uint32_t x0[G::EC], x1[G::EC];
+      bconv_accumulate2<G::EC, CTL::CT>(y4, pos, K, r0, r1, P0, P1, x0, x1);
+      col_ntt_store<G, TC>(dp, x0, i0, d0, colbuf, l, jj, c, slice);
+      col_ntt_store<G, TC>(dp, x1, i1, d1, colbuf, l, jj, c, slice);
+    }
+  }
+  for (; m < M; m += step) {
+    const int32_t* row;
+    int id;
+    uint32_t* dst;
+    tgt(m, row, id, dst);
+    const PrimeConst P = dp.pc[id];
+    uint32_t x[G::EC];
+    bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, row, P, x);
+    col_ntt_store<G, TC>(dp, x, id, dst, colbuf, l, jj, c, slice);
+  }
+}
+
+// Launch shape (section "Launch shapes" below): SL slices per block; blockIdx.z
+// of gridDim.z blocks per column tile takes targets m = slice + SL z (mod
+// SL gridDim.z), all of them recomputing the shared input iNTT columns.
+
+// C1: ModUp column kernel. grid (W/TC, digits, Z), block SL * CT.
+template <class G, int TC, int SL, int TP>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
+                                                                               const uint32_t* S, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int j = blockIdx.y;
+  const int alpha = dp.alpha, L = dp.L, ext = n + alpha;
+  const int lo = j * alpha, hi = min(n, lo + alpha), K = hi - lo;
+  const int2 off = dp.ks.up_off[n * dp.dnum + j];
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, lo, dp.ks.up_cin + off.x, y4,
+                    colbuf, l, jj, c, pos, slice, SL);
+  __syncthreads();
+  const int M = ext - K;
+  auto tgt = [&](int m, const int32_t*& row, int& id, uint32_t*& dst) {
+    const int t = m < lo ? m : m + K;  // skip the digit's own limbs
+    row = dp.ks.up_mat + off.y + t * K;
+    id = prime_of(t, n, L);
+    dst = T + ((size_t)(j * ext + t) << dp.log_n);
+  };
+  col_targets<G, TC, TP>(dp, y4, K, M, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
+}
+
+// C2: ModDown column kernel. grid (W/TC, 2 polys, Z). Input S [2][alpha][N]
+// (P limbs after the row-phase iNTT); output T [2][n][N].
+template <class G, int TC, int SL, int TP>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
+                                                                                 const uint32_t* S, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  const int alpha = dp.alpha;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
+                    y4, colbuf, l, jj, c, pos, slice, SL);
+  __syncthreads();
+  auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.dn_mat + i * alpha;
+    id = i;
+    dst = T + ((size_t)(u * n + i) << dp.log_n);
+  };
+  col_targets<G, TC, TP>(dp, y4, alpha, n, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
+                         slice);
+}
+
+
+// ModDown fused with rescaling, first column kernel: the P limbs' iNTT
+// columns give the centered coefficients y (kept in Y for the second
+// kernel); only the top limb q_l is converted here (its ModDown output is
+// needed in the coefficient domain before the others). grid (W/TC, 2 polys).
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
+                                                                                        const uint32_t* S,
+                                                                                        uint32_t* T, uint32_t* Y) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  const int alpha = dp.alpha, top = n - 1;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
+                    y4, colbuf, l, jj, c, pos, slice, SL, Y + ((size_t)(u * alpha) << dp.log_n));
+  __syncthreads();
+  auto tgt = [&](int, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.dn_mat + top * alpha;
+    id = top;
+    dst = T + ((size_t)u << dp.log_n);
+  };
+  col_targets<G, TC, 1>(dp, y4, alpha, 1, slice, SL, tgt, colbuf, l, jj, c, pos, slice);
+}
+
+// ModDown fused with rescaling, second column kernel: iNTT columns of the top
+// limb's ModDown output (row phase already applied) give c_l, centered; with
+// the stored y it forms K = alpha + 1 inputs whose conversion to q_i (matrix
+// rs_mat: the ModDown row plus [P]_{q_i}) is w_i = z_i + P [c_l]_{q_i}; then
+// the NTT columns. grid (W/TC, 2 polys, Z); targets i < l.
+template <class G, int TC, int SL, int TP>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
+                                                                                  const uint32_t* V,
+                                                                                  const uint32_t* Y, uint32_t* T) {
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  const int alpha = dp.alpha, top = n - 1, K = alpha + 1;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  // stored centered P-limb coefficients, A layout along h
+  for (int k = slice; k < alpha; k += SL) {
+    const uint32_t* yk = Y + ((size_t)(u * alpha + k) << dp.log_n);
+    int32_t y[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) y[i] = (int32_t)yk[(jj + G::EC * i) * G::W + l];
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+  }
+  if (slice == SL - 1) {
+    const PrimeConst Pt = dp.pc[top];
+    const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
+    const uint32_t* s = V + ((size_t)u << dp.log_n);
+    uint32_t x[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
+    if (Pt.q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    int32_t y[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], Pt.ninv, Pt.ninv_sh, Pt.q), Pt.q), Pt.q);
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos] =
+          make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
+  }
+  __syncthreads();
+  auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = dp.ks.rs_mat + i * K;
+    id = i;
+    dst = T + ((size_t)(u * top + i) << dp.log_n);
+  };
+  col_targets<G, TC, TP>(dp, y4, K, top, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
+}
+
+template <class G, int TC, int SL>
+static size_t col_smem_bytes(int K) {
+  using CTL = ColTile<G, TC>;
+  return (size_t)K * (G::EC / 4) * CTL::CT * sizeof(int4) + (size_t)SL * CTL::BUF * sizeof(uint32_t);
+}
+
+// Raise a kernel's dynamic shared-memory limit once per process (and only
+// when a larger size is needed), so that steady-state launches and graph
+// captures issue no attribute calls.
+static void set_col_smem(const void* f, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = done[f];
+  if (bytes > cur) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch shapes of the column kernels
+//
+// A shape is (tc, sl, z): column-tile width, slices per block and blocks per
+// tile. Every shape computes the same values (only the division of targets
+// among threads changes), so the choice affects time alone. The default
+// follows a fixed rule; ckks_tune times every candidate at a level and
+// records the fastest in the context's tuning table, which launches read.
+// ---------------------------------------------------------------------------
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// Calls f(IC<TC>, IC<SL>, IC<TP>) for a shape's compile-time parameters.
+template <class F>
+static bool with_shape(const ColShape& s, F f) {
+  auto sl_tp = [&](auto tc) {
+    switch (s.sl * 4 + s.tp) {
+      case 2 * 4 + 1: f(tc, IC<2>{}, IC<1>{}); return true;
+      case 4 * 4 + 1: f(tc, IC<4>{}, IC<1>{}); return true;
+      case 8 * 4 + 1: f(tc, IC<8>{}, IC<1>{}); return true;
+      case 2 * 4 + 2: f(tc, IC<2>{}, IC<2>{}); return true;
+      case 4 * 4 + 2: f(tc, IC<4>{}, IC<2>{}); return true;
+      case 8 * 4 + 2: f(tc, IC<8>{}, IC<2>{}); return true;
+      default: return false;
+    }
+  };
+  if (s.tc == 8) return sl_tp(IC<8>{});
+  if (s.tc == 4) return sl_tp(IC<4>{});
+  return false;
+}
+
+// Default shape: 8 columns (32-byte row segments) when that already gives
+// two blocks per SM, else 4 to double the block count; four slices; no split.
+template <class G>
+static ColShape default_shape(int blocks_per_tile_column) {
+  ColShape s;
+  s.tc = ((G::W / 8) * blocks_per_tile_column >= 2 * 152 || G::W / 4 < 16) ? 8 : 4;
+  s.sl = 4;
+  s.z = 1;
+  s.tp = 1;
+  return s;
+}
+
+// A shape is launchable when the tile width divides the row, a slice is a
+// whole number of warps (each slice synchronizes its transposes with a named
+// barrier, whose thread count must be a multiple of the warp size) and the
+// parameters are among the compiled ones.
+template <class G>
+static bool shape_ok(const ColShape& s) {
+  return (s.tc == 4 || s.tc == 8) && G::W % s.tc == 0 && (s.tc * G::EC) % 32 == 0 &&
+         (s.sl == 2 || s.sl == 4 || s.sl == 8) && s.z >= 1 && s.z <= 4 && (s.tp == 1 || s.tp == 2);
+}
+
+template <class G>
+static ColShape pick_shape(const Scratch& sc, ColKernel k, int n, const ColShape& def) {
+  if (sc.tune) {
+    const ColShape s = sc.tune->get(k, n);
+    if (s.valid() && shape_ok<G>(s)) return s;
+  }
+  return def;
+}
+
+
+template <class G>
+void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, const ColShape& s,
+                              cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl, auto tp) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_modup_cols<G, TC, SL, TP>, sm);
+    k_ks_modup_cols<G, TC, SL, TP><<<dim3(G::W / TC, digits, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S,
+                                                                                                      sc.T);
+    count_launch(1);
+  });
+}
+
+template <class G>
+void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, const ColShape& s, cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl, auto tp) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_moddown_cols<G, TC, SL, TP>, sm);
+    k_ks_moddown_cols<G, TC, SL, TP><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S,
+                                                                                                   sc.T);
+    count_launch(1);
+  });
+}
+
+template <class G>
+void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint32_t* Y, cudaStream_t st) {
+  ColShape s = default_shape<G>(2);
+  with_shape(s, [&](auto tc, auto sl, auto) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    set_col_smem((const void*)k_ks_moddown_cols_top<G, TC, SL>, sm);
+    k_ks_moddown_cols_top<G, TC, SL><<<dim3(G::W / TC, 2), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T,
+                                                                                             Y);
+    count_launch(1);
+  });
+}
+
+template <class G>
+void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
+                                 const ColShape& s, cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl, auto tp) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
+    set_col_smem((const void*)k_rs_cols_fused<G, TC, SL, TP>, sm);
+    k_rs_cols_fused<G, TC, SL, TP><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, V, Y, T3);
+    count_launch(1);
+  });
+}
+
+}  // namespace ckks

@@ -140,12 +140,13 @@ void count_launch(int k);
 // Scratch buffers owned by the context.
 // Column kernels with a tunable launch shape, and the table of tuned shapes
 // (one per context, shared with its clones). A shape is (tc, sl, z): column
-// tile width, slices per block, blocks per tile. Entries are atomics so that
+// tile width, slices per block, blocks per tile, plus tp, the conversion
+// targets per pass. Entries are atomics so that
 // lanes on other host threads may read while ckks_tune writes.
 enum ColKernel { CK_MODUP = 0, CK_MODDOWN = 1, CK_RS_FUSED = 2, CK_COUNT = 3 };
 
 struct ColShape {
-  int tc = 0, sl = 0, z = 0;
+  int tc = 0, sl = 0, z = 0, tp = 1;  // tp: conversion targets per pass (1 or 2)
   bool valid() const { return tc > 0; }
 };
 
@@ -167,6 +168,7 @@ struct Tuning {
       s.tc = (int)(v & 0xff);
       s.sl = (int)((v >> 8) & 0xff);
       s.z = (int)((v >> 16) & 0xff);
+      s.tp = (int)((v >> 24) & 0xff);
     }
     return s;
   }
@@ -175,7 +177,8 @@ struct Tuning {
   }
   void set(int k, int n, const ColShape& s, float t_us) {
     if (k < 0 || k >= CK_COUNT || n < 1 || n > max_n) return;
-    const uint32_t v = s.valid() ? (uint32_t)s.tc | ((uint32_t)s.sl << 8) | ((uint32_t)s.z << 16) : 0u;
+    const uint32_t v =
+        s.valid() ? (uint32_t)s.tc | ((uint32_t)s.sl << 8) | ((uint32_t)s.z << 16) | ((uint32_t)s.tp << 24) : 0u;
     packed[k * (max_n + 1) + n].store(v, std::memory_order_relaxed);
     us[k * (max_n + 1) + n].store(t_us);
   }
@@ -226,7 +229,7 @@ void launch_smr(const DevParams& dp, const int64_t* x, int32_t* y, int n, int pr
 
 // ---- launchers (k_keyswitch.cu) ----
 // Full key switch of one polynomial (mode), result written per a.extra.
-bool col_shape_supported(int log_n, int tc, int sl, int z);
+bool col_shape_supported(int log_n, int tc, int sl, int z, int tp);
 int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int reps, cudaStream_t st);
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st);

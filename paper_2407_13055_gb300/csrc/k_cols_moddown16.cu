@@ -1,0 +1,9 @@
+// ModDown column kernels at N = 2^16, every launch shape.
+#include "cols.cuh"
+
+namespace ckks {
+
+template void launch_moddown_cols<Geo<8, 32>>(const DevParams&, int, const Scratch&, const ColShape&, cudaStream_t);
+template void launch_moddown_cols_top<Geo<8, 32>>(const DevParams&, int, const Scratch&, uint32_t*, cudaStream_t);
+
+}  // namespace ckks

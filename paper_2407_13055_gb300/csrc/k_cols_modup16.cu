@@ -1,0 +1,8 @@
+// ModUp column kernels at N = 2^16, every launch shape.
+#include "cols.cuh"
+
+namespace ckks {
+
+template void launch_modup_cols<Geo<8, 32>>(const DevParams&, int, int, const Scratch&, const ColShape&, cudaStream_t);
+
+}  // namespace ckks

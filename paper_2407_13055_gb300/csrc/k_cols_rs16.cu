@@ -1,0 +1,9 @@
+// Fused ModDown + rescale column kernels at N = 2^16, every launch shape.
+#include "cols.cuh"
+
+namespace ckks {
+
+template void launch_rs_cols_fused<Geo<8, 32>>(const DevParams&, int, const uint32_t*, const uint32_t*, uint32_t*,
+                                               const ColShape&, cudaStream_t);
+
+}  // namespace ckks

@@ -442,7 +442,7 @@ def test_linear_transform_rejects_bad_calls(K, O):
 
 # --------------------------------------------- launch-shape fine-tuning ---
 
-SHAPES = [(tc, sl, z) for tc in (8, 4) for sl in (2, 4, 8) for z in (1, 2, 3, 4)]
+SHAPES = [(tc, sl, z, tp) for tc in (8, 4) for sl in (2, 4, 8) for z in (1, 2, 3, 4) for tp in (1, 2)]
 
 
 def _set_all(K, ctx, level, shape):
@@ -474,7 +474,7 @@ def test_every_column_shape_gives_identical_results(K, O, name, n_q):
             got, _ = _run_hrot(K, O, ctx, P, c1, evk, 1)
             assert np.array_equal(got, want_r), shape
     finally:
-        _set_all(K, ctx, n_q - 1, (0, 4, 1))
+        _set_all(K, ctx, n_q - 1, (0, 4, 1, 1))
 
 
 def test_tune_records_a_shape_and_keeps_results(K, O):
@@ -483,8 +483,8 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
     K.ckks_tune(ctx, n_q - 1, 2)
     try:
         for kern in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
-            tc, sl, z, us = K.ckks_tune_get(ctx, kern, n_q - 1)
-            assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and us > 0
+            tc, sl, z, tp, us = K.ckks_tune_get(ctx, kern, n_q - 1)
+            assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and tp in (1, 2) and us > 0
         # a clone shares the table
         import torch
         s = torch.cuda.Stream()
@@ -498,17 +498,17 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
         got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
         assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
     finally:
-        _set_all(K, ctx, n_q - 1, (0, 4, 1))
+        _set_all(K, ctx, n_q - 1, (0, 4, 1, 1))
 
 
 def test_tune_rejects_bad_arguments(K, O):
     ctx, P = get(K, O, "tiny")
     with pytest.raises(RuntimeError):
-        K.ckks_tune_set(ctx, 0, 0, 16, 4, 1)
+        K.ckks_tune_set(ctx, 0, 0, 16, 4, 1, 1)
     with pytest.raises(RuntimeError):
-        K.ckks_tune_set(ctx, 3, 0, 8, 4, 1)
+        K.ckks_tune_set(ctx, 3, 0, 8, 4, 1, 1)
     with pytest.raises(RuntimeError):
-        K.ckks_tune_set(ctx, 0, P.L, 8, 4, 1)
+        K.ckks_tune_set(ctx, 0, P.L, 8, 4, 1, 1)
     with pytest.raises(RuntimeError):
         K.ckks_tune(ctx, 0, 0)
 
