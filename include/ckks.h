@@ -154,6 +154,14 @@ int ckks_ct_export(ckks_ctx* ctx, const ckks_ct* ct, uint32_t* host, size_t word
                    double* scale);
 /* Re-import host residues into an existing ciphertext (no allocation). */
 int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* ct, const uint32_t* host, int level, double scale);
+/* Asynchronous forms for pipelining host transfers with work on other
+ * streams: they only enqueue the copy and the layout permutation on the
+ * context stream (staged through the context's scratch, so in order with its
+ * operations). `host` should be page-locked for the copy to be asynchronous;
+ * the caller must keep it unchanged (upload) or not read it (export) until
+ * the stream has passed the copy (ckks_sync or a CUDA event). */
+int ckks_ct_upload_async(ckks_ctx* ctx, ckks_ct* ct, const uint32_t* host, int level, double scale);
+int ckks_ct_export_async(ckks_ctx* ctx, const ckks_ct* ct, uint32_t* host, size_t words);
 /* Borrow a device buffer of [2][level+1][N] uint32 in the internal layout. */
 int ckks_ct_wrap_device(ckks_ctx* ctx, uint32_t* dev_ptr, int level, double scale, ckks_ct** out);
 int ckks_ct_info(const ckks_ct* ct, int* level, double* scale, uint32_t** dev_ptr);

@@ -98,6 +98,8 @@ _SIGS = {
     "ckks_ct_import": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
     "ckks_ct_export": (_i, [_vp, _vp, _vp, _sz, _P(_i), _P(_d)]),
     "ckks_ct_upload": (_i, [_vp, _vp, _vp, _i, _d]),
+    "ckks_ct_upload_async": (_i, [_vp, _vp, _vp, _i, _d]),
+    "ckks_ct_export_async": (_i, [_vp, _vp, _vp, _sz]),
     "ckks_ct_wrap_device": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
     "ckks_ct_info": (_i, [_vp, _P(_i), _P(_d), _P(_vp)]),
     "ckks_pt_import": (_i, [_vp, _vp, _i, _d, _P(_vp)]),
@@ -284,6 +286,24 @@ def ckks_ct_import(ctx, host, level: int, scale: float):
 def ckks_ct_upload(ctx, ct, host, level: int, scale: float):
     h = _u32(host)
     check(ctx, lib.ckks_ct_upload(ctx, ct, _ptr(h), level, scale))
+
+
+def _pinned_view(host) -> np.ndarray:
+    """The caller's own uint32 buffer (no temporary copy may be handed to an
+    asynchronous transfer)."""
+    if not (isinstance(host, np.ndarray) and host.dtype == np.uint32 and host.flags["C_CONTIGUOUS"]):
+        raise TypeError("asynchronous transfers need a C-contiguous uint32 array (page-locked for overlap)")
+    return host
+
+
+def ckks_ct_upload_async(ctx, ct, host, level: int, scale: float):
+    h = _pinned_view(host)
+    check(ctx, lib.ckks_ct_upload_async(ctx, ct, _ptr(h), level, scale))
+
+
+def ckks_ct_export_async(ctx, ct, host):
+    h = _pinned_view(host)
+    check(ctx, lib.ckks_ct_export_async(ctx, ct, _ptr(h), h.size))
 
 
 def ckks_ct_info(ct):

@@ -316,7 +316,7 @@ int ckks_ct_create(ckks_ctx* ctx, int cap_level, ckks_ct** out) {
   return CKKS_OK;
 }
 
-int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale) {
+static int ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale, bool sync) {
   if (!ctx || !c || !host) return CKKS_EINVAL;
   if (level < 0 || level > c->cap_level) return fail(ctx, CKKS_ELEVEL, "level %d exceeds capacity %d", level, c->cap_level);
   const int n = level + 1;
@@ -333,8 +333,16 @@ int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, d
   c->level = level;
   c->scale = scale;
   int rc = launched(ctx, "permute");
-  if (rc) return rc;
+  if (rc || !sync) return rc;
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload");
+}
+
+int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale) {
+  return ct_upload(ctx, c, host, level, scale, true);
+}
+
+int ckks_ct_upload_async(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale) {
+  return ct_upload(ctx, c, host, level, scale, false);
 }
 
 int ckks_ct_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_ct** out) {
@@ -349,7 +357,8 @@ int ckks_ct_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
   return rc;
 }
 
-int ckks_ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words, int* level, double* scale) {
+static int ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words, int* level, double* scale,
+                     bool sync) {
   if (!ctx || !c || !host) return CKKS_EINVAL;
   const int n = c->level + 1;
   const size_t lw = limb_words(ctx);
@@ -362,10 +371,18 @@ int ckks_ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words
   rc = cuda_check(ctx, cudaMemcpyAsync(host, stage, 2 * (size_t)n * lw * 4, cudaMemcpyDeviceToHost, ctx->stream),
                   "export");
   if (rc) return rc;
-  rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "export");
+  if (sync) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "export");
   if (level) *level = c->level;
   if (scale) *scale = c->scale;
   return rc;
+}
+
+int ckks_ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words, int* level, double* scale) {
+  return ct_export(ctx, c, host, words, level, scale, true);
+}
+
+int ckks_ct_export_async(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words) {
+  return ct_export(ctx, c, host, words, nullptr, nullptr, false);
 }
 
 int ckks_ct_wrap_device(ckks_ctx* ctx, uint32_t* dev_ptr, int level, double scale, ckks_ct** out) {

@@ -513,6 +513,31 @@ def test_tune_rejects_bad_arguments(K, O):
         K.ckks_tune(ctx, 0, 0)
 
 
+def test_async_transfers_match_synchronous_ones(K, O):
+    """Asynchronous upload / export on a lane give the same residues as the
+    synchronous calls."""
+    import torch
+    ctx, P = get(K, O, "n16d3")
+    n_q = 6
+    c = rand_ct(P, n_q, 131)
+    host = torch.empty((2, n_q, P.n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    host[:] = c
+    out = torch.empty((2, n_q, P.n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    s = torch.cuda.Stream()
+    lane = K.ckks_ctx_clone(ctx, s.cuda_stream)
+    ct = K.ckks_ct_create(ctx, n_q - 1)
+    try:
+        K.ckks_ct_upload_async(lane, ct, host, n_q - 1, 2.0**30)
+        K.ckks_ct_export_async(lane, ct, out)
+        K.ckks_sync(lane)
+        assert np.array_equal(out, c)
+        with pytest.raises(TypeError):
+            K.ckks_ct_upload_async(lane, ct, c.astype(np.int64), n_q - 1, 1.0)
+    finally:
+        K.ckks_free(ct)
+        K.ckks_ctx_destroy(lane)
+
+
 # ----------------------------------------- decryption after operations ---
 
 @pytest.mark.parametrize("name", ["toyT1", "toyT2", "n16d3"])
