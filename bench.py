@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 LOG_N, L, DNUM, ALPHA, HW, SCALE = 16, 40, 3, 14, 192, 2.0**30
 LEVEL = L - 1
-BATCH = 16
+BATCH = 256          # distinct resident ciphertexts per timed step (5.4 GB, far above L2)
+E2E_HOST = 16        # distinct pinned host ciphertexts cycled by the end-to-end leg
 METRIC = "HMult/HRot key-switch ops/sec at N=2^16 (1 GB300)"
 UNIT = "key-switch ops/s"
 LIMB_BYTES = (1 << LOG_N) * 4
@@ -45,7 +46,7 @@ def workload_config(extra=None):
                     "HMult+relin+rescale and HRot(1) per ciphertext",
         "N": 1 << LOG_N, "limbs": L, "alpha": ALPHA, "dnum": DNUM, "level": LEVEL, "secret_hw": HW,
         "batch_ciphertexts": BATCH, "ops_per_step": 2 * BATCH,
-        "l2": "inputs larger than L2 (16 ciphertexts = 335 MB + 2 keys = 170 MB, rotated; no flush)",
+        "l2": "inputs larger than L2 (256 ciphertexts = 5.4 GB + 2 keys = 170 MB, rotated; no flush)",
     }
     if extra:
         cfg.update(extra)
@@ -256,6 +257,7 @@ def run_native(args, rank, world, local_rank):
     q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, seed=rank,
                             stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 1000 + rank)
     rk = K.ckks_keygen_relin(ctx, sk, 2000 + rank)
     gk = K.ckks_keygen_rot(ctx, sk, 1, 3000 + rank)
@@ -330,8 +332,8 @@ def run_native(args, rank, world, local_rank):
     n = 1 << LOG_N
     nl = args.lanes
     pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
-    host_in = [pinned((2, L, n)) for _ in range(BATCH)]
-    for i in range(BATCH):
+    host_in = [pinned((2, L, n)) for _ in range(E2E_HOST)]
+    for i in range(E2E_HOST):
         K.ckks_ct_export(ctx, cts[i], n, out=host_in[i])
     lane_a = [K.ckks_ct_create(ctx, LEVEL) for _ in range(nl)]
     lane_b = [K.ckks_ct_create(ctx, LEVEL) for _ in range(nl)]
@@ -339,9 +341,9 @@ def run_native(args, rank, world, local_rank):
     host_out_r = [pinned((2, L, n)) for _ in range(nl)]
 
     def e2e_step():
-        for i in range(BATCH):
+        for i in range(E2E_HOST):
             l = i % nl
-            ln, j = lanes[l], (i + 1) % BATCH
+            ln, j = lanes[l], (i + 1) % E2E_HOST
             K.ckks_ct_upload_async(ln, lane_a[l], host_in[i], LEVEL, SCALE)
             K.ckks_ct_upload_async(ln, lane_b[l], host_in[j], LEVEL, SCALE)
             K.ckks_hmult(ln, lane_a[l], lane_b[l], rk, K.CKKS_RESCALE, outs_m[l])
@@ -359,9 +361,10 @@ def run_native(args, rank, world, local_rank):
     barrier()
     e2e_dt = replicas.max_over_ranks(time.perf_counter() - t0)
     ct_bytes = 2 * L * n * 4
-    e2e = {"value": replicas.job_throughput(2 * BATCH * e2e_steps, 1e3 * e2e_dt, world), "unit": UNIT,
-           "h2d_bytes_per_step": BATCH * 3 * ct_bytes,
-           "d2h_bytes_per_step": BATCH * (ct_bytes * (L - 1) // L + ct_bytes),
+    e2e = {"value": replicas.job_throughput(2 * E2E_HOST * e2e_steps, 1e3 * e2e_dt, world), "unit": UNIT,
+           "h2d_bytes_per_step": E2E_HOST * 3 * ct_bytes,
+           "d2h_bytes_per_step": E2E_HOST * (ct_bytes * (L - 1) // L + ct_bytes),
+           "ops_per_step": 2 * E2E_HOST,
            "note": f"{nl} lanes, asynchronous copies from/to pinned host memory, wall clock"}
     for h in lane_a + lane_b:
         K.ckks_free(h)
@@ -402,6 +405,7 @@ def run_native(args, rank, world, local_rank):
         "config": workload_config({"parallelism": f"replicas{world}",
                                    "lanes": f"{args.lanes} concurrent CUDA streams (context clones), "
                                             "independent ciphertexts per lane",
+                                   "programmatic_dependent_launch": args.pdl,
                                    "column_shapes": ({k: list(v) for k, v in tuned[LEVEL].items()} if tuned
                                                      else "default rule")}),
         "one_lane": {"value": seq_ops_per_s, "unit": UNIT, "hmult_rescale_us": hmult_us, "hrot_us": hrot_us,
@@ -433,6 +437,7 @@ def run_batched(args, local_rank):
     stream = torch.cuda.current_stream()
     q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 11)
     rk = K.ckks_keygen_relin(ctx, sk, 12)
     gk = K.ckks_keygen_rot(ctx, sk, 1, 13)
@@ -493,6 +498,82 @@ def run_batched(args, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# single-op latency table: dnum in {1, 3, 5} x top / middle / bottom level
+# ----------------------------------------------------------------------------
+
+def run_latency(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = measured_peaks()
+    reps = max(50, args.steps)
+    flush = torch.empty(2 * 129 * (1 << 20) // 4 * 2, dtype=torch.int32, device="cuda")  # 2 x L2
+    rows = []
+    r_rand = 12345
+    for dnum in (1, 3, 5):
+        alpha = -(-L // dnum)
+        q, p = K.ckks_gen_primes(LOG_N, L, alpha)
+        ctx = K.ckks_ctx_create(LOG_N, q, p, dnum, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+        K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
+        sk = K.ckks_keygen_secret(ctx, 61)
+        rk = K.ckks_keygen_relin(ctx, sk, 62)
+        gks = {r: K.ckks_keygen_rot(ctx, sk, r, 63 + r % 1000) for r in (1, 5, r_rand)}
+        for level in (L - 1, 20, 1):
+            if not args.no_tune:
+                K.ckks_tune(ctx, level, 3)
+            a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(64, (1 << LOG_N) // 2), level, SCALE), 65)
+            b = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(66, (1 << LOG_N) // 2), level, SCALE), 67)
+            out = K.ckks_ct_create(ctx, level)
+            ops = {"hmult_rescale": lambda: K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, out),
+                   "hmult": lambda: K.ckks_hmult(ctx, a, b, rk, 0, out)}
+            for r in (1, 5, r_rand):
+                ops[f"hrot_{r}"] = (lambda r=r: K.ckks_hrot(ctx, a, r, gks[r], out))
+            n = level + 1
+            hm_b, hr_b = algorithmic_bytes(n, alpha)
+            for name, fn in ops.items():
+                res = {}
+                for mode in ("cold", "warm"):
+                    ts = []
+                    for _ in range(3):
+                        fn()
+                    for _ in range(reps):
+                        if mode == "cold":
+                            flush.add_(1)          # writes 2 x L2 between repetitions
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fn()
+                        e1.record(stream)
+                        e1.synchronize()
+                        ts.append(e0.elapsed_time(e1) * 1e3)
+                    res[mode] = float(np.median(ts))
+                alg = hr_b if name.startswith("hrot") else (hm_b if name == "hmult_rescale" else
+                                                              hm_b - 2 * (n - 1) * LIMB_BYTES + 2 * n * LIMB_BYTES)
+                rows.append({"dnum": dnum, "alpha": alpha, "level": level, "op": name,
+                             "median_us_cold_l2": res["cold"], "median_us_warm_l2": res["warm"],
+                             "algorithmic_mb": alg / 1e6,
+                             "hbm_frac_cold": alg / (res["cold"] * 1e-6) / 1e9 / peaks["hbm_gbs"]})
+            for h in (a, b, out):
+                K.ckks_free(h)
+        for h in list(gks.values()) + [sk, rk]:
+            K.ckks_free(h)
+        K.ckks_ctx_destroy(ctx)
+    top3 = [r for r in rows if r["dnum"] == 3 and r["level"] == L - 1 and r["op"] in ("hmult_rescale", "hrot_1")]
+    value = 2 / sum(r["median_us_cold_l2"] * 1e-6 for r in top3)
+    line = {"metric": "single-op key-switch latency at N=2^16 (1 GB300): median of >=50, cold and warm L2",
+            "value": value, "unit": "key-switch ops/s (one at a time, cold L2, dnum=3 top level)", "n_gpus": 1,
+            "steps": reps, "warmup": 3, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (fresh encryptions)",
+            "config": {"workload": "HMult (with and without rescale) and HRot (r = 1, 5, 12345) at levels 39 / 20 / 1 "
+                                   "for dnum = 1, 3, 5; cold L2 = a 2 x L2 buffer written between repetitions",
+                       "N": 1 << LOG_N, "limbs_top": L,
+                       "column_shapes": "default rule" if args.no_tune else "tuned per level"},
+            "table": rows, "hbm_peak": {"value": peaks["hbm_gbs"], "source": peak_kind}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
 # hoisted rotations: one ModUp shared by many rotations of one ciphertext
 # ----------------------------------------------------------------------------
 
@@ -504,6 +585,7 @@ def run_hoisted(args, local_rank):
     stream = torch.cuda.current_stream()
     q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 41)
     rots = list(range(1, 33))
     gks = [K.ckks_keygen_rot(ctx, sk, r, 500 + r) for r in rots]
@@ -584,6 +666,7 @@ def run_bootstrap(args, local_rank):
     stream = torch.cuda.current_stream()
     q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 51)
     spec = TraceSpec()
     slots = (1 << LOG_N) // 2
@@ -643,6 +726,7 @@ def run_serve(args, local_rank):
     stream = torch.cuda.current_stream()
     q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 21)
     rk = K.ckks_keygen_relin(ctx, sk, 22)
     n_keys = 64
@@ -713,14 +797,16 @@ def run_serve(args, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
+    ap.add_argument("--pdl", choices=["on", "off"], default="on",
+                    help="programmatic dependent launch for the key-switch kernels")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -739,6 +825,9 @@ def main():
         return
     if args.workload == "bootstrap":
         run_bootstrap(args, local_rank)
+        return
+    if args.workload == "latency":
+        run_latency(args, local_rank)
         return
     if world > 1:
         import torch

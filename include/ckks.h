@@ -275,6 +275,16 @@ void ckks_batch_destroy(ckks_batch* batch);
  * stream capture. Asynchronous on the context stream. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint32_t* out_dev);
 
+/* --- launch options ---
+ * CKKS_LAUNCH_PDL (default on): the key-switch kernels use programmatic
+ * dependent launch, so each one is scheduled and loads its twiddles and
+ * constants while its predecessor on the stream finishes (lower latency for
+ * one stream of operations). Its blocks then hold SM resources while they
+ * wait, which can cost throughput when several lanes share the GPU. A clone
+ * inherits its parent's flags when it is created. */
+#define CKKS_LAUNCH_PDL 1
+int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
+
 /* --- launch-shape fine-tuning (Sec. 4.2, "Fine-tuning"; Sec. 6) ---
  * The three BConv column kernels (ModUp conversion, ModDown conversion,
  * fused ModDown + rescale conversion) can run in several launch shapes

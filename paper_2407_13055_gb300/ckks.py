@@ -119,6 +119,7 @@ _SIGS = {
     "ckks_batch_create": (_i, [_vp, _vp, _i, _i, _i, _P(_vp)]),
     "ckks_batch_run": (_i, [_vp]),
     "ckks_batch_destroy": (None, [_vp]),
+    "ckks_set_launch_flags": (_i, [_vp, _i]),
     "ckks_tune": (_i, [_vp, _i, _i]),
     "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
     "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
@@ -427,6 +428,11 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
 
 
 CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED = 0, 1, 2
+CKKS_LAUNCH_PDL = 1
+
+
+def ckks_set_launch_flags(ctx, flags: int):
+    check(ctx, lib.ckks_set_launch_flags(ctx, flags))
 
 
 def ckks_tune(ctx, level: int, reps: int = 5):

@@ -132,6 +132,7 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   ctx->sc.prof = &ctx->prof;
   ctx->tune = std::make_shared<ckks::Tuning>(L);
   ctx->sc.tune = ctx->tune.get();
+  ctx->dp.pdl = 1;
   *out = ctx;
   return CKKS_OK;
 }
@@ -177,6 +178,12 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
+}
+
+int ckks_set_launch_flags(ckks_ctx* ctx, int flags) {
+  if (!ctx || (flags & ~CKKS_LAUNCH_PDL)) return CKKS_EINVAL;
+  ctx->dp.pdl = (flags & CKKS_LAUNCH_PDL) ? 1 : 0;
+  return CKKS_OK;
 }
 
 int ckks_tune(ckks_ctx* ctx, int level, int reps) {

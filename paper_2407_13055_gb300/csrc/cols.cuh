@@ -13,6 +13,7 @@
 
 #include "geo.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace ckks {
 
@@ -226,6 +227,8 @@ __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4,
 template <class G, int TC, int SL, int TP>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
                                                                                const uint32_t* S, uint32_t* T) {
+  pdl_wait();
+  pdl_trigger();
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
   const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
@@ -255,6 +258,8 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevPar
 template <class G, int TC, int SL, int TP>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
                                                                                  const uint32_t* S, uint32_t* T) {
+  pdl_wait();
+  pdl_trigger();
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
   const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
@@ -285,6 +290,8 @@ template <class G, int TC, int SL>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
                                                                                         const uint32_t* S,
                                                                                         uint32_t* T, uint32_t* Y) {
+  pdl_wait();
+  pdl_trigger();
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
   const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
@@ -314,6 +321,8 @@ template <class G, int TC, int SL, int TP>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
                                                                                   const uint32_t* V,
                                                                                   const uint32_t* Y, uint32_t* T) {
+  pdl_wait();
+  pdl_trigger();
   using CTL = ColTile<G, TC>;
   extern __shared__ int4 smem4[];
   const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
@@ -450,8 +459,8 @@ void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
     set_col_smem((const void*)k_ks_modup_cols<G, TC, SL, TP>, sm);
-    k_ks_modup_cols<G, TC, SL, TP><<<dim3(G::W / TC, digits, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S,
-                                                                                                      sc.T);
+    launch_pdl(dp.pdl, k_ks_modup_cols<G, TC, SL, TP>, dim3(G::W / TC, digits, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st,
+               dp, n, (const uint32_t*)sc.S, sc.T);
     count_launch(1);
   });
 }
@@ -462,8 +471,8 @@ void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, const Co
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
     set_col_smem((const void*)k_ks_moddown_cols<G, TC, SL, TP>, sm);
-    k_ks_moddown_cols<G, TC, SL, TP><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S,
-                                                                                                   sc.T);
+    launch_pdl(dp.pdl, k_ks_moddown_cols<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st,
+               dp, n, (const uint32_t*)sc.S, sc.T);
     count_launch(1);
   });
 }
@@ -475,8 +484,8 @@ void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
     set_col_smem((const void*)k_ks_moddown_cols_top<G, TC, SL>, sm);
-    k_ks_moddown_cols_top<G, TC, SL><<<dim3(G::W / TC, 2), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, sc.S, sc.T,
-                                                                                             Y);
+    launch_pdl(dp.pdl, k_ks_moddown_cols_top<G, TC, SL>, dim3(G::W / TC, 2), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
+               n, (const uint32_t*)sc.S, sc.T, Y);
     count_launch(1);
   });
 }
@@ -488,7 +497,8 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
     set_col_smem((const void*)k_rs_cols_fused<G, TC, SL, TP>, sm);
-    k_rs_cols_fused<G, TC, SL, TP><<<dim3(G::W / TC, 2, s.z), SL * ColTile<G, TC>::CT, sm, st>>>(dp, n, V, Y, T3);
+    launch_pdl(dp.pdl, k_rs_cols_fused<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
+               n, V, Y, T3);
     count_launch(1);
   });
 }

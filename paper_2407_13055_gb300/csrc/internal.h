@@ -49,6 +49,7 @@ struct DevParams {
   const uint2* tw;       // [L + alpha][N] forward twiddles (w, Shoup companion)
   const uint2* itw;      // [L + alpha][N] inverse twiddles
   KsTables ks;
+  int pdl;  // host-side launch option: key-switch kernels use programmatic dependent launch
 };
 
 // Limb -> prime id. Either an explicit device array, or the extended-
@@ -137,7 +138,6 @@ struct Prof {
 uint64_t launch_count();
 void count_launch(int k);
 
-// Scratch buffers owned by the context.
 // Column kernels with a tunable launch shape, and the table of tuned shapes
 // (one per context, shared with its clones). A shape is (tc, sl, z): column
 // tile width, slices per block, blocks per tile, plus tp, the conversion
@@ -187,6 +187,7 @@ struct Tuning {
   std::unique_ptr<std::atomic<float>[]> us;
 };
 
+// Scratch buffers owned by the context.
 struct Scratch {
   uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
   uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)

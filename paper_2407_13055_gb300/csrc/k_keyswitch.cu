@@ -26,6 +26,7 @@
 
 #include "cols.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 #include "rows.cuh"
 
 namespace ckks {
@@ -63,6 +64,8 @@ bool col_shape_supported(int log_n, int tc, int sl, int z, int tp) {
 template <class G>
 __global__ void __launch_bounds__(G::CT) k_rs_cols(DevParams dp, int n, const uint32_t* S, uint32_t* T,
                                                   int groups) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t colbuf[G::COLBUF];
   const int c = threadIdx.x % G::TC, jj = threadIdx.x / G::TC;
   const int l = blockIdx.x * G::TC + c;
@@ -136,6 +139,17 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
   const PrimeConst P = dp.pc[id];
   const uint32_t p0 = stream_pos();
   uint32_t x[D][4], e0[D][4], e1[D][4];
+  // the key was written long before the previous kernel: stream it before
+  // waiting for that kernel (programmatic dependent launch)
+  if (km_out != KM_MODUP) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      load_vec_stream<4>(e0[j], a.evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e1[j], a.evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const int lo = j * alpha, hi = min(n, lo + alpha);
@@ -156,11 +170,6 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
     for (int j = 0; j < D; ++j) store_vec<4>(km_dst + ((size_t)(j * ext + t) << dp.log_n) + p0, x[j]);
     return;
   }
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    load_vec_stream<4>(e0[j], a.evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
-    load_vec_stream<4>(e1[j], a.evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
-  }
   uint32_t acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int j = 0; j < D; ++j)
@@ -178,7 +187,7 @@ static void launch_keymult(int digits, dim3 g, int th, cudaStream_t st, const De
                            const uint32_t* T, uint32_t* A, int km_out, uint32_t* km_dst) {
   switch (digits) {
 #define CKKS_KM(D) \
-  case D: k_ks_keymult<D><<<g, th, 0, st>>>(dp, a, T, A, km_out, km_dst); break;
+  case D: launch_pdl(dp.pdl, k_ks_keymult<D>, g, dim3(th), 0, st, dp, a, T, A, km_out, km_dst); break;
     CKKS_KM(1) CKKS_KM(2) CKKS_KM(3) CKKS_KM(4) CKKS_KM(5) CKKS_KM(6) CKKS_KM(7) CKKS_KM(8)
 #undef CKKS_KM
     default:
@@ -194,6 +203,8 @@ static void launch_keymult(int digits, dim3 g, int th, cudaStream_t st, const De
 // the sum stays in Q_l P until one ModDown. A = [2][n + alpha][N].
 template <int D>
 __global__ void k_lt_keymult(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* T, uint32_t* A) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.y;
   const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
   const int id = prime_of(t, n, L);
@@ -240,7 +251,7 @@ static void launch_lt_keymult(int digits, dim3 g, int th, cudaStream_t st, const
                               const LtArgs& lt, const uint32_t* T, uint32_t* A) {
   switch (digits) {
 #define CKKS_LT(D) \
-  case D: k_lt_keymult<D><<<g, th, 0, st>>>(dp, a, lt, T, A); break;
+  case D: launch_pdl(dp.pdl, k_lt_keymult<D>, g, dim3(th), 0, st, dp, a, lt, T, A); break;
     CKKS_LT(1) CKKS_LT(2) CKKS_LT(3) CKKS_LT(4) CKKS_LT(5) CKKS_LT(6) CKKS_LT(7) CKKS_LT(8)
 #undef CKKS_LT
     default:
@@ -254,6 +265,8 @@ static void launch_lt_keymult(int digits, dim3 g, int th, cudaStream_t st, const
 // ks = 0 (no rotated term): the key-switch part is zero and A, Z are not read.
 __global__ void k_lt_epilogue(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* Z, const uint32_t* A,
                               size_t a_stride, int ks) {
+  pdl_wait();
+  pdl_trigger();
   const int n = a.n;
   const int u = blockIdx.y / n, i = blockIdx.y % n;
   const PrimeConst P = dp.pc[i];
@@ -318,6 +331,8 @@ __device__ __forceinline__ void ks_extra4(const DevParams& dp, const KsArgs& a, 
 // hide (fused into the NTT rows it measured 60 us against 24 + 21 us apart).
 // Rescaled ModDown output, limbs i < l: (A_u[i] - w_u[i]) (P q_l)^-1 + extra_u[i] q_l^-1.
 __global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
+  pdl_wait();
+  pdl_trigger();
   const int top = a.n - 1;
   const int u = blockIdx.y / top, i = blockIdx.y % top;
   const PrimeConst P = dp.pc[i];
@@ -492,7 +507,7 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   dim3 g;
   int th;
   stream_grid(dp.log_n, 2 * top, g, th);
-  k_ks_epilogue_rs<<<g, th, 0, st>>>(dp, a, T3, A, a_stride);
+  launch_pdl(dp.pdl, k_ks_epilogue_rs, g, dim3(th), 0, st, dp, a, (const uint32_t*)T3, A, a_stride);
   count_launch(1);
   prof_mark(sc, st, P_RS_EPILOGUE);
 }
@@ -701,7 +716,8 @@ void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArg
       prof_mark(sc, st, P_MODDOWN_ROWS);
     }
     stream_grid(dp.log_n, 2 * n, g, th);
-    k_lt_epilogue<<<g, th, 0, st>>>(dp, a, lt, down.T, sc.A, (size_t)ext * limb, lt.rotated > 0 ? 1 : 0);
+    launch_pdl(dp.pdl, k_lt_epilogue, g, dim3(th), 0, st, dp, a, lt, (const uint32_t*)down.T, (const uint32_t*)sc.A,
+               (size_t)ext * limb, lt.rotated > 0 ? 1 : 0);
     count_launch(1);
     prof_mark(sc, st, P_KS_EPILOGUE);
   });
@@ -731,7 +747,7 @@ void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, 
     prof_mark(sc, st, P_RS_IN_ROWS);
     const int tiles = G::W / G::TC;
     const int gr = groups_for(tiles * 2, top);
-    k_rs_cols<G><<<dim3(tiles, 2, gr), G::CT, 0, st>>>(dp, n, sc.S, sc.T, gr);
+    launch_pdl(dp.pdl, k_rs_cols<G>, dim3(tiles, 2, gr), dim3(G::CT), 0, st, dp, n, (const uint32_t*)sc.S, sc.T, gr);
     count_launch(1);
     prof_mark(sc, st, P_RS_COLS);
     launch_rows_fwd<G>(dp, sc.T, EpiRescale{in, sin, top, out, sout}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L},

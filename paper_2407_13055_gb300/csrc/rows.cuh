@@ -7,6 +7,7 @@
 #pragma once
 #include "geo.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace ckks {
 
@@ -164,7 +165,8 @@ struct RowLoad {
 
 // Forward row phase: src in A layout (column-phase output, natural
 // positions); the epilogue receives the B-layout results normalized to
-// [0, q).
+// [0, q). Launched with programmatic dependent launch: the twiddles are
+// loaded before waiting for the previous kernel.
 template <class G, class Epi>
 __global__ void __launch_bounds__(G::RT) k_rows_fwd_t(DevParams dp, const uint32_t* src, Epi epi, LimbMap map) {
   __shared__ uint32_t buf[G::RPC * G::ROWBUF];
@@ -176,12 +178,14 @@ __global__ void __launch_bounds__(G::RT) k_rows_fwd_t(DevParams dp, const uint32
   const uint2* tw = dp.tw + ((size_t)lm.y << dp.log_n);
   uint2 twb[G::ER - 1];
   load_pass_b_twiddles<G::ER, G::H>(twb, tw, h, jj);
+  uint2* tr = twa + r * (G::ER - 1);
+  stage_row_twiddles<G::ER, G::H>(tr, tw, h, jj);
+  pdl_wait();
+  pdl_trigger();
   const uint32_t* s = src + ((size_t)lm.x << dp.log_n) + (size_t)h * G::W;
   uint32_t x[G::ER];
 #pragma unroll
   for (int i = 0; i < G::ER; ++i) x[i] = s[jj + G::ER * i];
-  uint2* tr = twa + r * (G::ER - 1);
-  stage_row_twiddles<G::ER, G::H>(tr, tw, h, jj);
   uint32_t* b = buf + r * G::ROWBUF;
   if (q < (1u << 30)) {
     ct_pass_sm<G::ER, true>(x, tr, q);
@@ -214,10 +218,12 @@ __global__ void __launch_bounds__(G::RT) k_rows_inv_t(DevParams dp, Src src, uin
   const uint2* itw = dp.itw + ((size_t)lm.y << dp.log_n);
   uint2 twb[G::ER - 1];
   load_pass_b_twiddles<G::ER, G::H>(twb, itw, h, jj);
-  uint32_t x[G::ER];
-  src(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * G::W + G::ER * jj));
   uint2* tr = twa + r * (G::ER - 1);
   stage_row_twiddles<G::ER, G::H>(tr, itw, h, jj);
+  pdl_wait();
+  pdl_trigger();
+  uint32_t x[G::ER];
+  src(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * G::W + G::ER * jj));
   uint32_t* b = buf + r * G::ROWBUF;
   if (q < (1u << 30)) {
     gs_pass_reg<G::ER, true>(x, twb, q);
@@ -238,7 +244,7 @@ template <class G, class Epi>
 inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi& epi, int limbs, LimbMap map,
                             cudaStream_t st) {
   if (limbs <= 0) return;
-  k_rows_fwd_t<G, Epi><<<dim3(G::H / G::RPC, limbs), G::RT, 0, st>>>(dp, src, epi, map);
+  launch_pdl(dp.pdl, k_rows_fwd_t<G, Epi>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, src, epi, map);
   count_launch(1);
 }
 
@@ -246,7 +252,8 @@ template <class G, class Src>
 inline void launch_rows_inv(const DevParams& dp, const Src& srcf, uint32_t* dst, int limbs, LimbMap map,
                             bool dst_compact, cudaStream_t st) {
   if (limbs <= 0) return;
-  k_rows_inv_t<G, Src><<<dim3(G::H / G::RPC, limbs), G::RT, 0, st>>>(dp, srcf, dst, map, dst_compact ? 1 : 0);
+  launch_pdl(dp.pdl, k_rows_inv_t<G, Src>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, srcf, dst, map,
+             dst_compact ? 1 : 0);
   count_launch(1);
 }
 
