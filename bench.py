@@ -574,6 +574,77 @@ def run_latency(args, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# ablation: Table 3 on this GPU, and sequential fusion of ModDown + rescale
+# ----------------------------------------------------------------------------
+
+def run_ablation(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
+    peaks, _ = measured_peaks()
+    # (1) modular multiplication methods: 8 chains per thread, enough threads
+    # for many waves; every method must return the same values
+    n, rounds = 152 * 2048 * 8, 2048
+    rng = np.random.default_rng(1)
+    mm = {}
+    for pid, label in ((1, "30-bit q_1"), (0, "31-bit q_0")):
+        qq = int(q[pid])
+        a = rng.integers(0, qq, n, dtype=np.int64).astype(np.uint32)
+        b = int(rng.integers(1, qq))
+        ref = None
+        for m, name in ((K.CKKS_MODMUL_BARRETT, "barrett64"), (K.CKKS_MODMUL_MONTGOMERY, "montgomery"),
+                        (K.CKKS_MODMUL_SHOUP, "shoup"), (K.CKKS_MODMUL_SMR, "signed_montgomery")):
+            out, ms = K.ckks_bench_modmul(ctx, m, pid, b, a, rounds)
+            ref = out if ref is None else ref
+            gmm = n * rounds / (ms * 1e-3) / 1e9
+            mm.setdefault(label, {})[name] = {"gmodmul_s": gmm, "ms": ms, "agrees": bool(np.array_equal(out, ref)),
+                                              "modmul_per_sm_clk": gmm * 1e9 / (152 * peaks.get("sm_max_mhz", 2070.0)
+                                                                                * 1e6)}
+    # (2) sequential fusion: HMult with ModDown + rescale fused vs HMult then
+    # a separate rescale (top level, one stream, median of 50)
+    sk = K.ckks_keygen_secret(ctx, 71)
+    rk = K.ckks_keygen_relin(ctx, sk, 72)
+    if not args.no_tune:
+        K.ckks_tune(ctx, LEVEL, 3)
+    a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(73, (1 << LOG_N) // 2), LEVEL, SCALE), 74)
+    b = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(75, (1 << LOG_N) // 2), LEVEL, SCALE), 76)
+    mid, out = K.ckks_ct_create(ctx, LEVEL), K.ckks_ct_create(ctx, LEVEL)
+    forms = {"fused_moddown_rescale": lambda: K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, out),
+             "hmult_then_rescale": lambda: (K.ckks_hmult(ctx, a, b, rk, 0, mid), K.ckks_rescale(ctx, mid, out))}
+    seq = {}
+    for name, fn in forms.items():
+        ts = []
+        for _ in range(3):
+            fn()
+        for _ in range(max(50, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        seq[name] = float(np.median(ts))
+    best = max(v["gmodmul_s"] for v in mm["30-bit q_1"].values())
+    line = {"metric": "ablation on 1 GB300: modular multiplication methods (Table 3) and ModDown+rescale fusion",
+            "value": best, "unit": "Gmodmul/s (best method, 30-bit prime)", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{n} elements x {rounds} dependent modular products, 8 chains per thread; "
+                                   "HMult+relin at level 39 (dnum=3) with fused vs separate rescale"},
+            "modmul": mm, "seq_fusion_us": seq,
+            "seq_fusion_speedup": seq["hmult_then_rescale"] / seq["fused_moddown_rescale"]}
+    print(json.dumps(line), flush=True)
+    for h in (a, b, mid, out, sk, rk):
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
 # hoisted rotations: one ModUp shared by many rotations of one ciphertext
 # ----------------------------------------------------------------------------
 
@@ -802,7 +873,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",
@@ -828,6 +899,9 @@ def main():
         return
     if args.workload == "latency":
         run_latency(args, local_rank)
+        return
+    if args.workload == "ablation":
+        run_ablation(args, local_rank)
         return
     if world > 1:
         import torch

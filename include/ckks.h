@@ -311,6 +311,19 @@ int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z
  * clears the entry with tc = 0. Changes no value any operation computes. */
 int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp);
 
+/* --- Table 3 on this GPU: modular multiplication methods (Sec. 4.1) ---
+ * Runs out[i] = a[i] * b^rounds mod q (q = prime_id of the context) as eight
+ * independent chains per thread with one reduction method per call, and
+ * reports the timed kernel's milliseconds (one untimed warm-up run first).
+ * Every method returns exactly the same values. Inputs must be < q.
+ * Synchronous; allocates its own device buffers. */
+#define CKKS_MODMUL_BARRETT 0    /* 64-bit Barrett: mulwide, mulhi64, mullo64 */
+#define CKKS_MODMUL_MONTGOMERY 1 /* unsigned Montgomery: mulwide32, mullo32, mulwide32 + add64 */
+#define CKKS_MODMUL_SHOUP 2      /* Shoup (constant operand): mulhi32, 2 mullo32 */
+#define CKKS_MODMUL_SMR 3        /* signed Montgomery (Alg. 2): mulwide32, mullo32, mulhi32 */
+int ckks_bench_modmul(ckks_ctx* ctx, int method, int prime_id, uint32_t b, const uint32_t* a, int n, int rounds,
+                      uint32_t* out, float* ms);
+
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */
 #define CKKS_PROF_KERNELS 13

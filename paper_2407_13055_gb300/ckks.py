@@ -123,6 +123,7 @@ _SIGS = {
     "ckks_tune": (_i, [_vp, _i, _i]),
     "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
     "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
+    "ckks_bench_modmul": (_i, [_vp, _i, _i, _u32, _vp, _i, _i, _vp, _P(C.c_float)]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -449,6 +450,19 @@ def ckks_tune_get(ctx, kernel: int, level: int):
 
 def ckks_tune_set(ctx, kernel: int, level: int, tc: int, sl: int = 4, z: int = 1, tp: int = 1):
     check(ctx, lib.ckks_tune_set(ctx, kernel, level, tc, sl, z, tp))
+
+
+CKKS_MODMUL_BARRETT, CKKS_MODMUL_MONTGOMERY, CKKS_MODMUL_SHOUP, CKKS_MODMUL_SMR = 0, 1, 2, 3
+
+
+def ckks_bench_modmul(ctx, method: int, prime_id: int, b: int, a, rounds: int):
+    """(a * b^rounds mod q per element, kernel milliseconds)."""
+    a = _u32(a)
+    out = np.zeros_like(a)
+    ms = C.c_float()
+    check(ctx, lib.ckks_bench_modmul(ctx, method, prime_id, int(b), _ptr(a), a.size, rounds, _ptr(out),
+                                     C.byref(ms)))
+    return out, ms.value
 
 
 CKKS_PROF_KERNELS = 13

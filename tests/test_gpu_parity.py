@@ -513,6 +513,23 @@ def test_tune_rejects_bad_arguments(K, O):
         K.ckks_tune(ctx, 0, 0)
 
 
+@pytest.mark.parametrize("prime_id,rounds", [(0, 1), (1, 2), (5, 37), (39, 1000)])
+def test_modmul_methods_agree_with_big_integers(K, O, prime_id, rounds):
+    """Barrett, Montgomery, Shoup and signed Montgomery (Table 3) all give
+    a b^rounds mod q exactly (31-bit q_0 and 30-bit q_i)."""
+    ctx, P = get(K, O, "n16d3")
+    q = int(P.q[prime_id])
+    rng = np.random.default_rng(prime_id + rounds)
+    a = rng.integers(0, q, 5000, dtype=np.int64).astype(np.uint32)
+    a[:4] = [0, 1, q - 1, q // 2]
+    b = int(rng.integers(1, q))
+    want = np.array([(int(x) * pow(b, rounds, q)) % q for x in a], dtype=np.uint32)
+    for m in (K.CKKS_MODMUL_BARRETT, K.CKKS_MODMUL_MONTGOMERY, K.CKKS_MODMUL_SHOUP, K.CKKS_MODMUL_SMR):
+        got, ms = K.ckks_bench_modmul(ctx, m, prime_id, b, a, rounds)
+        assert np.array_equal(got, want), m
+        assert ms >= 0
+
+
 def test_async_transfers_match_synchronous_ones(K, O):
     """Asynchronous upload / export on a lane give the same residues as the
     synchronous calls."""
