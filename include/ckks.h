@@ -69,7 +69,17 @@ typedef struct ckks_evk ckks_evk;
  * q < 2^31 (Sec. 3). log_n must be 8, 12 or 16. scale is the default
  * encoding scale Delta; secret_hw is the Hamming weight of the ternary secret
  * drawn by ckks_keygen_secret (0 = uniform ternary); sigma is the error
- * standard deviation (3.2); seed seeds the library's own sampler. */
+ * standard deviation (3.2); seed seeds the library's own sampler.
+ *
+ * Levels. With n_levels = 0 (single rescaling), level l holds the primes
+ * q_0..q_l and rescaling drops q_l. With n_levels > 0, level l holds the
+ * contiguous window q[level_first[l] .. level_first[l] + level_count[l]) of
+ * the prime list, as in the 25-30 prime system with its inverted-terminal
+ * order (Sec. 3.2, Sec. 3.3), and rescaling from level l to l - 1 is
+ * rational (Sec. 3.1): the primes the lower window lacks are divided out and
+ * those it adds multiplied in. Key-switching digits are the fixed groups of
+ * n_p consecutive primes of the whole list, and the evaluation keys cover
+ * every prime, so one key serves every level (Sec. 3.2). */
 typedef struct {
   int log_n;
   int n_q;
@@ -81,6 +91,9 @@ typedef struct {
   int secret_hw;
   double sigma;
   uint64_t seed;
+  int n_levels;
+  const int* level_first;
+  const int* level_count;
 } ckks_params;
 
 /* Library's prime rule (Eq. 3 with q < 2^31): q_0 is the largest prime below
@@ -88,6 +101,19 @@ typedef struct {
  * decreasing order, p_0..p_{n_p-1} the next largest such primes below 2^31.
  * Host only. Returns CKKS_EINVAL if not enough primes exist. */
 int ckks_gen_primes(int log_n, int n_q, int n_p, uint32_t* q_out, uint32_t* p_out);
+/* The exemplar 25-30 prime system of Table 2 (Sec. 3.2): 15 ciphertext
+ * primes in inverted-terminal order [tau_3, tau_2, tau_1, tau_0, q_0..q_10]
+ * (tau_i = 1 mod 2N near 2^25, q_i = 1 mod 2N near 2^30) and 9 levels, each a
+ * window of that list: levels 1-4 keep Delta ~ 2^40 by rational rescaling
+ * (4 -> 3 and 3 -> 2 drop three q's and add two taus, 2 -> 1 drops four
+ * taus and adds two q's, 1 -> 0 drops three q's and adds two taus), levels
+ * 5-8 add {tau_i, q_(7+i)} for double rescaling at Delta ~ 2^55. The taus
+ * are the four such primes nearest 2^25; each q_i is chosen so that every
+ * rescaling of the cycle divides by as nearly 2^40 (2^55) as the primes
+ * allow; the n_p auxiliary primes are the largest = 1 mod 2N below 2^31.
+ * Writes q_out[15], p_out[n_p], level_first[9], level_count[9]. */
+int ckks_gen_prime_system_2530(int log_n, int n_p, uint32_t* q_out, uint32_t* p_out, int* level_first,
+                               int* level_count);
 
 /* Context: validates the parameters, builds and uploads the per-prime tables
  * (twiddles, Montgomery/Shoup constants, BConv matrices for every level) and
@@ -95,6 +121,10 @@ int ckks_gen_primes(int log_n, int n_q, int n_p, uint32_t* q_out, uint32_t* p_ou
  * legacy default stream) on the current device, which must be an sm_103 GPU. */
 int ckks_ctx_create(const ckks_params* params, void* cuda_stream, ckks_ctx** out);
 void ckks_ctx_destroy(ckks_ctx* ctx);
+/* Ciphertext limbs per polynomial at `level` (level + 1 with single
+ * rescaling, the window size with level windows); CKKS_ELEVEL if out of
+ * range. */
+int ckks_level_limbs(ckks_ctx* ctx, int level);
 /* Execution lane: a context that shares `parent`'s parameters and device
  * tables but has its own CUDA stream and key-switching scratch, so that
  * operations issued on different lanes can run concurrently on the GPU.

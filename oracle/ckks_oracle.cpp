@@ -156,13 +156,28 @@ void intt_fast(u32* a, int log_n, u32 q) {
   }
 }
 
+// q is the list of all L ciphertext primes in their fixed order; a
+// polynomial at a level holds the n_q consecutive primes q[base ..
+// base + n_q) (base = 0 for single rescaling; the 25-30 prime system of
+// Sec. 3.2 uses other windows, see or_rescale_rational). Key-switching digits
+// are the fixed groups q[j alpha .. (j+1) alpha) of that list, cut to the
+// window, and a key limb is selected by its global prime index.
 struct Params {
   int log_n, L, alpha, dnum;
   const u32* q;
   const u32* p;
+  int base = 0;
   u32 n() const { return 1u << log_n; }
   // prime of limb t of an extended polynomial at level with n_q limbs
-  u32 ext_prime(int t, int n_q) const { return t < n_q ? q[t] : p[t - n_q]; }
+  u32 ext_prime(int t, int n_q) const { return t < n_q ? q[base + t] : p[t - n_q]; }
+  int first_digit() const { return base / alpha; }
+  // window limbs [lo, hi) of the j-th active digit
+  void digit(int j, int n_q, int& lo, int& hi) const {
+    int g = first_digit() + j;
+    lo = std::max(0, g * alpha - base);
+    hi = std::min(n_q, (g + 1) * alpha - base);
+  }
+  int key_limb(int t, int n_q) const { return t < n_q ? base + t : L + (t - n_q); }
 };
 
 // Fast basis conversion (Eq. 2) with centered y_j (reading of Sec. 4.2,
@@ -216,8 +231,8 @@ void automorph_ntt(const u32* a, u32* out, u32 n, u32 k) {
   }
 }
 
-// Number of digits active at a level with n_q ciphertext limbs.
-int n_digits(int n_q, int alpha) { return (n_q + alpha - 1) / alpha; }
+// Number of digits active at a level with n_q ciphertext limbs from prime base.
+int n_digits(int n_q, int alpha, int base = 0) { return (base + n_q - 1) / alpha - base / alpha + 1; }
 
 // ModUp (Alg. 1 as ModSwitch Q_j -> PQ, Sec. 2.3): for every active digit j,
 // bring its limbs to the coefficient domain, convert to every other prime of
@@ -225,13 +240,15 @@ int n_digits(int n_q, int alpha) { return (n_q + alpha - 1) / alpha; }
 // copied. out is [n_digits][n_q + alpha][N].
 void modup(const Params& P, const u32* d, int n_q, u32* out) {
   u32 n = P.n();
-  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha);
+  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha, P.base);
   for (int j = 0; j < nd; ++j) {
-    int lo = j * P.alpha, hi = std::min(n_q, lo + P.alpha), k_src = hi - lo;
+    int lo, hi;
+    P.digit(j, n_q, lo, hi);
+    int k_src = hi - lo;
     std::vector<u32> coef(size_t(k_src) * n);
     std::vector<u32> src(k_src);
     for (int s = 0; s < k_src; ++s) {
-      src[s] = P.q[lo + s];
+      src[s] = P.q[P.base + lo + s];
       std::memcpy(&coef[size_t(s) * n], d + size_t(lo + s) * n, n * 4);
       intt_fast(&coef[size_t(s) * n], P.log_n, src[s]);
     }
@@ -258,16 +275,16 @@ void modup(const Params& P, const u32* d, int n_q, u32* out) {
 // top-level key is truncated by skipping limbs n_q .. L-1.
 void keymult(const Params& P, const u32* up, int n_q, const u32* evk, u32* acc) {
   u32 n = P.n();
-  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha), ext_top = P.L + P.alpha;
+  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha, P.base), ext_top = P.L + P.alpha;
   for (int t = 0; t < 2; ++t)
     for (int l = 0; l < ext; ++l) {
       u32 q = P.ext_prime(l, n_q);
-      int key_limb = l < n_q ? l : P.L + (l - n_q);
+      int key_limb = P.key_limb(l, n_q);
       for (u32 c = 0; c < n; ++c) {
         u32 s = 0;
         for (int j = 0; j < nd; ++j) {
           u32 x = up[(size_t(j) * ext + l) * n + c];
-          u32 e = evk[((size_t(j) * 2 + t) * ext_top + key_limb) * n + c];
+          u32 e = evk[((size_t(P.first_digit() + j) * 2 + t) * ext_top + key_limb) * n + c];
           s = add_mod(s, mul_mod(x, e, q), q);
         }
         acc[(size_t(t) * ext + l) * n + c] = s;
@@ -289,9 +306,9 @@ void moddown(const Params& P, const u32* acc, int n_q, u32* out) {
       intt_fast(&xp[size_t(k) * n], P.log_n, P.p[k]);
     }
     std::vector<u32> z(size_t(n_q) * n);
-    bconv(xp.data(), P.alpha, P.p, z.data(), n_q, P.q, n);
+    bconv(xp.data(), P.alpha, P.p, z.data(), n_q, P.q + P.base, n);
     for (int i = 0; i < n_q; ++i) {
-      u32 q = P.q[i];
+      u32 q = P.q[P.base + i];
       ntt_fast(&z[size_t(i) * n], P.log_n, q);
       u32 pinv = 1;
       for (int k = 0; k < P.alpha; ++k) pinv = mul_mod(pinv, P.p[k] % q, q);
@@ -306,7 +323,7 @@ void moddown(const Params& P, const u32* acc, int n_q, u32* out) {
 // out = ModDown(KeyMult(ModUp(d), evk)), two polynomials of n_q limbs.
 void keyswitch(const Params& P, const u32* d, int n_q, const u32* evk, u32* out) {
   u32 n = P.n();
-  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha);
+  int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha, P.base);
   std::vector<u32> up(size_t(nd) * ext * n), acc(size_t(2) * ext * n);
   modup(P, d, n_q, up.data());
   keymult(P, up.data(), n_q, evk, acc.data());
@@ -422,21 +439,21 @@ void or_tensor(const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t
     }
 }
 
-void or_modup(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+void or_modup(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
               const uint32_t* d, int n_q, uint32_t* out) {
-  Params P{log_n, L, alpha, dnum, q, p};
+  Params P{log_n, L, alpha, dnum, q, p, base};
   modup(P, d, n_q, out);
 }
 
-void or_keymult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+void or_keymult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
                 const uint32_t* up, int n_q, const uint32_t* evk, uint32_t* acc) {
-  Params P{log_n, L, alpha, dnum, q, p};
+  Params P{log_n, L, alpha, dnum, q, p, base};
   keymult(P, up, n_q, evk, acc);
 }
 
-void or_moddown(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+void or_moddown(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
                 const uint32_t* acc, int n_q, uint32_t* out) {
-  Params P{log_n, L, alpha, dnum, q, p};
+  Params P{log_n, L, alpha, dnum, q, p, base};
   moddown(P, acc, n_q, out);
 }
 
@@ -462,15 +479,78 @@ void or_rescale(const uint32_t* in, int polys, int n_q, const uint32_t* q, int l
   }
 }
 
+// Rational rescaling between two windows of the prime list q (Sec. 3.1
+// "Rational rescaling", Sec. 3.2, Sec. 5.1 with Fig. 4): the primes of the
+// old window [s_old, s_old + n_old) that the new window [s_new, s_new +
+// n_new) lacks are divided out (their product T_drop) and the primes the new
+// window adds are multiplied in (T_add): c' = (c T_add - X) / T_drop with
+// X = BConv_{drop -> new}([c T_add]_{T_drop}) (Eq. 2 with centered
+// representatives). Steps, per polynomial: for every dropped prime d,
+// x_d = iNTT(c_d) T_add mod d; X_t = BConv(x)_t for every prime t of the
+// new window, back to the NTT domain; c'_t = (c_t T_add - X_t) T_drop^-1 mod
+// t, where c_t T_add = 0 for an added prime. in [polys][n_old][N] ->
+// out [polys][n_new][N], both in window order.
+void or_rescale_rational(const uint32_t* in, int polys, const uint32_t* q, int s_old, int n_old, int s_new,
+                         int n_new, int log_n, uint32_t* out) {
+  u32 n = 1u << log_n;
+  auto in_old = [&](int g) { return g >= s_old && g < s_old + n_old; };
+  auto in_new = [&](int g) { return g >= s_new && g < s_new + n_new; };
+  std::vector<int> drop, add;
+  for (int g = s_old; g < s_old + n_old; ++g)
+    if (!in_new(g)) drop.push_back(g);
+  for (int g = s_new; g < s_new + n_new; ++g)
+    if (!in_old(g)) add.push_back(g);
+  auto prod_mod = [&](const std::vector<int>& set, u32 m) {
+    u32 r = 1 % m;
+    for (int g : set) r = mul_mod(r, q[g] % m, m);
+    return r;
+  };
+  const int K = (int)drop.size();
+  std::vector<u32> src(K), dst(n_new);
+  for (int k = 0; k < K; ++k) src[k] = q[drop[k]];
+  for (int i = 0; i < n_new; ++i) dst[i] = q[s_new + i];
+  for (int t = 0; t < polys; ++t) {
+    const u32* c = in + size_t(t) * n_old * n;
+    u32* o = out + size_t(t) * n_new * n;
+    if (K == 0) {  // nothing dropped: only T_add multiplies in
+      for (int i = 0; i < n_new; ++i) {
+        int g = s_new + i;
+        u32 qq = q[g], ta = prod_mod(add, qq);
+        for (u32 k = 0; k < n; ++k) o[size_t(i) * n + k] = in_old(g) ? mul_mod(c[size_t(g - s_old) * n + k], ta, qq) : 0;
+      }
+      continue;
+    }
+    std::vector<u32> x(size_t(K) * n), conv(size_t(n_new) * n);
+    for (int k = 0; k < K; ++k) {
+      u32 d = src[k], ta = prod_mod(add, d);
+      std::memcpy(&x[size_t(k) * n], c + size_t(drop[k] - s_old) * n, n * 4);
+      intt_fast(&x[size_t(k) * n], log_n, d);
+      for (u32 j = 0; j < n; ++j) x[size_t(k) * n + j] = mul_mod(x[size_t(k) * n + j], ta, d);
+    }
+    bconv(x.data(), K, src.data(), conv.data(), n_new, dst.data(), n);
+    for (int i = 0; i < n_new; ++i) {
+      int g = s_new + i;
+      u32 qq = q[g];
+      ntt_fast(&conv[size_t(i) * n], log_n, qq);
+      u32 ta = prod_mod(add, qq), tdi = inv_mod(prod_mod(drop, qq), qq);
+      for (u32 k = 0; k < n; ++k) {
+        u32 ct = in_old(g) ? mul_mod(c[size_t(g - s_old) * n + k], ta, qq) : 0;
+        o[size_t(i) * n + k] = mul_mod(sub_mod(ct, conv[size_t(i) * n + k], qq), tdi, qq);
+      }
+    }
+  }
+}
+
 // HMult (Sec. 2.1): tensor, relinearize with evk (key switching of d2),
 // optionally rescale. ct = [2][n_q][N]; out = [2][n_q][N] or [2][n_q-1][N].
-void or_hmult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+void or_hmult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
               const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t* evk, int rescale,
               uint32_t* out) {
-  Params P{log_n, L, alpha, dnum, q, p};
+  Params P{log_n, L, alpha, dnum, q, p, base};
   u32 n = P.n();
   size_t poly = size_t(n_q) * n;
   std::vector<u32> d(3 * poly), ks(2 * poly), res(2 * poly);
+  q += base;
   or_tensor(ct1, ct2, n_q, q, log_n, d.data());
   keyswitch(P, d.data() + 2 * poly, n_q, evk, ks.data());
   for (int t = 0; t < 2; ++t)
@@ -487,11 +567,12 @@ void or_hmult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p,
 // key for phi_k(s); k = 5^r mod 2N for a rotation by r, k = 2N - 1 for
 // conjugation. Automorphism first (the equivalent order of the paper's
 // ModUp -> KeyMult -> MAC -> automorphism -> ModDown; see the design notes).
-void or_hrot(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+void or_hrot(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
              const uint32_t* ct, int n_q, uint32_t k, const uint32_t* evk, uint32_t* out) {
-  Params P{log_n, L, alpha, dnum, q, p};
+  Params P{log_n, L, alpha, dnum, q, p, base};
   u32 n = P.n();
   size_t poly = size_t(n_q) * n;
+  q += base;
   std::vector<u32> rb(poly), ra(poly), ks(2 * poly);
   or_automorph_ntt(ct, rb.data(), n_q, log_n, k);
   or_automorph_ntt(ct + poly, ra.data(), n_q, log_n, k);

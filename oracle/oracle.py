@@ -19,6 +19,8 @@ import subprocess
 import threading
 from dataclasses import dataclass
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,12 +63,13 @@ def lib():
                 "or_automorph_ntt": (None, [U32P, U32P, i, i, u32]),
                 "or_automorph_coeff": (None, [U32P, U32P, i, U32P, i, u32]),
                 "or_tensor": (None, [U32P, U32P, i, U32P, i, U32P]),
-                "or_modup": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P]),
-                "or_keymult": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P, U32P]),
-                "or_moddown": (None, [i, i, U32P, i, U32P, i, U32P, i, U32P]),
+                "or_modup": (None, [i, i, U32P, i, U32P, i, i, U32P, i, U32P]),
+                "or_keymult": (None, [i, i, U32P, i, U32P, i, i, U32P, i, U32P, U32P]),
+                "or_moddown": (None, [i, i, U32P, i, U32P, i, i, U32P, i, U32P]),
+                "or_rescale_rational": (None, [U32P, i, U32P, i, i, i, i, i, U32P]),
                 "or_rescale": (None, [U32P, i, i, U32P, i, U32P]),
-                "or_hmult": (None, [i, i, U32P, i, U32P, i, U32P, U32P, i, U32P, i, U32P]),
-                "or_hrot": (None, [i, i, U32P, i, U32P, i, U32P, i, u32, U32P, U32P]),
+                "or_hmult": (None, [i, i, U32P, i, U32P, i, i, U32P, U32P, i, U32P, i, U32P]),
+                "or_hrot": (None, [i, i, U32P, i, U32P, i, i, U32P, i, u32, U32P, U32P]),
                 "or_hadd": (None, [U32P, U32P, i, U32P, i, U32P]),
                 "or_pmult": (None, [U32P, U32P, i, U32P, i, U32P]),
                 "or_small_to_ntt": (None, [I64P, i, U32P, i, U32P]),
@@ -121,8 +124,9 @@ class Params:
     def all_primes(self) -> np.ndarray:
         return self.ext_primes(self.L)
 
-    def digits(self, n_q: int) -> int:
-        return -(-n_q // self.alpha)
+    def digits(self, n_q: int, base: int = 0) -> int:
+        """Digits active in the window [base, base + n_q) of the prime list."""
+        return (base + n_q - 1) // self.alpha - base // self.alpha + 1
 
     def args(self):
         return (self.log_n, self.L, _u32(self.q), self.alpha, _u32(self.p), self.dnum)
@@ -232,22 +236,100 @@ def tensor(ct1, ct2, q) -> np.ndarray:
     return out
 
 
-def modup(P: Params, d, n_q: int) -> np.ndarray:
+def modup(P: Params, d, n_q: int, base: int = 0) -> np.ndarray:
+    """ModUp of the window q[base .. base + n_q); digits are the fixed groups
+    of alpha consecutive primes of the whole list, cut to the window."""
     d = _u32(d)
-    out = np.zeros((P.digits(n_q), n_q + P.alpha, P.n), np.uint32)
-    lib().or_modup(*P.args(), d, n_q, out)
+    out = np.zeros((P.digits(n_q, base), n_q + P.alpha, P.n), np.uint32)
+    lib().or_modup(*P.args(), base, d, n_q, out)
     return out
 
 
-def keymult(P: Params, up, n_q: int, evk) -> np.ndarray:
+def keymult(P: Params, up, n_q: int, evk, base: int = 0) -> np.ndarray:
     out = np.zeros((2, n_q + P.alpha, P.n), np.uint32)
-    lib().or_keymult(*P.args(), _u32(up), n_q, _u32(evk), out)
+    lib().or_keymult(*P.args(), base, _u32(up), n_q, _u32(evk), out)
     return out
 
 
-def moddown(P: Params, acc, n_q: int) -> np.ndarray:
+def moddown(P: Params, acc, n_q: int, base: int = 0) -> np.ndarray:
     out = np.zeros((2, n_q, P.n), np.uint32)
-    lib().or_moddown(*P.args(), _u32(acc), n_q, out)
+    lib().or_moddown(*P.args(), base, _u32(acc), n_q, out)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# 25-30 prime system (Sec. 3.2, Table 2)
+# ----------------------------------------------------------------------------
+
+def _primes_near(center_bits: int, count: int, log_n: int):
+    """The `count` primes q = 1 mod 2N nearest to 2^center_bits (ties: the
+    smaller one first), with log2(q) - center_bits."""
+    m = 2 << log_n
+    c = 1 << center_bits
+    up = (c // m + 1) * m + 1
+    dn = (c // m) * m + 1
+    if dn >= c:
+        dn -= m
+    found = []
+    while len(found) < count:
+        for v in (dn, up):
+            if is_prime(v):
+                found.append(v)
+        up += m
+        dn -= m
+    found.sort(key=lambda v: (abs(v - c), v))
+    return found[:count]
+
+
+def prime_system_2530(log_n: int, alpha: int):
+    """The exemplar 25-30 prime system of Table 2 (Delta ~ 2^40 at levels 1-4,
+    double rescaling with Delta ~ 2^55 at the bootstrapping levels 5-8).
+
+    Returns (Params, levels): the prime list in inverted-terminal order
+    [tau_3, tau_2, tau_1, tau_0, q_0, ..., q_10] (Sec. 3.3), which makes every
+    level a contiguous window, and levels[l] = (first index, count) of level l.
+    Rescaling cycle (Sec. 3.2): 4 -> 3 drops q_4..q_6 and adds tau_1, tau_0;
+    3 -> 2 drops q_1..q_3 and adds tau_3, tau_2; 2 -> 1 drops the four taus
+    and adds q_1, q_2; 1 -> 0 drops q_0..q_2 and adds tau_1, tau_0; levels 5-8
+    add {tau_i, q_(7+i)} by double rescaling.
+
+    Reading of the "carefully chosen lists" (the paper gives no rule): the
+    taus are the four primes = 1 mod 2N nearest to 2^25 (tau_0 nearest); with
+    b_i = log2(tau_i) - 25 and a_i = log2(q_i) - 30, each q_i is the unused
+    prime = 1 mod 2N near 2^30 whose a_i is nearest to the value that makes
+    every rescaling of the cycle divide by exactly 2^40 (2^55 at the double
+    rescalings): a_0 = -(b_2 + b_3), a_1 = a_2 = (b_0 + .. + b_3) / 2,
+    a_3 = -(b_0 + b_1), a_4 = a_5 = a_6 = (b_0 + b_1) / 3, a_(7+i) = -b_i.
+    The auxiliary primes are the largest 31-bit primes = 1 mod 2N."""
+    t25 = _primes_near(25, 4, log_n)
+    b = [math.log2(t) - 25 for t in t25]
+    pool = _primes_near(30, 200, log_n)
+    targets = [-(b[2] + b[3]), sum(b) / 2, sum(b) / 2, -(b[0] + b[1])] + [(b[0] + b[1]) / 3] * 3 + \
+        [-b[0], -b[1], -b[2], -b[3]]
+    used, q30 = set(), []
+    for tgt in targets:
+        best = min((v for v in pool if v not in used), key=lambda v: (abs(math.log2(v) - 30 - tgt), v))
+        used.add(best)
+        q30.append(best)
+    g = [t25[3], t25[2], t25[1], t25[0]] + q30
+    m = 2 << log_n
+    p, c = [], ((1 << 31) - 1) // m * m + 1
+    while len(p) < alpha:
+        if is_prime(c) and c not in g:
+            p.append(c)
+        c -= m
+    levels = [(2, 2), (4, 3), (0, 5), (2, 6), (4, 7), (3, 9), (2, 11), (1, 13), (0, 15)]
+    dnum = -(-len(g) // alpha)
+    return Params(log_n, np.array(g, np.uint32), np.array(p, np.uint32), dnum), levels
+
+
+def rescale_rational(P: Params, ct, s_old: int, n_old: int, s_new: int, n_new: int) -> np.ndarray:
+    """Rational rescaling from window [s_old, s_old + n_old) of the prime list
+    to [s_new, s_new + n_new) (Sec. 3.1, Sec. 3.2, Sec. 5.1)."""
+    ct = _u32(ct)
+    polys = ct.shape[0]
+    out = np.zeros((polys, n_new, P.n), np.uint32)
+    lib().or_rescale_rational(ct, polys, _u32(P.q), s_old, n_old, s_new, n_new, P.log_n, out)
     return out
 
 
@@ -259,19 +341,19 @@ def rescale(ct, q) -> np.ndarray:
     return out
 
 
-def hmult(P: Params, ct1, ct2, evk, rescale: bool = True) -> np.ndarray:
+def hmult(P: Params, ct1, ct2, evk, rescale: bool = True, base: int = 0) -> np.ndarray:
     ct1, ct2 = _u32(ct1), _u32(ct2)
     n_q = ct1.shape[1]
     out = np.zeros((2, n_q - (1 if rescale else 0), P.n), np.uint32)
-    lib().or_hmult(*P.args(), ct1, ct2, n_q, _u32(evk), int(bool(rescale)), out)
+    lib().or_hmult(*P.args(), base, ct1, ct2, n_q, _u32(evk), int(bool(rescale)), out)
     return out
 
 
-def hrot(P: Params, ct, k: int, evk) -> np.ndarray:
+def hrot(P: Params, ct, k: int, evk, base: int = 0) -> np.ndarray:
     ct = _u32(ct)
     n_q = ct.shape[1]
     out = np.zeros((2, n_q, P.n), np.uint32)
-    lib().or_hrot(*P.args(), ct, n_q, int(k), _u32(evk), out)
+    lib().or_hrot(*P.args(), base, ct, n_q, int(k), _u32(evk), out)
     return out
 
 
@@ -282,7 +364,7 @@ def encode_ext(P: Params, u, scale: float, n_q: int) -> np.ndarray:
     return small_to_ntt(m, list(P.q[:n_q]) + list(P.p), P.log_n)
 
 
-def linear_transform(P: Params, ct, rots, evks, pts_ext) -> np.ndarray:
+def linear_transform(P: Params, ct, rots, evks, pts_ext, base: int = 0) -> np.ndarray:
     """Linear transform sum_i pt_i (.) HRot_{r_i}(ct) with a shared ModUp and
     one ModDown (Par. 4, Par. 5; the hoisting of the cited linear-transform
     method). With M_j = ModUp_j(a) (Alg. 1) and phi_i the automorphism of r_i
@@ -294,8 +376,8 @@ def linear_transform(P: Params, ct, rots, evks, pts_ext) -> np.ndarray:
     evks[i] is ignored for r_i = 0."""
     ct = _u32(ct)
     n_q = ct.shape[1]
-    qcol = np.array(P.q[:n_q], np.uint64)[:, None]
-    ecol = np.array(list(P.q[:n_q]) + list(P.p), np.uint64)[:, None]
+    qcol = np.array(P.q[base:base + n_q], np.uint64)[:, None]
+    ecol = np.array(list(P.q[base:base + n_q]) + list(P.p), np.uint64)[:, None]
     b, a = ct[0].astype(np.uint64), ct[1].astype(np.uint64)
     out = np.zeros((2, n_q, P.n), np.uint64)
     acc = np.zeros((2, n_q + P.alpha, P.n), np.uint64)
@@ -309,15 +391,15 @@ def linear_transform(P: Params, ct, rots, evks, pts_ext) -> np.ndarray:
             out[1] = (out[1] + pt[:n_q] * a) % qcol
             continue
         if up is None:
-            up = modup(P, ct[1], n_q)
+            up = modup(P, ct[1], n_q, base)
         rotated = True
         upk = np.stack([automorph_ntt(up[j], k) for j in range(up.shape[0])])
-        km = keymult(P, upk, n_q, evk).astype(np.uint64)
+        km = keymult(P, upk, n_q, evk, base).astype(np.uint64)
         acc = (acc + km * pt[None]) % ecol[None]
         bk = automorph_ntt(ct[0], k).astype(np.uint64)
         out[0] = (out[0] + pt[:n_q] * bk) % qcol
     if rotated:
-        out = (out + moddown(P, acc.astype(np.uint32), n_q).astype(np.uint64)) % qcol[None]
+        out = (out + moddown(P, acc.astype(np.uint32), n_q, base).astype(np.uint64)) % qcol[None]
     return out.astype(np.uint32)
 
 

@@ -49,6 +49,9 @@ class ckks_params(C.Structure):
         ("secret_hw", C.c_int),
         ("sigma", C.c_double),
         ("seed", C.c_uint64),
+        ("n_levels", C.c_int),
+        ("level_first", C.POINTER(C.c_int)),
+        ("level_count", C.POINTER(C.c_int)),
     ]
 
 
@@ -77,6 +80,8 @@ _vp, _i, _u32, _u64, _d, _sz = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_
 _P = C.POINTER
 _SIGS = {
     "ckks_gen_primes": (_i, [_i, _i, _i, _vp, _vp]),
+    "ckks_gen_prime_system_2530": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
+    "ckks_level_limbs": (_i, [_vp, _i]),
     "ckks_ctx_create": (_i, [_P(ckks_params), _vp, _P(_vp)]),
     "ckks_ctx_destroy": (None, [_vp]),
     "ckks_ctx_clone": (_i, [_vp, _vp, _P(_vp)]),
@@ -171,15 +176,37 @@ def ckks_gen_primes(log_n: int, n_q: int, n_p: int):
     return q, p[:n_p].copy()
 
 
+def ckks_gen_prime_system_2530(log_n: int, n_p: int):
+    """(q [15], p [n_p], levels [(first, count)] x 9) of the exemplar 25-30 system."""
+    q = np.zeros(15, np.uint32)
+    p = np.zeros(n_p, np.uint32)
+    lf = np.zeros(9, np.int32)
+    lc = np.zeros(9, np.int32)
+    check(None, lib.ckks_gen_prime_system_2530(log_n, n_p, _ptr(q), _ptr(p), _ptr(lf), _ptr(lc)))
+    return q, p, list(zip(lf.tolist(), lc.tolist()))
+
+
 def ckks_ctx_create(log_n: int, q, p, dnum: int, scale: float = 2.0**30, secret_hw: int = 0,
-                    sigma: float = 3.2, seed: int = 0, stream: int | None = None):
+                    sigma: float = 3.2, seed: int = 0, stream: int | None = None, levels=None):
+    """levels: None (single rescaling) or a list of (first, count) windows of
+    the prime list, one per level (rational rescaling between them)."""
     q, p = _u32(q), _u32(p)
+    nl = 0 if levels is None else len(levels)
+    lf = (C.c_int * max(nl, 1))(*[int(a) for a, _ in (levels or [])])
+    lc = (C.c_int * max(nl, 1))(*[int(b) for _, b in (levels or [])])
     prm = ckks_params(log_n, len(q), q.ctypes.data_as(_P(C.c_uint32)), len(p), p.ctypes.data_as(_P(C.c_uint32)),
-                      dnum, scale, secret_hw, sigma, seed)
+                      dnum, scale, secret_hw, sigma, seed, nl, lf, lc)
     out = _vp()
     rc = lib.ckks_ctx_create(C.byref(prm), stream, C.byref(out))
     check(None, rc)
     return out
+
+
+def ckks_level_limbs(ctx, level: int) -> int:
+    n = lib.ckks_level_limbs(ctx, level)
+    if n < 0:
+        check(ctx, n)
+    return n
 
 
 def ckks_ctx_destroy(ctx):
@@ -318,7 +345,7 @@ def ckks_ct_export(ctx, ct, n: int, out: np.ndarray | None = None):
     lv, sc = C.c_int(), C.c_double()
     level, _, _ = ckks_ct_info(ct)
     if out is None:
-        out = np.zeros((2, level + 1, n), np.uint32)
+        out = np.zeros((2, ckks_level_limbs(ctx, level), n), np.uint32)
     check(ctx, lib.ckks_ct_export(ctx, ct, _ptr(out), out.size, C.byref(lv), C.byref(sc)))
     return out, lv.value, sc.value
 
@@ -344,7 +371,7 @@ def ckks_pt_import_ext(ctx, host, level: int, scale: float):
 
 
 def ckks_pt_export(ctx, pt, level: int, n: int):
-    out = np.zeros((level + 1, n), np.uint32)
+    out = np.zeros((ckks_level_limbs(ctx, level), n), np.uint32)
     lv, sc = C.c_int(), C.c_double()
     check(ctx, lib.ckks_pt_export(ctx, pt, _ptr(out), out.size, C.byref(lv), C.byref(sc)))
     return out, lv.value, sc.value

@@ -82,6 +82,12 @@ int ckks_gen_primes(int log_n, int n_q, int n_p, uint32_t* q_out, uint32_t* p_ou
   return host_gen_primes(log_n, n_q, n_p, q_out, p_out);
 }
 
+int ckks_gen_prime_system_2530(int log_n, int n_p, uint32_t* q_out, uint32_t* p_out, int* level_first,
+                               int* level_count) {
+  if (!q_out || !p_out || !level_first || !level_count) return CKKS_EINVAL;
+  return host_gen_prime_system_2530(log_n, n_p, q_out, p_out, level_first, level_count);
+}
+
 int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   if (!prm || !out) return CKKS_EINVAL;
   *out = nullptr;
@@ -105,6 +111,12 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
     return bad(fail(ctx, CKKS_EINVAL, "dnum (%d) must equal ceil(n_q / n_p) = %d", prm->dnum,
                     (L + alpha - 1) / alpha));
   if (prm->dnum > 8) return bad(fail(ctx, CKKS_EINVAL, "dnum %d above the supported maximum of 8", prm->dnum));
+  if (prm->n_levels < 0 || (prm->n_levels > 0 && (!prm->level_first || !prm->level_count)))
+    return bad(fail(ctx, CKKS_EINVAL, "level windows: n_levels %d without tables", prm->n_levels));
+  for (int l = 0; l < prm->n_levels; ++l)
+    if (prm->level_first[l] < 0 || prm->level_count[l] < 1 || prm->level_first[l] + prm->level_count[l] > L)
+      return bad(fail(ctx, CKKS_EINVAL, "level %d window [%d, +%d) outside the %d primes", l, prm->level_first[l],
+                      prm->level_count[l], L));
   const uint64_t two_n = 2ull << log_n;
   std::vector<uint32_t> all(prm->q, prm->q + L);
   all.insert(all.end(), prm->p, prm->p + alpha);
@@ -157,6 +169,12 @@ int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
   c->owns_tables = false;
   c->gadget_p = parent->gadget_p;
   c->device = parent->device;
+  c->windowed = parent->windowed;
+  c->lvl_first = parent->lvl_first;
+  c->lvl_count = parent->lvl_count;
+  c->rows_off = parent->rows_off;
+  c->rows_cnt = parent->rows_cnt;
+  c->rr = parent->rr;
   c->d_scratch = nullptr;
   const int rc = alloc_scratch(c);
   if (rc != CKKS_OK) {
@@ -188,9 +206,11 @@ int ckks_set_launch_flags(ckks_ctx* ctx, int flags) {
 
 int ckks_tune(ckks_ctx* ctx, int level, int reps) {
   if (!ctx || !ctx->tune) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   if (reps < 1 || reps > 1000) return fail(ctx, CKKS_EINVAL, "tune: reps %d out of [1, 1000]", reps);
-  const int rc = ckks::tune_columns(ctx->dp, ctx->sc, *ctx->tune, level + 1, reps, ctx->stream);
+  KsArgs lvl{};
+  ctx->set_level(lvl, level);
+  const int rc = ckks::tune_columns(ctx->dp, ctx->sc, *ctx->tune, lvl, reps, ctx->stream);
   if (rc != CKKS_OK) return fail(ctx, rc, "tune: %s", cudaGetErrorString(cudaGetLastError()));
   return CKKS_OK;
 }
@@ -198,7 +218,7 @@ int ckks_tune(ckks_ctx* ctx, int level, int reps) {
 int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us) {
   if (!ctx || !ctx->tune || !tc || !sl || !z || !tp || !us) return CKKS_EINVAL;
   if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   const ckks::ColShape s = ctx->tune->get(kernel, level + 1);
   *tc = s.tc;
   *sl = s.sl;
@@ -211,7 +231,7 @@ int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z
 int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp) {
   if (!ctx || !ctx->tune) return CKKS_EINVAL;
   if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   ckks::ColShape s;
   if (tc != 0) {
     if (!ckks::col_shape_supported(ctx->dp.log_n, tc, sl, z, tp))
@@ -224,6 +244,12 @@ int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, i
   }
   ctx->tune->set(kernel, level + 1, s, 0.f);
   return CKKS_OK;
+}
+
+int ckks_level_limbs(ckks_ctx* ctx, int level) {
+  if (!ctx) return CKKS_EINVAL;
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  return ctx->lvl_n(level);
 }
 
 int ckks_profile(ckks_ctx* ctx, int enable) {
@@ -308,14 +334,15 @@ void ckks_free(void* handle) {
 
 int ckks_ct_create(ckks_ctx* ctx, int cap_level, ckks_ct** out) {
   if (!ctx || !out) return CKKS_EINVAL;
-  if (cap_level < 0 || cap_level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "capacity level %d out of range", cap_level);
+  if (cap_level < 0 || cap_level >= ctx->n_levels())
+    return fail(ctx, CKKS_ELEVEL, "capacity level %d out of range", cap_level);
   ckks_ct* c = new_obj<ckks_ct>(ctx, K_CT);
   if (!c) return CKKS_ENOMEM;
   c->level = cap_level;
   c->cap_level = cap_level;
   c->scale = ctx->scale;
   c->borrowed = false;
-  if (cudaMalloc(&c->d, 2 * (size_t)(cap_level + 1) * limb_words(ctx) * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&c->d, 2 * (size_t)ctx->cap_limbs(cap_level) * limb_words(ctx) * sizeof(uint32_t)) != cudaSuccess) {
     delete c;
     return fail(ctx, CKKS_ENOMEM, "ciphertext allocation failed");
   }
@@ -326,7 +353,7 @@ int ckks_ct_create(ckks_ctx* ctx, int cap_level, ckks_ct** out) {
 static int ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale, bool sync) {
   if (!ctx || !c || !host) return CKKS_EINVAL;
   if (level < 0 || level > c->cap_level) return fail(ctx, CKKS_ELEVEL, "level %d exceeds capacity %d", level, c->cap_level);
-  const int n = level + 1;
+  const int n = ctx->lvl_n(level);
   const size_t lw = limb_words(ctx);
   uint32_t* stage = ctx->sc.A;  // 2 L limbs of staging
   for (int u = 0; u < 2; ++u) {
@@ -367,7 +394,7 @@ int ckks_ct_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
 static int ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t words, int* level, double* scale,
                      bool sync) {
   if (!ctx || !c || !host) return CKKS_EINVAL;
-  const int n = c->level + 1;
+  const int n = ctx->lvl_n(c->level);
   const size_t lw = limb_words(ctx);
   if (words < 2 * (size_t)n * lw) return fail(ctx, CKKS_EINVAL, "export buffer too small");
   uint32_t* stage = ctx->sc.A;
@@ -394,11 +421,11 @@ int ckks_ct_export_async(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t
 
 int ckks_ct_wrap_device(ckks_ctx* ctx, uint32_t* dev_ptr, int level, double scale, ckks_ct** out) {
   if (!ctx || !dev_ptr || !out) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
   ckks_ct* c = new_obj<ckks_ct>(ctx, K_CT);
   if (!c) return CKKS_ENOMEM;
   c->d = dev_ptr;
-  c->level = c->cap_level = level;
+  c->level = c->cap_level = level;  // the buffer holds [2][limbs of level][N]
   c->scale = scale;
   c->borrowed = true;
   *out = c;
@@ -419,7 +446,7 @@ static int pt_alloc(ckks_ctx* ctx, int level, double scale, ckks_pt** out, int e
   p->level = level;
   p->scale = scale;
   p->ext = ext;
-  if (cudaMalloc(&p->d, (size_t)(level + 1 + ext) * limb_words(ctx) * 4) != cudaSuccess) {
+  if (cudaMalloc(&p->d, (size_t)(ctx->lvl_n(level) + ext) * limb_words(ctx) * 4) != cudaSuccess) {
     delete p;
     return fail(ctx, CKKS_ENOMEM, "plaintext allocation failed");
   }
@@ -429,10 +456,10 @@ static int pt_alloc(ckks_ctx* ctx, int level, double scale, ckks_pt** out, int e
 
 int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out) {
   if (!ctx || !host || !out) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
   int rc = pt_alloc(ctx, level, scale, out);
   if (rc) return rc;
-  const int n = level + 1;
+  const int n = ctx->lvl_n(level);
   const size_t lw = limb_words(ctx);
   rc = cuda_check(ctx, cudaMemcpyAsync(ctx->sc.A, host, (size_t)n * lw * 4, cudaMemcpyHostToDevice, ctx->stream),
                   "upload");
@@ -450,11 +477,11 @@ int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
 
 int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double scale, ckks_pt** out) {
   if (!ctx || !host || !out) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
   const int alpha = ctx->dp.alpha;
   int rc = pt_alloc(ctx, level, scale, out, alpha);
   if (rc) return rc;
-  const int n = level + 1 + alpha;
+  const int n = ctx->lvl_n(level) + alpha;
   const size_t lw = limb_words(ctx);
   rc = cuda_check(ctx, cudaMemcpyAsync(ctx->sc.A, host, (size_t)n * lw * 4, cudaMemcpyHostToDevice, ctx->stream),
                   "upload");
@@ -472,7 +499,7 @@ int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double sc
 
 int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* p, uint32_t* host, size_t words, int* level, double* scale) {
   if (!ctx || !p || !host) return CKKS_EINVAL;
-  const int n = p->level + 1;
+  const int n = ctx->lvl_n(p->level);
   const size_t lw = limb_words(ctx);
   if (words < (size_t)n * lw) return fail(ctx, CKKS_EINVAL, "export buffer too small");
   launch_permute(ctx->dp, p->d, ctx->sc.A, n, false, ctx->stream);
@@ -653,18 +680,18 @@ int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_e
 
 int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out) {
   if (!ctx || !re_im || !out) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
   std::vector<int64_t> m;
   host_encode(re_im, ctx->dp.log_n, scale, m);
   int rc = pt_alloc(ctx, level, scale, out);
   if (rc) return rc;
   DevBuf tmp;
-  const int n = level + 1;
+  const int n = ctx->lvl_n(level), base = ctx->lvl_base(level);
   rc = tmp.alloc(m.size() * 8) ? fail(ctx, CKKS_ENOMEM, "encode scratch") : CKKS_OK;
   if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(tmp.p, m.data(), m.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "upload");
   if (!rc) {
-    launch_small_to_res(ctx->dp, tmp.as<int64_t>(), (*out)->d, n, id_ct(n, ctx->dp.L), ctx->stream);
-    launch_ntt(ctx->dp, (*out)->d, n, id_ct(n, ctx->dp.L), false, ctx->stream);
+    launch_small_to_res(ctx->dp, tmp.as<int64_t>(), (*out)->d, n, id_ct(n, ctx->dp.L, base), ctx->stream);
+    launch_ntt(ctx->dp, (*out)->d, n, id_ct(n, ctx->dp.L, base), false, ctx->stream);
     rc = launched(ctx, "encode");
   }
   if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encode");
@@ -677,17 +704,17 @@ int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckk
 
 int ckks_encode_ext(ckks_ctx* ctx, const double* re_im, int level, double scale, ckks_pt** out) {
   if (!ctx || !re_im || !out) return CKKS_EINVAL;
-  if (level < 0 || level >= ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
+  if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "level %d out of range", level);
   std::vector<int64_t> m;
   host_encode(re_im, ctx->dp.log_n, scale, m);
-  const int alpha = ctx->dp.alpha, n = level + 1;
+  const int alpha = ctx->dp.alpha, n = ctx->lvl_n(level), base = ctx->lvl_base(level);
   int rc = pt_alloc(ctx, level, scale, out, alpha);
   if (rc) return rc;
   DevBuf tmp;
   rc = tmp.alloc(m.size() * 8) ? fail(ctx, CKKS_ENOMEM, "encode scratch") : CKKS_OK;
   if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(tmp.p, m.data(), m.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "upload");
   if (!rc) {
-    const IdMap ids = id_ext(n, ctx->dp.L, alpha);
+    const IdMap ids = id_ext(n, ctx->dp.L, alpha, base);
     launch_small_to_res(ctx->dp, tmp.as<int64_t>(), (*out)->d, n + alpha, ids, ctx->stream);
     launch_ntt(ctx->dp, (*out)->d, n + alpha, ids, false, ctx->stream);
     rc = launched(ctx, "encode");
@@ -702,26 +729,26 @@ int ckks_encode_ext(ckks_ctx* ctx, const double* re_im, int level, double scale,
 
 int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out) {
   if (!ctx || !pt || !re_im_out) return CKKS_EINVAL;
-  const int n = pt->level + 1;
+  const int n = ctx->lvl_n(pt->level), base = ctx->lvl_base(pt->level);
   const size_t lw = limb_words(ctx);
   DevBuf tmp;
   if (tmp.alloc((size_t)n * lw * 4)) return fail(ctx, CKKS_ENOMEM, "decode scratch");
   int rc = cuda_check(ctx, cudaMemcpyAsync(tmp.p, pt->d, (size_t)n * lw * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
   if (rc) return rc;
-  launch_ntt(ctx->dp, tmp.as<uint32_t>(), n, id_ct(n, ctx->dp.L), true, ctx->stream);
+  launch_ntt(ctx->dp, tmp.as<uint32_t>(), n, id_ct(n, ctx->dp.L, base), true, ctx->stream);
   rc = launched(ctx, "decode");
   if (rc) return rc;
   std::vector<uint32_t> res((size_t)n * lw);
   rc = cuda_check(ctx, cudaMemcpyAsync(res.data(), tmp.p, res.size() * 4, cudaMemcpyDeviceToHost, ctx->stream), "download");
   if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "decode");
   if (rc) return rc;
-  host_decode(res.data(), n, ctx->q.data(), ctx->dp.log_n, pt->scale, re_im_out);
+  host_decode(res.data(), n, ctx->q.data() + base, ctx->dp.log_n, pt->scale, re_im_out);
   return CKKS_OK;
 }
 
 int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t seed, ckks_ct** out) {
   if (!ctx || !sk || !pt || !out) return CKKS_EINVAL;
-  const int n = pt->level + 1;
+  const int n = ctx->lvl_n(pt->level), base = ctx->lvl_base(pt->level);
   const size_t lw = limb_words(ctx);
   int rc = ckks_ct_create(ctx, pt->level, out);
   if (rc) return rc;
@@ -730,7 +757,7 @@ int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t s
   Sampler smp(seed ^ 0xC1F3E7ull);
   std::vector<uint32_t> a((size_t)n * lw);
   for (int i = 0; i < n; ++i)
-    for (size_t k = 0; k < lw; ++k) a[(size_t)i * lw + k] = smp.uniform(ctx->pc_host[i].q);
+    for (size_t k = 0; k < lw; ++k) a[(size_t)i * lw + k] = smp.uniform(ctx->pc_host[base + i].q);
   std::vector<int64_t> e(lw);
   for (size_t k = 0; k < lw; ++k) e[k] = smp.gaussian(ctx->sigma, 20);
   DevBuf d_e, d_en;
@@ -740,10 +767,11 @@ int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t s
   if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(ad, a.data(), a.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "upload");
   if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(d_e.p, e.data(), lw * 8, cudaMemcpyHostToDevice, ctx->stream), "upload");
   if (!rc) {
-    IdMap ids = id_ct(n, ctx->dp.L);
+    IdMap ids = id_ct(n, ctx->dp.L, base);
     launch_small_to_res(ctx->dp, d_e.as<int64_t>(), d_en.as<uint32_t>(), n, ids, ctx->stream);
     launch_ntt(ctx->dp, d_en.as<uint32_t>(), n, ids, false, ctx->stream);
-    launch_lincomb(ctx->dp, ad, sk->d_s, -1, pt->d, d_en.as<uint32_t>(), b, n, ids, ctx->stream);
+    launch_lincomb(ctx->dp, ad, sk->d_s + ((size_t)base << ctx->dp.log_n), -1, pt->d, d_en.as<uint32_t>(), b, n, ids,
+                   ctx->stream);
     rc = launched(ctx, "encrypt");
   }
   if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encrypt");
@@ -756,11 +784,11 @@ int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t s
 
 int ckks_decrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_ct* c, ckks_pt** out) {
   if (!ctx || !sk || !c || !out) return CKKS_EINVAL;
-  const int n = c->level + 1;
+  const int n = ctx->lvl_n(c->level), base = ctx->lvl_base(c->level);
   int rc = pt_alloc(ctx, c->level, c->scale, out);
   if (rc) return rc;
-  launch_lincomb(ctx->dp, c->d + c->poly_stride(), sk->d_s, 1, c->d, nullptr, (*out)->d, n, id_ct(n, ctx->dp.L),
-                 ctx->stream);
+  launch_lincomb(ctx->dp, c->d + c->poly_stride(), sk->d_s + ((size_t)base << ctx->dp.log_n), 1, c->d, nullptr,
+                 (*out)->d, n, id_ct(n, ctx->dp.L, base), ctx->stream);
   rc = launched(ctx, "decrypt");
   if (rc) {
     ckks_free(*out);
@@ -778,7 +806,8 @@ int ckks_hadd(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
   if (a->level != b->level) return fail(ctx, CKKS_ELEVEL, "hadd: levels %d and %d differ", a->level, b->level);
   if (!scales_match(a->scale, b->scale)) return fail(ctx, CKKS_ESCALE, "hadd: scales differ");
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "hadd: output capacity too small");
-  launch_hadd(ctx->dp, a->d, b->d, out->d, a->level + 1, a->poly_stride(), b->poly_stride(), out->poly_stride(),
+  launch_hadd(ctx->dp, a->d, b->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
+              b->poly_stride(), out->poly_stride(),
               ctx->stream);
   out->level = a->level;
   out->scale = a->scale;
@@ -789,7 +818,10 @@ int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out)
   if (!ctx || !a || !pt || !out) return CKKS_EINVAL;
   if (pt->level < a->level) return fail(ctx, CKKS_ELEVEL, "pmult: plaintext level %d below %d", pt->level, a->level);
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "pmult: output capacity too small");
-  launch_pmult(ctx->dp, a->d, pt->d, out->d, a->level + 1, a->poly_stride(), out->poly_stride(), ctx->stream);
+  if (ctx->windowed && pt->level != a->level)
+    return fail(ctx, CKKS_ELEVEL, "pmult: plaintext level %d differs from %d (level windows)", pt->level, a->level);
+  launch_pmult(ctx->dp, a->d, pt->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
+               out->poly_stride(), ctx->stream);
   out->level = a->level;
   out->scale = a->scale * pt->scale;
   return launched(ctx, "pmult");
@@ -800,20 +832,43 @@ int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out) 
   if (pt->level < a->level) return fail(ctx, CKKS_ELEVEL, "padd: plaintext level %d below %d", pt->level, a->level);
   if (!scales_match(a->scale, pt->scale)) return fail(ctx, CKKS_ESCALE, "padd: scales differ");
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "padd: output capacity too small");
-  launch_padd(ctx->dp, a->d, pt->d, out->d, a->level + 1, a->poly_stride(), out->poly_stride(), ctx->stream);
+  if (ctx->windowed && pt->level != a->level)
+    return fail(ctx, CKKS_ELEVEL, "padd: plaintext level %d differs from %d (level windows)", pt->level, a->level);
+  launch_padd(ctx->dp, a->d, pt->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
+              out->poly_stride(), ctx->stream);
   out->level = a->level;
   out->scale = a->scale;
   return launched(ctx, "padd");
 }
 
+// Scale factor of the rescaling from `level`: 1 / q_level (single), or
+// T_add / T_drop between the level windows (rational).
+static double rescale_factor(const ckks_ctx* ctx, int level) {
+  if (!ctx->windowed) return 1.0 / (double)ctx->q[level];
+  const int s0 = ctx->lvl_first[level], n0 = ctx->lvl_count[level];
+  const int s1 = ctx->lvl_first[level - 1], n1 = ctx->lvl_count[level - 1];
+  double f = 1.0;
+  for (int g = s0; g < s0 + n0; ++g)
+    if (g < s1 || g >= s1 + n1) f /= (double)ctx->q[g];
+  for (int g = s1; g < s1 + n1; ++g)
+    if (g < s0 || g >= s0 + n0) f *= (double)ctx->q[g];
+  return f;
+}
+
+// Rescale of [2][limbs] at `in` (poly stride sin) from `level` into out.
+static void rescale_into(ckks_ctx* ctx, int level, const uint32_t* in, size_t sin, uint32_t* out, size_t sout) {
+  if (ctx->windowed) launch_rational_rescale(ctx->dp, ctx->sc, ctx->rr[level], in, sin, out, sout, ctx->stream);
+  else launch_rescale(ctx->dp, ctx->sc, in, sin, level + 1, out, sout, ctx->stream);
+}
+
 int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out) {
   if (!ctx || !in || !out) return CKKS_EINVAL;
   if (in->level < 1) return fail(ctx, CKKS_ELEVEL, "rescale at level 0");
-  if (out == in) return fail(ctx, CKKS_EINVAL, "rescale: output aliases input");
+  if (out == in || out->d == in->d) return fail(ctx, CKKS_EINVAL, "rescale: output aliases input");
   if (out->cap_level < in->level - 1) return fail(ctx, CKKS_ELEVEL, "rescale: output capacity too small");
-  launch_rescale(ctx->dp, ctx->sc, in->d, in->poly_stride(), in->level + 1, out->d, out->poly_stride(), ctx->stream);
+  rescale_into(ctx, in->level, in->d, in->poly_stride(), out->d, out->poly_stride());
   out->level = in->level - 1;
-  out->scale = in->scale / (double)ctx->q[in->level];
+  out->scale = in->scale * rescale_factor(ctx, in->level);
   return launched(ctx, "rescale");
 }
 
@@ -824,11 +879,10 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   if (out == a || out == b) return fail(ctx, CKKS_EINVAL, "hmult: output aliases an input");
   const bool rs = flags & CKKS_RESCALE;
   if (rs && a->level < 1) return fail(ctx, CKKS_ELEVEL, "hmult: cannot rescale at level 0");
-  const int n = a->level + 1;
   if (out->cap_level < a->level - (rs ? 1 : 0)) return fail(ctx, CKKS_ELEVEL, "hmult: output capacity too small");
   const size_t lw = limb_words(ctx);
   KsArgs k{};
-  k.n = n;
+  ctx->set_level(k, a->level);
   k.mode = KS_TENSOR;
   k.x0 = a->d;
   k.x1 = b->d;
@@ -836,13 +890,17 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   k.poly_stride1 = b->poly_stride();
   k.evk = evk->d;
   k.extra = 1;
-  k.rescale = rs ? 1 : 0;  // rescaling fused into ModDown
-  k.out = out->d;
-  k.out_stride = out->poly_stride();
-  (void)lw;
+  // single rescaling is fused into ModDown; a rational one follows the key
+  // switch (its ciphertext-size intermediate lives in the scratch U)
+  const bool fused = rs && !ctx->windowed;
+  k.rescale = fused ? 1 : 0;
+  const bool staged = rs && ctx->windowed;
+  k.out = staged ? ctx->sc.U : out->d;
+  k.out_stride = staged ? (size_t)ctx->lvl_n(a->level) * lw : out->poly_stride();
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
+  if (staged) rescale_into(ctx, a->level, ctx->sc.U, k.out_stride, out->d, out->poly_stride());
   out->level = rs ? a->level - 1 : a->level;
-  out->scale = a->scale * b->scale / (rs ? (double)ctx->q[a->level] : 1.0);
+  out->scale = a->scale * b->scale * (rs ? rescale_factor(ctx, a->level) : 1.0);
   return launched(ctx, "hmult");
 }
 
@@ -851,7 +909,7 @@ static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_ev
   if (out == c) return fail(ctx, CKKS_EINVAL, "output aliases the input");
   if (out->cap_level < c->level) return fail(ctx, CKKS_ELEVEL, "output capacity too small");
   KsArgs k{};
-  k.n = c->level + 1;
+  ctx->set_level(k, c->level);
   k.mode = KS_AUTO;
   k.x0 = c->d;
   k.poly_stride0 = c->poly_stride();
@@ -894,7 +952,7 @@ int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* c, int count, const int* r, 
     for (int j = 0; j < i; ++j)
       if (outs[j]->d == out->d) return fail(ctx, CKKS_EINVAL, "hoisted rotations %d and %d share an output", j, i);
     KsArgs& k = ks[(size_t)i];
-    k.n = c->level + 1;
+    ctx->set_level(k, c->level);
     k.mode = KS_AUTO;
     k.x0 = c->d;
     k.poly_stride0 = c->poly_stride();
@@ -927,11 +985,12 @@ int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* c, int count, const int*
     if (!pt) return fail(ctx, CKKS_EINVAL, "linear transform: term %d has no plaintext", i);
     if (pt->ext != ctx->dp.alpha)
       return fail(ctx, CKKS_EINVAL, "linear transform: term %d needs an extended plaintext (ckks_encode_ext)", i);
-    if (pt->level < c->level) return fail(ctx, CKKS_ELEVEL, "linear transform: term %d plaintext level too low", i);
+    if (pt->level < c->level || (ctx->windowed && pt->level != c->level))
+      return fail(ctx, CKKS_ELEVEL, "linear transform: term %d plaintext level does not match", i);
     if (std::fabs(pt->scale - pscale) > 1e-9 * pscale)
       return fail(ctx, CKKS_ESCALE, "linear transform: term %d plaintext scale differs", i);
     lt.pt[i] = pt->d;
-    lt.pt_p[i] = pt->level + 1;
+    lt.pt_p[i] = ctx->lvl_n(pt->level);
     const uint32_t galois = galois_rot(r[i], ctx->dp.log_n);
     if (galois == 1) {
       lt.galois[i] = 1;
@@ -948,7 +1007,7 @@ int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* c, int count, const int*
     ++lt.rotated;
   }
   KsArgs k{};
-  k.n = c->level + 1;
+  ctx->set_level(k, c->level);
   k.x0 = c->d;
   k.poly_stride0 = c->poly_stride();
   k.out = out->d;
@@ -1106,6 +1165,7 @@ int ckks_step_automorph(ckks_ctx* ctx, const uint32_t* in, int limbs, uint32_t g
 static int step_ks(ckks_ctx* ctx, const uint32_t* d, int n_q, const ckks_evk* evk, int km, uint32_t* out,
                    size_t out_limbs) {
   if (n_q < 1 || n_q > ctx->dp.L) return fail(ctx, CKKS_ELEVEL, "%d limbs out of range", n_q);
+  if (ctx->windowed) return fail(ctx, CKKS_EINVAL, "step entries need single-rescaling levels");
   const size_t lw = limb_words(ctx), w = (size_t)n_q * lw;
   DevBuf din, dcan, dout;
   if (din.alloc(w * 4) || dcan.alloc(w * 4) || dout.alloc(out_limbs * lw * 4)) return fail(ctx, CKKS_ENOMEM, "scratch");
@@ -1113,7 +1173,7 @@ static int step_ks(ckks_ctx* ctx, const uint32_t* d, int n_q, const ckks_evk* ev
   if (rc) return rc;
   launch_permute(ctx->dp, dcan.as<uint32_t>(), din.as<uint32_t>(), n_q, true, ctx->stream);
   KsArgs k{};
-  k.n = n_q;
+  ctx->set_level(k, n_q - 1);  // step entries: single-rescaling levels only
   k.mode = KS_PLAIN;
   k.x0 = din.as<uint32_t>();
   k.evk = evk ? evk->d : nullptr;

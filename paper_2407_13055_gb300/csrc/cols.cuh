@@ -21,7 +21,8 @@ namespace {
 
 __device__ __forceinline__ uint32_t addm(uint32_t a, uint32_t b, uint32_t q) { return csub(a + b, q); }
 
-__device__ __forceinline__ int prime_of(int t, int n, int L) { return t < n ? t : L + (t - n); }
+// Prime id of extended limb t at a level whose window starts at prime base.
+__device__ __forceinline__ int prime_of(int t, int n, int L, int base) { return t < n ? base + t : L + (t - n); }
 
 // BConv of EC coefficient-domain values per thread: out[i] = sum_k y[k][i] *
 // mat[k] reduced modulo p (Eq. 2 with the 2^32 factor folded into mat).
@@ -145,10 +146,11 @@ struct ColTile {
 template <class G, int TC>
 __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* src, size_t src_stride, int K,
                                            int id0, const uint2* cin, int4* y4, uint32_t* colbuf, int l, int jj,
-                                           int c, int pos, int slice, int GS, uint32_t* ycopy = nullptr) {
+                                           int c, int pos, int slice, int GS, uint32_t* ycopy = nullptr,
+                                           const int2* idtab = nullptr) {
   using CTL = ColTile<G, TC>;
   for (int k = slice; k < K; k += GS) {
-    const int id = id0 + k;
+    const int id = idtab ? idtab[k].y : id0 + k;
     const uint32_t q = dp.pc[id].q;
     const uint2* itw = dp.itw + ((size_t)id << dp.log_n);
     const uint32_t* s = src + k * src_stride;
@@ -225,7 +227,7 @@ __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4,
 
 // C1: ModUp column kernel. grid (W/TC, digits, Z), block SL * CT.
 template <class G, int TC, int SL, int TP>
-__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n,
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevParams dp, int n, int base, int tix,
                                                                                const uint32_t* S, uint32_t* T) {
   pdl_wait();
   pdl_trigger();
@@ -234,20 +236,21 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevPar
   const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
   const int c = pos % TC, jj = pos / TC;
   const int l = blockIdx.x * TC + c;
-  const int j = blockIdx.y;
+  const int j = blockIdx.y;  // j-th active digit of the window
   const int alpha = dp.alpha, L = dp.L, ext = n + alpha;
-  const int lo = j * alpha, hi = min(n, lo + alpha), K = hi - lo;
-  const int2 off = dp.ks.up_off[n * dp.dnum + j];
+  const int g = base / alpha + j;
+  const int lo = max(0, g * alpha - base), hi = min(n, (g + 1) * alpha - base), K = hi - lo;
+  const int2 off = dp.ks.up_off[tix * dp.dnum + j];
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
-  col_inputs<G, TC>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, lo, dp.ks.up_cin + off.x, y4,
-                    colbuf, l, jj, c, pos, slice, SL);
+  col_inputs<G, TC>(dp, S + ((size_t)lo << dp.log_n), (size_t)1 << dp.log_n, K, base + lo, dp.ks.up_cin + off.x,
+                    y4, colbuf, l, jj, c, pos, slice, SL);
   __syncthreads();
   const int M = ext - K;
   auto tgt = [&](int m, const int32_t*& row, int& id, uint32_t*& dst) {
     const int t = m < lo ? m : m + K;  // skip the digit's own limbs
     row = dp.ks.up_mat + off.y + t * K;
-    id = prime_of(t, n, L);
+    id = prime_of(t, n, L, base);
     dst = T + ((size_t)(j * ext + t) << dp.log_n);
   };
   col_targets<G, TC, TP>(dp, y4, K, M, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevPar
 // C2: ModDown column kernel. grid (W/TC, 2 polys, Z). Input S [2][alpha][N]
 // (P limbs after the row-phase iNTT); output T [2][n][N].
 template <class G, int TC, int SL, int TP>
-__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n,
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevParams dp, int n, int base,
                                                                                  const uint32_t* S, uint32_t* T) {
   pdl_wait();
   pdl_trigger();
@@ -273,8 +276,8 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevP
                     y4, colbuf, l, jj, c, pos, slice, SL);
   __syncthreads();
   auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
-    row = dp.ks.dn_mat + i * alpha;
-    id = i;
+    row = dp.ks.dn_mat + (base + i) * alpha;
+    id = base + i;
     dst = T + ((size_t)(u * n + i) << dp.log_n);
   };
   col_targets<G, TC, TP>(dp, y4, alpha, n, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
@@ -453,26 +456,27 @@ static ColShape pick_shape(const Scratch& sc, ColKernel k, int n, const ColShape
 
 
 template <class G>
-void launch_modup_cols(const DevParams& dp, int n, int digits, const Scratch& sc, const ColShape& s,
-                              cudaStream_t st) {
+void launch_modup_cols(const DevParams& dp, int n, int base, int tix, int digits, const Scratch& sc,
+                       const ColShape& s, cudaStream_t st) {
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
     set_col_smem((const void*)k_ks_modup_cols<G, TC, SL, TP>, sm);
     launch_pdl(dp.pdl, k_ks_modup_cols<G, TC, SL, TP>, dim3(G::W / TC, digits, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st,
-               dp, n, (const uint32_t*)sc.S, sc.T);
+               dp, n, base, tix, (const uint32_t*)sc.S, sc.T);
     count_launch(1);
   });
 }
 
 template <class G>
-void launch_moddown_cols(const DevParams& dp, int n, const Scratch& sc, const ColShape& s, cudaStream_t st) {
+void launch_moddown_cols(const DevParams& dp, int n, int base, const Scratch& sc, const ColShape& s,
+                         cudaStream_t st) {
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
     set_col_smem((const void*)k_ks_moddown_cols<G, TC, SL, TP>, sm);
     launch_pdl(dp.pdl, k_ks_moddown_cols<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st,
-               dp, n, (const uint32_t*)sc.S, sc.T);
+               dp, n, base, (const uint32_t*)sc.S, sc.T);
     count_launch(1);
   });
 }
@@ -501,6 +505,46 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
                n, V, Y, T3);
     count_launch(1);
   });
+}
+
+
+// Rational rescaling, column kernel (Sec. 3.1, Sec. 5.1): the K dropped
+// limbs (row-phase iNTT already applied, S = [K][2]) finish their iNTT
+// columns and are scaled by N^-1 [T_add (T_drop/d_k)^-1]_{d_k}; BConv (Eq. 2,
+// centered) to every prime of the new window, then the NTT columns into
+// T = [2][n1]. grid (W/TC, 2 polys), block SL * CT.
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rr_cols(DevParams dp, RrArgs r, const uint32_t* S,
+                                                                    uint32_t* T) {
+  pdl_wait();
+  pdl_trigger();
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)r.K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)u << dp.log_n), (size_t)2 << dp.log_n, r.K, 0, r.cin, y4, colbuf, l, jj, c,
+                    pos, slice, SL, nullptr, r.drop);
+  __syncthreads();
+  auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = r.mat + i * r.K;
+    id = r.s1 + i;
+    dst = T + ((size_t)(u * r.n1 + i) << dp.log_n);
+  };
+  col_targets<G, TC, 1>(dp, y4, r.K, r.n1, slice, SL, tgt, colbuf, l, jj, c, pos, slice);
+}
+
+template <class G>
+void launch_rr_cols(const DevParams& dp, const RrArgs& r, const Scratch& sc, cudaStream_t st) {
+  constexpr int TC = 8, SL = 4;
+  const size_t sm = col_smem_bytes<G, TC, SL>(r.K);
+  set_col_smem((const void*)k_rr_cols<G, TC, SL>, sm);
+  launch_pdl(dp.pdl, k_rr_cols<G, TC, SL>, dim3(G::W / TC, 2), dim3(SL * ColTile<G, TC>::CT), sm, st, dp, r,
+             (const uint32_t*)sc.S, sc.T);
+  count_launch(1);
 }
 
 }  // namespace ckks

@@ -3,6 +3,9 @@
 #include <complex>
 #include <cstring>
 
+#include <algorithm>
+#include <cmath>
+
 #include "internal.h"
 
 namespace ckks {
@@ -109,6 +112,74 @@ int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p) {
   q[0] = top[0];
   for (int i = 0; i < n_p; ++i) p[i] = top[1 + i];
   if (n_q > 1 && !scan(1ull << 30, q + 1, n_q - 1, 0)) return CKKS_EINVAL;
+  return CKKS_OK;
+}
+
+// The exemplar 25-30 prime system (Sec. 3.2, Table 2). `count` primes
+// = 1 mod 2N nearest to 2^bits (by distance, the smaller first on a tie).
+static std::vector<uint32_t> primes_near(int bits, int count, int log_n) {
+  const uint64_t step = 2ull << log_n, c = 1ull << bits;
+  uint64_t up = (c / step + 1) * step + 1, dn = (c / step) * step + 1;
+  if (dn >= c) dn -= step;
+  std::vector<uint64_t> found;
+  while ((int)found.size() < count) {
+    if (host_is_prime(dn)) found.push_back(dn);
+    if (host_is_prime(up)) found.push_back(up);
+    up += step;
+    dn -= step;
+  }
+  std::sort(found.begin(), found.end(), [&](uint64_t a, uint64_t b) {
+    const uint64_t da = a > c ? a - c : c - a, db = b > c ? b - c : c - b;
+    return da != db ? da < db : a < b;
+  });
+  return std::vector<uint32_t>(found.begin(), found.begin() + count);
+}
+
+int host_gen_prime_system_2530(int log_n, int n_p, uint32_t* q, uint32_t* p, int* first, int* count) {
+  if (log_n < 2 || log_n > 17 || n_p < 1) return CKKS_EINVAL;
+  const std::vector<uint32_t> tau = primes_near(25, 4, log_n);
+  double b[4];
+  for (int i = 0; i < 4; ++i) b[i] = std::log2((double)tau[i]) - 25.0;
+  const std::vector<uint32_t> pool = primes_near(30, 200, log_n);
+  // deviations a_i = log2(q_i) - 30 that make every rescaling of the cycle
+  // divide by exactly 2^40 (levels 1-4) or 2^55 (double rescaling, 5-8)
+  const double sb = b[0] + b[1] + b[2] + b[3];
+  const double target[11] = {-(b[2] + b[3]), sb / 2, sb / 2, -(b[0] + b[1]), (b[0] + b[1]) / 3,
+                             (b[0] + b[1]) / 3, (b[0] + b[1]) / 3, -b[0], -b[1], -b[2], -b[3]};
+  std::vector<bool> used(pool.size(), false);
+  uint32_t qs[11];
+  for (int i = 0; i < 11; ++i) {
+    int best = -1;
+    double bd = 0;
+    for (size_t k = 0; k < pool.size(); ++k) {
+      if (used[k]) continue;
+      const double d = std::fabs(std::log2((double)pool[k]) - 30.0 - target[i]);
+      if (best < 0 || d < bd || (d == bd && pool[k] < pool[best])) {
+        best = (int)k;
+        bd = d;
+      }
+    }
+    used[best] = true;
+    qs[i] = pool[best];
+  }
+  q[0] = tau[3];
+  q[1] = tau[2];
+  q[2] = tau[1];
+  q[3] = tau[0];
+  for (int i = 0; i < 11; ++i) q[4 + i] = qs[i];
+  const uint64_t step = 2ull << log_n;
+  uint64_t c = ((1ull << 31) - 1) / step * step + 1;
+  for (int got = 0; got < n_p; c -= step) {
+    if (c < (1ull << 30)) return CKKS_EINVAL;
+    bool in_q = false;
+    for (int i = 0; i < 15; ++i) in_q |= q[i] == c;
+    if (!in_q && host_is_prime(c)) p[got++] = (uint32_t)c;
+  }
+  static const int kFirst[9] = {2, 4, 0, 2, 4, 3, 2, 1, 0}, kCount[9] = {2, 3, 5, 6, 7, 9, 11, 13, 15};
+  for (int l = 0; l < 9; ++l) {
+    first[l] = kFirst[l];
+    count[l] = kCount[l];
+  }
   return CKKS_OK;
 }
 
@@ -295,24 +366,46 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
     c.mont_sh = shoup_of(r1, q);
   }
 
-  // key-switching constants
+  // levels: windows of the prime list (given) or prefixes (single rescaling)
+  ctx->windowed = prm->n_levels > 0;
+  if (ctx->windowed) {
+    ctx->lvl_first.assign(prm->level_first, prm->level_first + prm->n_levels);
+    ctx->lvl_count.assign(prm->level_count, prm->level_count + prm->n_levels);
+  } else {
+    ctx->lvl_first.assign(L, 0);
+    ctx->lvl_count.resize(L);
+    for (int l = 0; l < L; ++l) ctx->lvl_count[l] = l + 1;
+  }
+  const int nlev = ctx->n_levels();
+
+  // key-switching constants, per level (table index tix = level + 1): the
+  // level's window [s, s + nl) meets the fixed digits q[j alpha .. (j+1) alpha)
+  // in the active digits j = s / alpha ..
   std::vector<uint2> up_cin;
   std::vector<int32_t> up_mat;
-  std::vector<int2> up_off((size_t)(L + 1) * dnum, make_int2(0, 0));
-  for (int nl = 1; nl <= L; ++nl) {
+  std::vector<int2> up_off((size_t)(std::max(L, nlev) + 1) * dnum, make_int2(0, 0));
+  std::vector<int2> up_rows;
+  ctx->rows_off.assign(nlev + 1, 0);
+  ctx->rows_cnt.assign(nlev + 1, 0);
+  for (int tix = 1; tix <= nlev; ++tix) {
+    const int s0 = ctx->lvl_first[tix - 1], nl = ctx->lvl_count[tix - 1];
     const int ext = nl + alpha;
-    const int digits = (nl + alpha - 1) / alpha;
+    const int j0 = s0 / alpha, digits = (s0 + nl - 1) / alpha - j0 + 1;
+    auto prime_of_t = [&](int t) { return t < nl ? s0 + t : L + (t - nl); };
+    ctx->rows_off[tix] = (int)up_rows.size();
     for (int j = 0; j < digits; ++j) {
-      const int lo = j * alpha, hi = std::min(nl, lo + alpha), K = hi - lo;
-      up_off[(size_t)nl * dnum + j] = make_int2((int)up_cin.size(), (int)up_mat.size());
+      const int g = j0 + j;
+      const int lo = std::max(0, g * alpha - s0), hi = std::min(nl, (g + 1) * alpha - s0);
+      up_off[(size_t)tix * dnum + j] = make_int2((int)up_cin.size(), (int)up_mat.size());
       for (int i = lo; i < hi; ++i) {
-        uint32_t hat = 1;  // Q_j / q_i mod q_i
+        const int pi = s0 + i;
+        uint32_t hat = 1;  // Q_j / q_i mod q_i over the digit's primes in the window
         for (int i2 = lo; i2 < hi; ++i2)
-          if (i2 != i) hat = mulm(hat, pr[i2] % pr[i], pr[i]);
-        up_cin.push_back(shoup_pair(mulm(invm(hat, pr[i]), ctx->pc_host[i].ninv, pr[i]), pr[i]));
+          if (i2 != i) hat = mulm(hat, pr[s0 + i2] % pr[pi], pr[pi]);
+        up_cin.push_back(shoup_pair(mulm(invm(hat, pr[pi]), ctx->pc_host[pi].ninv, pr[pi]), pr[pi]));
       }
       for (int t = 0; t < ext; ++t) {
-        const int id = t < nl ? t : L + (t - nl);
+        const int id = prime_of_t(t);
         const uint32_t d = pr[id];
         for (int i = lo; i < hi; ++i) {
           if (t >= lo && t < hi) {
@@ -321,22 +414,14 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
           }
           uint32_t hat = 1;
           for (int i2 = lo; i2 < hi; ++i2)
-            if (i2 != i) hat = mulm(hat, pr[i2] % d, d);
+            if (i2 != i) hat = mulm(hat, pr[s0 + i2] % d, d);
           up_mat.push_back(centered_h(mulm(hat, ctx->pc_host[id].mont, d), d));
         }
       }
-      (void)K;
-    }
-  }
-  std::vector<int2> up_rows;
-  for (int nl = 1; nl <= L; ++nl) {
-    const int ext = nl + alpha;
-    const int digits = (nl + alpha - 1) / alpha;
-    for (int j = 0; j < digits; ++j) {
-      const int lo = j * alpha, hi = std::min(nl, lo + alpha);
       for (int t = 0; t < ext; ++t)
-        if (t < lo || t >= hi) up_rows.push_back(make_int2(j * ext + t, t < nl ? t : L + (t - nl)));
+        if (t < lo || t >= hi) up_rows.push_back(make_int2(j * ext + t, prime_of_t(t)));
     }
+    ctx->rows_cnt[tix] = (int)up_rows.size() - ctx->rows_off[tix];
   }
   std::vector<uint2> dn_cin(alpha), dn_pinv(L);
   std::vector<int32_t> dn_mat((size_t)L * alpha);
@@ -376,6 +461,63 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   std::vector<uint2> rs_qinv((size_t)L * L, make_uint2(0, 0));
   for (int l = 1; l < L; ++l)
     for (int i = 0; i < l; ++i) rs_qinv[(size_t)l * L + i] = shoup_pair(invm(pr[l] % pr[i], pr[i]), pr[i]);
+
+  // rational rescaling transitions l -> l - 1 (windowed levels only)
+  std::vector<int2> rr_drop, rr_rows;
+  std::vector<uint2> rr_cin;
+  std::vector<int32_t> rr_mat;
+  std::vector<RrEpi> rr_epi;
+  struct RrOff {
+    size_t drop, rows, cin, mat, epi;
+  };
+  std::vector<RrOff> rr_off(nlev);
+  ctx->rr.assign(nlev, RrArgs{});
+  if (ctx->windowed) {
+    for (int l = 1; l < nlev; ++l) {
+      const int s0 = ctx->lvl_first[l], n0 = ctx->lvl_count[l];
+      const int s1 = ctx->lvl_first[l - 1], n1 = ctx->lvl_count[l - 1];
+      std::vector<int> drop, add;
+      for (int g = s0; g < s0 + n0; ++g)
+        if (g < s1 || g >= s1 + n1) drop.push_back(g);
+      for (int g = s1; g < s1 + n1; ++g)
+        if (g < s0 || g >= s0 + n0) add.push_back(g);
+      auto prod_mod = [&](const std::vector<int>& set, uint32_t m, int skip) {
+        uint32_t r = 1 % m;
+        for (int g : set)
+          if (g != skip) r = mulm(r, pr[g] % m, m);
+        return r;
+      };
+      const int K = (int)drop.size();
+      rr_off[l] = RrOff{rr_drop.size(), rr_rows.size(), rr_cin.size(), rr_mat.size(), rr_epi.size()};
+      for (int k = 0; k < K; ++k) {
+        const int g = drop[k];
+        const uint32_t d = pr[g];
+        rr_drop.push_back(make_int2(g - s0, g));
+        rr_rows.push_back(make_int2(0, g));
+        rr_rows.push_back(make_int2(0, g));
+        const uint32_t c = mulm(mulm(prod_mod(add, d, -1), invm(prod_mod(drop, d, g), d), d), ctx->pc_host[g].ninv, d);
+        rr_cin.push_back(shoup_pair(c, d));
+      }
+      for (int i = 0; i < n1; ++i) {
+        const int g = s1 + i;
+        const uint32_t t = pr[g];
+        for (int k = 0; k < K; ++k)
+          rr_mat.push_back(centered_h(mulm(prod_mod(drop, t, drop[k]), ctx->pc_host[g].mont, t), t));
+        const uint32_t tdi = K ? invm(prod_mod(drop, t, -1), t) : 1;
+        RrEpi e;
+        e.old_limb = (g >= s0 && g < s0 + n0) ? g - s0 : -1;
+        e.ta_tdi = shoup_pair(mulm(prod_mod(add, t, -1), tdi, t), t);
+        e.tdi = shoup_pair(tdi, t);
+        rr_epi.push_back(e);
+      }
+      RrArgs& r = ctx->rr[l];
+      r.K = K;
+      r.s0 = s0;
+      r.n0 = n0;
+      r.s1 = s1;
+      r.n1 = n1;
+    }
+  }
 
   // twiddles: tw[id][k] = psi^brev(k), itw[id][k] = psi^-brev(k)
   std::vector<uint2> tw((size_t)np * n), itw((size_t)np * n);
@@ -417,6 +559,11 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {up_rows.data(), up_rows.size() * sizeof(int2), 0},
       {rs_mat.data(), rs_mat.size() * sizeof(int32_t), 0},
       {dn_pqinv.data(), dn_pqinv.size() * sizeof(uint2), 0},
+      {rr_drop.data(), rr_drop.size() * sizeof(int2), 0},
+      {rr_cin.data(), rr_cin.size() * sizeof(uint2), 0},
+      {rr_mat.data(), rr_mat.size() * sizeof(int32_t), 0},
+      {rr_epi.data(), rr_epi.size() * sizeof(RrEpi), 0},
+      {rr_rows.data(), rr_rows.size() * sizeof(int2), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -450,6 +597,14 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   dp.ks.up_rows = reinterpret_cast<const int2*>(base + parts[10].off);
   dp.ks.rs_mat = reinterpret_cast<const int32_t*>(base + parts[11].off);
   dp.ks.dn_pqinv = reinterpret_cast<const uint2*>(base + parts[12].off);
+  for (int l = 1; l < nlev && ctx->windowed; ++l) {
+    RrArgs& r = ctx->rr[l];
+    r.drop = reinterpret_cast<const int2*>(base + parts[13].off) + rr_off[l].drop;
+    r.cin = reinterpret_cast<const uint2*>(base + parts[14].off) + rr_off[l].cin;
+    r.mat = reinterpret_cast<const int32_t*>(base + parts[15].off) + rr_off[l].mat;
+    r.epi = reinterpret_cast<const RrEpi*>(base + parts[16].off) + rr_off[l].epi;
+    r.rows = reinterpret_cast<const int2*>(base + parts[17].off) + rr_off[l].rows;
+  }
 
   ctx->owns_tables = true;
   const int rc = alloc_scratch(ctx);
@@ -467,7 +622,7 @@ int alloc_scratch(ckks_ctx* ctx) {
   const DevParams& dp = ctx->dp;
   const int L = dp.L, np = dp.L + dp.alpha;
   const size_t limb = (size_t)1 << dp.log_n;
-  const size_t s_limbs = std::max(L, 2 * dp.alpha);
+  const size_t s_limbs = std::max(L, 2 * dp.alpha);  // windows are at most L primes
   // T: the ModUp limbs (dnum (L + alpha)) followed by room for the ModDown
   // conversions (2L), so that hoisted rotations keep the ModUp limbs
   const size_t t_limbs = std::max((size_t)dp.dnum * np + 2 * (size_t)L, (size_t)2 * L + 4);

@@ -54,18 +54,21 @@ struct DevParams {
 
 // Limb -> prime id. Either an explicit device array, or the extended-
 // polynomial rule: limb t (mod per_poly) < n -> q_t, else p_{t - n}.
+// Limb t of a polynomial whose ciphertext limbs are the window q[base ..
+// base + n) of the prime list is q_(base + t) for t < n, else p_(t - n).
 struct IdMap {
   const int* ids;
   int per_poly, n, L;
+  int base = 0;
   __host__ __device__ int operator()(int limb) const {
     if (ids) return ids[limb];
     int t = limb % per_poly;
-    return t < n ? t : L + (t - n);
+    return t < n ? base + t : L + (t - n);
   }
 };
 
-inline IdMap id_ct(int n, int L) { return IdMap{nullptr, n, n, L}; }
-inline IdMap id_ext(int n, int L, int alpha) { return IdMap{nullptr, n + alpha, n, L}; }
+inline IdMap id_ct(int n, int L, int base = 0) { return IdMap{nullptr, n, n, L, base}; }
+inline IdMap id_ext(int n, int L, int alpha, int base = 0) { return IdMap{nullptr, n + alpha, n, L, base}; }
 inline IdMap id_arr(const int* d) { return IdMap{d, 1 << 30, 0, 0}; }
 
 // Key-switch input modes (what polynomial is key-switched).
@@ -75,6 +78,9 @@ enum KmOut { KM_KEYSWITCH = 0, KM_ACC_ALL = 1, KM_MODUP = 2 };
 
 struct KsArgs {
   int n;                 // active ciphertext limbs
+  int base;              // their primes are q[base .. base + n) (0 unless the levels are windows)
+  int tix;               // level + 1: index of the level's key-switch tables and tuned shapes
+  int rows_off, rows_cnt;  // the level's range in the ModUp row table (ks.up_rows)
   int mode;              // KsMode
   const uint32_t* x0;    // KS_PLAIN: d [n][N]; KS_TENSOR: ct1; KS_AUTO: ct
   const uint32_t* x1;    // KS_TENSOR: ct2
@@ -103,6 +109,29 @@ struct LtArgs {
   const uint32_t* evk[kLtMax];
   const uint32_t* pt[kLtMax];
   int pt_p[kLtMax];
+};
+
+// Rational rescaling from the window of level l to that of level l - 1
+// (Sec. 3.1, Sec. 3.2): K dropped primes (their product T_drop) are divided
+// out and the added primes (T_add) multiplied in. Device tables of the
+// transition: drop[k] = (limb of the old window, prime id) of dropped prime
+// k; cin[k] = Shoup pair of N^-1 [T_add (T_drop/d_k)^-1]_{d_k}; mat[i K + k]
+// = [(T_drop/d_k) 2^32]_{t_i} centered for prime t_i of the new window;
+// epi[i] = (old limb of t_i or -1 if added, Shoup pair of [T_add T_drop^-1],
+// Shoup pair of [T_drop^-1]) packed as below.
+struct RrEpi {
+  int old_limb;
+  uint2 ta_tdi;  // [T_add T_drop^-1]_t, Shoup pair
+  uint2 tdi;     // [T_drop^-1]_t, Shoup pair
+};
+struct RrArgs {
+  int K;                  // dropped primes
+  int s0, n0, s1, n1;     // old and new windows
+  const int2* drop;
+  const int2* rows;       // [2K]: (unused, prime id of drop[y / 2]) for the row kernels
+  const uint2* cin;
+  const int32_t* mat;
+  const RrEpi* epi;
 };
 
 // Kernel ids of the key-switch and rescale pipelines (measurement support).
@@ -207,11 +236,11 @@ void launch_ntt(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, bool 
 void launch_rows_inv_only(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, cudaStream_t st);
 void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int limbs, bool to_internal,
                     cudaStream_t st);
-void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, size_t sa,
+void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, int base, size_t sa,
                  size_t sb, size_t so, cudaStream_t st);
-void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base, size_t sa,
                  size_t so, cudaStream_t st);
-void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
+void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base, size_t sa,
                   size_t so, cudaStream_t st);
 void launch_tensor(const DevParams& dp, const uint32_t* c1, const uint32_t* c2, uint32_t* out, int n,
                    cudaStream_t st);
@@ -231,7 +260,7 @@ void launch_smr(const DevParams& dp, const int64_t* x, int32_t* y, int n, int pr
 // ---- launchers (k_keyswitch.cu) ----
 // Full key switch of one polynomial (mode), result written per a.extra.
 bool col_shape_supported(int log_n, int tc, int sl, int z, int tp);
-int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int reps, cudaStream_t st);
+int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArgs& lvl, int reps, cudaStream_t st);
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st);
 // ModDown only: acc [2][n + alpha][N] (internal layout) -> out [2][n][N].
@@ -239,6 +268,8 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
                               cudaStream_t st);
 void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
                              cudaStream_t st);
+void launch_rational_rescale(const DevParams& dp, const Scratch& sc, const RrArgs& r, const uint32_t* in,
+                             size_t sin, uint32_t* out, size_t sout, cudaStream_t st);
 void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
                     cudaStream_t st);
 // Rescale: in [2][n][N] (stride sin) -> out [2][n-1][N] (stride sout).
@@ -283,6 +314,29 @@ struct ckks_ctx {
   std::vector<uint2> gadget_p;  // [L + alpha] Shoup pair of [P]_{prime}
   std::string err;
   int device;
+  // Levels: level l holds the primes q[lvl_first[l] .. lvl_first[l] +
+  // lvl_count[l]). Single rescaling: lvl_first = 0, lvl_count = l + 1. With
+  // given windows (the 25-30 prime system) rescaling is rational.
+  bool windowed = false;
+  std::vector<int> lvl_first, lvl_count;
+  std::vector<int> rows_off, rows_cnt;  // per level + 1: ModUp row-table range
+  std::vector<ckks::RrArgs> rr;         // per level l >= 1 (windowed): transition l -> l - 1
+  int n_levels() const { return (int)lvl_count.size(); }
+  int lvl_n(int level) const { return lvl_count[level]; }
+  int lvl_base(int level) const { return lvl_first[level]; }
+  int cap_limbs(int cap_level) const {
+    int m = 0;
+    for (int l = 0; l <= cap_level && l < n_levels(); ++l) m = lvl_count[l] > m ? lvl_count[l] : m;
+    return m;
+  }
+  // key-switch level arguments (n, base, table index, ModUp row range)
+  void set_level(ckks::KsArgs& k, int level) const {
+    k.n = lvl_count[level];
+    k.base = lvl_first[level];
+    k.tix = level + 1;
+    k.rows_off = rows_off[level + 1];
+    k.rows_cnt = rows_cnt[level + 1];
+  }
 };
 
 struct ckks_ct {
@@ -291,7 +345,7 @@ struct ckks_ct {
   int level, cap_level;
   double scale;
   bool borrowed;
-  size_t poly_stride() const { return (size_t)(cap_level + 1) << h.ctx->dp.log_n; }
+  size_t poly_stride() const { return (size_t)h.ctx->cap_limbs(cap_level) << h.ctx->dp.log_n; }
 };
 
 struct ckks_pt {
@@ -321,6 +375,7 @@ int alloc_scratch(ckks_ctx* ctx);
 bool host_is_prime(uint64_t n);
 uint32_t host_find_psi(uint32_t q, int log_n);
 int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p);
+int host_gen_prime_system_2530(int log_n, int n_p, uint32_t* q, uint32_t* p, int* first, int* count);
 // Encoding (fp64): N/2 complex slots -> N rounded integer coefficients.
 void host_encode(const double* re_im, int log_n, double scale, std::vector<int64_t>& coeffs);
 // Decoding from canonical residues [n][N] (coefficient domain).

@@ -158,10 +158,12 @@ void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int 
 __device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t q) { return csub(a + b, q); }
 __device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, uint32_t q) { return csub(a - b + q, q); }
 
-__global__ void k_hadd(DevParams dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, size_t sa,
-                       size_t sb, size_t so) {
+// Element-wise kernels over the n limbs of a level whose primes are
+// q[base .. base + n).
+__global__ void k_hadd(DevParams dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, int base,
+                       size_t sa, size_t sb, size_t so) {
   const int t = blockIdx.y / n, i = blockIdx.y % n;
-  const uint32_t q = dp.pc[i].q;
+  const uint32_t q = dp.pc[base + i].q;
   const size_t off = ((size_t)i << dp.log_n) + 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const uint4 x = *reinterpret_cast<const uint4*>(a + t * sa + off);
   const uint4 y = *reinterpret_cast<const uint4*>(b + t * sb + off);
@@ -170,10 +172,10 @@ __global__ void k_hadd(DevParams dp, const uint32_t* a, const uint32_t* b, uint3
 }
 
 // PAdd: (b + pt, a) limb by limb.
-__global__ void k_padd(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
-                       size_t so) {
+__global__ void k_padd(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base,
+                       size_t sa, size_t so) {
   const int t = blockIdx.y / n, i = blockIdx.y % n;
-  const uint32_t q = dp.pc[i].q;
+  const uint32_t q = dp.pc[base + i].q;
   const size_t off = ((size_t)i << dp.log_n) + 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   uint4 x = *reinterpret_cast<const uint4*>(a + t * sa + off);
   if (t == 0) {
@@ -183,10 +185,10 @@ __global__ void k_padd(DevParams dp, const uint32_t* a, const uint32_t* pt, uint
   *reinterpret_cast<uint4*>(out + t * so + off) = x;
 }
 
-__global__ void k_pmult(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
-                        size_t so) {
+__global__ void k_pmult(DevParams dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base,
+                        size_t sa, size_t so) {
   const int t = blockIdx.y / n, i = blockIdx.y % n;
-  const PrimeConst P = dp.pc[i];
+  const PrimeConst P = dp.pc[base + i];
   const size_t off = ((size_t)i << dp.log_n) + 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const uint4 x = *reinterpret_cast<const uint4*>(a + t * sa + off);
   const uint4 y = *reinterpret_cast<const uint4*>(pt + off);
@@ -262,24 +264,24 @@ static dim3 grid_elems(const DevParams& dp, int per_thread, int rows, int thread
   return dim3(((1 << dp.log_n) / per_thread + threads - 1) / threads, rows);
 }
 
-void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, size_t sa,
-                 size_t sb, size_t so, cudaStream_t st) {
+void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, int base,
+                 size_t sa, size_t sb, size_t so, cudaStream_t st) {
   const int th = 64;
-  k_hadd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, b, out, n, sa, sb, so);
+  k_hadd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, b, out, n, base, sa, sb, so);
   count_launch(1);
 }
 
-void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
-                 size_t so, cudaStream_t st) {
+void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base,
+                 size_t sa, size_t so, cudaStream_t st) {
   const int th = 64;
-  k_padd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, sa, so);
+  k_padd<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, base, sa, so);
   count_launch(1);
 }
 
-void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, size_t sa,
-                  size_t so, cudaStream_t st) {
+void launch_pmult(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base,
+                  size_t sa, size_t so, cudaStream_t st) {
   const int th = 64;
-  k_pmult<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, sa, so);
+  k_pmult<<<grid_elems(dp, 4, 2 * n, th), th, 0, st>>>(dp, a, pt, out, n, base, sa, so);
   count_launch(1);
 }
 

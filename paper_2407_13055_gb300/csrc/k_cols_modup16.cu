@@ -3,6 +3,6 @@
 
 namespace ckks {
 
-template void launch_modup_cols<Geo<8, 32>>(const DevParams&, int, int, const Scratch&, const ColShape&, cudaStream_t);
+template void launch_modup_cols<Geo<8, 32>>(const DevParams&, int, int, int, int, const Scratch&, const ColShape&, cudaStream_t);
 
 }  // namespace ckks

@@ -36,9 +36,9 @@ using G16 = Geo<8, 32>;
 using G12 = Geo<8, 8>;
 using G8 = Geo<4, 4>;
 #define CKKS_COL_DECL(G)                                                                                        \
-  extern template void launch_modup_cols<G>(const DevParams&, int, int, const Scratch&, const ColShape&,        \
+  extern template void launch_modup_cols<G>(const DevParams&, int, int, int, int, const Scratch&, const ColShape&, \
                                             cudaStream_t);                                                      \
-  extern template void launch_moddown_cols<G>(const DevParams&, int, const Scratch&, const ColShape&,           \
+  extern template void launch_moddown_cols<G>(const DevParams&, int, int, const Scratch&, const ColShape&,      \
                                               cudaStream_t);                                                    \
   extern template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*,             \
                                                   cudaStream_t);                                                \
@@ -112,7 +112,7 @@ __device__ __forceinline__ void ks_input4(const DevParams& dp, const KsArgs& a, 
   if (a.mode == KS_PLAIN) {
     load_vec<4>(v, a.x0 + off);
   } else if (a.mode == KS_TENSOR) {
-    const PrimeConst P = dp.pc[i];
+    const PrimeConst P = dp.pc[a.base + i];
     uint32_t a1[4], a2[4];
     load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
     load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
@@ -134,8 +134,9 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
                              uint32_t* km_dst) {
   const int t = blockIdx.y;
   const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
-  const int id = prime_of(t, n, L);
-  const int key_limb = t < n ? t : L + (t - n);
+  const int id = prime_of(t, n, L, a.base);
+  const int key_limb = id;  // keys cover every prime: limb = global prime index
+  const int g0 = a.base / alpha;  // first active digit of the window
   const PrimeConst P = dp.pc[id];
   const uint32_t p0 = stream_pos();
   uint32_t x[D][4], e0[D][4], e1[D][4];
@@ -144,15 +145,15 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
   if (km_out != KM_MODUP) {
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      load_vec_stream<4>(e0[j], a.evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
-      load_vec_stream<4>(e1[j], a.evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e0[j], a.evk + ((size_t)(((g0 + j) * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e1[j], a.evk + ((size_t)(((g0 + j) * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
     }
   }
   pdl_wait();
   pdl_trigger();
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    const int lo = j * alpha, hi = min(n, lo + alpha);
+    const int lo = max(0, (g0 + j) * alpha - a.base), hi = min(n, (g0 + j + 1) * alpha - a.base);
     const uint32_t* tj = T + ((size_t)(j * ext + t) << dp.log_n);
     if (t >= lo && t < hi) {
       ks_input4(dp, a, t, p0, x[j]);
@@ -207,8 +208,9 @@ __global__ void k_lt_keymult(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* 
   pdl_trigger();
   const int t = blockIdx.y;
   const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
-  const int id = prime_of(t, n, L);
-  const int key_limb = t < n ? t : L + (t - n);
+  const int id = prime_of(t, n, L, a.base);
+  const int key_limb = id;
+  const int g0 = a.base / alpha;
   const PrimeConst P = dp.pc[id];
   const uint32_t p0 = stream_pos();
   const uint32_t* ain = a.x0 + a.poly_stride0 + ((size_t)t << dp.log_n);
@@ -220,12 +222,12 @@ __global__ void k_lt_keymult(DevParams dp, KsArgs a, LtArgs lt, const uint32_t* 
     uint32_t x[D][4], e0[D][4], e1[D][4], w[4];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const int lo = j * alpha, hi = min(n, lo + alpha);
+      const int lo = max(0, (g0 + j) * alpha - a.base), hi = min(n, (g0 + j + 1) * alpha - a.base);
       const uint32_t* src = (t >= lo && t < hi) ? ain : T + ((size_t)(j * ext + t) << dp.log_n);
 #pragma unroll
       for (int k = 0; k < 4; ++k) x[j][k] = __ldg(src + auto_src(p0 + k, g, dp.log_n));
-      load_vec_stream<4>(e0[j], evk + ((size_t)((j * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
-      load_vec_stream<4>(e1[j], evk + ((size_t)((j * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e0[j], evk + ((size_t)(((g0 + j) * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+      load_vec_stream<4>(e1[j], evk + ((size_t)(((g0 + j) * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
     }
     const int pl = t < n ? t : lt.pt_p[i] + (t - n);
     load_vec<4>(w, lt.pt[i] + ((size_t)pl << dp.log_n) + p0);
@@ -269,12 +271,12 @@ __global__ void k_lt_epilogue(DevParams dp, KsArgs a, LtArgs lt, const uint32_t*
   pdl_trigger();
   const int n = a.n;
   const int u = blockIdx.y / n, i = blockIdx.y % n;
-  const PrimeConst P = dp.pc[i];
+  const PrimeConst P = dp.pc[a.base + i];
   const uint32_t p0 = stream_pos();
   const size_t off = ((size_t)i << dp.log_n) + p0;
   uint32_t z[4] = {0, 0, 0, 0};
   if (ks) {
-    const uint2 pinv = dp.ks.dn_pinv[i];
+    const uint2 pinv = dp.ks.dn_pinv[a.base + i];
     uint32_t acc[4];
     load_vec<4>(z, Z + ((size_t)(u * n + i) << dp.log_n) + p0);
     load_vec<4>(acc, A + u * a_stride + off);
@@ -381,8 +383,8 @@ struct EpiModDown {
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {
     const int n = a.n, u = y / n, i = y % n;
-    const PrimeConst P = dp.pc[i];
-    const uint2 pinv = dp.ks.dn_pinv[i];
+    const PrimeConst P = dp.pc[a.base + i];
+    const uint2 pinv = dp.ks.dn_pinv[a.base + i];
     const size_t limb = (size_t)i << dp.log_n;
 #pragma unroll
     for (int c = 0; c < E / 4; ++c) {
@@ -452,6 +454,52 @@ struct EpiRescale {
   }
 };
 
+// Dropped limbs of a rational rescaling before the iNTT rows: launch limb
+// y = 2k + u is limb drop[k].x of polynomial u.
+struct SrcDrop {
+  const uint32_t* in;
+  size_t sin;
+  const int2* drop;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    load_vec<E>(x, in + (y & 1) * sin + ((size_t)drop[y >> 1].x << dp.log_n) + pos0);
+  }
+};
+
+// Rational rescaling after the NTT rows of X (launch limb y = u n1 + i):
+// out_u[i] = (c_u[i] T_add - X) T_drop^-1 mod t_i, c_u[i] taken from the old
+// window (0 for an added prime).
+struct EpiRational {
+  RrArgs r;
+  const uint32_t* in;
+  size_t sin;
+  uint32_t* out;
+  size_t sout;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int u = y / r.n1, i = y % r.n1;
+    const uint32_t q = dp.pc[r.s1 + i].q;
+    const RrEpi e = r.epi[i];
+    const uint32_t* c = e.old_limb >= 0 ? in + u * sin + ((size_t)e.old_limb << dp.log_n) : nullptr;
+    uint32_t* o = out + u * sout + ((size_t)i << dp.log_n);
+#pragma unroll
+    for (int k4 = 0; k4 < E / 4; ++k4) {
+      const uint32_t p = pos0 + 4 * k4;
+      uint32_t cv[4] = {0, 0, 0, 0}, z[4];
+      if (c) load_vec<4>(cv, c + p);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t a = csub(shoup(cv[k], e.ta_tdi.x, e.ta_tdi.y, q), q);
+        const uint32_t b = csub(shoup(x[4 * k4 + k], e.tdi.x, e.tdi.y, q), q);
+        z[k] = csub(a + q - b, q);
+      }
+      store_vec<4>(o + p, z);
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -470,13 +518,15 @@ static void stream_grid(int log_n, int limbs, dim3& grid, int& threads) {
   grid = dim3(quads / threads, limbs);
 }
 
-// Offset and count of the level's entries in the ModUp limb table (the
-// NTT'd ModUp limbs (j, t), t outside digit j).
-static void modup_rows_range(int n, int alpha, int& off, int& cnt) {
-  auto count = [&](int m) { return ((m + alpha - 1) / alpha) * (m + alpha) - m; };
-  off = 0;
-  for (int m = 1; m < n; ++m) off += count(m);
-  cnt = count(n);
+// Digits active at the level: the fixed groups of alpha primes that meet the
+// window [base, base + n).
+static int active_digits(const KsArgs& a, int alpha) { return (a.base + a.n - 1) / alpha - a.base / alpha + 1; }
+
+// Row map of the level's n ciphertext limbs (window primes).
+static LimbMap window_map(const KsArgs& a, int L) {
+  LimbMap m{nullptr, 0, a.n, a.n, L};
+  m.base = a.base;
+  return m;
 }
 
 // ModDown fused with rescaling by q_l (l = n - 1): out gets n - 1 limbs.
@@ -500,7 +550,7 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_MODDOWN_ROWS);
   launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
   prof_mark(sc, st, P_RS_IN_ROWS);
-  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, n, default_shape<G>(2)), st);
+  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_g<G>(dp, false, T3, T3, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
   prof_mark(sc, st, P_RS_ROWS);
@@ -521,28 +571,27 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
                    LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  launch_moddown_cols<G>(dp, n, sc, pick_shape<G>(sc, CK_MODDOWN, n, default_shape<G>(2)), st);
+  launch_moddown_cols<G>(dp, n, a.base, sc, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
   prof_mark(sc, st, P_MODDOWN_COLS);
-  launch_rows_fwd<G>(dp, sc.T, EpiModDown{a, A, a_stride}, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, st);
+  launch_rows_fwd<G>(dp, sc.T, EpiModDown{a, A, a_stride}, 2 * n, window_map(a, dp.L), st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
 }
 
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st) {
   const int n = a.n, alpha = dp.alpha, ext = n + alpha;
-  const int digits = (n + alpha - 1) / alpha;
+  const int digits = active_digits(a, alpha);
   const size_t limb = (size_t)1 << dp.log_n;
   dim3 g;
   int th;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
-    launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
+    launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, n, window_map(a, dp.L), true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
-    launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
+    launch_modup_cols<G>(dp, n, a.base, a.tix, digits, sc,
+                         pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits)), st);
     prof_mark(sc, st, P_MODUP_COLS);
-    int off, cnt;
-    modup_rows_range(n, alpha, off, cnt);
-    launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+    launch_rows_g<G>(dp, false, sc.T, sc.T, a.rows_cnt, LimbMap{dp.ks.up_rows + a.rows_off, 0, 1, 0, 0}, false, st);
     prof_mark(sc, st, P_MODUP_ROWS);
     stream_grid(dp.log_n, ext, g, th);
     launch_keymult(digits, g, th, st, dp, a, sc.T, sc.A, km_out, km_dst);
@@ -582,7 +631,8 @@ static std::vector<ColShape> shape_candidates(int targets, const ColShape& def) 
   return v;
 }
 
-int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int reps, cudaStream_t st) {
+int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArgs& lvl, int reps, cudaStream_t st) {
+  const int n = lvl.n, base = lvl.base, tix = lvl.tix;
   if (n < 1 || n > dp.L || reps < 1) return CKKS_EINVAL;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return CKKS_ECUDA;
@@ -592,21 +642,21 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int 
   }
   int rc = CKKS_OK;
   const size_t limb = (size_t)1 << dp.log_n;
-  const int alpha = dp.alpha, digits = (n + alpha - 1) / alpha;
+  const int alpha = dp.alpha, digits = active_digits(lvl, alpha);
   CKKS_DISPATCH_LOGN(dp.log_n, {
     for (int k = 0; k < CK_COUNT && rc == CKKS_OK; ++k) {
-      if (k == CK_RS_FUSED && n < 2) continue;
+      if (k == CK_RS_FUSED && (n < 2 || base != 0)) continue;  // single rescaling only
       ColShape def;
       int targets;
       std::function<void(const ColShape&)> run;
       if (k == CK_MODUP) {
         def = default_shape<G>(digits);
         targets = n;  // fewest targets of a digit: n + alpha - (digit size)
-        run = [&](const ColShape& s) { launch_modup_cols<G>(dp, n, digits, sc, s, st); };
+        run = [&](const ColShape& s) { launch_modup_cols<G>(dp, n, base, tix, digits, sc, s, st); };
       } else if (k == CK_MODDOWN) {
         def = default_shape<G>(2);
         targets = n;
-        run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, sc, s, st); };
+        run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, base, sc, s, st); };
       } else {
         def = default_shape<G>(2);
         targets = n - 1;
@@ -632,7 +682,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, int n, int 
           best = s;
         }
       }
-      if (rc == CKKS_OK) tu.set(k, n, best, 1e3f * best_ms / reps);
+      if (rc == CKKS_OK) tu.set(k, tix, best, 1e3f * best_ms / reps);
     }
   });
   cudaEventDestroy(e0);
@@ -652,7 +702,7 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
   if (count < 1) return;
   const KsArgs& a0 = rots[0];
   const int n = a0.n, alpha = dp.alpha, ext = n + alpha;
-  const int digits = (n + alpha - 1) / alpha;
+  const int digits = active_digits(a0, alpha);
   const size_t limb = (size_t)1 << dp.log_n;
   Scratch down = sc;
   down.T = sc.T + (size_t)digits * ext * limb;
@@ -660,13 +710,13 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
   int th;
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
-    launch_rows_g<G>(dp, true, a0.x0 + a0.poly_stride0, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
+    launch_rows_g<G>(dp, true, a0.x0 + a0.poly_stride0, sc.S, n, window_map(a0, dp.L), true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
-    launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
+    launch_modup_cols<G>(dp, n, a0.base, a0.tix, digits, sc,
+                         pick_shape<G>(sc, CK_MODUP, a0.tix, default_shape<G>(digits)), st);
     prof_mark(sc, st, P_MODUP_COLS);
-    int off, cnt;
-    modup_rows_range(n, alpha, off, cnt);
-    launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+    launch_rows_g<G>(dp, false, sc.T, sc.T, a0.rows_cnt, LimbMap{dp.ks.up_rows + a0.rows_off, 0, 1, 0, 0}, false,
+                     st);
     prof_mark(sc, st, P_MODUP_ROWS);
     for (int i = 0; i < count; ++i) {
       stream_grid(dp.log_n, ext, g, th);
@@ -685,7 +735,7 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
 void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
                              cudaStream_t st) {
   const int n = a.n, alpha = dp.alpha, ext = n + alpha;
-  const int digits = (n + alpha - 1) / alpha;
+  const int digits = active_digits(a, alpha);
   const size_t limb = (size_t)1 << dp.log_n;
   Scratch down = sc;
   down.T = sc.T + (size_t)digits * ext * limb;
@@ -694,13 +744,13 @@ void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArg
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
     if (lt.rotated > 0) {
-      launch_rows_g<G>(dp, true, a.x0 + a.poly_stride0, sc.S, n, LimbMap{nullptr, 0, n, n, dp.L}, true, st);
+      launch_rows_g<G>(dp, true, a.x0 + a.poly_stride0, sc.S, n, window_map(a, dp.L), true, st);
       prof_mark(sc, st, P_KS_IN_ROWS);
-      launch_modup_cols<G>(dp, n, digits, sc, pick_shape<G>(sc, CK_MODUP, n, default_shape<G>(digits)), st);
+      launch_modup_cols<G>(dp, n, a.base, a.tix, digits, sc,
+                           pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits)), st);
       prof_mark(sc, st, P_MODUP_COLS);
-      int off, cnt;
-      modup_rows_range(n, alpha, off, cnt);
-      launch_rows_g<G>(dp, false, sc.T, sc.T, cnt, LimbMap{dp.ks.up_rows + off, 0, 1, 0, 0}, false, st);
+      launch_rows_g<G>(dp, false, sc.T, sc.T, a.rows_cnt, LimbMap{dp.ks.up_rows + a.rows_off, 0, 1, 0, 0}, false,
+                       st);
       prof_mark(sc, st, P_MODUP_ROWS);
       stream_grid(dp.log_n, ext, g, th);
       launch_lt_keymult(digits, g, th, st, dp, a, lt, sc.T, sc.A);
@@ -710,9 +760,9 @@ void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArg
       launch_rows_g<G>(dp, true, sc.A, down.S, 2 * alpha,
                        LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
       prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-      launch_moddown_cols<G>(dp, n, down, pick_shape<G>(sc, CK_MODDOWN, n, default_shape<G>(2)), st);
+      launch_moddown_cols<G>(dp, n, a.base, down, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
       prof_mark(sc, st, P_MODDOWN_COLS);
-      launch_rows_g<G>(dp, false, down.T, down.T, 2 * n, LimbMap{nullptr, 0, n, n, dp.L}, false, st);
+      launch_rows_g<G>(dp, false, down.T, down.T, 2 * n, window_map(a, dp.L), false, st);
       prof_mark(sc, st, P_MODDOWN_ROWS);
     }
     stream_grid(dp.log_n, 2 * n, g, th);
@@ -723,10 +773,33 @@ void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArg
   });
 }
 
+// Rational rescaling (Sec. 3.1, Sec. 3.2, Sec. 5.1): iNTT rows of each
+// dropped limb of both polynomials (S = [K][2]), the conversion column
+// kernel (T = [2][n1]), NTT rows with the epilogue. `in` is [2][n0] limbs of
+// the old window (poly stride sin words), `out` [2][n1] of the new one.
+void launch_rational_rescale(const DevParams& dp, const Scratch& sc, const RrArgs& r, const uint32_t* in,
+                             size_t sin, uint32_t* out, size_t sout, cudaStream_t st) {
+  CKKS_DISPATCH_LOGN(dp.log_n, {
+    prof_mark(sc, st, -1);
+    if (r.K > 0) {
+      // every dropped limb of both polynomials: launch limb y = 2k + u -> S[y]
+      launch_rows_inv<G>(dp, SrcDrop{in, sin, r.drop}, sc.S, 2 * r.K, LimbMap{r.rows, 0, 1, 0, 0}, true, st);
+      prof_mark(sc, st, P_RS_IN_ROWS);
+      launch_rr_cols<G>(dp, r, sc, st);
+      prof_mark(sc, st, P_RS_COLS);
+    }
+    LimbMap m{nullptr, 0, r.n1, r.n1, dp.L};
+    m.base = r.s1;
+    launch_rows_fwd<G>(dp, sc.T, EpiRational{r, in, sin, out, sout}, 2 * r.n1, m, st);
+    prof_mark(sc, st, P_RS_ROWS);
+  });
+}
+
 void launch_moddown(const DevParams& dp, const Scratch& sc, const uint32_t* acc, int n, uint32_t* out,
                     cudaStream_t st) {
   KsArgs a{};
   a.n = n;
+  a.tix = n;
   a.out = out;
   a.out_stride = (size_t)n << dp.log_n;
   a.extra = 0;

@@ -49,6 +49,10 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int l
     ctx->err = "rescale_noalloc: level must be in [1, n_q - 1]";
     return CKKS_ELEVEL;
   }
+  if (ctx->windowed) {
+    ctx->err = "rescale_noalloc: single-rescaling levels only";
+    return CKKS_EINVAL;
+  }
   const size_t limb = (size_t)1 << ctx->dp.log_n;
   const size_t need = (2 + 2 * (size_t)level) * limb;  // top limb of both polys + level limbs of both
   if (need > kScratchWords) {

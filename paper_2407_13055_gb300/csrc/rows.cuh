@@ -14,18 +14,20 @@ namespace ckks {
 // Limb list of a row launch: launch index y -> (data limb index, prime id).
 // Rule (no table): y = u * pl + r selects limb first + r of polynomial u,
 // whose limbs start at data limb u * ps; that limb's extended index
-// t = (first + r) % per is q_t for t < n, else p_(t - n).
+// t = (first + r) % per is q_(base + t) for t < n, else p_(t - n) (base: the
+// first prime of the level's window).
 struct LimbMap {
   const int2* tab;  // explicit table, or null for the rule
   int first;
   int per, n, L;
   int pl = 1 << 30, ps = 0;
   int fixed = -1;   // >= 0: every limb uses this prime id
+  int base = 0;
   __device__ __forceinline__ int2 operator()(int y) const {
     if (tab) return tab[y];
     const int u = y / pl, r = y % pl;
     const int t = (first + r) % per;
-    return make_int2(u * ps + first + r, fixed >= 0 ? fixed : (t < n ? t : L + (t - n)));
+    return make_int2(u * ps + first + r, fixed >= 0 ? fixed : (t < n ? base + t : L + (t - n)));
   }
 };
 

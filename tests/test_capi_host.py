@@ -62,3 +62,13 @@ def test_ctx_create_without_gpu_fails_cleanly(K, O):
     with pytest.raises(K.CkksError) as e:
         K.ckks_ctx_create(12, q, p, 4)
     assert e.value.code == K.CKKS_ECUDA
+
+
+@pytest.mark.parametrize("log_n", [8, 12, 16])
+def test_prime_system_2530_matches_oracle(K, O, log_n):
+    """The library's 25-30 prime system (its own code) equals the oracle's."""
+    q, p, levels = K.ckks_gen_prime_system_2530(log_n, 5)
+    P, lv = O.prime_system_2530(log_n, 5)
+    assert q.tolist() == [int(v) for v in P.q]
+    assert p.tolist() == [int(v) for v in P.p]
+    assert levels == [tuple(x) for x in lv]

@@ -1,0 +1,156 @@
+"""The 25-30 prime system (Sec. 3.2, Table 2) and rational rescaling in the
+oracle, pinned against the paper's table, big-integer arithmetic and
+decryption."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2407_13055_gb300 import inputs
+
+# Table 2: per level, number of 25-bit primes (tau) and 30-bit primes (q), log2 Q, log2 Delta
+TABLE2 = [(2, 0, 50, None), (0, 3, 90, 40), (4, 1, 130, 40), (2, 4, 170, 40), (0, 7, 210, 40),
+          (1, 8, 265, 55), (2, 9, 320, 55), (3, 10, 375, 55), (4, 11, 430, 55)]
+
+
+def _window(P, lv):
+    s, n = lv
+    return [int(v) for v in P.q[s:s + n]]
+
+
+@pytest.mark.parametrize("log_n", [6, 12, 16])
+def test_prime_system_matches_table2(O, log_n):
+    P, levels = O.prime_system_2530(log_n, 5)
+    m = 2 << log_n
+    allp = [int(v) for v in P.q] + [int(v) for v in P.p]
+    assert len(set(allp)) == len(allp)
+    for v in allp:
+        assert v % m == 1 and O.is_prime(v)
+    taus, qs = [int(v) for v in P.q[:4]], [int(v) for v in P.q[4:]]
+    # "sufficiently close to 2^k": the candidates are 2N apart (2^17 at N = 2^16)
+    assert all(abs(math.log2(t) - 25) < 0.2 for t in taus)
+    assert all(abs(math.log2(q) - 30) < 0.3 for q in qs)
+    for lv, (nt, nq, logq, _) in zip(levels, TABLE2):
+        w = _window(P, lv)
+        assert sum(1 for v in w if v in taus) == nt and sum(1 for v in w if v in qs) == nq
+        assert abs(sum(math.log2(v) for v in w) - logq) < 0.5
+    # every level is a contiguous window; the top level holds every prime (Q_max)
+    assert levels[-1] == (0, len(P.q))
+
+
+def test_rescaling_cycle_keeps_scale_within_a_tenth_of_a_bit(O):
+    """Sec. 3.2: with the fixed prime order, Delta stays within 2^39.9 .. 2^40.1
+    through the rescaling cycle (and ~2^55 at the double-rescaling levels)."""
+    P, levels = O.prime_system_2530(16, 5)
+    for top, delta in ((4, 40.0), (8, 55.0)):
+        logd = delta
+        for lv in range(top, 0 if top == 4 else 5, -1):
+            old, new = set(range(*_span(levels[lv]))), set(range(*_span(levels[lv - 1])))
+            drop = sum(math.log2(int(P.q[g])) for g in old - new)
+            add = sum(math.log2(int(P.q[g])) for g in new - old)
+            logd = 2 * logd + add - drop          # HMult squares the scale, then the rescale
+            want = 40.0 if lv - 1 <= 4 else 55.0
+            assert abs(logd - want) < 0.1, (lv, logd)
+
+
+def _span(lv):
+    return lv[0], lv[0] + lv[1]
+
+
+def _crt(res, primes):
+    Q = math.prod(primes)
+    x = 0
+    for r, q in zip(res, primes):
+        qh = Q // q
+        x += int(r) * qh * pow(qh % q, -1, q)
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+@pytest.mark.parametrize("step", [(4, 3), (3, 2), (2, 1), (1, 0), (8, 7), (5, 4)])
+def test_rational_rescale_is_division_by_t_drop_times_t_add(O, step):
+    """c' = (c T_add - X) / T_drop with X = c T_add (mod T_drop) and
+    |X| <= (K/2 + 1/2) T_drop (fast BConv of K dropped primes), checked per
+    coefficient in big integers."""
+    P, levels = O.prime_system_2530(6, 5)
+    (s0, n0), (s1, n1) = levels[step[0]], levels[step[1]]
+    rng = np.random.default_rng(step[0])
+    old = [int(v) for v in P.q[s0:s0 + n0]]
+    new = [int(v) for v in P.q[s1:s1 + n1]]
+    ct = np.stack([np.stack([rng.integers(0, q, P.n) for q in old]) for _ in range(2)]).astype(np.uint32)
+    out = O.rescale_rational(P, ct, s0, n0, s1, n1)
+    drop = [q for g, q in zip(range(s0, s0 + n0), old) if not s1 <= g < s1 + n1]
+    add = [q for g, q in zip(range(s1, s1 + n1), new) if not s0 <= g < s0 + n0]
+    t_drop, t_add, K = math.prod(drop), math.prod(add), len(drop)
+    for u in range(2):
+        c_coef = O.intt(ct[u], old)
+        o_coef = O.intt(out[u], new)
+        for k in range(0, P.n, 7):
+            c = _crt([c_coef[i][k] for i in range(n0)], old)
+            o = _crt([o_coef[i][k] for i in range(n1)], new)
+            x = c * t_add - o * t_drop
+            assert (x - c * t_add) % t_drop == 0
+            assert abs(x) <= (K / 2 + 0.5) * t_drop
+
+
+def test_hmult_through_the_rescaling_cycle_decrypts(O):
+    """Encrypt at level 4 (Delta = 2^40), square with HMult + rational
+    rescaling down to level 0: every decryption is u^(2^k) within 1e-3.
+    HRot at a window level decrypts to the rotation."""
+    P, levels = O.prime_system_2530(10, 5)
+    seed = 11
+    s = inputs.ternary_secret(seed, P.n, None)
+    allp = P.all_primes()
+    a = np.stack([inputs.uniform_residues(seed, allp, P.n, 100 + j) for j in range(P.dnum)])
+    e = np.stack([inputs.gaussian_error(seed, P.n, 100 + j) for j in range(P.dnum)])
+    rk = O.keygen_relin(P, s, a, e)
+    u = 0.9 * inputs.messages(seed, P.n // 2)
+    sc = 2.0 ** 40
+    s4, n4 = levels[4]
+    m = O.encode_coeffs(u, sc, P.log_n)
+    pt = O.small_to_ntt(m, [int(v) for v in P.q[s4:s4 + n4]], P.log_n)
+    ai = inputs.uniform_residues(seed, [int(v) for v in P.q[s4:s4 + n4]], P.n, 7)
+    ct = _encrypt_window(O, P, s, pt, ai, inputs.gaussian_error(seed, P.n, 7), s4, n4)
+    want = u.copy()
+    for lv in range(4, 0, -1):
+        (so, no), (sn, nn) = levels[lv], levels[lv - 1]
+        prod = O.hmult(P, ct, ct, rk, rescale=False, base=so)
+        ct = O.rescale_rational(P, prod, so, no, sn, nn)
+        drop = [int(P.q[g]) for g in range(so, so + no) if not sn <= g < sn + nn]
+        add = [int(P.q[g]) for g in range(sn, sn + nn) if not so <= g < so + no]
+        sc = sc * sc * math.prod(add) / math.prod(drop)
+        want = want * want
+        got = _decrypt_window(O, P, s, ct, sn, nn, sc)
+        assert np.max(np.abs(got - want)) < 1e-3, lv
+    # HRot by 3 at level 3 (window base 2)
+    a2 = np.stack([inputs.uniform_residues(seed, allp, P.n, 200 + j) for j in range(P.dnum)])
+    e2 = np.stack([inputs.gaussian_error(seed, P.n, 200 + j) for j in range(P.dnum)])
+    k = O.rot_k(3, P.log_n)
+    gk = O.keygen_auto(P, s, k, a2, e2)
+    s3, n3 = levels[3]
+    pt3 = O.small_to_ntt(O.encode_coeffs(u, 2.0 ** 40, P.log_n), [int(v) for v in P.q[s3:s3 + n3]], P.log_n)
+    ai3 = inputs.uniform_residues(seed, [int(v) for v in P.q[s3:s3 + n3]], P.n, 9)
+    c3 = _encrypt_window(O, P, s, pt3, ai3, inputs.gaussian_error(seed, P.n, 9), s3, n3)
+    rot = O.hrot(P, c3, k, gk, base=s3)
+    got = _decrypt_window(O, P, s, rot, s3, n3, 2.0 ** 40)
+    assert np.max(np.abs(got - np.roll(u, -3))) < 1e-3
+
+
+def _encrypt_window(O, P, s, pt, a, e, base, n):
+    primes = [int(v) for v in P.q[base:base + n]]
+    sh = O.small_to_ntt(s, primes, P.log_n).astype(np.uint64)
+    eh = O.small_to_ntt(e, primes, P.log_n).astype(np.uint64)
+    qc = np.array(primes, np.uint64)[:, None]
+    a = a.astype(np.uint64)
+    b = (pt.astype(np.uint64) + eh + (qc - a * sh % qc)) % qc
+    return np.stack([b, a]).astype(np.uint32)
+
+
+def _decrypt_window(O, P, s, ct, base, n, scale):
+    primes = [int(v) for v in P.q[base:base + n]]
+    sh = O.small_to_ntt(s, primes, P.log_n).astype(np.uint64)
+    qc = np.array(primes, np.uint64)[:, None]
+    m = (ct[0].astype(np.uint64) + ct[1].astype(np.uint64) * sh % qc) % qc
+    coef = O.intt(m.astype(np.uint32), primes)
+    big = O.crt_centered(coef, primes)
+    return O.decode_coeffs(np.array([float(b) for b in big]), scale, P.log_n)
