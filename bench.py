@@ -574,6 +574,78 @@ def run_latency(args, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# 25-30 prime system (Table 2): per-level latency with rational rescaling
+# ----------------------------------------------------------------------------
+
+def run_rns2530(args, local_rank):
+    import math
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    alpha = 5
+    q, p, levels = K.ckks_gen_prime_system_2530(LOG_N, alpha)
+    dnum = -(-len(q) // alpha)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, dnum, scale=2.0**40, secret_hw=HW, stream=stream.cuda_stream,
+                            levels=levels)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
+    sk = K.ckks_keygen_secret(ctx, 81)
+    rk = K.ckks_keygen_relin(ctx, sk, 82)
+    gk = K.ckks_keygen_rot(ctx, sk, 1, 83)
+    reps = max(50, args.steps)
+    rows = []
+
+    def median_us(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts))
+
+    for lv in range(len(levels)):
+        if not args.no_tune:
+            K.ckks_tune(ctx, lv, 3)
+        delta = 2.0 ** (55 if lv >= 5 else 40)
+        a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(84, (1 << LOG_N) // 2), lv, delta), 85)
+        out = K.ckks_ct_create(ctx, lv)
+        s0, n0 = levels[lv]
+        row = {"level": lv, "taus": sum(1 for g in range(s0, s0 + n0) if g < 4),
+               "qs": sum(1 for g in range(s0, s0 + n0) if g >= 4),
+               "log2_Q": sum(math.log2(int(q[g])) for g in range(s0, s0 + n0)),
+               "hrot_us": median_us(lambda: K.ckks_hrot(ctx, a, 1, gk, out)),
+               "hmult_us": median_us(lambda: K.ckks_hmult(ctx, a, a, rk, 0, out))}
+        if lv >= 1:
+            row["hmult_rational_rescale_us"] = median_us(lambda: K.ckks_hmult(ctx, a, a, rk, K.CKKS_RESCALE, out))
+            row["rational_rescale_us"] = median_us(lambda: K.ckks_rescale(ctx, a, out))
+            K.ckks_hmult(ctx, a, a, rk, K.CKKS_RESCALE, out)
+            row["log2_scale_after_hmult"] = math.log2(K.ckks_ct_info(out)[1])
+        rows.append(row)
+        K.ckks_free(a)
+        K.ckks_free(out)
+    top = rows[4]
+    line = {"metric": "25-30 prime system (Table 2) at N=2^16 (1 GB300): HMult+rational rescale latency",
+            "value": 1e6 / top["hmult_rational_rescale_us"], "unit": "HMult+rescale/s at level 4 (one at a time)",
+            "n_gpus": 1, "steps": reps, "warmup": 3, "ms_per_step": top["hmult_rational_rescale_us"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (fresh encryptions)",
+            "config": {"workload": "levels 0-8 of the 25-30 system (15 primes, alpha=5, dnum=3, one key for all "
+                                   "levels); median of >=50, warm L2",
+                       "N": 1 << LOG_N, "primes": [int(v) for v in q], "levels": levels},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+    for h in (sk, rk, gk):
+        K.ckks_free(h)
+    K.ckks_ctx_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
 # ablation: Table 3 on this GPU, and sequential fusion of ModDown + rescale
 # ----------------------------------------------------------------------------
 
@@ -873,7 +945,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation", "rns2530"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",
@@ -902,6 +974,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args, local_rank)
+        return
+    if args.workload == "rns2530":
+        run_rns2530(args, local_rank)
         return
     if world > 1:
         import torch
