@@ -46,7 +46,8 @@ def workload_config(extra=None):
                     "HMult+relin+rescale and HRot(1) per ciphertext",
         "N": 1 << LOG_N, "limbs": L, "alpha": ALPHA, "dnum": DNUM, "level": LEVEL, "secret_hw": HW,
         "batch_ciphertexts": BATCH, "ops_per_step": 2 * BATCH,
-        "l2": "inputs larger than L2 (256 ciphertexts = 5.4 GB + 2 keys = 170 MB, rotated; no flush)",
+        "l2": f"inputs larger than L2 ({BATCH} ciphertexts = {BATCH * 2 * L * (1 << LOG_N) * 4 / 1e9:.2f} GB + 2 keys "
+              f"= 170 MB, rotated; no flush)",
     }
     if extra:
         cfg.update(extra)
@@ -97,9 +98,9 @@ def kernel_models(n=L, alpha=ALPHA):
 # describe the kernel sources they were taken on: when the SHA-1 of csrc/
 # differs, the figures are stale and the bench reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "07a22a9cb52d4129139b3b63b3962d92a86ce547",
-    "bytes_per_launch": {"modup_cols": 10.63e6, "keymult": 143.79e6, "modup_rows": 60.92e6,
-                         "rescale_cols": 7.92e6, "rescale_rows": 40.93e6},
+    "sources_sha1": "e7607fba4c914068a98dc7199f998577911af243",
+    "bytes_per_launch": {"modup_cols": 10.62e6, "keymult": 131.89e6, "modup_rows": 60.96e6,
+                         "moddown_cols": 7.40e6, "moddown_rows": 76.51e6},
 }
 
 
@@ -305,7 +306,9 @@ def run_native(args, rank, world, local_rank):
     barrier()
     launches0 = K.ckks_launch_count()
     with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")
         ms = timed(args.steps, args.lanes)
+        torch.cuda.nvtx.range_pop()
     launches = K.ckks_launch_count() - launches0
     ms = replicas.max_over_ranks(ms)
     ops = 2 * BATCH * args.steps * world
@@ -314,7 +317,9 @@ def run_native(args, rank, world, local_rank):
     # one lane, in order: per-kernel CUDA-event times on the launching stream
     seq_steps = max(3, args.steps // 4)
     K.ckks_profile(ctx, True)
+    torch.cuda.nvtx.range_push("one_lane")   # profilers can scope to this phase
     ms_seq = timed(seq_steps, 1)
+    torch.cuda.nvtx.range_pop()
     K.ckks_profile(ctx, False)
     prof = K.ckks_profile_read(ctx)
     seq_ops_per_s = 2 * BATCH * seq_steps / (ms_seq / 1e3)
@@ -938,6 +943,7 @@ def run_serve(args, local_rank):
 
 
 def main():
+    global BATCH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -948,9 +954,12 @@ def main():
     ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation", "rns2530"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="resident ciphertexts per step of the single-op workload (smaller only for profiling)")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",
                     help="programmatic dependent launch for the key-switch kernels")
     args = ap.parse_args()
+    BATCH = args.batch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

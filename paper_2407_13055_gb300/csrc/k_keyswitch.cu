@@ -140,15 +140,8 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
   const PrimeConst P = dp.pc[id];
   const uint32_t p0 = stream_pos();
   uint32_t x[D][4], e0[D][4], e1[D][4];
-  // the key was written long before the previous kernel: stream it before
-  // waiting for that kernel (programmatic dependent launch)
-  if (km_out != KM_MODUP) {
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      load_vec_stream<4>(e0[j], a.evk + ((size_t)(((g0 + j) * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
-      load_vec_stream<4>(e1[j], a.evk + ((size_t)(((g0 + j) * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
-    }
-  }
+  // (streaming the key before the wait kept every key word live across it:
+  // 86 registers and a third of the occupancy, so the wait comes first)
   pdl_wait();
   pdl_trigger();
 #pragma unroll
@@ -170,6 +163,11 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
 #pragma unroll
     for (int j = 0; j < D; ++j) store_vec<4>(km_dst + ((size_t)(j * ext + t) << dp.log_n) + p0, x[j]);
     return;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    load_vec_stream<4>(e0[j], a.evk + ((size_t)(((g0 + j) * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
+    load_vec_stream<4>(e1[j], a.evk + ((size_t)(((g0 + j) * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
   }
   uint32_t acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
 #pragma unroll
