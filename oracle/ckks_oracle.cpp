@@ -563,6 +563,61 @@ void or_hmult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p,
   else std::memcpy(out, res.data(), 2 * poly * 4);
 }
 
+// HMult with ModDown merged into the rescaling (the merge the paper takes
+// from MAD, Sec. 6): with Y_u = KeyMult(ModUp(d2))_u + P d_u over Q_l and P
+// (d_u the tensor's d0, d1; P d_u = 0 on the P limbs), one fast basis
+// conversion from the primes P and q_l (Eq. 2, centered) gives
+// X = BConv([Y]_{P q_l}) on q_0 .. q_{l-1}, and out_i = (Y_i - X_i)
+// (P q_l)^-1. This divides by P q_l in one rounding instead of ModDown then
+// rescale, so its result differs from or_hmult(..., rescale = 1) by a small
+// polynomial. ct = [2][n_q][N]; out = [2][n_q - 1][N]. Single rescaling.
+void or_hmult_merged(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
+                     const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t* evk, uint32_t* out) {
+  Params P{log_n, L, alpha, dnum, q, p, 0};
+  u32 n = P.n();
+  const int ext = n_q + alpha, l = n_q - 1, nd = n_digits(n_q, alpha);
+  size_t poly = size_t(n_q) * n;
+  std::vector<u32> d(3 * poly), up(size_t(nd) * ext * n), acc(size_t(2) * ext * n);
+  or_tensor(ct1, ct2, n_q, q, log_n, d.data());
+  modup(P, d.data() + 2 * poly, n_q, up.data());
+  keymult(P, up.data(), n_q, evk, acc.data());
+  std::vector<u32> src(alpha + 1), dst(l);
+  for (int k = 0; k < alpha; ++k) src[k] = p[k];
+  src[alpha] = q[l];
+  for (int i = 0; i < l; ++i) dst[i] = q[i];
+  for (int u = 0; u < 2; ++u) {
+    const u32* a = acc.data() + size_t(u) * ext * n;
+    const u32* du = d.data() + size_t(u) * poly;
+    // Y on q_i: acc_i + [P]_{q_i} d_i; on p_k: acc_(n_q + k)
+    auto pmod = [&](u32 m) {
+      u32 r = 1;
+      for (int k = 0; k < alpha; ++k) r = mul_mod(r, p[k] % m, m);
+      return r;
+    };
+    std::vector<u32> y(size_t(alpha + 1) * n);
+    for (int k = 0; k < alpha; ++k) {
+      std::memcpy(&y[size_t(k) * n], a + size_t(n_q + k) * n, n * 4);
+      intt_fast(&y[size_t(k) * n], log_n, p[k]);
+    }
+    u32 pl = pmod(q[l]);
+    for (u32 c = 0; c < n; ++c)
+      y[size_t(alpha) * n + c] = add_mod(a[size_t(l) * n + c], mul_mod(pl, du[size_t(l) * n + c], q[l]), q[l]);
+    intt_fast(&y[size_t(alpha) * n], log_n, q[l]);
+    std::vector<u32> x(size_t(l) * n);
+    bconv(y.data(), alpha + 1, src.data(), x.data(), l, dst.data(), n);
+    for (int i = 0; i < l; ++i) {
+      u32 qi = q[i];
+      ntt_fast(&x[size_t(i) * n], log_n, qi);
+      u32 pi = pmod(qi);
+      u32 inv = inv_mod(mul_mod(pi, q[l] % qi, qi), qi);
+      for (u32 c = 0; c < n; ++c) {
+        u32 yi = add_mod(a[size_t(i) * n + c], mul_mod(pi, du[size_t(i) * n + c], qi), qi);
+        out[(size_t(u) * l + i) * n + c] = mul_mod(sub_mod(yi, x[size_t(i) * n + c], qi), inv, qi);
+      }
+    }
+  }
+}
+
 // HRot / HConj (Sec. 2.3): out = (phi_k(b), 0) + KeySwitch(phi_k(a)) with the
 // key for phi_k(s); k = 5^r mod 2N for a rotation by r, k = 2N - 1 for
 // conjugation. Automorphism first (the equivalent order of the paper's

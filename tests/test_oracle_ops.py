@@ -416,3 +416,40 @@ def test_linear_transform_single_rotation_is_pmult_of_hrot_up_to_moddown(O):
         big = O.crt_centered(coeff[u_], P.q[:n_q])
         # |pt (.) rounding| <= N * max|m| * (alpha + 1) / 2 per coefficient (rounding in [-K/2, K/2] per limb)
         assert max(abs(int(x)) for x in big) <= P.n * 3 * (P.alpha + 2)
+
+
+def test_merged_moddown_rescale_differs_by_a_small_polynomial(O):
+    """HMult with ModDown merged into the rescaling (one division by P q_l)
+    and the exact ModDown-then-rescale differ per coefficient by at most a
+    few units: both are (Y - X) / (P q_l) with X of bounded size."""
+    P = O.make_params(8, 6, 3)
+    rng = np.random.default_rng(21)
+    n_q = 6
+    mk = lambda: np.stack([np.stack([rng.integers(0, int(v), P.n) for v in P.q[:n_q]]) for _ in range(2)]).astype(np.uint32)
+    c1, c2 = mk(), mk()
+    evk = np.stack([np.stack([np.stack([rng.integers(0, int(v), P.n) for v in P.all_primes()]) for _ in range(2)])
+                    for _ in range(P.dnum)]).astype(np.uint32)
+    merged = O.hmult_merged(P, c1, c2, evk)
+    exact = O.hmult(P, c1, c2, evk, rescale=True)
+    primes = [int(v) for v in P.q[:n_q - 1]]
+    for u in range(2):
+        diff = (merged[u].astype(np.int64) - exact[u].astype(np.int64)) % np.array(primes, np.int64)[:, None]
+        coef = O.intt(diff.astype(np.uint32), primes)
+        big = O.crt_centered(coef, primes)
+        assert max(abs(int(x)) for x in big) <= P.alpha + 3
+
+
+def test_merged_hmult_decrypts(O):
+    P = O.make_params(12, 4, 4, 1)
+    seed = 4
+    s, ks = _keys(O, P, seed, None)
+    scale = 2.0**28
+    u = inputs.messages(seed, P.n // 2)
+    v = inputs.messages(seed + 1, P.n // 2)
+    ct1 = _enc(O, P, s, u, scale, P.L, seed, 1)
+    ct2 = _enc(O, P, s, v, scale, P.L, seed, 2)
+    a, e = ks(1)
+    evk = O.keygen_relin(P, s, a, e)
+    prod = O.hmult_merged(P, ct1, ct2, evk)
+    err = np.max(np.abs(O.decode(P, O.decrypt(P, s, prod), scale * scale / float(P.q[P.L - 1])) - u * v))
+    assert err < 1e-3, err
