@@ -564,55 +564,80 @@ void or_hmult(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p,
 }
 
 // HMult with ModDown merged into the rescaling (the merge the paper takes
-// from MAD, Sec. 6): with Y_u = KeyMult(ModUp(d2))_u + P d_u over Q_l and P
-// (d_u the tensor's d0, d1; P d_u = 0 on the P limbs), one fast basis
-// conversion from the primes P and q_l (Eq. 2, centered) gives
-// X = BConv([Y]_{P q_l}) on q_0 .. q_{l-1}, and out_i = (Y_i - X_i)
-// (P q_l)^-1. This divides by P q_l in one rounding instead of ModDown then
-// rescale, so its result differs from or_hmult(..., rescale = 1) by a small
-// polynomial. ct = [2][n_q][N]; out = [2][n_q - 1][N]. Single rescaling.
-void or_hmult_merged(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum,
-                     const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t* evk, uint32_t* out) {
-  Params P{log_n, L, alpha, dnum, q, p, 0};
+// from MAD and extends to its prime system, Sec. 6). The level's window is
+// q[base .. base + n_q) (Params.base), the next level's q[s_new .. s_new +
+// n_new); D = primes leaving the window (T_drop their product), A = primes
+// entering it (T_add; empty and 1 for the usual rescaling by q_l, Sec. 3.2
+// for the rational one). With Y_u = KeyMult(ModUp(d2))_u + P d_u on the
+// window and P (d_u the tensor's d0, d1; P d_u = 0 on the P limbs), one fast
+// basis conversion (Eq. 2, centered) from the primes P and D gives
+// X = BConv([Y T_add]_{P T_drop}) on the new window, and
+//   out_t = (Y_t T_add - X_t) (P T_drop)^-1   (Y_t = 0 for t in A).
+// This divides by P T_drop in one rounding instead of ModDown then rescale,
+// so the result differs from the two-step one by a small polynomial.
+// ct = [2][n_q][N]; out = [2][n_new][N].
+void or_hmult_merged(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
+                     const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t* evk, int s_new,
+                     int n_new, uint32_t* out) {
+  Params P{log_n, L, alpha, dnum, q, p, base};
   u32 n = P.n();
-  const int ext = n_q + alpha, l = n_q - 1, nd = n_digits(n_q, alpha);
+  const int ext = n_q + alpha, nd = n_digits(n_q, alpha, base);
   size_t poly = size_t(n_q) * n;
+  auto in_old = [&](int g) { return g >= base && g < base + n_q; };
+  auto in_new = [&](int g) { return g >= s_new && g < s_new + n_new; };
+  std::vector<int> drop, add;
+  for (int g = base; g < base + n_q; ++g)
+    if (!in_new(g)) drop.push_back(g);
+  for (int g = s_new; g < s_new + n_new; ++g)
+    if (!in_old(g)) add.push_back(g);
+  auto pmod = [&](u32 m) {
+    u32 r = 1 % m;
+    for (int k = 0; k < alpha; ++k) r = mul_mod(r, p[k] % m, m);
+    return r;
+  };
+  auto prod_mod = [&](const std::vector<int>& set, u32 m) {
+    u32 r = 1 % m;
+    for (int g : set) r = mul_mod(r, q[g] % m, m);
+    return r;
+  };
   std::vector<u32> d(3 * poly), up(size_t(nd) * ext * n), acc(size_t(2) * ext * n);
-  or_tensor(ct1, ct2, n_q, q, log_n, d.data());
+  or_tensor(ct1, ct2, n_q, q + base, log_n, d.data());
   modup(P, d.data() + 2 * poly, n_q, up.data());
   keymult(P, up.data(), n_q, evk, acc.data());
-  std::vector<u32> src(alpha + 1), dst(l);
+  const int K = alpha + (int)drop.size();
+  std::vector<u32> src(K), dst(n_new);
   for (int k = 0; k < alpha; ++k) src[k] = p[k];
-  src[alpha] = q[l];
-  for (int i = 0; i < l; ++i) dst[i] = q[i];
+  for (size_t k = 0; k < drop.size(); ++k) src[alpha + k] = q[drop[k]];
+  for (int t = 0; t < n_new; ++t) dst[t] = q[s_new + t];
   for (int u = 0; u < 2; ++u) {
     const u32* a = acc.data() + size_t(u) * ext * n;
     const u32* du = d.data() + size_t(u) * poly;
-    // Y on q_i: acc_i + [P]_{q_i} d_i; on p_k: acc_(n_q + k)
-    auto pmod = [&](u32 m) {
-      u32 r = 1;
-      for (int k = 0; k < alpha; ++k) r = mul_mod(r, p[k] % m, m);
-      return r;
+    // Y on window prime g (limb g - base): acc + [P]_g d
+    auto y_at = [&](int g, u32 c) {
+      u32 m = q[g];
+      size_t o = size_t(g - base) * n + c;
+      return add_mod(a[o], mul_mod(pmod(m), du[o], m), m);
     };
-    std::vector<u32> y(size_t(alpha + 1) * n);
-    for (int k = 0; k < alpha; ++k) {
-      std::memcpy(&y[size_t(k) * n], a + size_t(n_q + k) * n, n * 4);
-      intt_fast(&y[size_t(k) * n], log_n, p[k]);
-    }
-    u32 pl = pmod(q[l]);
-    for (u32 c = 0; c < n; ++c)
-      y[size_t(alpha) * n + c] = add_mod(a[size_t(l) * n + c], mul_mod(pl, du[size_t(l) * n + c], q[l]), q[l]);
-    intt_fast(&y[size_t(alpha) * n], log_n, q[l]);
-    std::vector<u32> x(size_t(l) * n);
-    bconv(y.data(), alpha + 1, src.data(), x.data(), l, dst.data(), n);
-    for (int i = 0; i < l; ++i) {
-      u32 qi = q[i];
-      ntt_fast(&x[size_t(i) * n], log_n, qi);
-      u32 pi = pmod(qi);
-      u32 inv = inv_mod(mul_mod(pi, q[l] % qi, qi), qi);
+    // [Y T_add]_s on the sources, coefficient domain
+    std::vector<u32> y(size_t(K) * n);
+    for (int k = 0; k < K; ++k) {
+      u32 m = src[k], ta = prod_mod(add, m);
       for (u32 c = 0; c < n; ++c) {
-        u32 yi = add_mod(a[size_t(i) * n + c], mul_mod(pi, du[size_t(i) * n + c], qi), qi);
-        out[(size_t(u) * l + i) * n + c] = mul_mod(sub_mod(yi, x[size_t(i) * n + c], qi), inv, qi);
+        u32 v = k < alpha ? a[size_t(n_q + k) * n + c] : y_at(drop[k - alpha], c);
+        y[size_t(k) * n + c] = mul_mod(v, ta, m);
+      }
+      intt_fast(&y[size_t(k) * n], log_n, m);
+    }
+    std::vector<u32> x(size_t(n_new) * n);
+    bconv(y.data(), K, src.data(), x.data(), n_new, dst.data(), n);
+    for (int t = 0; t < n_new; ++t) {
+      const int g = s_new + t;
+      u32 m = q[g];
+      ntt_fast(&x[size_t(t) * n], log_n, m);
+      u32 ta = prod_mod(add, m), inv = inv_mod(mul_mod(pmod(m), prod_mod(drop, m), m), m);
+      for (u32 c = 0; c < n; ++c) {
+        u32 yt = in_old(g) ? mul_mod(y_at(g, c), ta, m) : 0;
+        out[(size_t(u) * n_new + t) * n + c] = mul_mod(sub_mod(yt, x[size_t(t) * n + c], m), inv, m);
       }
     }
   }

@@ -67,7 +67,7 @@ def lib():
                 "or_keymult": (None, [i, i, U32P, i, U32P, i, i, U32P, i, U32P, U32P]),
                 "or_moddown": (None, [i, i, U32P, i, U32P, i, i, U32P, i, U32P]),
                 "or_rescale_rational": (None, [U32P, i, U32P, i, i, i, i, i, U32P]),
-                "or_hmult_merged": (None, [i, i, U32P, i, U32P, i, U32P, U32P, i, U32P, U32P]),
+                "or_hmult_merged": (None, [i, i, U32P, i, U32P, i, i, U32P, U32P, i, U32P, i, i, U32P]),
                 "or_rescale": (None, [U32P, i, i, U32P, i, U32P]),
                 "or_hmult": (None, [i, i, U32P, i, U32P, i, i, U32P, U32P, i, U32P, i, U32P]),
                 "or_hrot": (None, [i, i, U32P, i, U32P, i, i, U32P, i, u32, U32P, U32P]),
@@ -350,13 +350,17 @@ def hmult(P: Params, ct1, ct2, evk, rescale: bool = True, base: int = 0) -> np.n
     return out
 
 
-def hmult_merged(P: Params, ct1, ct2, evk) -> np.ndarray:
-    """HMult with ModDown merged into the rescaling: one conversion from P and
-    q_l of KeyMult + P d, divided by P q_l (the MAD merge cited in Sec. 6)."""
+def hmult_merged(P: Params, ct1, ct2, evk, base: int = 0, new=None) -> np.ndarray:
+    """HMult with ModDown merged into the rescaling (the MAD merge that
+    Sec. 6 extends to its prime system): one conversion from P and the
+    dropped primes of (KeyMult + P d) T_add, divided by P T_drop. The level's
+    window starts at `base`; `new` = (start, count) of the next level's window
+    (default: the usual rescaling by the top prime)."""
     ct1, ct2 = _u32(ct1), _u32(ct2)
     n_q = ct1.shape[1]
-    out = np.zeros((2, n_q - 1, P.n), np.uint32)
-    lib().or_hmult_merged(*P.args(), ct1, ct2, n_q, _u32(evk), out)
+    s_new, n_new = new if new is not None else (base, n_q - 1)
+    out = np.zeros((2, n_new, P.n), np.uint32)
+    lib().or_hmult_merged(*P.args(), base, ct1, ct2, n_q, _u32(evk), s_new, n_new, out)
     return out
 
 

@@ -93,10 +93,12 @@ def test_rational_rescale_is_division_by_t_drop_times_t_add(O, step):
             assert abs(x) <= (K / 2 + 0.5) * t_drop
 
 
-def test_hmult_through_the_rescaling_cycle_decrypts(O):
+@pytest.mark.parametrize("merged", [False, True])
+def test_hmult_through_the_rescaling_cycle_decrypts(O, merged):
     """Encrypt at level 4 (Delta = 2^40), square with HMult + rational
-    rescaling down to level 0: every decryption is u^(2^k) within 1e-3.
-    HRot at a window level decrypts to the rotation."""
+    rescaling down to level 0 (two steps, or ModDown merged into the
+    rescaling, Sec. 6): every decryption is u^(2^k) within 1e-3. HRot at a
+    window level decrypts to the rotation."""
     P, levels = O.prime_system_2530(10, 5)
     seed = 11
     s = inputs.ternary_secret(seed, P.n, None)
@@ -114,14 +116,19 @@ def test_hmult_through_the_rescaling_cycle_decrypts(O):
     want = u.copy()
     for lv in range(4, 0, -1):
         (so, no), (sn, nn) = levels[lv], levels[lv - 1]
-        prod = O.hmult(P, ct, ct, rk, rescale=False, base=so)
-        ct = O.rescale_rational(P, prod, so, no, sn, nn)
+        if merged:
+            ct = O.hmult_merged(P, ct, ct, rk, base=so, new=(sn, nn))
+        else:
+            prod = O.hmult(P, ct, ct, rk, rescale=False, base=so)
+            ct = O.rescale_rational(P, prod, so, no, sn, nn)
         drop = [int(P.q[g]) for g in range(so, so + no) if not sn <= g < sn + nn]
         add = [int(P.q[g]) for g in range(sn, sn + nn) if not so <= g < so + no]
         sc = sc * sc * math.prod(add) / math.prod(drop)
         want = want * want
         got = _decrypt_window(O, P, s, ct, sn, nn, sc)
         assert np.max(np.abs(got - want)) < 1e-3, lv
+    if merged:
+        return
     # HRot by 3 at level 3 (window base 2)
     a2 = np.stack([inputs.uniform_residues(seed, allp, P.n, 200 + j) for j in range(P.dnum)])
     e2 = np.stack([inputs.gaussian_error(seed, P.n, 200 + j) for j in range(P.dnum)])
@@ -134,6 +141,30 @@ def test_hmult_through_the_rescaling_cycle_decrypts(O):
     rot = O.hrot(P, c3, k, gk, base=s3)
     got = _decrypt_window(O, P, s, rot, s3, n3, 2.0 ** 40)
     assert np.max(np.abs(got - np.roll(u, -3))) < 1e-3
+
+
+@pytest.mark.parametrize("step", [(4, 3), (1, 0), (8, 7), (5, 4)])
+def test_merged_moddown_rescale_is_near_the_two_step_result(O, step):
+    """ModDown merged into the rational rescaling (one division by P T_drop)
+    and ModDown followed by the rational rescaling agree per coefficient to
+    within a few units (both approximate c P^-1 T_add / T_drop, Sec. 3.2,
+    Sec. 6); random ciphertexts and keys."""
+    P, levels = O.prime_system_2530(6, 5)
+    (s0, n0), (s1, n1) = levels[step[0]], levels[step[1]]
+    rng = np.random.default_rng(40 + step[0])
+    old = [int(v) for v in P.q[s0:s0 + n0]]
+    new = [int(v) for v in P.q[s1:s1 + n1]]
+    mk = lambda: np.stack([np.stack([rng.integers(0, q, P.n) for q in old]) for _ in range(2)]).astype(np.uint32)
+    c1, c2 = mk(), mk()
+    evk = np.stack([np.stack([np.stack([rng.integers(0, int(v), P.n) for v in P.all_primes()]) for _ in range(2)])
+                    for _ in range(P.dnum)]).astype(np.uint32)
+    merged = O.hmult_merged(P, c1, c2, evk, base=s0, new=(s1, n1))
+    two = O.rescale_rational(P, O.hmult(P, c1, c2, evk, rescale=False, base=s0), s0, n0, s1, n1)
+    K = sum(1 for g in range(s0, s0 + n0) if not s1 <= g < s1 + n1)
+    for u in range(2):
+        diff = (merged[u].astype(np.int64) - two[u].astype(np.int64)) % np.array(new, np.int64)[:, None]
+        coef = O.intt(diff.astype(np.uint32), new)
+        assert max(abs(int(x)) for x in O.crt_centered(coef, new)) <= P.alpha + K + 3
 
 
 def _encrypt_window(O, P, s, pt, a, e, base, n):
