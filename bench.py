@@ -628,6 +628,8 @@ def run_rns2530(args, local_rank):
                "hmult_us": median_us(lambda: K.ckks_hmult(ctx, a, a, rk, 0, out))}
         if lv >= 1:
             row["hmult_rational_rescale_us"] = median_us(lambda: K.ckks_hmult(ctx, a, a, rk, K.CKKS_RESCALE, out))
+            row["hmult_merged_rescale_us"] = median_us(
+                lambda: K.ckks_hmult(ctx, a, a, rk, K.CKKS_RESCALE_MERGED, out))
             row["rational_rescale_us"] = median_us(lambda: K.ckks_rescale(ctx, a, out))
             K.ckks_hmult(ctx, a, a, rk, K.CKKS_RESCALE, out)
             row["log2_scale_after_hmult"] = math.log2(K.ckks_ct_info(out)[1])
@@ -692,6 +694,7 @@ def run_ablation(args, local_rank):
     b = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(75, (1 << LOG_N) // 2), LEVEL, SCALE), 76)
     mid, out = K.ckks_ct_create(ctx, LEVEL), K.ckks_ct_create(ctx, LEVEL)
     forms = {"fused_moddown_rescale": lambda: K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, out),
+             "merged_moddown_rescale": lambda: K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE_MERGED, out),
              "hmult_then_rescale": lambda: (K.ckks_hmult(ctx, a, b, rk, 0, mid), K.ckks_rescale(ctx, mid, out))}
     seq = {}
     for name, fn in forms.items():
@@ -706,15 +709,26 @@ def run_ablation(args, local_rank):
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e3)
         seq[name] = float(np.median(ts))
+    # precision of the exact fused form and of the merged one (Sec. 6): both
+    # decrypt to u v; max slot error
+    u, v = inputs.messages(73, (1 << LOG_N) // 2), inputs.messages(75, (1 << LOG_N) // 2)
+    dec_err = {}
+    for name, fl in (("fused_moddown_rescale", K.CKKS_RESCALE), ("merged_moddown_rescale", K.CKKS_RESCALE_MERGED)):
+        K.ckks_hmult(ctx, a, b, rk, fl, out)
+        pt = K.ckks_decrypt(ctx, sk, out)
+        dec_err[name] = float(np.max(np.abs(K.ckks_decode(ctx, pt, u.size) - u * v)))
+        K.ckks_free(pt)
     best = max(v["gmodmul_s"] for v in mm["30-bit q_1"].values())
     line = {"metric": "ablation on 1 GB300: modular multiplication methods (Table 3) and ModDown+rescale fusion",
             "value": best, "unit": "Gmodmul/s (best method, 30-bit prime)", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"{n} elements x {rounds} dependent modular products, 8 chains per thread; "
-                                   "HMult+relin at level 39 (dnum=3) with fused vs separate rescale"},
+                                   "HMult+relin at level 39 (dnum=3) with fused, merged or separate rescale"},
             "modmul": mm, "seq_fusion_us": seq,
-            "seq_fusion_speedup": seq["hmult_then_rescale"] / seq["fused_moddown_rescale"]}
+            "seq_fusion_speedup": seq["hmult_then_rescale"] / seq["fused_moddown_rescale"],
+            "merged_speedup_over_fused": seq["fused_moddown_rescale"] / seq["merged_moddown_rescale"],
+            "decrypt_max_err": dec_err}
     print(json.dumps(line), flush=True)
     for h in (a, b, mid, out, sk, rk):
         K.ckks_free(h)

@@ -56,6 +56,7 @@ extern "C" {
 #define CKKS_EBUSY (-8)    /* admission refused (memory footprint) */
 
 #define CKKS_RESCALE 1     /* ckks_hmult flag: rescale the product (Sec. 2.1) */
+#define CKKS_RESCALE_MERGED 2 /* ckks_hmult flag: rescale with ModDown merged into it (Sec. 6) */
 
 typedef struct ckks_ctx ckks_ctx;
 typedef struct ckks_ct ckks_ct;
@@ -213,8 +214,13 @@ int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
  * may alias a. */
 int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
 /* HMult: tensor (d0, d1, d2), relinearize d2 with evk (ModUp, KeyMult,
- * ModDown; Sec. 2.3) and, with CKKS_RESCALE, rescale by q_l. out must not
- * alias a or b. */
+ * ModDown; Sec. 2.3) and, with CKKS_RESCALE, rescale by q_l (rationally
+ * with prime windows, Sec. 3.2). With CKKS_RESCALE_MERGED instead, ModDown
+ * and the rescaling are one division by P T_drop (the merge of Sec. 6): one
+ * basis conversion from P and the primes leaving the window of KeyMult +
+ * P d. Its residues differ from CKKS_RESCALE's by a polynomial of a few
+ * units, far below the encryption noise; level and scale are the same.
+ * Other flag bits: CKKS_EINVAL. out must not alias a or b. */
 int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags,
                ckks_ct* out);
 /* Rescale (single rescaling): c'_i = (c_i - [c_l]_centered) * q_l^-1, scale /= q_l.

@@ -29,6 +29,7 @@ CKKS_ECUDA = -6
 CKKS_ETIMEOUT = -7
 CKKS_EBUSY = -8
 CKKS_RESCALE = 1
+CKKS_RESCALE_MERGED = 2
 
 
 class CkksError(RuntimeError):

@@ -175,6 +175,7 @@ int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
   c->rows_off = parent->rows_off;
   c->rows_cnt = parent->rows_cnt;
   c->rr = parent->rr;
+  c->mm = parent->mm;
   c->d_scratch = nullptr;
   const int rc = alloc_scratch(c);
   if (rc != CKKS_OK) {
@@ -874,10 +875,12 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out) {
 
 int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out) {
   if (!ctx || !a || !b || !evk || !out) return CKKS_EINVAL;
+  if (flags & ~(CKKS_RESCALE | CKKS_RESCALE_MERGED)) return fail(ctx, CKKS_EINVAL, "hmult: unknown flags %d", flags);
   if (evk->galois != 0) return fail(ctx, CKKS_ENOKEY, "hmult needs a relinearization key");
   if (a->level != b->level) return fail(ctx, CKKS_ELEVEL, "hmult: levels %d and %d differ", a->level, b->level);
   if (out == a || out == b) return fail(ctx, CKKS_EINVAL, "hmult: output aliases an input");
-  const bool rs = flags & CKKS_RESCALE;
+  const bool merged = flags & CKKS_RESCALE_MERGED;
+  const bool rs = (flags & CKKS_RESCALE) || merged;
   if (rs && a->level < 1) return fail(ctx, CKKS_ELEVEL, "hmult: cannot rescale at level 0");
   if (out->cap_level < a->level - (rs ? 1 : 0)) return fail(ctx, CKKS_ELEVEL, "hmult: output capacity too small");
   const size_t lw = limb_words(ctx);
@@ -891,10 +894,12 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   k.evk = evk->d;
   k.extra = 1;
   // single rescaling is fused into ModDown; a rational one follows the key
-  // switch (its ciphertext-size intermediate lives in the scratch U)
-  const bool fused = rs && !ctx->windowed;
+  // switch (its ciphertext-size intermediate lives in the scratch U); the
+  // merged form divides by P T_drop at once in either system
+  const bool fused = rs && (!ctx->windowed || merged);
   k.rescale = fused ? 1 : 0;
-  const bool staged = rs && ctx->windowed;
+  k.mm = merged ? &ctx->mm[a->level] : nullptr;
+  const bool staged = rs && ctx->windowed && !merged;
   k.out = staged ? ctx->sc.U : out->d;
   k.out_stride = staged ? (size_t)ctx->lvl_n(a->level) * lw : out->poly_stride();
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);

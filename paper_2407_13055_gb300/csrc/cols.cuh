@@ -371,6 +371,36 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevPar
   col_targets<G, TC, TP>(dp, y4, K, top, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
 }
 
+// ModDown merged into the rescaling (Sec. 6), column kernel: the K source
+// limbs of polynomial u (P primes, then the dropped window primes; row-phase
+// iNTT already applied, S = [2][K]) finish their iNTT columns and are scaled
+// by cin; BConv (Eq. 2, centered) to the n1 primes of the new window, then
+// the NTT columns into T = [2][n1]. grid (W/TC, 2 polys, Z).
+template <class G, int TC, int SL, int TP>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_mm_cols(DevParams dp, MmArgs m, const uint32_t* S,
+                                                                    uint32_t* T) {
+  pdl_wait();
+  pdl_trigger();
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y;
+  int4* y4 = smem4;
+  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)m.K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  col_inputs<G, TC>(dp, S + ((size_t)(u * m.K) << dp.log_n), (size_t)1 << dp.log_n, m.K, 0, m.cin, y4, colbuf, l,
+                    jj, c, pos, slice, SL, nullptr, m.rows);
+  __syncthreads();
+  auto tgt = [&](int t, const int32_t*& row, int& id, uint32_t*& dst) {
+    row = m.mat + t * m.K;
+    id = m.s1 + t;
+    dst = T + ((size_t)(u * m.n1 + t) << dp.log_n);
+  };
+  col_targets<G, TC, TP>(dp, y4, m.K, m.n1, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
+                         slice);
+}
+
 template <class G, int TC, int SL>
 static size_t col_smem_bytes(int K) {
   using CTL = ColTile<G, TC>;
@@ -503,6 +533,18 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
     set_col_smem((const void*)k_rs_cols_fused<G, TC, SL, TP>, sm);
     launch_pdl(dp.pdl, k_rs_cols_fused<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
                n, V, Y, T3);
+    count_launch(1);
+  });
+}
+
+template <class G>
+void launch_mm_cols(const DevParams& dp, const MmArgs& m, const Scratch& sc, const ColShape& s, cudaStream_t st) {
+  with_shape(s, [&](auto tc, auto sl, auto tp) {
+    constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
+    const size_t sm = col_smem_bytes<G, TC, SL>(m.K);
+    set_col_smem((const void*)k_mm_cols<G, TC, SL, TP>, sm);
+    launch_pdl(dp.pdl, k_mm_cols<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
+               m, (const uint32_t*)sc.S, sc.T);
     count_launch(1);
   });
 }

@@ -519,6 +519,66 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
     }
   }
 
+  // ModDown merged into the rescaling l -> l - 1 (Sec. 6), every level l >= 1:
+  // sources p_0 .. p_(alpha-1) and the primes leaving the window, targets the
+  // new window (constants as documented with MmArgs)
+  std::vector<int2> mm_rows;
+  std::vector<uint2> mm_cin;
+  std::vector<int32_t> mm_mat;
+  std::vector<MmEpi> mm_epi;
+  struct MmOff {
+    size_t rows, cin, mat, epi;
+  };
+  std::vector<MmOff> mm_off(nlev);
+  ctx->mm.assign(nlev, MmArgs{});
+  for (int l = 1; l < nlev; ++l) {
+    const int s0 = ctx->lvl_first[l], n0 = ctx->lvl_count[l];
+    const int s1 = ctx->lvl_first[l - 1], n1 = ctx->lvl_count[l - 1];
+    std::vector<int> src, drop, add;  // prime ids
+    for (int k = 0; k < alpha; ++k) src.push_back(L + k);
+    for (int g = s0; g < s0 + n0; ++g)
+      if (g < s1 || g >= s1 + n1) drop.push_back(g);
+    for (int g = s1; g < s1 + n1; ++g)
+      if (g < s0 || g >= s0 + n0) add.push_back(g);
+    src.insert(src.end(), drop.begin(), drop.end());
+    auto prod_ids = [&](const std::vector<int>& ids, uint32_t m, int skip) {
+      uint32_t r = 1 % m;
+      for (int id : ids)
+        if (id != skip) r = mulm(r, pr[id] % m, m);
+      return r;
+    };
+    const int K = (int)src.size();
+    mm_off[l] = MmOff{mm_rows.size(), mm_cin.size(), mm_mat.size(), mm_epi.size()};
+    for (int u = 0; u < 2; ++u)
+      for (int id : src) {
+        const int t = id >= L ? n0 + (id - L) : id - s0;
+        mm_rows.push_back(make_int2(u * (n0 + alpha) + t, id));
+      }
+    for (int id : src) {
+      const uint32_t m = pr[id];
+      uint32_t c = mulm(prod_ids(add, m, -1), invm(prod_ids(src, m, id), m), m);
+      if (id < L) c = mulm(c, ctx->gadget_p[id].x, m);
+      mm_cin.push_back(shoup_pair(mulm(c, ctx->pc_host[id].ninv, m), m));
+    }
+    for (int t = 0; t < n1; ++t) {
+      const int g = s1 + t;
+      const uint32_t m = pr[g];
+      for (int id : src) mm_mat.push_back(centered_h(mulm(prod_ids(src, m, id), ctx->pc_host[g].mont, m), m));
+      const uint32_t ptd_inv = invm(prod_ids(src, m, -1), m), ta = prod_ids(add, m, -1);
+      MmEpi e;
+      e.old_limb = (g >= s0 && g < s0 + n0) ? g - s0 : -1;
+      e.c1 = shoup_pair(mulm(ta, ptd_inv, m), m);
+      e.c2 = shoup_pair(mulm(ta, invm(prod_ids(drop, m, -1), m), m), m);
+      e.c3 = shoup_pair(ptd_inv, m);
+      mm_epi.push_back(e);
+    }
+    MmArgs& a = ctx->mm[l];
+    a.K = K;
+    a.n0 = n0;
+    a.s1 = s1;
+    a.n1 = n1;
+  }
+
   // twiddles: tw[id][k] = psi^brev(k), itw[id][k] = psi^-brev(k)
   std::vector<uint2> tw((size_t)np * n), itw((size_t)np * n);
   std::vector<uint32_t> pw(n), ipw(n);
@@ -564,6 +624,10 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {rr_mat.data(), rr_mat.size() * sizeof(int32_t), 0},
       {rr_epi.data(), rr_epi.size() * sizeof(RrEpi), 0},
       {rr_rows.data(), rr_rows.size() * sizeof(int2), 0},
+      {mm_rows.data(), mm_rows.size() * sizeof(int2), 0},
+      {mm_cin.data(), mm_cin.size() * sizeof(uint2), 0},
+      {mm_mat.data(), mm_mat.size() * sizeof(int32_t), 0},
+      {mm_epi.data(), mm_epi.size() * sizeof(MmEpi), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -605,6 +669,13 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
     r.epi = reinterpret_cast<const RrEpi*>(base + parts[16].off) + rr_off[l].epi;
     r.rows = reinterpret_cast<const int2*>(base + parts[17].off) + rr_off[l].rows;
   }
+  for (int l = 1; l < nlev; ++l) {
+    MmArgs& a = ctx->mm[l];
+    a.rows = reinterpret_cast<const int2*>(base + parts[18].off) + mm_off[l].rows;
+    a.cin = reinterpret_cast<const uint2*>(base + parts[19].off) + mm_off[l].cin;
+    a.mat = reinterpret_cast<const int32_t*>(base + parts[20].off) + mm_off[l].mat;
+    a.epi = reinterpret_cast<const MmEpi*>(base + parts[21].off) + mm_off[l].epi;
+  }
 
   ctx->owns_tables = true;
   const int rc = alloc_scratch(ctx);
@@ -622,7 +693,9 @@ int alloc_scratch(ckks_ctx* ctx) {
   const DevParams& dp = ctx->dp;
   const int L = dp.L, np = dp.L + dp.alpha;
   const size_t limb = (size_t)1 << dp.log_n;
-  const size_t s_limbs = std::max(L, 2 * dp.alpha);  // windows are at most L primes
+  // windows are at most L primes; the merged ModDown + rescaling takes 2K limbs
+  size_t s_limbs = std::max(L, 2 * dp.alpha);
+  for (const MmArgs& m : ctx->mm) s_limbs = std::max(s_limbs, 2 * (size_t)m.K);
   // T: the ModUp limbs (dnum (L + alpha)) followed by room for the ModDown
   // conversions (2L), so that hoisted rotations keep the ModUp limbs
   const size_t t_limbs = std::max((size_t)dp.dnum * np + 2 * (size_t)L, (size_t)2 * L + 4);

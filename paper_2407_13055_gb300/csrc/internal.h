@@ -76,6 +76,8 @@ enum KsMode { KS_PLAIN = 0, KS_TENSOR = 1, KS_AUTO = 2 };
 // What the KeyMult row kernel writes.
 enum KmOut { KM_KEYSWITCH = 0, KM_ACC_ALL = 1, KM_MODUP = 2 };
 
+struct MmArgs;
+
 struct KsArgs {
   int n;                 // active ciphertext limbs
   int base;              // their primes are q[base .. base + n) (0 unless the levels are windows)
@@ -94,6 +96,8 @@ struct KsArgs {
   int extra;             // ModDown epilogue: 0 none, 1 HMult (d0, d1), 2 HRot (phi(b), 0)
   int hoisted;           // 1: the ModUp limbs in scratch are of a itself (hoisted rotations), so
                          //    KeyMult applies the automorphism phi_galois while loading them
+  const MmArgs* mm;      // with rescale: ModDown merged into the rescaling (host pointer, read by
+                         // the launcher; null for ModDown then rescale)
 };
 
 // Terms of a linear transform sum_i pt_i (.) HRot_{r_i}(ct) (Par. 4, Par. 5),
@@ -124,6 +128,26 @@ struct RrEpi {
   uint2 ta_tdi;  // [T_add T_drop^-1]_t, Shoup pair
   uint2 tdi;     // [T_drop^-1]_t, Shoup pair
 };
+// ModDown merged into the rescaling (Sec. 6), transition from level l to
+// l - 1: one conversion from the alpha P primes and the K - alpha primes that
+// leave the window (T_drop their product; T_add that of the entering ones,
+// 1 for the usual rescaling by q_l) to the new window's n1 primes.
+struct MmEpi {
+  int old_limb;  // target's limb in the old window, or -1 for a prime that enters it
+  uint2 c1;      // [T_add (P T_drop)^-1]_t, Shoup pair (accumulator limb)
+  uint2 c2;      // [T_add T_drop^-1]_t (ModDown extra: d_u for HMult)
+  uint2 c3;      // [(P T_drop)^-1]_t (conversion X)
+};
+struct MmArgs {
+  int K;               // sources: p_0 .. p_(alpha-1), then the dropped primes
+  int n0, s1, n1;      // old window size; new window start and size
+  const int2* rows;    // [2K]: (limb u (n0 + alpha) + t of the accumulator, prime id) for u = 0, 1
+  const uint2* cin;    // [K]: Shoup pair of N^-1 [T_add (P T_drop / s_k)^-1 m_k]_{s_k}, m_k = P for a
+                       //      dropped prime (its row source is Y P^-1), 1 for p_k
+  const int32_t* mat;  // [n1][K]: [(P T_drop / s_k) 2^32]_t, centered
+  const MmEpi* epi;    // [n1]
+};
+
 struct RrArgs {
   int K;                  // dropped primes
   int s0, n0, s1, n1;     // old and new windows
@@ -321,6 +345,7 @@ struct ckks_ctx {
   std::vector<int> lvl_first, lvl_count;
   std::vector<int> rows_off, rows_cnt;  // per level + 1: ModUp row-table range
   std::vector<ckks::RrArgs> rr;         // per level l >= 1 (windowed): transition l -> l - 1
+  std::vector<ckks::MmArgs> mm;         // per level l >= 1: merged ModDown + rescaling l -> l - 1
   int n_levels() const { return (int)lvl_count.size(); }
   int lvl_n(int level) const { return lvl_count[level]; }
   int lvl_base(int level) const { return lvl_first[level]; }

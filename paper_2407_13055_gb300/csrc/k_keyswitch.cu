@@ -43,7 +43,9 @@ using G8 = Geo<4, 4>;
   extern template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*,             \
                                                   cudaStream_t);                                                \
   extern template void launch_rs_cols_fused<G>(const DevParams&, int, const uint32_t*, const uint32_t*,         \
-                                               uint32_t*, const ColShape&, cudaStream_t);
+                                               uint32_t*, const ColShape&, cudaStream_t);                       \
+  extern template void launch_mm_cols<G>(const DevParams&, const MmArgs&, const Scratch&, const ColShape&,     \
+                                         cudaStream_t);
 CKKS_COL_DECL(G16)
 CKKS_COL_DECL(G12)
 CKKS_COL_DECL(G8)
@@ -349,6 +351,33 @@ __global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, cons
   store_vec<4>(a.out + u * a.out_stride + off, w);
 }
 
+// ModDown merged into the rescaling (Sec. 6), output limb t of the new window:
+// out_u[t] = A_u[t'] c1 + extra_u[t'] c2 - X_u[t] c3, t' the target's limb in
+// the old window (the first two terms are absent for a prime that enters it).
+__global__ void k_ks_epilogue_mm(DevParams dp, KsArgs a, MmArgs m, const uint32_t* X, const uint32_t* A,
+                                 size_t a_stride) {
+  pdl_wait();
+  pdl_trigger();
+  const int u = blockIdx.y / m.n1, t = blockIdx.y % m.n1;
+  const MmEpi e = m.epi[t];
+  const PrimeConst P = dp.pc[m.s1 + t];
+  const uint32_t q = P.q, p0 = stream_pos();
+  uint32_t w[4];
+  load_vec<4>(w, X + ((size_t)(u * m.n1 + t) << dp.log_n) + p0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w[k] = csub(q - csub(shoup(w[k], e.c3.x, e.c3.y, q), q), q);
+  if (e.old_limb >= 0) {
+    uint32_t acc[4], ex[4];
+    load_vec<4>(acc, A + u * a_stride + ((size_t)e.old_limb << dp.log_n) + p0);
+    ks_extra4(dp, a, u, e.old_limb, p0, P, ex);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = addm(addm(w[k], csub(shoup(acc[k], e.c1.x, e.c1.y, q), q), q), csub(shoup(ex[k], e.c2.x, e.c2.y, q), q),
+                  q);
+  }
+  store_vec<4>(a.out + u * a.out_stride + ((size_t)t << dp.log_n) + p0, w);
+}
+
 // ---------------------------------------------------------------------------
 // Row-kernel sources and epilogues (the streaming steps fused into the row
 // phases): a thread handles positions pos0 .. pos0 + E - 1 of launch limb y,
@@ -448,6 +477,32 @@ struct EpiRescale {
 #pragma unroll
       for (int k = 0; k < 4; ++k) z[k] = csub(shoup(cv[k] - x[4 * c + k] + P.q, qinv.x, qinv.y, P.q), P.q);
       store_vec<4>(out + u * sout + limb + p, z);
+    }
+  }
+};
+
+// Sources of the merged ModDown + rescaling before the iNTT rows (launch
+// limb y = u K + k, accumulator limb lm.x = u ext + t): a P limb as it is; a
+// dropped window limb t as Y P^-1 = A_u[t] P^-1 + extra_u[t].
+struct SrcMerged {
+  KsArgs a;
+  const uint32_t* A;
+  int ext;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int, int2 lm,
+                                             uint32_t pos0) const {
+    load_vec<E>(x, A + ((size_t)lm.x << dp.log_n) + pos0);
+    const int u = lm.x / ext, t = lm.x % ext;
+    if (t >= a.n) return;
+    const PrimeConst P = dp.pc[lm.y];
+    const uint2 pinv = dp.ks.dn_pinv[lm.y];
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      uint32_t e[4];
+      ks_extra4(dp, a, u, t, pos0 + 4 * c, P, e);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        x[4 * c + k] = addm(csub(shoup(x[4 * c + k], pinv.x, pinv.y, P.q), P.q), e[k], P.q);
     }
   }
 };
@@ -560,6 +615,30 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_RS_EPILOGUE);
 }
 
+// ModDown merged into the rescaling (Sec. 6): one conversion from P and the
+// dropped primes replaces the ModDown conversion, the top limb's NTT and
+// iNTT, and the rescale conversion of moddown_rescale_tail.
+template <class G>
+static void merged_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
+                        size_t a_stride, cudaStream_t st) {
+  const MmArgs& m = *a.mm;
+  const int ext = a.n + dp.alpha;
+  launch_rows_inv<G>(dp, SrcMerged{a, A, ext}, sc.S, 2 * m.K, LimbMap{m.rows, 0, 0, 0, 0}, true, st);
+  prof_mark(sc, st, P_MODDOWN_IN_ROWS);
+  launch_mm_cols<G>(dp, m, sc, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2)), st);
+  prof_mark(sc, st, P_RS_COLS);
+  LimbMap out_map{nullptr, 0, m.n1, m.n1, dp.L};
+  out_map.base = m.s1;
+  launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * m.n1, out_map, false, st);
+  prof_mark(sc, st, P_RS_ROWS);
+  dim3 g;
+  int th;
+  stream_grid(dp.log_n, 2 * m.n1, g, th);
+  launch_pdl(dp.pdl, k_ks_epilogue_mm, g, dim3(th), 0, st, dp, a, m, (const uint32_t*)sc.T, A, a_stride);
+  count_launch(1);
+  prof_mark(sc, st, P_RS_EPILOGUE);
+}
+
 template <class G>
 static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
                          size_t a_stride, cudaStream_t st) {
@@ -596,7 +675,8 @@ void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, i
     count_launch(1);
     prof_mark(sc, st, P_KEYMULT);
     if (km_out == KM_KEYSWITCH) {
-      if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+      if (a.rescale && a.mm) merged_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
+      else if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
       else moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
     }
   });

@@ -93,6 +93,11 @@ def test_hmult_hrot_at_windows_match_oracle(K, O, log_n, level):
             got, lv, _ = K.ckks_ct_export(ctx, out, P.n)
             assert lv == level - 1
             assert np.array_equal(got, O.rescale_rational(P, want_m, s0, n0, s1, n1))
+            # ModDown merged into the rational rescaling (Sec. 6)
+            K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE_MERGED, out)
+            got, lv, _ = K.ckks_ct_export(ctx, out, P.n)
+            assert lv == level - 1
+            assert np.array_equal(got, O.hmult_merged(P, c1, c2, evk, base=s0, new=(s1, n1)))
     finally:
         for h in (a, b, rk, gk, out):
             K.ckks_free(h)
@@ -123,11 +128,13 @@ def test_hoisted_and_linear_transform_at_windows_match_oracle(K, O, level):
             K.ckks_free(h)
 
 
+@pytest.mark.parametrize("merged", [False, True])
 @pytest.mark.parametrize("log_n", [12, 16])
-def test_squaring_through_the_rescaling_cycle_decrypts(K, O, log_n):
+def test_squaring_through_the_rescaling_cycle_decrypts(K, O, log_n, merged):
     """Library keys and encryption at level 4 (Delta = 2^40); HMult + rational
-    rescaling down to level 0: each decryption is u^(2^k) within 1e-3 and the
-    scale stays within 0.1 bits of 2^40 (Sec. 3.2)."""
+    rescaling (or ModDown merged into it, Sec. 6) down to level 0: each
+    decryption is u^(2^k) within 1e-3 and the scale stays within 0.1 bits of
+    2^40 (Sec. 3.2)."""
     ctx, P, levels = system(K, O, log_n)
     sk = K.ckks_keygen_secret(ctx, 21)
     rk = K.ckks_keygen_relin(ctx, sk, 22)
@@ -142,7 +149,7 @@ def test_squaring_through_the_rescaling_cycle_decrypts(K, O, log_n):
         for lv in range(4, 0, -1):
             out = K.ckks_ct_create(ctx, lv - 1)
             handles.append(out)
-            K.ckks_hmult(ctx, ct, ct, rk, K.CKKS_RESCALE, out)
+            K.ckks_hmult(ctx, ct, ct, rk, K.CKKS_RESCALE_MERGED if merged else K.CKKS_RESCALE, out)
             ct = out
             want = want * want
             _, scale = K.ckks_ct_info(ct)[:2]

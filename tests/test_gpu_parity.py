@@ -222,14 +222,16 @@ def test_hadd_pmult_padd_match_oracle(K, O):
 
 # -------------------------------------------------- full HMult / HRot ---
 
-def _run_hmult(K, ctx, P, c1, c2, evk, rescale):
+def _run_hmult(K, ctx, P, c1, c2, evk, rescale, flags=None):
     n_q = c1.shape[1]
     a = K.ckks_ct_import(ctx, c1, n_q - 1, 2.0**30)
     b = K.ckks_ct_import(ctx, c2, n_q - 1, 2.0**30)
     ek = K.ckks_evk_import(ctx, evk, 0)
     out = K.ckks_ct_create(ctx, n_q - 1)
+    if flags is None:
+        flags = K.CKKS_RESCALE if rescale else 0
     try:
-        K.ckks_hmult(ctx, a, b, ek, K.CKKS_RESCALE if rescale else 0, out)
+        K.ckks_hmult(ctx, a, b, ek, flags, out)
         return K.ckks_ct_export(ctx, out, P.n)
     finally:
         for h in (a, b, ek, out):
@@ -265,6 +267,23 @@ def test_hmult_matches_oracle(K, O, name, n_q, rescale):
     assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=rescale))
 
 
+@pytest.mark.parametrize("name,n_q", [("tiny", 6), ("tiny", 2), ("toyT1", 4), ("toyT2", 3), ("toyT2", 2),
+                                      ("n16d3", 40), ("n16d3", 17), ("n16d3", 2)])
+def test_hmult_merged_matches_oracle(K, O, name, n_q):
+    """ModDown merged into the rescaling (Sec. 6): residues equal the oracle's
+    merged definition bit for bit; level and scale as with CKKS_RESCALE."""
+    ctx, P = get(K, O, name)
+    c1, c2 = rand_ct(P, n_q, 131), rand_ct(P, n_q, 133)
+    evk = rand_evk(P, 135)
+    got, level, scale = _run_hmult(K, ctx, P, c1, c2, evk, True, K.CKKS_RESCALE_MERGED)
+    assert level == n_q - 2
+    assert scale == pytest.approx(2.0**60 / float(P.q[n_q - 1]), rel=1e-12)
+    assert np.array_equal(got, O.hmult_merged(P, c1, c2, evk))
+    # both flags together mean the merged form
+    got2, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True, K.CKKS_RESCALE | K.CKKS_RESCALE_MERGED)
+    assert np.array_equal(got2, got)
+
+
 @pytest.mark.parametrize("name,n_q,r", [("tiny", 6, 1), ("tiny", 1, 3), ("toyT1", 4, 1), ("toyT2", 4, 7),
                                         ("toyT2", 4, None), ("n16d3", 40, 1), ("n16d3", 21, 5),
                                         ("n16d3", 2, 12345), ("n16d3", 40, None)])
@@ -286,6 +305,8 @@ def test_hmult_full_size_other_dnum(K, O, dnum):
         evk = rand_evk(P, 55)
         got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
         assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True, K.CKKS_RESCALE_MERGED)
+        assert np.array_equal(got, O.hmult_merged(P, c1, c2, evk))
         got, k = _run_hrot(K, O, ctx, P, c1, evk, 1)
         assert np.array_equal(got, O.hrot(P, c1, k, evk))
     finally:
@@ -302,6 +323,8 @@ def test_more_auxiliary_than_ciphertext_primes(K, O):
         evk = rand_evk(P, 61)
         got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
         assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True, K.CKKS_RESCALE_MERGED)
+        assert np.array_equal(got, O.hmult_merged(P, c1, c2, evk))
         got, k = _run_hrot(K, O, ctx, P, c1, evk, 3)
         assert np.array_equal(got, O.hrot(P, c1, k, evk))
     finally:
@@ -587,6 +610,8 @@ def test_library_keys_decrypt_within_tolerance(K, O, name):
         assert np.max(np.abs(dec(cu) - u)) < 1e-3
         K.ckks_hmult(ctx, cu, cv, rk, K.CKKS_RESCALE, out)
         assert np.max(np.abs(dec(out) - u * v)) < 1e-3
+        K.ckks_hmult(ctx, cu, cv, rk, K.CKKS_RESCALE_MERGED, out)
+        assert np.max(np.abs(dec(out) - u * v)) < 1e-3
         K.ckks_hrot(ctx, cu, 3, gk, out)
         assert np.max(np.abs(dec(out) - np.roll(u, -3))) < 1e-3
         K.ckks_hconj(ctx, cu, ck, out)
@@ -657,6 +682,9 @@ def test_error_codes(K, O):
         assert e.value.code == K.CKKS_ENOKEY
         with pytest.raises(K.CkksError) as e:
             K.ckks_hrot(ctx, c3, 1, rk, c3)           # aliasing
+        assert e.value.code == K.CKKS_EINVAL
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_hmult(ctx, c3, c3, rk, 4, out)     # unknown flag
         assert e.value.code == K.CKKS_EINVAL
     finally:
         for h in (c3, c4, c0, out, rk):
