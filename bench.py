@@ -281,14 +281,36 @@ def run_native(args, rank, world, local_rank):
             K.ckks_hmult(lanes[l], cts[i], cts[(i + 1) % BATCH], rk, K.CKKS_RESCALE, outs_m[l])
             K.ckks_hrot(lanes[l], cts[i], 1, gk, outs_r[l])
 
+    # the timed step through the batch API: the same 2 x BATCH independent
+    # operations (own outputs), lane l taking HMult and HRot of ciphertexts
+    # i = l mod lanes, issued by the library (direct) or replayed as one CUDA
+    # graph per step (graph); "python" issues them one call at a time
+    batch, outs_b = None, []
+    if args.issue != "python":
+        nl = args.lanes
+        outs_b = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2 * BATCH)]
+        ops = []
+        for g0 in range(0, BATCH, nl):
+            grp = range(g0, min(g0 + nl, BATCH))
+            ops += [dict(op=K.CKKS_OP_HMULT, a=cts[i], b=cts[(i + 1) % BATCH], evk=rk, flags=K.CKKS_RESCALE,
+                         out=outs_b[2 * i]) for i in grp]
+            ops += [dict(op=K.CKKS_OP_HROT, a=cts[i], r=1, evk=gk, out=outs_b[2 * i + 1]) for i in grp]
+        batch = K.ckks_batch_create(ctx, ops, nl, args.issue == "graph")
+
     def barrier():
         replicas.barrier()
         torch.cuda.synchronize()
 
-    def timed(n_steps, n_lanes):
+    def timed(n_steps, n_lanes, use_batch=False):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         ev0.record(stream)
+        if use_batch:
+            for _ in range(n_steps):
+                K.ckks_batch_run(ctx, batch)
+            ev1.record(stream)
+            barrier()
+            return ev0.elapsed_time(ev1)
         for s_ in streams[1:n_lanes]:
             s_.wait_event(ev0)
         for _ in range(n_steps):
@@ -302,12 +324,15 @@ def run_native(args, rank, world, local_rank):
         return ev0.elapsed_time(ev1)
 
     for _ in range(args.warmup):
-        step(args.lanes)
+        if batch is not None:
+            K.ckks_batch_run(ctx, batch)
+        else:
+            step(args.lanes)
     barrier()
     launches0 = K.ckks_launch_count()
     with ClockSampler(local_rank) as clk:
         torch.cuda.nvtx.range_push("timed")
-        ms = timed(args.steps, args.lanes)
+        ms = timed(args.steps, args.lanes, batch is not None)
         torch.cuda.nvtx.range_pop()
     launches = K.ckks_launch_count() - launches0
     ms = replicas.max_over_ranks(ms)
@@ -410,6 +435,11 @@ def run_native(args, rank, world, local_rank):
         "config": workload_config({"parallelism": f"replicas{world}",
                                    "lanes": f"{args.lanes} concurrent CUDA streams (context clones), "
                                             "independent ciphertexts per lane",
+                                   "issue": {"graph": "ckks_batch_run: the step's operations replayed as one "
+                                                      "CUDA graph",
+                                             "direct": "ckks_batch_run: the library issues the step's "
+                                                       "operations across the lanes",
+                                             "python": "one binding call per operation"}[args.issue],
                                    "programmatic_dependent_launch": args.pdl,
                                    "column_shapes": ({k: list(v) for k, v in tuned[LEVEL].items()} if tuned
                                                      else "default rule")}),
@@ -422,7 +452,9 @@ def run_native(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for h in cts + outs_m + outs_r + [sk, rk, gk]:
+    if batch is not None:
+        K.ckks_batch_destroy(batch)
+    for h in cts + outs_m + outs_r + outs_b + [sk, rk, gk]:
         K.ckks_free(h)
     for c in lanes[1:]:
         K.ckks_ctx_destroy(c)
@@ -968,6 +1000,8 @@ def main():
     ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation", "rns2530"], default="single")
     ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
+    ap.add_argument("--issue", choices=["graph", "direct", "python"], default="graph",
+                    help="single workload: how the timed step's operations are issued")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="resident ciphertexts per step of the single-op workload (smaller only for profiling)")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",

@@ -48,17 +48,40 @@ __device__ __forceinline__ void mac4(int64_t (&acc)[EC], const int4* __restrict_
   }
 }
 
-// Chunks of four products, unrolled: the bound 2^29 p per product allows
-// eight before the first range reduction and four after each one, so the
-// fold runs after every chunk but the first, and once at the end.
+// Sum of the sources' centered bounds, sum_k (s_k - 1) / 2 (float: it is only
+// compared with 2^63 at a margin far above its rounding error).
+__device__ __forceinline__ float src_bound(const DevParams& dp, int K, int id0, const int2* idtab = nullptr) {
+  float s = 0.f;
+  for (int k = 0; k < K; ++k) s += (float)(dp.pc[idtab ? idtab[k].y : id0 + k].q >> 1);
+  return s;
+}
+
+// With |y_k| <= (s_k - 1)/2 and |mat_k| <= (p - 1)/2, the whole sum stays
+// below 2^63 when sum_k (s_k - 1)/2 * (p - 1)/2 does, and then only the final
+// range reduction is needed (2^63 = 9.22e18).
+__device__ __forceinline__ bool no_fold(float sy, uint32_t p) { return sy * (float)(p >> 1) < 9.0e18f; }
+
+// Chunks of four products, unrolled. Without the bound above (nofold false),
+// 2^29 p per product allows eight before the first range reduction and four
+// after each one, so the fold runs after every chunk but the first, and once
+// at the end.
 template <int EC, int NT>
 __device__ __forceinline__ void bconv_accumulate(const int4* __restrict__ y4, int pos, int K,
                                                  const int32_t* __restrict__ mat, const PrimeConst& P,
-                                                 uint32_t (&out)[EC]) {
+                                                 uint32_t (&out)[EC], bool nofold) {
   int64_t acc[EC];
 #pragma unroll
   for (int i = 0; i < EC; ++i) acc[i] = 0;
   int k = 0;
+  if (nofold) {
+    for (; k + 4 <= K; k += 4) {
+      const int64_t b0 = __ldg(mat + k), b1 = __ldg(mat + k + 1), b2 = __ldg(mat + k + 2), b3 = __ldg(mat + k + 3);
+      mac4<EC, NT>(acc, y4, pos, k, b0);
+      mac4<EC, NT>(acc, y4, pos, k + 1, b1);
+      mac4<EC, NT>(acc, y4, pos, k + 2, b2);
+      mac4<EC, NT>(acc, y4, pos, k + 3, b3);
+    }
+  }
   for (; k + 4 <= K; k += 4) {
     const int64_t b0 = __ldg(mat + k), b1 = __ldg(mat + k + 1), b2 = __ldg(mat + k + 2), b3 = __ldg(mat + k + 3);
     mac4<EC, NT>(acc, y4, pos, k, b0);
@@ -99,11 +122,18 @@ template <int EC, int NT>
 __device__ __forceinline__ void bconv_accumulate2(const int4* __restrict__ y4, int pos, int K,
                                                   const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
                                                   const PrimeConst& P0, const PrimeConst& P1, uint32_t (&o0)[EC],
-                                                  uint32_t (&o1)[EC]) {
+                                                  uint32_t (&o1)[EC], bool nofold) {
   int64_t a0[EC], a1[EC];
 #pragma unroll
   for (int i = 0; i < EC; ++i) a0[i] = a1[i] = 0;
   int k = 0;
+  if (nofold) {
+    for (; k + 4 <= K; k += 4) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mac4x2<EC, NT>(a0, a1, y4, pos, k + kk, (int64_t)__ldg(m0 + k + kk), (int64_t)__ldg(m1 + k + kk));
+    }
+  }
   for (; k + 4 <= K; k += 4) {
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
@@ -192,7 +222,7 @@ __device__ __forceinline__ void col_ntt_store(const DevParams& dp, uint32_t (&x)
 template <class G, int TC, int TP, class Target>
 __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4, int K, int M, int m0, int step,
                                             Target tgt, uint32_t* colbuf, int l, int jj, int c, int pos,
-                                            int slice) {
+                                            int slice, float sy) {
   using CTL = ColTile<G, TC>;
   int m = m0;
   if (TP == 2) {
@@ -204,7 +234,7 @@ __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4,
       tgt(m + step, r1, i1, d1);
       const PrimeConst P0 = dp.pc[i0], P1 = dp.pc[i1];
       uint32_t x0[G::EC], x1[G::EC];
-      bconv_accumulate2<G::EC, CTL::CT>(y4, pos, K, r0, r1, P0, P1, x0, x1);
+      bconv_accumulate2<G::EC, CTL::CT>(y4, pos, K, r0, r1, P0, P1, x0, x1, no_fold(sy, P0.q) && no_fold(sy, P1.q));
       col_ntt_store<G, TC>(dp, x0, i0, d0, colbuf, l, jj, c, slice);
       col_ntt_store<G, TC>(dp, x1, i1, d1, colbuf, l, jj, c, slice);
     }
@@ -216,7 +246,7 @@ __device__ __forceinline__ void col_targets(const DevParams& dp, const int4* y4,
     tgt(m, row, id, dst);
     const PrimeConst P = dp.pc[id];
     uint32_t x[G::EC];
-    bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, row, P, x);
+    bconv_accumulate<G::EC, CTL::CT>(y4, pos, K, row, P, x, no_fold(sy, P.q));
     col_ntt_store<G, TC>(dp, x, id, dst, colbuf, l, jj, c, slice);
   }
 }
@@ -253,7 +283,8 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_modup_cols(DevPar
     id = prime_of(t, n, L, base);
     dst = T + ((size_t)(j * ext + t) << dp.log_n);
   };
-  col_targets<G, TC, TP>(dp, y4, K, M, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
+  col_targets<G, TC, TP>(dp, y4, K, M, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice,
+                         src_bound(dp, K, base + lo));
 }
 
 // C2: ModDown column kernel. grid (W/TC, 2 polys, Z). Input S [2][alpha][N]
@@ -281,7 +312,7 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevP
     dst = T + ((size_t)(u * n + i) << dp.log_n);
   };
   col_targets<G, TC, TP>(dp, y4, alpha, n, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
-                         slice);
+                         slice, src_bound(dp, alpha, dp.L));
 }
 
 
@@ -312,7 +343,7 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(
     id = top;
     dst = T + ((size_t)u << dp.log_n);
   };
-  col_targets<G, TC, 1>(dp, y4, alpha, 1, slice, SL, tgt, colbuf, l, jj, c, pos, slice);
+  col_targets<G, TC, 1>(dp, y4, alpha, 1, slice, SL, tgt, colbuf, l, jj, c, pos, slice, src_bound(dp, alpha, dp.L));
 }
 
 // ModDown fused with rescaling, second column kernel: iNTT columns of the top
@@ -368,7 +399,8 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevPar
     id = i;
     dst = T + ((size_t)(u * top + i) << dp.log_n);
   };
-  col_targets<G, TC, TP>(dp, y4, K, top, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice);
+  col_targets<G, TC, TP>(dp, y4, K, top, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos, slice,
+                         src_bound(dp, alpha, dp.L) + (float)(dp.pc[top].q >> 1));
 }
 
 // ModDown merged into the rescaling (Sec. 6), column kernel: the K source
@@ -398,7 +430,7 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_mm_cols(DevParams dp
     dst = T + ((size_t)(u * m.n1 + t) << dp.log_n);
   };
   col_targets<G, TC, TP>(dp, y4, m.K, m.n1, slice + SL * blockIdx.z, SL * gridDim.z, tgt, colbuf, l, jj, c, pos,
-                         slice);
+                         slice, src_bound(dp, m.K, 0, m.rows));
 }
 
 template <class G, int TC, int SL>
@@ -576,7 +608,8 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rr_cols(DevParams dp
     id = r.s1 + i;
     dst = T + ((size_t)(u * r.n1 + i) << dp.log_n);
   };
-  col_targets<G, TC, 1>(dp, y4, r.K, r.n1, slice, SL, tgt, colbuf, l, jj, c, pos, slice);
+  col_targets<G, TC, 1>(dp, y4, r.K, r.n1, slice, SL, tgt, colbuf, l, jj, c, pos, slice,
+                        src_bound(dp, r.K, 0, r.drop));
 }
 
 template <class G>

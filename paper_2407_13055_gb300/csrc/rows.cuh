@@ -242,11 +242,230 @@ __global__ void __launch_bounds__(G::RT) k_rows_inv_t(DevParams dp, Src src, uin
   for (int i = 0; i < G::ER; ++i) o[jj + G::ER * i] = x[i];
 }
 
+// ---------------------------------------------------------------------------
+// Rows of W = 1024 words (N = 2^16) in three register passes of 4, 3 and 3
+// stages on 64 threads per row, 16 values per thread, so that a thread keeps
+// 16 values and 21 twiddle pairs (7 shared by its pass-B groups, 14 for its
+// two pass-C groups) instead of 32 values and 31 pairs: twice the resident
+// warps of the two-pass form. Element e of the row (0 .. 1023) sits at
+//   A layout (pass A):  thread t, value i < 16:         e = t + 64 i
+//   B layout (pass B):  thread t, group g < 2, i < 8:   e = 64 (t >> 2) + 8 i + 2 (t & 3) + g
+//   C layout (pass C):  thread t, group g < 2, i < 8:   e = 16 t + 8 g + i
+// so the row's forward output (C layout) is the same B-layout run of 16
+// consecutive words per thread that the epilogues expect. Forward stage k
+// (0 .. 9 of the row) uses twiddle (H + h) 2^k + (e >> (10 - k)); pass A's
+// 15 depend on the row only and are staged in shared memory, pass B's on
+// o = t >> 2 (base (H + h) 16 + o), pass C's on the group (base (H + h) 128
+// + 2 t + g). Launch bounds of 6 blocks of 4 warps per SM (80 registers):
+// 24 resident warps, against 16 for the two-pass form at 128 registers.
+// Transposes go through one 1024-word buffer per row with an XOR
+// swizzle of the bank bits by bits 5-8 of e, conflict-free for the three
+// access patterns (32 consecutive e; fixed i, g over a warp in B; fixed i
+// over a warp in C).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int row3_swz(int e) {
+  const int b5 = (e >> 5) & 1, b6 = (e >> 6) & 1, b7 = (e >> 7) & 1, b8 = (e >> 8) & 1;
+  return e ^ ((b8 << 4) | (b7 << 3) | (b5 << 2) | (b8 << 1) | b6);
+}
+__device__ __forceinline__ int row3_eb(int t, int g, int i) { return 64 * (t >> 2) + 8 * i + 2 * (t & 3) + g; }
+
+// Pass-B and pass-C twiddles of thread t in row h: local stage s, block b at
+// entry (2^s - 1) + b, global index base 2^s + b.
+template <int H>
+__device__ __forceinline__ void row3_load_twiddles(uint2 (&tb)[7], uint2 (&tc)[2][7], const uint2* __restrict__ t,
+                                                   int h, int tid) {
+  const uint32_t bb = (uint32_t)(H + h) * 16 + (tid >> 2);
+  tb[0] = __ldg(t + bb);
+  {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t + 2 * bb));
+    tb[1] = make_uint2(v.x, v.y);
+    tb[2] = make_uint2(v.z, v.w);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t + 4 * bb) + k);
+    tb[3 + 2 * k] = make_uint2(v.x, v.y);
+    tb[4 + 2 * k] = make_uint2(v.z, v.w);
+  }
+  // pass C: the two groups' blocks are adjacent, so each stage is one run
+  const uint32_t bc = (uint32_t)(H + h) * 128 + 2 * tid;
+  {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t + bc));
+    tc[0][0] = make_uint2(v.x, v.y);
+    tc[1][0] = make_uint2(v.z, v.w);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {  // stage 1: entries 2 bc + 2 g + b
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t + 2 * bc) + k);
+    tc[k][1] = make_uint2(v.x, v.y);
+    tc[k][2] = make_uint2(v.z, v.w);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // stage 2: entries 4 bc + 4 g + b
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t + 4 * bc) + k);
+    tc[k >> 1][3 + 2 * (k & 1)] = make_uint2(v.x, v.y);
+    tc[k >> 1][4 + 2 * (k & 1)] = make_uint2(v.z, v.w);
+  }
+}
+
+// Pass-A twiddles of row h (15 entries, shared by its 64 threads).
+template <int H>
+__device__ __forceinline__ void row3_stage_a(uint2* sm, const uint2* __restrict__ t, int h, int tid) {
+  if (tid < 15) {
+    const int s = 31 - __clz(tid + 1);
+    const int b = tid + 1 - (1 << s);
+    sm[tid] = __ldg(t + ((uint32_t)(H + h) << s) + b);
+  }
+}
+
+template <class G, class Epi>
+__global__ void __launch_bounds__(128, 6) k_rows3_fwd_t(DevParams dp, const uint32_t* src, Epi epi, LimbMap map) {
+  static_assert(G::W == 1024, "three-pass rows are for W = 1024");
+  __shared__ uint32_t buf[2][1024];
+  __shared__ uint2 twa[2][15];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int h = blockIdx.x * 2 + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  const uint2* tw = dp.tw + ((size_t)lm.y << dp.log_n);
+  uint2 tb[7], tc[2][7];
+  row3_load_twiddles<G::H>(tb, tc, tw, h, t);
+  row3_stage_a<G::H>(twa[r], tw, h, t);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  const uint32_t* s = src + ((size_t)lm.x << dp.log_n) + (size_t)h * 1024;
+  uint32_t x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = s[t + 64 * i];
+  uint32_t* b = buf[r];
+  uint32_t y0[8], y1[8];
+  if (q < (1u << 30)) ct_pass_sm<16, true>(x, twa[r], q);
+  else ct_pass_sm<16, false>(x, twa[r], q);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) b[row3_swz(t + 64 * i)] = x[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(row3_eb(t, 0, i))];
+    y1[i] = b[row3_swz(row3_eb(t, 1, i))];
+  }
+  __syncthreads();
+  if (q < (1u << 30)) {
+    ct_pass_reg<8, true>(y0, tb, q);
+    ct_pass_reg<8, true>(y1, tb, q);
+  } else {
+    ct_pass_reg<8, false>(y0, tb, q);
+    ct_pass_reg<8, false>(y1, tb, q);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(row3_eb(t, 0, i))] = y0[i];
+    b[row3_swz(row3_eb(t, 1, i))] = y1[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(16 * t + i)];
+    y1[i] = b[row3_swz(16 * t + 8 + i)];
+  }
+  if (q < (1u << 30)) {
+    ct_pass_reg<8, true>(y0, tc[0], q);
+    ct_pass_reg<8, true>(y1, tc[1], q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = normalize<true>(y0[i], q);
+      x[8 + i] = normalize<true>(y1[i], q);
+    }
+  } else {
+    ct_pass_reg<8, false>(y0, tc[0], q);
+    ct_pass_reg<8, false>(y1, tc[1], q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = normalize<false>(y0[i], q);
+      x[8 + i] = normalize<false>(y1[i], q);
+    }
+  }
+  epi(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * 1024 + 16 * t));
+}
+
+template <class G, class Src>
+__global__ void __launch_bounds__(128, 6) k_rows3_inv_t(DevParams dp, Src src, uint32_t* dst, LimbMap map,
+                                                     int dst_compact) {
+  static_assert(G::W == 1024, "three-pass rows are for W = 1024");
+  __shared__ uint32_t buf[2][1024];
+  __shared__ uint2 twa[2][15];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int h = blockIdx.x * 2 + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  const uint2* itw = dp.itw + ((size_t)lm.y << dp.log_n);
+  uint2 tb[7], tc[2][7];
+  row3_load_twiddles<G::H>(tb, tc, itw, h, t);
+  row3_stage_a<G::H>(twa[r], itw, h, t);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  uint32_t x[16];
+  src(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * 1024 + 16 * t));
+  uint32_t* b = buf[r];
+  uint32_t y0[8], y1[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = x[i];
+    y1[i] = x[8 + i];
+  }
+  if (q < (1u << 30)) {
+    gs_pass_reg<8, true>(y0, tc[0], q);
+    gs_pass_reg<8, true>(y1, tc[1], q);
+  } else {
+    gs_pass_reg<8, false>(y0, tc[0], q);
+    gs_pass_reg<8, false>(y1, tc[1], q);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(16 * t + i)] = y0[i];
+    b[row3_swz(16 * t + 8 + i)] = y1[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(row3_eb(t, 0, i))];
+    y1[i] = b[row3_swz(row3_eb(t, 1, i))];
+  }
+  __syncthreads();
+  if (q < (1u << 30)) {
+    gs_pass_reg<8, true>(y0, tb, q);
+    gs_pass_reg<8, true>(y1, tb, q);
+  } else {
+    gs_pass_reg<8, false>(y0, tb, q);
+    gs_pass_reg<8, false>(y1, tb, q);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(row3_eb(t, 0, i))] = y0[i];
+    b[row3_swz(row3_eb(t, 1, i))] = y1[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = b[row3_swz(t + 64 * i)];
+  if (q < (1u << 30)) gs_pass_sm<16, true>(x, twa[r], q);
+  else gs_pass_sm<16, false>(x, twa[r], q);
+  const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
+  uint32_t* o = dst + (dl << dp.log_n) + (size_t)h * 1024;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) o[t + 64 * i] = x[i];
+}
+
 template <class G, class Epi>
 inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi& epi, int limbs, LimbMap map,
                             cudaStream_t st) {
   if (limbs <= 0) return;
-  launch_pdl(dp.pdl, k_rows_fwd_t<G, Epi>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, src, epi, map);
+  if constexpr (G::W == 1024)
+    launch_pdl(dp.pdl, k_rows3_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
+  else
+    launch_pdl(dp.pdl, k_rows_fwd_t<G, Epi>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, src, epi, map);
   count_launch(1);
 }
 
@@ -254,8 +473,12 @@ template <class G, class Src>
 inline void launch_rows_inv(const DevParams& dp, const Src& srcf, uint32_t* dst, int limbs, LimbMap map,
                             bool dst_compact, cudaStream_t st) {
   if (limbs <= 0) return;
-  launch_pdl(dp.pdl, k_rows_inv_t<G, Src>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, srcf, dst, map,
-             dst_compact ? 1 : 0);
+  if constexpr (G::W == 1024)
+    launch_pdl(dp.pdl, k_rows3_inv_t<G, Src>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, srcf, dst, map,
+               dst_compact ? 1 : 0);
+  else
+    launch_pdl(dp.pdl, k_rows_inv_t<G, Src>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, srcf, dst, map,
+               dst_compact ? 1 : 0);
   count_launch(1);
 }
 
