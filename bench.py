@@ -85,9 +85,9 @@ def kernel_models(n=L, alpha=ALPHA):
         "moddown_rows": dict(bytes=2 * n * lb // 2, modmul=2 * n * row + 2 * n * N * 2),
         "rescale_in_rows": dict(bytes=0, modmul=2 * row),
         "rescale_cols": dict(bytes=0, modmul=2 * col + 2 * (n - 1) * (col + N)),
-        "rescale_rows": dict(bytes=0, modmul=2 * (n - 1) * row),
-        # HMult: (A - w) (P q_l)^-1 + d q_l^-1 with d0/d1 re-formed, writing 2(n-1) limbs
-        "rescale_epilogue": dict(bytes=2 * (n - 1) * lb, modmul=2 * (n - 1) * N * 3),
+        # HMult: NTT rows with the epilogue (A - w) (P q_l)^-1 + d q_l^-1 fused,
+        # d0/d1 re-formed, writing 2(n-1) limbs
+        "rescale_rows": dict(bytes=2 * (n - 1) * lb, modmul=2 * (n - 1) * (row + N * 3)),
     }
     return m
 
@@ -350,7 +350,7 @@ def run_native(args, rank, world, local_rank):
     seq_ops_per_s = 2 * BATCH * seq_steps / (ms_seq / 1e3)
     hm_stages = ("ks_prep", "ks_in_rows", "modup_cols", "modup_rows", "keymult", "moddown_in_rows",
                  "moddown_cols", "moddown_rows", "ks_epilogue", "rescale_in_rows", "rescale_cols",
-                 "rescale_rows", "rescale_epilogue")   # ks_prep and ks_epilogue are fused: no launches
+                 "rescale_rows", "rescale_epilogue")   # ks_prep, ks_epilogue, rescale_epilogue: fused, no launches
     per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
     hmult_us = 1e3 * sum(per_launch[k] for k in hm_stages)
     hrot_us = 1e3 * sum(per_launch[k] for k in hm_stages[:9])

@@ -172,7 +172,7 @@ enum ProfId {
   P_RS_IN_ROWS,       // rescale: iNTT rows of the top limb
   P_RS_COLS,          // rescale: iNTT cols, reduce, NTT cols
   P_RS_ROWS,          // rescale: NTT rows
-  P_RS_EPILOGUE,      // rescale: (c - r) q_l^-1 (streaming)
+  P_RS_EPILOGUE,      // HMult rescale epilogue: fused into the rescale rows (no launches)
   P_COUNT
 };
 

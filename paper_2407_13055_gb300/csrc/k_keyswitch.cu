@@ -328,56 +328,6 @@ __device__ __forceinline__ void ks_extra4(const DevParams& dp, const KsArgs& a, 
   }
 }
 
-// The rescaled ModDown epilogue stays a streaming kernel: it re-forms d0/d1
-// from four input limbs, whose loads a row kernel at its occupancy cannot
-// hide (fused into the NTT rows it measured 60 us against 24 + 21 us apart).
-// Rescaled ModDown output, limbs i < l: (A_u[i] - w_u[i]) (P q_l)^-1 + extra_u[i] q_l^-1.
-__global__ void k_ks_epilogue_rs(DevParams dp, KsArgs a, const uint32_t* T, const uint32_t* A, size_t a_stride) {
-  pdl_wait();
-  pdl_trigger();
-  const int top = a.n - 1;
-  const int u = blockIdx.y / top, i = blockIdx.y % top;
-  const PrimeConst P = dp.pc[i];
-  const uint2 pq = dp.ks.dn_pqinv[top * dp.L + i], qi = dp.ks.rs_qinv[top * dp.L + i];
-  const uint32_t p0 = stream_pos();
-  const size_t off = ((size_t)i << dp.log_n) + p0;
-  uint32_t w[4], acc[4], e[4];
-  load_vec<4>(w, T + ((size_t)(u * top + i) << dp.log_n) + p0);
-  load_vec<4>(acc, A + u * a_stride + off);
-  ks_extra4(dp, a, u, i, p0, P, e);
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    w[k] = addm(csub(shoup(acc[k] - w[k] + P.q, pq.x, pq.y, P.q), P.q), csub(shoup(e[k], qi.x, qi.y, P.q), P.q), P.q);
-  store_vec<4>(a.out + u * a.out_stride + off, w);
-}
-
-// ModDown merged into the rescaling (Sec. 6), output limb t of the new window:
-// out_u[t] = A_u[t'] c1 + extra_u[t'] c2 - X_u[t] c3, t' the target's limb in
-// the old window (the first two terms are absent for a prime that enters it).
-__global__ void k_ks_epilogue_mm(DevParams dp, KsArgs a, MmArgs m, const uint32_t* X, const uint32_t* A,
-                                 size_t a_stride) {
-  pdl_wait();
-  pdl_trigger();
-  const int u = blockIdx.y / m.n1, t = blockIdx.y % m.n1;
-  const MmEpi e = m.epi[t];
-  const PrimeConst P = dp.pc[m.s1 + t];
-  const uint32_t q = P.q, p0 = stream_pos();
-  uint32_t w[4];
-  load_vec<4>(w, X + ((size_t)(u * m.n1 + t) << dp.log_n) + p0);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) w[k] = csub(q - csub(shoup(w[k], e.c3.x, e.c3.y, q), q), q);
-  if (e.old_limb >= 0) {
-    uint32_t acc[4], ex[4];
-    load_vec<4>(acc, A + u * a_stride + ((size_t)e.old_limb << dp.log_n) + p0);
-    ks_extra4(dp, a, u, e.old_limb, p0, P, ex);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      w[k] = addm(addm(w[k], csub(shoup(acc[k], e.c1.x, e.c1.y, q), q), q), csub(shoup(ex[k], e.c2.x, e.c2.y, q), q),
-                  q);
-  }
-  store_vec<4>(a.out + u * a.out_stride + ((size_t)t << dp.log_n) + p0, w);
-}
-
 // ---------------------------------------------------------------------------
 // Row-kernel sources and epilogues (the streaming steps fused into the row
 // phases): a thread handles positions pos0 .. pos0 + E - 1 of launch limb y,
@@ -450,6 +400,71 @@ struct EpiModDownTop {
       for (int k = 0; k < 4; ++k)
         z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
       store_vec<4>(V + ((size_t)u << dp.log_n) + p, z);
+    }
+  }
+};
+
+// Output of the fused ModDown + rescale after the NTT rows of the conversion
+// w (launch limb y = u top + i, top = l): out_u[i] = (A_u[i] - w)(P q_l)^-1 +
+// extra_u[i] q_l^-1, d0/d1 re-formed from the four input limbs (at the
+// three-pass rows' 24 warps per SM their loads hide: 39 us against 23 + 23
+// us as rows then a streaming kernel).
+struct EpiRsOut {
+  KsArgs a;
+  const uint32_t* A;
+  size_t a_stride;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int top = a.n - 1, u = y / top, i = y % top;
+    const PrimeConst P = dp.pc[i];
+    const uint2 pq = dp.ks.dn_pqinv[top * dp.L + i], qi = dp.ks.rs_qinv[top * dp.L + i];
+    const size_t limb = (size_t)i << dp.log_n;
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      const uint32_t p = pos0 + 4 * c;
+      uint32_t acc[4], e[4], z[4];
+      load_vec<4>(acc, A + u * a_stride + limb + p);
+      ks_extra4(dp, a, u, i, p, P, e);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pq.x, pq.y, P.q), P.q),
+                    csub(shoup(e[k], qi.x, qi.y, P.q), P.q), P.q);
+      store_vec<4>(a.out + u * a.out_stride + limb + p, z);
+    }
+  }
+};
+
+// Output of the merged ModDown + rescaling after the NTT rows of X (launch
+// limb y = u n1 + t): out_u[t] = A_u[t'] c1 + extra_u[t'] c2 - X c3.
+struct EpiMmOut {
+  KsArgs a;
+  MmArgs m;
+  const uint32_t* A;
+  size_t a_stride;
+  template <int E>
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+                                             uint32_t pos0) const {
+    const int u = y / m.n1, t = y % m.n1;
+    const MmEpi e = m.epi[t];
+    const PrimeConst P = dp.pc[m.s1 + t];
+    const uint32_t q = P.q;
+#pragma unroll
+    for (int c = 0; c < E / 4; ++c) {
+      const uint32_t p = pos0 + 4 * c;
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = csub(q - csub(shoup(x[4 * c + k], e.c3.x, e.c3.y, q), q), q);
+      if (e.old_limb >= 0) {
+        uint32_t acc[4], ex[4];
+        load_vec<4>(acc, A + u * a_stride + ((size_t)e.old_limb << dp.log_n) + p);
+        ks_extra4(dp, a, u, e.old_limb, p, P, ex);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          w[k] = addm(addm(w[k], csub(shoup(acc[k], e.c1.x, e.c1.y, q), q), q),
+                      csub(shoup(ex[k], e.c2.x, e.c2.y, q), q), q);
+      }
+      store_vec<4>(a.out + u * a.out_stride + ((size_t)t << dp.log_n) + p, w);
     }
   }
 };
@@ -605,14 +620,8 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_RS_IN_ROWS);
   launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2)), st);
   prof_mark(sc, st, P_RS_COLS);
-  launch_rows_g<G>(dp, false, T3, T3, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, false, st);
+  launch_rows_fwd<G>(dp, T3, EpiRsOut{a, A, a_stride}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, st);
   prof_mark(sc, st, P_RS_ROWS);
-  dim3 g;
-  int th;
-  stream_grid(dp.log_n, 2 * top, g, th);
-  launch_pdl(dp.pdl, k_ks_epilogue_rs, g, dim3(th), 0, st, dp, a, (const uint32_t*)T3, A, a_stride);
-  count_launch(1);
-  prof_mark(sc, st, P_RS_EPILOGUE);
 }
 
 // ModDown merged into the rescaling (Sec. 6): one conversion from P and the
@@ -629,14 +638,8 @@ static void merged_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a,
   prof_mark(sc, st, P_RS_COLS);
   LimbMap out_map{nullptr, 0, m.n1, m.n1, dp.L};
   out_map.base = m.s1;
-  launch_rows_g<G>(dp, false, sc.T, sc.T, 2 * m.n1, out_map, false, st);
+  launch_rows_fwd<G>(dp, sc.T, EpiMmOut{a, m, A, a_stride}, 2 * m.n1, out_map, st);
   prof_mark(sc, st, P_RS_ROWS);
-  dim3 g;
-  int th;
-  stream_grid(dp.log_n, 2 * m.n1, g, th);
-  launch_pdl(dp.pdl, k_ks_epilogue_mm, g, dim3(th), 0, st, dp, a, m, (const uint32_t*)sc.T, A, a_stride);
-  count_launch(1);
-  prof_mark(sc, st, P_RS_EPILOGUE);
 }
 
 template <class G>
