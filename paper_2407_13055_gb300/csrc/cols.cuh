@@ -179,14 +179,24 @@ __device__ __forceinline__ void col_inputs(const DevParams& dp, const uint32_t* 
                                            int c, int pos, int slice, int GS, uint32_t* ycopy = nullptr,
                                            const int2* idtab = nullptr) {
   using CTL = ColTile<G, TC>;
+  // the next source's loads are issued before this one's iNTT columns
+  uint32_t nx[G::EC];
+  if (slice < K) {
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) nx[i] = src[slice * src_stride + (G::EC * jj + i) * G::W + l];
+  }
   for (int k = slice; k < K; k += GS) {
     const int id = idtab ? idtab[k].y : id0 + k;
     const uint32_t q = dp.pc[id].q;
     const uint2* itw = dp.itw + ((size_t)id << dp.log_n);
-    const uint32_t* s = src + k * src_stride;
     uint32_t x[G::EC];
 #pragma unroll
-    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
+    for (int i = 0; i < G::EC; ++i) x[i] = nx[i];
+    if (k + GS < K) {
+      const uint32_t* s = src + (k + GS) * src_stride;
+#pragma unroll
+      for (int i = 0; i < G::EC; ++i) nx[i] = s[(G::EC * jj + i) * G::W + l];
+    }
     if (q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
     else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, q, slice + 1, CTL::CT);
     const uint2 w = cin[k];
