@@ -63,10 +63,14 @@ def algorithmic_bytes(n=L, alpha=ALPHA):
 
 
 def kernel_models(n=L, alpha=ALPHA):
-    """Per-launch algorithmic work of each pipeline stage, averaged over one
-    HMult+rescale and one HRot: compulsory HBM bytes (evaluation-key stream,
-    the op's inputs and outputs; scratch is meant to stay in L2) and modular
-    multiplications (NTT butterflies, BConv products, element-wise products)."""
+    """Per-launch algorithmic work of each pipeline stage (dnum=3 top level):
+    compulsory HBM bytes (evaluation-key stream, the op's inputs and outputs;
+    scratch is meant to stay in L2) and modular multiplications by kind:
+    `shoup` (NTT butterflies and products by a constant: one mad.hi and two
+    mad.lo), `mac` (BConv products: one mad.wide each, reduced lazily) and
+    `smr` (variable x variable products: mad.wide, mad.lo, mad.hi).
+    modmul = shoup + mac + smr. Stages shared by HMult and HRot count HRot's
+    work (ModDown converts 2n targets for HRot, the top limb for HMult)."""
     N = 1 << LOG_N
     d = -(-n // alpha)
     ext = n + alpha
@@ -74,44 +78,61 @@ def kernel_models(n=L, alpha=ALPHA):
     targets = sum(ext - min(alpha, n - j * alpha) for j in range(d))
     lb = LIMB_BYTES
     m = {
-        # input preparation fused into the iNTT rows: reads the inputs
-        "ks_in_rows": dict(bytes=(2 * n + n) * lb // 2, modmul=n * row + n * N // 2),
-        "modup_cols": dict(bytes=0, modmul=(n + targets) * col + targets * N * alpha),
-        "modup_rows": dict(bytes=0, modmul=targets * row),
-        "keymult": dict(bytes=2 * d * ext * lb, modmul=2 * d * ext * N),
-        "moddown_in_rows": dict(bytes=0, modmul=2 * alpha * row),
-        "moddown_cols": dict(bytes=0, modmul=2 * (alpha + n) * col + 2 * n * N * alpha),
+        # input preparation fused into the iNTT rows: reads the inputs (a1 a2 for HMult)
+        "ks_in_rows": dict(bytes=(2 * n + n) * lb // 2, shoup=n * row, smr=n * N // 2),
+        "modup_cols": dict(bytes=0, shoup=(n + targets) * col, mac=targets * N * alpha),
+        "modup_rows": dict(bytes=0, shoup=targets * row),
+        "keymult": dict(bytes=2 * d * ext * lb, smr=2 * d * ext * N),
+        "moddown_in_rows": dict(bytes=0, shoup=2 * alpha * row),
+        "moddown_cols": dict(bytes=0, shoup=2 * (alpha + n) * col, mac=2 * n * N * alpha),
         # HRot: NTT rows + ModDown epilogue writing the output (2n limbs)
-        "moddown_rows": dict(bytes=2 * n * lb // 2, modmul=2 * n * row + 2 * n * N * 2),
-        "rescale_in_rows": dict(bytes=0, modmul=2 * row),
-        "rescale_cols": dict(bytes=0, modmul=2 * col + 2 * (n - 1) * (col + N)),
+        "moddown_rows": dict(bytes=2 * n * lb // 2, shoup=2 * n * row + 2 * n * N * 2),
+        "rescale_in_rows": dict(bytes=0, shoup=2 * row),
+        "rescale_cols": dict(bytes=0, shoup=2 * col + 2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1)),
         # HMult: NTT rows with the epilogue (A - w) (P q_l)^-1 + d q_l^-1 fused,
         # d0/d1 re-formed, writing 2(n-1) limbs
-        "rescale_rows": dict(bytes=2 * (n - 1) * lb, modmul=2 * (n - 1) * (row + N * 3)),
+        "rescale_rows": dict(bytes=2 * (n - 1) * lb, shoup=2 * (n - 1) * (row + N * 2), smr=2 * (n - 1) * N * 3 // 2),
     }
+    for v in m.values():
+        v["modmul"] = sum(v.get(k, 0) for k in ("shoup", "mac", "smr"))
     return m
+
+
+def multiply_costs(rates):
+    """SM clocks per modular product of each kind at the measured issue rates
+    (instructions per SM per clock of mad.lo, mad.hi, mad.wide)."""
+    lo, hi, wide = 1.0 / rates["mad_lo"], 1.0 / rates["mad_hi"], 1.0 / rates["mad_wide"]
+    return {"shoup": hi + 2 * lo, "mac": wide, "smr": wide + lo + hi}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # one-lane pipeline's kernels from one `ncu --set full` capture (cold cache;
 # command in profiles/keyswitch_n16_l40_dnum3_top.md), keyed by stage. They
-# describe the kernel sources they were taken on: when the SHA-1 of csrc/
-# differs, the figures are stale and the bench reports null.
+# describe the kernel sources they were taken on: when the SHA-1 of those
+# sources (kernel_sources) differs, the figures are stale and the bench
+# reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "57c7d8053f01ec39e7a3eeff0101f88a2df45173",
+    "sources_sha1": "3b16975ae1311080335d660de8006594d7f808fc",
     "bytes_per_launch": {"modup_cols": 10.75e6, "keymult": 137.22e6, "modup_rows": 61.02e6,
                          "moddown_cols": 7.40e6, "moddown_rows": 76.96e6},
 }
 
 
+# Sources of the key-switch pipeline's kernels (the ones the ncu capture
+# covers): the headers they include, the launch sequences and the column
+# kernels' instantiations. Host code and the ablation probes are not part of it.
+def kernel_sources():
+    d = os.path.join(ROOT, "paper_2407_13055_gb300", "csrc")
+    return [os.path.join(d, n) for n in sorted(os.listdir(d))
+            if n.endswith((".cuh", ".h")) or n == "k_keyswitch.cu" or n.startswith("k_cols_")]
+
+
 def csrc_sha1():
     import hashlib
     h = hashlib.sha1()
-    d = os.path.join(ROOT, "paper_2407_13055_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for path in kernel_sources():
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + b"\0" + f.read())
     return h.hexdigest()
 
 
@@ -439,12 +460,25 @@ def run_native(args, rank, world, local_rank):
     hbm = {"bound": "hbm", "kernel": dom, "achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": f"{peak_kind} hbm_gbs",
            "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": ncu_traffic(dom)}
-    imad_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    alu_peak = imad_peak / 3 / 1e12
+    # integer-ALU peak of the dominant kernel: its own mix of modular products
+    # issued back to back at this GPU's measured multiply issue rates (152 SMs
+    # at the maximum SM clock)
+    clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    rates = {}
+    for op, name in ((K.CKKS_INTOP_MAD_LO, "mad_lo"), (K.CKKS_INTOP_MAD_HI, "mad_hi"),
+                     (K.CKKS_INTOP_MAD_WIDE, "mad_wide")):
+        n_ops, ms_op = K.ckks_bench_intop(ctx, op, 4096)
+        rates[name] = n_ops / (ms_op * 1e-3) / (152 * clk_hz)
+    cost = multiply_costs(rates)
+    sm_clocks = sum(mdl.get(k, 0) * cost[k] for k in cost)
+    alu_peak = mdl["modmul"] / (sm_clocks / (152 * clk_hz)) / 1e12
     alu_ach = mdl["modmul"] / avg_s / 1e12
     alu = {"bound": "alu", "kernel": dom, "achieved": alu_ach, "peak": alu_peak, "unit": "Tmodmul/s",
-           "frac": alu_ach / alu_peak, "peak_source": "derived: 152 SM x 128 IMAD/clk x sm_max_mhz / 3",
-           "algorithmic_modmul_per_launch": mdl["modmul"], "traffic": ncu_traffic(dom)}
+           "frac": alu_ach / alu_peak,
+           "peak_source": "derived: 152 SM x sm_max_mhz / (the kernel's products x SM clocks per product at "
+                          "the measured mad.lo / mad.hi / mad.wide issue rates)",
+           "int_multiply_per_sm_clk": rates, "algorithmic_modmul_per_launch": mdl["modmul"],
+           "mix": {k: mdl.get(k, 0) for k in ("shoup", "mac", "smr")}, "traffic": ncu_traffic(dom)}
     roof, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
     roof = dict(roof, other={k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")})
     stage = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
@@ -740,6 +774,14 @@ def run_ablation(args, local_rank):
             mm.setdefault(label, {})[name] = {"gmodmul_s": gmm, "ms": ms, "agrees": bool(np.array_equal(out, ref)),
                                               "modmul_per_sm_clk": gmm * 1e9 / (152 * peaks.get("sm_max_mhz", 2070.0)
                                                                                 * 1e6)}
+    # integer multiply issue rates per SM per clock (the unit counts behind
+    # the integer-ALU roofline)
+    clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    int_rates = {}
+    for op, name in ((K.CKKS_INTOP_MAD_LO, "mad_lo"), (K.CKKS_INTOP_MAD_HI, "mad_hi"),
+                     (K.CKKS_INTOP_MAD_WIDE, "mad_wide")):
+        n_ops, ms_op = K.ckks_bench_intop(ctx, op, 4096)
+        int_rates[name] = n_ops / (ms_op * 1e-3) / (152 * clk_hz)
     # (2) sequential fusion: HMult with ModDown + rescale fused vs HMult then
     # a separate rescale (top level, one stream, median of 50)
     sk = K.ckks_keygen_secret(ctx, 71)
@@ -781,7 +823,7 @@ def run_ablation(args, local_rank):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"{n} elements x {rounds} dependent modular products, 8 chains per thread; "
                                    "HMult+relin at level 39 (dnum=3) with fused, merged or separate rescale"},
-            "modmul": mm, "seq_fusion_us": seq,
+            "modmul": mm, "int_multiply_per_sm_clk": int_rates, "seq_fusion_us": seq,
             "seq_fusion_speedup": seq["hmult_then_rescale"] / seq["fused_moddown_rescale"],
             "merged_speedup_over_fused": seq["fused_moddown_rescale"] / seq["merged_moddown_rescale"],
             "decrypt_max_err": dec_err}

@@ -360,6 +360,17 @@ int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, i
 int ckks_bench_modmul(ckks_ctx* ctx, int method, int prime_id, uint32_t b, const uint32_t* a, int n, int rounds,
                       uint32_t* out, float* ms);
 
+/* Integer multiply issue rate of this GPU (the denominator of the integer-ALU
+ * roofline): 8 blocks of 256 threads per SM, each thread advancing 16
+ * independent dependent chains of one instruction form for `rounds` steps on
+ * the context stream. *ops = instructions executed (per thread lane),
+ * *ms = CUDA-event time of the timed launch (one untimed launch first).
+ * CKKS_EINVAL on a bad argument. */
+#define CKKS_INTOP_MAD_LO 0   /* mad.lo.u32 */
+#define CKKS_INTOP_MAD_HI 1   /* mad.hi.u32 */
+#define CKKS_INTOP_MAD_WIDE 2 /* mad.wide.u32 (32 x 32 + 64) */
+int ckks_bench_intop(ckks_ctx* ctx, int op, int rounds, double* ops, float* ms);
+
 /* --- measurement support --- */
 /* Number of kernel ids reported by ckks_profile_read. */
 #define CKKS_PROF_KERNELS 13

@@ -130,6 +130,7 @@ _SIGS = {
     "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
     "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
     "ckks_bench_modmul": (_i, [_vp, _i, _i, _u32, _vp, _i, _i, _vp, _P(C.c_float)]),
+    "ckks_bench_intop": (_i, [_vp, _i, _i, _P(C.c_double), _P(C.c_float)]),
     "ckks_profile": (_i, [_vp, _i]),
     "ckks_profile_read": (_i, [_vp, _vp, _vp]),
     "ckks_profile_name": (C.c_char_p, [_i]),
@@ -491,6 +492,17 @@ def ckks_bench_modmul(ctx, method: int, prime_id: int, b: int, a, rounds: int):
     check(ctx, lib.ckks_bench_modmul(ctx, method, prime_id, int(b), _ptr(a), a.size, rounds, _ptr(out),
                                      C.byref(ms)))
     return out, ms.value
+
+
+CKKS_INTOP_MAD_LO, CKKS_INTOP_MAD_HI, CKKS_INTOP_MAD_WIDE = 0, 1, 2
+
+
+def ckks_bench_intop(ctx, op: int, rounds: int = 4096):
+    """(instructions executed, kernel milliseconds) of the integer-multiply
+    issue-rate probe for one instruction form."""
+    ops, ms = C.c_double(), C.c_float()
+    check(ctx, lib.ckks_bench_intop(ctx, op, rounds, C.byref(ops), C.byref(ms)))
+    return ops.value, ms.value
 
 
 CKKS_PROF_KERNELS = 13

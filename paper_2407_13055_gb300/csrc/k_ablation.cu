@@ -69,6 +69,33 @@ __global__ void k_modmul_chain(MulConsts c, const uint32_t* in, uint32_t* out, i
     if (base + k < n) out[base + k] = a[k];
 }
 
+// Integer multiply issue rates: 16 independent dependent chains per thread of
+// one instruction form (mad.lo, mad.hi, mad.wide), enough warps for every
+// scheduler; the chains' xor is stored so that nothing is removed.
+template <int OP>
+__global__ void k_intop_chain(uint32_t c, uint32_t d, uint32_t* out, int rounds) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[16];
+  uint64_t w[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    x[k] = tid * 16 + k;
+    w[k] = (uint64_t)(tid * 16 + k) << 7;
+  }
+  for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (OP == 0) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(c), "r"(d));
+      if (OP == 1) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(c), "r"(d));
+      if (OP == 2) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[k]) : "r"((uint32_t)(w[k] >> 16)), "r"(c));
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc ^= x[k] ^ (uint32_t)w[k] ^ (uint32_t)(w[k] >> 32);
+  out[tid] = acc;
+}
+
 uint32_t inv_pow2_32(uint32_t q) {  // q^-1 mod 2^32 for odd q (Newton iteration)
   uint32_t x = q;
   for (int i = 0; i < 5; ++i) x *= 2u - q * x;
@@ -132,6 +159,46 @@ extern "C" int ckks_bench_modmul(ckks_ctx* ctx, int method, int prime_id, uint32
   cudaFree(dout);
   if (e != cudaSuccess) {
     ctx->err = std::string("bench_modmul: ") + cudaGetErrorString(e);
+    return CKKS_ECUDA;
+  }
+  return CKKS_OK;
+}
+
+extern "C" int ckks_bench_intop(ckks_ctx* ctx, int op, int rounds, double* ops, float* ms) {
+  if (!ctx || !ops || !ms || op < CKKS_INTOP_MAD_LO || op > CKKS_INTOP_MAD_WIDE || rounds < 1) return CKKS_EINVAL;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8;
+  uint32_t* dout = nullptr;
+  if (cudaMalloc(&dout, (size_t)threads * blocks * 4) != cudaSuccess) return CKKS_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStream_t st = ctx->stream;
+  const uint32_t c = 0x9E3779B1u, d = 0x7F4A7C15u;
+  auto run = [&]() {
+    switch (op) {
+      case CKKS_INTOP_MAD_LO: k_intop_chain<0><<<blocks, threads, 0, st>>>(c, d, dout, rounds); break;
+      case CKKS_INTOP_MAD_HI: k_intop_chain<1><<<blocks, threads, 0, st>>>(c, d, dout, rounds); break;
+      default: k_intop_chain<2><<<blocks, threads, 0, st>>>(c, d, dout, rounds); break;
+    }
+    count_launch(1);
+  };
+  run();  // warm-up
+  cudaEventRecord(e0, st);
+  run();
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  float t = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  *ms = t;
+  *ops = (double)threads * blocks * 16 * rounds;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(dout);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("bench_intop: ") + cudaGetErrorString(e);
     return CKKS_ECUDA;
   }
   return CKKS_OK;

@@ -536,6 +536,19 @@ def test_tune_rejects_bad_arguments(K, O):
         K.ckks_tune(ctx, 0, 0)
 
 
+def test_integer_multiply_probe_runs(K, O):
+    """The issue-rate probe behind the integer-ALU roofline returns a plausible
+    rate for each form (between 1 and 256 per SM per clock at 1-2.1 GHz)."""
+    ctx, P = get(K, O, "tiny")
+    for op in (K.CKKS_INTOP_MAD_LO, K.CKKS_INTOP_MAD_HI, K.CKKS_INTOP_MAD_WIDE):
+        n_ops, ms = K.ckks_bench_intop(ctx, op, 64)
+        assert n_ops > 0 and ms > 0
+        per_sm_clk = n_ops / (ms * 1e-3) / 152 / 2.07e9
+        assert 0.5 < per_sm_clk < 300
+    with pytest.raises(K.CkksError):
+        K.ckks_bench_intop(ctx, 7, 64)
+
+
 @pytest.mark.parametrize("prime_id,rounds", [(0, 1), (1, 2), (5, 37), (39, 1000)])
 def test_modmul_methods_agree_with_big_integers(K, O, prime_id, rounds):
     """Barrett, Montgomery, Shoup and signed Montgomery (Table 3) all give
