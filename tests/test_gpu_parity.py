@@ -591,6 +591,70 @@ def test_async_transfers_match_synchronous_ones(K, O):
         K.ckks_ctx_destroy(lane)
 
 
+def test_pipelined_transfers_across_lanes_match_oracle(K, O):
+    """The end-to-end pattern: uploads on a transfer-only clone, HMult+rescale
+    and HRot on a compute lane, exports on a second transfer-only clone, with
+    CUDA events between the stages and two buffer slots per lane reused in
+    flight. Every exported result equals the oracle's."""
+    import torch
+    ctx, P = get(K, O, "toyT1")
+    n_q, nl, ns, pairs = P.L, 2, 2, 6
+    pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    cts = [rand_ct(P, n_q, 140 + i) for i in range(pairs + 1)]
+    host_in = [pinned((2, n_q, P.n)) for _ in cts]
+    for h, c in zip(host_in, cts):
+        h[:] = c
+    evk_m, evk_r = rand_evk(P, 150), rand_evk(P, 151)
+    k = O.rot_k(1, P.log_n)
+    rk, gk = K.ckks_evk_import(ctx, evk_m, 0), K.ckks_evk_import(ctx, evk_r, k)
+    cs = [torch.cuda.Stream() for _ in range(nl)]
+    us = [torch.cuda.Stream() for _ in range(nl)]
+    ds = [torch.cuda.Stream() for _ in range(nl)]
+    lanes = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in cs]
+    up = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in us]
+    dn = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in ds]
+    slot = lambda: [[K.ckks_ct_create(ctx, n_q - 1) for _ in range(ns)] for _ in range(nl)]
+    da, db, dm, dr = slot(), slot(), slot(), slot()
+    out_m = [pinned((2, n_q - 1, P.n)) for _ in range(pairs)]
+    out_r = [pinned((2, n_q, P.n)) for _ in range(pairs)]
+    ev = lambda: [[torch.cuda.Event() for _ in range(ns)] for _ in range(nl)]
+    eu, ec, ed = ev(), ev(), ev()
+    main = torch.cuda.current_stream()
+    for l in range(nl):
+        for j in range(ns):
+            ec[l][j].record(main)
+            ed[l][j].record(main)
+    try:
+        for i in range(pairs):
+            l, j = i % nl, (i // nl) % ns
+            us[l].wait_event(ec[l][j])
+            K.ckks_ct_upload_async(up[l], da[l][j], host_in[i], n_q - 1, 2.0**30)
+            K.ckks_ct_upload_async(up[l], db[l][j], host_in[i + 1], n_q - 1, 2.0**30)
+            eu[l][j].record(us[l])
+            cs[l].wait_event(eu[l][j])
+            cs[l].wait_event(ed[l][j])
+            K.ckks_hmult(lanes[l], da[l][j], db[l][j], rk, K.CKKS_RESCALE, dm[l][j])
+            K.ckks_hrot(lanes[l], da[l][j], 1, gk, dr[l][j])
+            ec[l][j].record(cs[l])
+            ds[l].wait_event(ec[l][j])
+            K.ckks_ct_export_async(dn[l], dm[l][j], out_m[i])
+            K.ckks_ct_export_async(dn[l], dr[l][j], out_r[i])
+            ed[l][j].record(ds[l])
+        torch.cuda.synchronize()
+        for i in range(pairs):
+            assert np.array_equal(out_m[i], O.hmult(P, cts[i], cts[i + 1], evk_m, rescale=True)), i
+            assert np.array_equal(out_r[i], O.hrot(P, cts[i], k, evk_r)), i
+    finally:
+        for grp in (da, db, dm, dr):
+            for row in grp:
+                for h in row:
+                    K.ckks_free(h)
+        for c in lanes + up + dn:
+            K.ckks_ctx_destroy(c)
+        K.ckks_free(rk)
+        K.ckks_free(gk)
+
+
 # ----------------------------------------- decryption after operations ---
 
 @pytest.mark.parametrize("name", ["toyT1", "toyT2", "n16d3"])
