@@ -274,32 +274,44 @@ def _oracle_worker_pair(_):
     return time.perf_counter() - t0
 
 
-def time_oracle_all_cores():
-    """(ops/s, wall seconds, workers, description) of one pair per host core."""
+def time_oracle_all_cores(rounds: int = 1, warmup: int = 0, budget_s: float = 0.0):
+    """(ops/s, wall seconds of the timed rounds, workers, description, rounds
+    timed): each round is one pair per host core; `warmup` untimed rounds
+    first; more than one timed round only while under `budget_s`."""
     import multiprocessing as mp
     from oracle import oracle as O
     O.build()
     nw = os.cpu_count() or 1
     with mp.get_context("spawn").Pool(nw, initializer=_oracle_worker_init) as pool:
         pool.map(_oracle_worker_ready, range(nw), chunksize=1)
-        t0 = time.perf_counter()
-        pool.map(_oracle_worker_pair, range(nw), chunksize=1)
-        wall = time.perf_counter() - t0
-    desc = (f"{nw} HMult+rescale and {nw} HRot(1) of the same workload, one pair per worker process "
-            f"({nw} host cores)")
-    return 2 * nw / wall, wall, nw, desc
+        for _ in range(warmup):
+            pool.map(_oracle_worker_pair, range(nw), chunksize=1)
+        done, wall = 0, 0.0
+        while done < 1 or (done < rounds and wall * (done + 1) / done < budget_s):
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker_pair, range(nw), chunksize=1)
+            wall += time.perf_counter() - t0
+            done += 1
+    desc = (f"{done} x {nw} HMult+rescale and HRot(1) pairs of the same workload, one pair per worker "
+            f"process per round ({nw} host cores)")
+    return 2 * nw * done / wall, wall, nw, desc, done
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    ops_per_s, dt, pairs, desc = time_oracle(max_pairs=max(1, args.steps), budget_s=120.0)
+    # the oracle as it stands on every host core: a step is one pair per core
+    # (spawned workers), warm-up rounds untimed, timed rounds bounded to
+    # about two minutes
+    ops_per_s, dt, nw, desc, rounds = time_oracle_all_cores(rounds=max(1, args.steps),
+                                                            warmup=min(args.warmup, 1), budget_s=120.0)
     line = {
         "impl": "reference", "metric": METRIC, "value": ops_per_s, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": pairs, "warmup": 0, "ms_per_step": 1e3 * dt / pairs, "higher_is_better": True,
+        "steps": rounds, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / rounds, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": workload_config({"sample": desc, "step": "one HMult+rescale and one HRot(1)"}),
-        "cpu_baseline": {"value": ops_per_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": workload_config({"sample": desc, "step": f"one HMult+rescale and one HRot(1) on each of {nw} "
+                                                           "host cores"}),
+        "cpu_baseline": {"value": ops_per_s, "unit": UNIT, "cores": nw, "kind": "oracle", "sample": desc},
         "e2e": {"value": ops_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -318,7 +330,7 @@ def run_native(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v1, dt1, _, desc1 = time_oracle(1)
-        v, dt, nw, desc = time_oracle_all_cores()
+        v, dt, nw, desc, _ = time_oracle_all_cores()
         cpu = {"value": v, "unit": UNIT, "cores": nw, "kind": "oracle", "sample": desc, "seconds": dt,
                "single_thread": {"value": v1, "cores": 1, "sample": desc1, "seconds": dt1}}
 
