@@ -2,15 +2,29 @@
 oracle, pinned against the paper's table, big-integer arithmetic and
 decryption."""
 import math
+import os
 
 import numpy as np
 import pytest
 
 from paper_2407_13055_gb300 import inputs
 
-# Table 2: per level, number of 25-bit primes (tau) and 30-bit primes (q), log2 Q, log2 Delta
-TABLE2 = [(2, 0, 50, None), (0, 3, 90, 40), (4, 1, 130, 40), (2, 4, 170, 40), (0, 7, 210, 40),
-          (1, 8, 265, 55), (2, 9, 320, 55), (3, 10, 375, 55), (4, 11, 430, 55)]
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _table2():
+    """Table 2 rows from tests/golden: (n_tau, n_q, log2 Q, log2 Delta or None) per level."""
+    rows = []
+    with open(os.path.join(GOLDEN, "table2_prime_system_2530.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                lv, nt, nq, lq, ld = line.split()
+                assert int(lv) == len(rows)
+                rows.append((int(nt), int(nq), int(lq), None if ld == "-" else int(ld)))
+    return rows
+
+
+TABLE2 = _table2()
 
 
 def _window(P, lv):
@@ -42,14 +56,14 @@ def test_rescaling_cycle_keeps_scale_within_a_tenth_of_a_bit(O):
     """Sec. 3.2: with the fixed prime order, Delta stays within 2^39.9 .. 2^40.1
     through the rescaling cycle (and ~2^55 at the double-rescaling levels)."""
     P, levels = O.prime_system_2530(16, 5)
-    for top, delta in ((4, 40.0), (8, 55.0)):
-        logd = delta
+    for top in (4, 8):
+        logd = float(TABLE2[top][3])
         for lv in range(top, 0 if top == 4 else 5, -1):
             old, new = set(range(*_span(levels[lv]))), set(range(*_span(levels[lv - 1])))
             drop = sum(math.log2(int(P.q[g])) for g in old - new)
             add = sum(math.log2(int(P.q[g])) for g in new - old)
             logd = 2 * logd + add - drop          # HMult squares the scale, then the rescale
-            want = 40.0 if lv - 1 <= 4 else 55.0
+            want = float(TABLE2[lv - 1][3] if TABLE2[lv - 1][3] is not None else TABLE2[lv][3])
             assert abs(logd - want) < 0.1, (lv, logd)
 
 

@@ -6,6 +6,7 @@
 * the negacyclic NTT (Sec. 2.2) against schoolbook products in
   Z_q[X]/(X^N+1) and against Horner evaluation at psi^(2i+1).
 """
+import os
 import random
 
 import numpy as np
@@ -55,7 +56,22 @@ def test_psi_is_smallest_primitive_root(O):
             assert pow(x, n, q) != q - 1
 
 
+def _table3_ranges():
+    """Output ranges of Table 3 (tests/golden), keyed by method."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_reduction_methods.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                method, _, _, rng = line.split()
+                out[method] = rng
+    return out
+
+
 def test_smr_definition_and_range(O):
+    """Alg. 2 returns x 2^-32 mod q in the output range Table 3 prints for the
+    signed Montgomery reduction, (-q, q), for every x in [-q 2^31, q 2^31)."""
+    assert _table3_ranges()["signed_montgomery"] == "(-q,q)"
     rng = random.Random(11)
     qs = [int(v) for v in O.gen_primes(16, 4, 2)[0]] + [int(v) for v in O.gen_primes(16, 1, 2)[1]] + [97, 12289]
     for q in qs:
