@@ -805,6 +805,39 @@ def test_lanes_give_identical_results_concurrently(K, O):
 
 # ------------------------------------------------------------ batched form ---
 
+def test_headline_configuration_matches_oracle(K, O):
+    """The launch configuration bench.py times, on sampled operations: N = 2^16,
+    40 limbs at the top level, dnum = 3, tuned column shapes, HMult+rescale and
+    HRot(1) of each ciphertext issued through the batch API over four lanes and
+    replayed as one CUDA graph (twice): every output equals the oracle's."""
+    ctx, P = get(K, O, "n16d3")
+    n_q, nl = P.L, 4
+    K.ckks_tune(ctx, n_q - 1, 1)
+    relin, rotk = rand_evk(P, 501), rand_evk(P, 502)
+    k1 = O.rot_k(1, P.log_n)
+    ek_r, ek_g = K.ckks_evk_import(ctx, relin, 0), K.ckks_evk_import(ctx, rotk, k1)
+    cts = [rand_ct(P, n_q, 510 + i) for i in range(3)]
+    hs = [K.ckks_ct_import(ctx, c, n_q - 1, 2.0**30) for c in cts]
+    outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in range(4)]
+    # as in the bench: a group of ciphertexts, their HMults on lanes 0.., then their HRots
+    ops = [dict(op=K.CKKS_OP_HMULT, a=hs[i], b=hs[i + 1], evk=ek_r, flags=K.CKKS_RESCALE, out=outs[i])
+           for i in range(2)]
+    ops += [dict(op=K.CKKS_OP_HROT, a=hs[i], r=1, evk=ek_g, out=outs[2 + i]) for i in range(2)]
+    batch = K.ckks_batch_create(ctx, ops, nl, True)
+    try:
+        K.ckks_batch_run(ctx, batch)
+        K.ckks_batch_run(ctx, batch)
+        K.ckks_sync(ctx)
+        for i in range(2):
+            assert np.array_equal(K.ckks_ct_export(ctx, outs[i], P.n)[0],
+                                  O.hmult(P, cts[i], cts[i + 1], relin, rescale=True)), i
+            assert np.array_equal(K.ckks_ct_export(ctx, outs[2 + i], P.n)[0], O.hrot(P, cts[i], k1, rotk)), i
+    finally:
+        K.ckks_batch_destroy(batch)
+        for h in hs + outs + [ek_r, ek_g]:
+            K.ckks_free(h)
+
+
 @pytest.mark.parametrize("lanes,use_graph", [(1, False), (3, False), (3, True)])
 def test_batch_mixed_levels_matches_oracle(K, O, lanes, use_graph):
     """Independent operations at mixed levels in one batch (direct or one CUDA
