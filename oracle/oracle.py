@@ -134,6 +134,8 @@ class Params:
 
 
 def gen_primes(log_n: int, n_q: int, n_p: int):
+    """The prime rule (reading of Eq. 3): q_0 the largest prime = 1 mod 2N below
+    2^31, q_1.. the largest below 2^30, p_0.. the next below 2^31."""
     q = np.zeros(max(n_q, 1), np.uint32)
     p = np.zeros(max(n_p, 1), np.uint32)
     if lib().or_gen_primes(log_n, n_q, n_p, q, p) != 0:
@@ -142,7 +144,8 @@ def gen_primes(log_n: int, n_q: int, n_p: int):
 
 
 def make_params(log_n: int, L: int, dnum: int, alpha: int | None = None) -> Params:
-    """alpha = ceil(L / dnum) auxiliary primes unless given."""
+    """Parameters of the prime rule (reading of Eq. 3): L ciphertext primes,
+    alpha = ceil(L / dnum) auxiliary primes unless given (Sec. 2.3 gadget)."""
     if alpha is None:
         alpha = -(-L // dnum)
     q, p = gen_primes(log_n, L, alpha)
@@ -150,14 +153,18 @@ def make_params(log_n: int, L: int, dnum: int, alpha: int | None = None) -> Para
 
 
 def is_prime(v: int) -> bool:
+    """Deterministic primality of v (the prime rule of Eq. 3 needs q prime)."""
     return bool(lib().or_is_prime(int(v)))
 
 
 def find_psi(q: int, log_n: int) -> int:
+    """Smallest psi with psi^N = -1 mod q: the primitive 2N-th root of the
+    negacyclic NTT (Eq. 3)."""
     return int(lib().or_find_psi(int(q), log_n))
 
 
 def smr(x: int, q: int) -> int:
+    """Signed Montgomery reduction of x (Alg. 2): x 2^-32 mod q in (-q, q)."""
     return int(lib().or_smr(int(x), int(q)))
 
 
@@ -166,18 +173,21 @@ def smr(x: int, q: int) -> int:
 # ----------------------------------------------------------------------------
 
 def ntt_naive(a, q: int, log_n: int) -> np.ndarray:
+    """O(N^2) negacyclic NTT, A_i = sum_k a_k psi^((2i+1)k) (Eq. 3), natural order."""
     out = np.zeros(1 << log_n, np.uint32)
     lib().or_ntt_naive(_u32(a), out, log_n, int(q))
     return out
 
 
 def intt_naive(a, q: int, log_n: int) -> np.ndarray:
+    """O(N^2) inverse of ntt_naive (Eq. 3)."""
     out = np.zeros(1 << log_n, np.uint32)
     lib().or_intt_naive(_u32(a), out, log_n, int(q))
     return out
 
 
 def ntt(a, primes) -> np.ndarray:
+    """Fast negacyclic NTT per limb (Eq. 3, natural order); limb i modulo primes[i]."""
     a = _u32(a).copy()
     primes = _u32(primes)
     log_n = int(a.shape[-1]).bit_length() - 1
@@ -186,6 +196,7 @@ def ntt(a, primes) -> np.ndarray:
 
 
 def intt(a, primes) -> np.ndarray:
+    """Fast inverse negacyclic NTT per limb (Eq. 3)."""
     a = _u32(a).copy()
     primes = _u32(primes)
     log_n = int(a.shape[-1]).bit_length() - 1
@@ -194,6 +205,7 @@ def intt(a, primes) -> np.ndarray:
 
 
 def bconv(x, src, dst) -> np.ndarray:
+    """Fast basis conversion (Eq. 2) with centered y_j (Sec. 4.2), coefficient domain."""
     x = _u32(x)
     src, dst = _u32(src), _u32(dst)
     log_n = int(x.shape[-1]).bit_length() - 1
@@ -203,6 +215,7 @@ def bconv(x, src, dst) -> np.ndarray:
 
 
 def automorph_ntt(a, k: int) -> np.ndarray:
+    """Automorphism X -> X^k on NTT-domain limbs (Eq. 4): an index permutation."""
     a = _u32(a)
     log_n = int(a.shape[-1]).bit_length() - 1
     limbs = a.size >> log_n
@@ -212,6 +225,7 @@ def automorph_ntt(a, k: int) -> np.ndarray:
 
 
 def automorph_coeff(a, primes, k: int) -> np.ndarray:
+    """Automorphism X -> X^k on coefficients (Eq. 4 stated on coefficients)."""
     a = _u32(a)
     primes = _u32(primes)
     log_n = int(a.shape[-1]).bit_length() - 1
@@ -226,10 +240,12 @@ def rot_k(r: int, log_n: int) -> int:
 
 
 def conj_k(log_n: int) -> int:
+    """Galois element of the conjugation (Sec. 2.1): 2N - 1."""
     return (2 << log_n) - 1
 
 
 def tensor(ct1, ct2, q) -> np.ndarray:
+    """HMult tensor (Sec. 2.1): d0 = b1 b2, d1 = a1 b2 + a2 b1, d2 = a1 a2 (NTT domain)."""
     ct1, ct2, q = _u32(ct1), _u32(ct2), _u32(q)
     n_q, n = ct1.shape[1], ct1.shape[2]
     out = np.zeros((3, n_q, n), np.uint32)
@@ -238,8 +254,8 @@ def tensor(ct1, ct2, q) -> np.ndarray:
 
 
 def modup(P: Params, d, n_q: int, base: int = 0) -> np.ndarray:
-    """ModUp of the window q[base .. base + n_q); digits are the fixed groups
-    of alpha consecutive primes of the whole list, cut to the window."""
+    """ModUp (Alg. 1, Eq. 2) of the window q[base .. base + n_q); digits are the
+    fixed groups of alpha consecutive primes of the whole list, cut to the window."""
     d = _u32(d)
     out = np.zeros((P.digits(n_q, base), n_q + P.alpha, P.n), np.uint32)
     lib().or_modup(*P.args(), base, d, n_q, out)
@@ -247,12 +263,15 @@ def modup(P: Params, d, n_q: int, base: int = 0) -> np.ndarray:
 
 
 def keymult(P: Params, up, n_q: int, evk, base: int = 0) -> np.ndarray:
+    """KeyMult + MAC (Sec. 2.3, Par. 1): acc_t = sum_j ModUp_j[t] evk_j[t] over the
+    extended primes of the window and P."""
     out = np.zeros((2, n_q + P.alpha, P.n), np.uint32)
     lib().or_keymult(*P.args(), base, _u32(up), n_q, _u32(evk), out)
     return out
 
 
 def moddown(P: Params, acc, n_q: int, base: int = 0) -> np.ndarray:
+    """ModDown (Sec. 2.3): (acc_Q - BConv_{P->Q}(acc_P)) P^-1 on the window."""
     out = np.zeros((2, n_q, P.n), np.uint32)
     lib().or_moddown(*P.args(), base, _u32(acc), n_q, out)
     return out
@@ -335,6 +354,7 @@ def rescale_rational(P: Params, ct, s_old: int, n_old: int, s_new: int, n_new: i
 
 
 def rescale(ct, q) -> np.ndarray:
+    """Rescale (Sec. 2.1): c_i = (c_i - [c_l]_centered) q_l^-1 mod q_i, i < l."""
     ct, q = _u32(ct), _u32(q)
     polys, n_q, n = ct.shape
     out = np.zeros((polys, n_q - 1, n), np.uint32)
@@ -343,6 +363,8 @@ def rescale(ct, q) -> np.ndarray:
 
 
 def hmult(P: Params, ct1, ct2, evk, rescale: bool = True, base: int = 0) -> np.ndarray:
+    """HMult (Sec. 2.1, Sec. 2.3): tensor, then (d0, d1) + KeySwitch(d2) with
+    ModUp, KeyMult and ModDown, optionally rescaled by the top prime."""
     ct1, ct2 = _u32(ct1), _u32(ct2)
     n_q = ct1.shape[1]
     out = np.zeros((2, n_q - (1 if rescale else 0), P.n), np.uint32)
@@ -365,6 +387,7 @@ def hmult_merged(P: Params, ct1, ct2, evk, base: int = 0, new=None) -> np.ndarra
 
 
 def hrot(P: Params, ct, k: int, evk, base: int = 0) -> np.ndarray:
+    """HRot / HConj (Sec. 2.3, Eq. 4): (phi_k(b), 0) + KeySwitch(phi_k(a))."""
     ct = _u32(ct)
     n_q = ct.shape[1]
     out = np.zeros((2, n_q, P.n), np.uint32)
@@ -373,7 +396,7 @@ def hrot(P: Params, ct, k: int, evk, base: int = 0) -> np.ndarray:
 
 
 def encode_ext(P: Params, u, scale: float, n_q: int) -> np.ndarray:
-    """Extended plaintext: the encoding's integer coefficients reduced modulo
+    """Extended plaintext (Par. 4, Par. 5): the encoding's integer coefficients reduced modulo
     q_0..q_{n_q-1} and then p_0..p_{alpha-1}, NTT domain [n_q + alpha][N]."""
     m = encode_coeffs(u, scale, P.log_n)
     return small_to_ntt(m, list(P.q[:n_q]) + list(P.p), P.log_n)
@@ -419,6 +442,7 @@ def linear_transform(P: Params, ct, rots, evks, pts_ext, base: int = 0) -> np.nd
 
 
 def hadd(x, y, q) -> np.ndarray:
+    """HAdd (Sec. 2.1): limb-wise sum modulo each prime."""
     x, y = _u32(x), _u32(y)
     out = np.zeros_like(x)
     lib().or_hadd(x, y, x.shape[1], _u32(q), x.shape[2].bit_length() - 1, out)
@@ -426,6 +450,7 @@ def hadd(x, y, q) -> np.ndarray:
 
 
 def pmult(x, pt, q) -> np.ndarray:
+    """PMult (Sec. 2.1): NTT-domain product of each ciphertext polynomial with pt."""
     x, pt = _u32(x), _u32(pt)
     out = np.zeros_like(x)
     lib().or_pmult(x, pt, x.shape[1], _u32(q), x.shape[2].bit_length() - 1, out)
@@ -433,6 +458,7 @@ def pmult(x, pt, q) -> np.ndarray:
 
 
 def small_to_ntt(v, primes, log_n: int) -> np.ndarray:
+    """Signed small integer coefficients reduced modulo each prime, then NTT (Eq. 3)."""
     primes = _u32(primes)
     out = np.zeros((len(primes), 1 << log_n), np.uint32)
     lib().or_small_to_ntt(_i64(v), len(primes), primes, log_n, out)
@@ -444,6 +470,7 @@ def small_to_ntt(v, primes, log_n: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 
 def encrypt(P: Params, s, pt, a, e) -> np.ndarray:
+    """Symmetric encryption (Eq. 1): (b, a) = (-a s + e + pt, a), NTT domain."""
     pt = _u32(pt)
     n_q = pt.shape[0]
     out = np.zeros((2, n_q, P.n), np.uint32)
@@ -452,6 +479,7 @@ def encrypt(P: Params, s, pt, a, e) -> np.ndarray:
 
 
 def decrypt(P: Params, s, ct) -> np.ndarray:
+    """Decryption (Sec. 2.1): b + a s, NTT domain."""
     ct = _u32(ct)
     n_q = ct.shape[1]
     out = np.zeros((n_q, P.n), np.uint32)
@@ -460,20 +488,22 @@ def decrypt(P: Params, s, ct) -> np.ndarray:
 
 
 def keygen_ks(P: Params, s, s_from_ntt, a, e) -> np.ndarray:
-    """Key-switching key [dnum][2][L+alpha][N] from s_from (NTT domain) to s."""
+    """Key-switching key (Sec. 2.3, gadget [P]_{q_i} on the digit limbs)
+    [dnum][2][L+alpha][N] from s_from (NTT domain) to s."""
     out = np.zeros((P.dnum, 2, P.L + P.alpha, P.n), np.uint32)
     lib().or_keygen_ks(*P.args(), _i64(s), _u32(s_from_ntt), _u32(a), _i64(e), out)
     return out
 
 
 def keygen_relin(P: Params, s, a, e) -> np.ndarray:
+    """Relinearization key (Sec. 2.3): key switching from s^2 to s."""
     sh = small_to_ntt(s, P.all_primes(), P.log_n)
     s2 = ((sh.astype(np.uint64) * sh) % P.all_primes()[:, None].astype(np.uint64)).astype(np.uint32)
     return keygen_ks(P, s, s2, a, e)
 
 
 def keygen_auto(P: Params, s, k: int, a, e) -> np.ndarray:
-    """Key for phi_k(s) -> s (rotation k = 5^r, conjugation k = 2N-1)."""
+    """Key for phi_k(s) -> s (Eq. 4; rotation k = 5^r, conjugation k = 2N-1)."""
     sh = small_to_ntt(s, P.all_primes(), P.log_n)
     return keygen_ks(P, s, automorph_ntt(sh, k), a, e)
 
@@ -493,7 +523,7 @@ def _slot_exponents(log_n: int) -> np.ndarray:
 
 
 def encode_coeffs(u, scale: float, log_n: int) -> np.ndarray:
-    """round(Delta * sigma^-1(u)) as int64 coefficients (half away from zero).
+    """Encoding (Sec. 2.1): round(Delta * sigma^-1(u)) as int64 coefficients (half away from zero).
 
     sigma^-1: the real polynomial m with m(zeta^(5^j)) = u_j and
     m(zeta^(-5^j)) = conj(u_j); m_k = (1/N) sum_{o odd} z_o zeta^(-o k),
@@ -513,7 +543,7 @@ def encode_coeffs(u, scale: float, log_n: int) -> np.ndarray:
 
 
 def decode_coeffs(m, scale: float, log_n: int) -> np.ndarray:
-    """Slots u_j = m(zeta^(5^j)) / Delta from real coefficients m."""
+    """Decoding (Sec. 2.1): slots u_j = m(zeta^(5^j)) / Delta from real coefficients m."""
     n = 1 << log_n
     k = np.arange(n)
     tw = np.asarray(m, dtype=np.float64) * np.exp(1j * np.pi * k / n)
@@ -523,7 +553,7 @@ def decode_coeffs(m, scale: float, log_n: int) -> np.ndarray:
 
 
 def encode_coeffs_naive(u, scale: float, log_n: int) -> np.ndarray:
-    """O(N^2) definition of encode_coeffs (small N only)."""
+    """O(N^2) definition of encode_coeffs (Sec. 2.1; small N only)."""
     n = 1 << log_n
     e = _slot_exponents(log_n)
     zeta = np.exp(1j * np.pi / n)
@@ -537,7 +567,7 @@ def encode_coeffs_naive(u, scale: float, log_n: int) -> np.ndarray:
 
 
 def crt_centered(res, primes) -> list:
-    """Centered CRT lift of residues [n][N] to Python integers in (-Q/2, Q/2]."""
+    """Centered CRT lift (Sec. 2.1, RNS) of residues [n][N] to Python integers in (-Q/2, Q/2]."""
     primes = [int(v) for v in primes]
     Q = 1
     for v in primes:
@@ -553,12 +583,13 @@ def crt_centered(res, primes) -> list:
 
 
 def encode(P: Params, u, scale: float, n_q: int) -> np.ndarray:
-    """Plaintext in the NTT domain [n_q][N]."""
+    """Encoding (Sec. 2.1) to a plaintext in the NTT domain [n_q][N]."""
     m = encode_coeffs(u, scale, P.log_n)
     return small_to_ntt(m, P.q[:n_q], P.log_n)
 
 
 def decode(P: Params, pt, scale: float) -> np.ndarray:
+    """Decoding (Sec. 2.1) of an NTT-domain plaintext: iNTT, centered CRT lift, slots."""
     pt = _u32(pt)
     n_q = pt.shape[0]
     coef = intt(pt, P.q[:n_q])
