@@ -232,6 +232,7 @@ void automorph_ntt(const u32* a, u32* out, u32 n, u32 k) {
 }
 
 // Number of digits active at a level with n_q ciphertext limbs from prime base.
+// (Sec. 2.3: hybrid key switching splits Q_l into digits of alpha primes.)
 int n_digits(int n_q, int alpha, int base = 0) { return (base + n_q - 1) / alpha - base / alpha + 1; }
 
 // ModUp (Alg. 1 as ModSwitch Q_j -> PQ, Sec. 2.3): for every active digit j,
@@ -321,6 +322,7 @@ void moddown(const Params& P, const u32* acc, int n_q, u32* out) {
 
 // Key switching of one polynomial d (NTT domain, n_q limbs) with evk:
 // out = ModDown(KeyMult(ModUp(d), evk)), two polynomials of n_q limbs.
+// (Sec. 2.3, the key-switching sequence.)
 void keyswitch(const Params& P, const u32* d, int n_q, const u32* evk, u32* out) {
   u32 n = P.n();
   int ext = n_q + P.alpha, nd = n_digits(n_q, P.alpha, P.base);
@@ -334,6 +336,7 @@ void keyswitch(const Params& P, const u32* d, int n_q, const u32* evk, u32* out)
 
 extern "C" {
 
+// Primality for the prime rule (Eq. 3: the NTT primes are primes q = 1 mod 2N).
 int or_is_prime(uint64_t v) { return is_prime_u32(v) ? 1 : 0; }
 
 // Prime lists (Eq. 3: q = 1 mod 2N; Sec. 3: q < 2^31). Reading of the paper's
@@ -360,6 +363,7 @@ int or_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p) {
   return 0;
 }
 
+// psi of the negacyclic NTT (Eq. 3): the smallest x with x^N = -1 mod q.
 uint32_t or_find_psi(uint32_t q, int log_n) { return find_psi(q, log_n); }
 
 // 32-bit signed Montgomery reduction (Alg. 2): for x in [-q 2^31, q 2^31),
@@ -375,7 +379,7 @@ int32_t or_smr(int64_t x, uint32_t q) {
   return x_hi - zh;
 }
 
-// Negacyclic NTT by its definition, O(N^2): out[i] = sum_k a_k psi^((2i+1)k).
+// Negacyclic NTT (Eq. 3) by its definition, O(N^2): out[i] = sum_k a_k psi^((2i+1)k).
 void or_ntt_naive(const uint32_t* a, uint32_t* out, int log_n, uint32_t q) {
   u32 n = 1u << log_n, psi = find_psi(q, log_n);
   for (u32 i = 0; i < n; ++i) {
@@ -386,7 +390,7 @@ void or_ntt_naive(const uint32_t* a, uint32_t* out, int log_n, uint32_t q) {
   }
 }
 
-// Inverse by its definition: a_k = N^-1 sum_i A_i psi^(-(2i+1)k).
+// Inverse NTT (Eq. 3) by its definition: a_k = N^-1 sum_i A_i psi^(-(2i+1)k).
 void or_intt_naive(const uint32_t* a, uint32_t* out, int log_n, uint32_t q) {
   u32 n = 1u << log_n, psi_inv = inv_mod(find_psi(q, log_n), q);
   u32 n_inv = inv_mod(n % q, q);
@@ -398,7 +402,7 @@ void or_intt_naive(const uint32_t* a, uint32_t* out, int log_n, uint32_t q) {
   }
 }
 
-// Fast NTT / iNTT over `limbs` limbs, limb i modulo primes[i], in place.
+// Fast NTT / iNTT (Eq. 3, Sec. 2.2) over `limbs` limbs, limb i modulo primes[i], in place.
 void or_ntt(uint32_t* a, int limbs, const uint32_t* primes, int log_n) {
   for (int i = 0; i < limbs; ++i) ntt_fast(a + (size_t(i) << log_n), log_n, primes[i]);
 }
@@ -412,6 +416,7 @@ void or_bconv(const uint32_t* x, int k_src, const uint32_t* src, uint32_t* out, 
   bconv(x, k_src, src, out, m_dst, dst, 1u << log_n);
 }
 
+// Automorphism X -> X^k (Eq. 4) on NTT-domain limbs, and on coefficients.
 void or_automorph_ntt(const uint32_t* a, uint32_t* out, int limbs, int log_n, uint32_t k) {
   u32 n = 1u << log_n;
   for (int i = 0; i < limbs; ++i) automorph_ntt(a + size_t(i) * n, out + size_t(i) * n, n, k);
@@ -439,6 +444,8 @@ void or_tensor(const uint32_t* ct1, const uint32_t* ct2, int n_q, const uint32_t
     }
 }
 
+// ModUp (Alg. 1, Eq. 2), KeyMult + MAC (Sec. 2.3, Par. 1) and ModDown
+// (Sec. 2.3) as separate steps, for the step-by-step parity tests.
 void or_modup(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, int dnum, int base,
               const uint32_t* d, int n_q, uint32_t* out) {
   Params P{log_n, L, alpha, dnum, q, p, base};
@@ -665,7 +672,7 @@ void or_hrot(int log_n, int L, const uint32_t* q, int alpha, const uint32_t* p, 
     }
 }
 
-// HAdd: limb-wise modular addition of two ciphertexts [2][n_q][N].
+// HAdd (Sec. 2.1): limb-wise modular addition of two ciphertexts [2][n_q][N].
 void or_hadd(const uint32_t* x, const uint32_t* y, int n_q, const uint32_t* q, int log_n, uint32_t* out) {
   u32 n = 1u << log_n;
   for (int t = 0; t < 2; ++t)
@@ -676,7 +683,7 @@ void or_hadd(const uint32_t* x, const uint32_t* y, int n_q, const uint32_t* q, i
       }
 }
 
-// PMult: ciphertext [2][n_q][N] times plaintext [n_q][N], NTT domain.
+// PMult (Sec. 2.1): ciphertext [2][n_q][N] times plaintext [n_q][N], NTT domain.
 void or_pmult(const uint32_t* x, const uint32_t* pt, int n_q, const uint32_t* q, int log_n, uint32_t* out) {
   u32 n = 1u << log_n;
   for (int t = 0; t < 2; ++t)
@@ -687,7 +694,7 @@ void or_pmult(const uint32_t* x, const uint32_t* pt, int n_q, const uint32_t* q,
       }
 }
 
-// Signed small coefficients -> residues modulo each prime, then NTT.
+// Signed small coefficients -> residues modulo each prime (RNS, Sec. 2.1), then NTT (Eq. 3).
 void or_small_to_ntt(const int64_t* v, int limbs, const uint32_t* primes, int log_n, uint32_t* out) {
   u32 n = 1u << log_n;
   for (int i = 0; i < limbs; ++i) {
@@ -715,7 +722,7 @@ void or_encrypt(const int64_t* s, const uint32_t* a, const int64_t* e, const uin
     }
 }
 
-// Decryption: m = b + a s (NTT domain).
+// Decryption (Sec. 2.1): m = b + a s (NTT domain).
 void or_decrypt(const int64_t* s, const uint32_t* ct, int n_q, const uint32_t* q, int log_n, uint32_t* out) {
   u32 n = 1u << log_n;
   size_t poly = size_t(n_q) * n;
@@ -728,8 +735,8 @@ void or_decrypt(const int64_t* s, const uint32_t* ct, int n_q, const uint32_t* q
     }
 }
 
-// Key-switching key from s_from to s (hybrid gadget; the paper cites Han-Ki
-// for it): for each digit j, b_j = -a_j s + e_j + g_j s_from over all L
+// Key-switching key from s_from to s (Sec. 2.3, hybrid gadget; the paper
+// cites Han-Ki for it): for each digit j, b_j = -a_j s + e_j + g_j s_from over all L
 // ciphertext and alpha auxiliary primes, with g_j = [P]_{q_i} on the limbs of
 // digit j and 0 on every other limb (including the auxiliary ones).
 // s: ternary secret coefficients; s_from_ntt: [L+alpha][N] NTT domain;
