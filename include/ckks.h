@@ -171,7 +171,8 @@ int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out);
 /* Eq. 1: (b, a) = (-a s + m + e, a) with a uniform and e Gaussian from the
  * library's sampler. */
 int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t seed, ckks_ct** out);
-/* m = b + a s. */
+/* Decryption (Sec. 2.1): m = b + a s, NTT domain; a new plaintext at the
+ * ciphertext's level and scale. */
 int ckks_decrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_ct* ct, ckks_pt** out);
 
 /* --- ciphertext and plaintext objects --- */
@@ -204,14 +205,14 @@ int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* pt, uint32_t* host, size_t word
                    double* scale);
 
 /* --- homomorphic operations (Sec. 2.1), all asynchronous on the context stream --- */
-/* HAdd: limb-wise addition; levels must match, scales within 2^-20. out may
- * alias a or b. */
+/* HAdd (Sec. 2.1): limb-wise addition; levels must match, scales within
+ * 2^-20 (else CKKS_ELEVEL / CKKS_ESCALE). out may alias a or b. */
 int ckks_hadd(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
-/* PAdd: (b + pt, a) limb-wise; the plaintext's level must be >= the
+/* PAdd (Sec. 2.1): (b + pt, a) limb-wise; the plaintext's level must be >= the
  * ciphertext's and its scale equal within 2^-20. out may alias a. */
 int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
-/* PMult: ciphertext times plaintext in the NTT domain; scale multiplies. out
- * may alias a. */
+/* PMult (Sec. 2.1): ciphertext times plaintext in the NTT domain; scale
+ * multiplies. out may alias a. */
 int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out);
 /* HMult: tensor (d0, d1, d2), relinearize d2 with evk (ModUp, KeyMult,
  * ModDown; Sec. 2.3) and, with CKKS_RESCALE, rescale by q_l (rationally
@@ -223,13 +224,15 @@ int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out)
  * Other flag bits: CKKS_EINVAL. out must not alias a or b. */
 int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags,
                ckks_ct* out);
-/* Rescale (single rescaling): c'_i = (c_i - [c_l]_centered) * q_l^-1, scale /= q_l.
+/* Rescale (Sec. 2.1; rational with level windows, Sec. 3.1): c'_i =
+ * (c_i - [c_l]_centered) * q_l^-1, scale /= q_l.
  * out must not alias in. */
 int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out);
 /* HRot by r slots to the left (Eq. 4 with k = 5^r mod 2N) with evk from
  * ckks_keygen_rot(r) or ckks_evk_import(galois = k). out must not alias ct. */
 int ckks_hrot(ckks_ctx* ctx, const ckks_ct* ct, int r, const ckks_evk* evk, ckks_ct* out);
-/* HConj (k = 2N - 1). out must not alias ct. */
+/* HConj (Sec. 2.1, Eq. 4 with k = 2N - 1) with evk from ckks_keygen_conj.
+ * out must not alias ct. */
 int ckks_hconj(ckks_ctx* ctx, const ckks_ct* ct, const ckks_evk* evk, ckks_ct* out);
 /* Hoisted rotations (Par. 5, Fig. 5): outs[i] = HRot(ct, r[i]) under evks[i]
  * for i < count, sharing one ModUp of ct's a part. Because the BConv of the
