@@ -156,7 +156,6 @@ void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int 
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t q) { return csub(a + b, q); }
-__device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, uint32_t q) { return csub(a - b + q, q); }
 
 // Element-wise kernels over the n limbs of a level whose primes are
 // q[base .. base + n).
