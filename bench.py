@@ -112,9 +112,9 @@ def multiply_costs(rates):
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "3b16975ae1311080335d660de8006594d7f808fc",
-    "bytes_per_launch": {"modup_cols": 10.75e6, "keymult": 137.22e6, "modup_rows": 61.02e6,
-                         "moddown_cols": 7.40e6, "moddown_rows": 76.96e6},
+    "sources_sha1": "044eb525937d426618e82dda000646a76bc1927e",
+    "bytes_per_launch": {"modup_cols": 10.74e6, "keymult": 137.27e6, "modup_rows": 60.94e6,
+                         "moddown_cols": 7.40e6, "moddown_rows": 76.79e6},
 }
 
 
@@ -143,11 +143,13 @@ def ncu_traffic(stage):
 
 
 def tune_levels(K, ctx, levels, enabled, reps=3):
-    """Run the column-kernel fine-tuner at each level (outside any timed
-    region) and return the chosen shapes {level: {kernel: (tc, sl, z, us)}}."""
+    """Run the fine-tuner at each level (outside any timed region) and return
+    the chosen column shapes and row-phase passes {level: {kernel: (tc, sl, z,
+    tp, us)}} (row_passes: tc = passes)."""
     if not enabled:
         return None
-    names = {K.CKKS_COL_MODUP: "modup_cols", K.CKKS_COL_MODDOWN: "moddown_cols", K.CKKS_COL_RS_FUSED: "rescale_cols"}
+    names = {K.CKKS_COL_MODUP: "modup_cols", K.CKKS_COL_MODDOWN: "moddown_cols", K.CKKS_COL_RS_FUSED: "rescale_cols",
+             K.CKKS_ROW_PASSES: "row_passes"}
     out = {}
     for lv in sorted(set(int(x) for x in levels)):
         K.ckks_tune(ctx, lv, reps)

@@ -336,9 +336,15 @@ int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
 #define CKKS_COL_MODUP 0
 #define CKKS_COL_MODDOWN 1
 #define CKKS_COL_RS_FUSED 2
+/* Not a column kernel: the row phase of the NTT at N = 2^16 runs as 2
+ * register passes (32 values per thread, radix 2^5 x 2^5) or 3 (16 values,
+ * 2^4 x 2^3 x 2^3); the entry's tc is the number of passes (sl = z = tp = 1),
+ * tuned on the level's ModUp NTT rows and used by that level's key
+ * switches. Without an entry: 3. */
+#define CKKS_ROW_PASSES 3
 /* Times every candidate shape of the three kernels at `level` (reps launches
- * each, CUDA events on the context stream, on the context's scratch) and
- * records the fastest. Synchronizes the stream: do not call it while the
+ * each, CUDA events on the context stream, on the context's scratch), and at
+ * N = 2^16 both row-phase forms, and records the fastest. Synchronizes the stream: do not call it while the
  * stream is being captured. level in [0, n_q - 1] (the fused rescale kernel
  * is tuned for level >= 1). */
 int ckks_tune(ckks_ctx* ctx, int level, int reps);
@@ -346,8 +352,9 @@ int ckks_tune(ckks_ctx* ctx, int level, int reps);
  * microseconds; *tc = 0 when the level has no entry. */
 int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us);
 /* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4, tp in
- * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps), or
- * clears the entry with tc = 0. Changes no value any operation computes. */
+ * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps; for
+ * CKKS_ROW_PASSES tc in {2, 3} at N = 2^16), or clears the entry with tc = 0.
+ * Changes no value any operation computes. */
 int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp);
 
 /* --- Table 3 on this GPU: modular multiplication methods (Sec. 4.1) ---

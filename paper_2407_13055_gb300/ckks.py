@@ -457,7 +457,7 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
     check(ctx, lib.ckks_rescale_noalloc(ctx, in_dev, level, out_dev))
 
 
-CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED = 0, 1, 2
+CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED, CKKS_ROW_PASSES = 0, 1, 2, 3
 CKKS_LAUNCH_PDL = 1
 
 

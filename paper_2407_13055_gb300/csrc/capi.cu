@@ -234,7 +234,11 @@ int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, i
   if (kernel < 0 || kernel >= ckks::CK_COUNT) return fail(ctx, CKKS_EINVAL, "tune: kernel %d unknown", kernel);
   if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   ckks::ColShape s;
-  if (tc != 0) {
+  if (tc != 0 && kernel == ckks::CK_ROWS) {
+    if (ctx->dp.log_n != 16 || (tc != 2 && tc != 3))
+      return fail(ctx, CKKS_EINVAL, "tune: row passes %d not supported at N = 2^%d", tc, ctx->dp.log_n);
+    s = ckks::ColShape{tc, 1, 1, 1};
+  } else if (tc != 0) {
     if (!ckks::col_shape_supported(ctx->dp.log_n, tc, sl, z, tp))
       return fail(ctx, CKKS_EINVAL, "tune: shape (%d, %d, %d, %d) not supported at N = 2^%d", tc, sl, z, tp,
                   ctx->dp.log_n);

@@ -50,6 +50,8 @@ struct DevParams {
   const uint2* itw;      // [L + alpha][N] inverse twiddles
   KsTables ks;
   int pdl;  // host-side launch option: key-switch kernels use programmatic dependent launch
+  int rows_passes = 3;  // host-side launch option at N = 2^16: row phase in 3 (16 values per
+                        // thread, 64 threads per row) or 2 (32 values, 32 threads) passes
 };
 
 // Limb -> prime id. Either an explicit device array, or the extended-
@@ -196,7 +198,9 @@ void count_launch(int k);
 // tile width, slices per block, blocks per tile, plus tp, the conversion
 // targets per pass. Entries are atomics so that
 // lanes on other host threads may read while ckks_tune writes.
-enum ColKernel { CK_MODUP = 0, CK_MODDOWN = 1, CK_RS_FUSED = 2, CK_COUNT = 3 };
+// CK_ROWS is not a column kernel: its entry's tc is the number of register
+// passes of the row phase at N = 2^16 (2 or 3), chosen by the same tuner.
+enum ColKernel { CK_MODUP = 0, CK_MODDOWN = 1, CK_RS_FUSED = 2, CK_ROWS = 3, CK_COUNT = 4 };
 
 struct ColShape {
   int tc = 0, sl = 0, z = 0, tp = 1;  // tp: conversion targets per pass (1 or 2)

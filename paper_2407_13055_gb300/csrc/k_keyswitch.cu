@@ -657,8 +657,20 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   prof_mark(sc, st, P_MODDOWN_ROWS);
 }
 
-void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
+// The row-phase form the fine-tuner chose for the level (N = 2^16: two or
+// three register passes), else the three-pass default.
+static DevParams tuned_rows(const DevParams& dp, const Scratch& sc, int tix) {
+  DevParams d = dp;
+  if (sc.tune) {
+    const ColShape s = sc.tune->get(CK_ROWS, tix);
+    if (s.tc == 2 || s.tc == 3) d.rows_passes = s.tc;
+  }
+  return d;
+}
+
+void launch_keyswitch(const DevParams& dp0, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st) {
+  const DevParams dp = tuned_rows(dp0, sc, a.tix);
   const int n = a.n, alpha = dp.alpha, ext = n + alpha;
   const int digits = active_digits(a, alpha);
   const size_t limb = (size_t)1 << dp.log_n;
@@ -765,6 +777,36 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
       }
       if (rc == CKKS_OK) tu.set(k, tix, best, 1e3f * best_ms / reps);
     }
+    // row phase at N = 2^16: two or three register passes, timed on the
+    // level's ModUp NTT rows (in place on the scratch, like the columns)
+    if constexpr (G::W == 1024) {
+      int best_p = 3;
+      float best_ms = -1.f;
+      for (int passes : {3, 2}) {
+        if (rc != CKKS_OK || lvl.rows_cnt < 1) break;
+        DevParams dv = dp;
+        dv.rows_passes = passes;
+        auto run = [&]() {
+          launch_rows_g<G>(dv, false, sc.T, sc.T, lvl.rows_cnt, LimbMap{dp.ks.up_rows + lvl.rows_off, 0, 1, 0, 0},
+                           false, st);
+        };
+        run();
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r) run();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = CKKS_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+          best_ms = ms;
+          best_p = passes;
+        }
+      }
+      if (rc == CKKS_OK && best_ms >= 0.f) tu.set(CK_ROWS, tix, ColShape{best_p, 1, 1, 1}, 1e3f * best_ms / reps);
+    }
   });
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -778,10 +820,11 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
 // ModDown and the epilogue adding phi_k(b). The ModDown conversions use the
 // scratch after the ModUp limbs so that those stay intact for the next
 // rotation. Bit-identical to one full key switch per rotation.
-void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsArgs* rots, int count,
+void launch_hoisted_rotations(const DevParams& dp0, const Scratch& sc, const KsArgs* rots, int count,
                               cudaStream_t st) {
   if (count < 1) return;
   const KsArgs& a0 = rots[0];
+  const DevParams dp = tuned_rows(dp0, sc, a0.tix);
   const int n = a0.n, alpha = dp.alpha, ext = n + alpha;
   const int digits = active_digits(a0, alpha);
   const size_t limb = (size_t)1 << dp.log_n;
@@ -813,8 +856,9 @@ void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsAr
 // terms with their extended plaintexts in one kernel, one ModDown of the
 // sum, and the epilogue adding the plaintext-weighted automorphisms of b
 // (and pt (.) a for unrotated terms).
-void launch_linear_transform(const DevParams& dp, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
+void launch_linear_transform(const DevParams& dp0, const Scratch& sc, const KsArgs& a, const LtArgs& lt,
                              cudaStream_t st) {
+  const DevParams dp = tuned_rows(dp0, sc, a.tix);
   const int n = a.n, alpha = dp.alpha, ext = n + alpha;
   const int digits = active_digits(a, alpha);
   const size_t limb = (size_t)1 << dp.log_n;

@@ -462,9 +462,14 @@ template <class G, class Epi>
 inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi& epi, int limbs, LimbMap map,
                             cudaStream_t st) {
   if (limbs <= 0) return;
-  if constexpr (G::W == 1024)
-    launch_pdl(dp.pdl, k_rows3_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
-  else
+  bool three = false;
+  if constexpr (G::W == 1024) {
+    if (dp.rows_passes != 2) {
+      launch_pdl(dp.pdl, k_rows3_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
+      three = true;
+    }
+  }
+  if (!three)
     launch_pdl(dp.pdl, k_rows_fwd_t<G, Epi>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, src, epi, map);
   count_launch(1);
 }
@@ -473,10 +478,15 @@ template <class G, class Src>
 inline void launch_rows_inv(const DevParams& dp, const Src& srcf, uint32_t* dst, int limbs, LimbMap map,
                             bool dst_compact, cudaStream_t st) {
   if (limbs <= 0) return;
-  if constexpr (G::W == 1024)
-    launch_pdl(dp.pdl, k_rows3_inv_t<G, Src>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, srcf, dst, map,
-               dst_compact ? 1 : 0);
-  else
+  bool three = false;
+  if constexpr (G::W == 1024) {
+    if (dp.rows_passes != 2) {
+      launch_pdl(dp.pdl, k_rows3_inv_t<G, Src>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, srcf, dst, map,
+                 dst_compact ? 1 : 0);
+      three = true;
+    }
+  }
+  if (!three)
     launch_pdl(dp.pdl, k_rows_inv_t<G, Src>, dim3(G::H / G::RPC, limbs), dim3(G::RT), 0, st, dp, srcf, dst, map,
                dst_compact ? 1 : 0);
   count_launch(1);

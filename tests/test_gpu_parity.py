@@ -508,6 +508,8 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
         for kern in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
             tc, sl, z, tp, us = K.ckks_tune_get(ctx, kern, n_q - 1)
             assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and tp in (1, 2) and us > 0
+        passes, _, _, _, us = K.ckks_tune_get(ctx, K.CKKS_ROW_PASSES, n_q - 1)
+        assert passes in (2, 3) and us > 0
         # a clone shares the table
         import torch
         s = torch.cuda.Stream()
@@ -522,6 +524,39 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
         assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
     finally:
         _set_all(K, ctx, n_q - 1, (0, 4, 1, 1))
+        K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
+
+
+@pytest.mark.parametrize("n_q", [40, 5])
+def test_row_phase_forms_give_identical_results(K, O, n_q):
+    """Both forms of the N = 2^16 row phase the tuner chooses between (two
+    register passes of radix 2^5, or three of 2^4 x 2^3 x 2^3) reproduce the
+    oracle bit for bit: HMult+rescale, HRot and hoisted rotations."""
+    ctx, P = get(K, O, "n16d3")
+    c1, c2 = rand_ct(P, n_q, 91), rand_ct(P, n_q, 93)
+    evk = rand_evk(P, 95)
+    want_m = O.hmult(P, c1, c2, evk, rescale=True)
+    k = O.rot_k(1, P.log_n)
+    want_r = O.hrot(P, c1, k, evk)
+    a = K.ckks_ct_import(ctx, c1, n_q - 1, 2.0**30)
+    ek = K.ckks_evk_import(ctx, evk, k)
+    outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in range(2)]
+    try:
+        for passes in (2, 3):
+            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, passes, 1, 1, 1)
+            got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
+            assert np.array_equal(got, want_m), passes
+            got, _ = _run_hrot(K, O, ctx, P, c1, evk, 1)
+            assert np.array_equal(got, want_r), passes
+            K.ckks_hrot_hoisted(ctx, a, [1, 1], [ek, ek], outs)
+            for o in outs:
+                assert np.array_equal(K.ckks_ct_export(ctx, o, P.n)[0], want_r), passes
+        with pytest.raises(K.CkksError):
+            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 4, 1, 1, 1)
+    finally:
+        K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
+        for h in [a, ek] + outs:
+            K.ckks_free(h)
 
 
 def test_tune_rejects_bad_arguments(K, O):
