@@ -72,3 +72,21 @@ def test_prime_system_2530_matches_oracle(K, O, log_n):
     assert q.tolist() == [int(v) for v in P.q]
     assert p.tolist() == [int(v) for v in P.p]
     assert levels == [tuple(x) for x in lv]
+
+
+def test_null_handles_are_rejected_without_a_gpu(K):
+    """Every operation validates its handles before touching the device:
+    null context, operands or outputs give CKKS_EINVAL."""
+    L = K.lib
+    E = K.CKKS_EINVAL
+    assert L.ckks_hmult(None, None, None, None, 0, None) == E
+    assert L.ckks_hrot(None, None, 1, None, None) == E
+    assert L.ckks_hconj(None, None, None, None) == E
+    assert L.ckks_rescale(None, None, None) == E
+    assert L.ckks_hadd(None, None, None, None) == E
+    assert L.ckks_pmult(None, None, None, None) == E
+    assert L.ckks_padd(None, None, None, None) == E
+    assert L.ckks_tune(None, 0, 1) == E
+    assert L.ckks_sync(None) == E
+    assert L.ckks_batch_run(None) == E
+    assert L.ckks_level_limbs(None, 0) == E
