@@ -261,9 +261,27 @@ int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* ct, int count, const int
  * A batch is a list of independent operations (no operation's output may be
  * an input or output of another one in the same batch) issued across `lanes`
  * execution lanes (ckks_ctx_clone) that fork from and join into the context
- * stream; with use_graph != 0 the whole list is captured once into a CUDA
- * graph and each ckks_batch_run is a single graph launch. Operations follow
- * the single-operation entry points (same checks, same results). */
+ * stream. use_graph is a set of mode flags:
+ *  CKKS_BATCH_GRAPH: the whole list is captured once into a CUDA graph and
+ *    each ckks_batch_run is a single graph launch;
+ *  CKKS_BATCH_PERSISTENT: stage-major form with a persistent kernel. Each
+ *    key-switching operation (HMult, HRot, HConj) runs its ModUp on its lane
+ *    into working memory of its own (the batch allocates (dnum + 2)(n + alpha)
+ *    limbs per such operation at creation), the lanes join, ONE persistent
+ *    kernel runs the KeyMult + MAC (Par. 1) of all of them and every HAdd,
+ *    PAdd and PMult of the batch, taking (operation, limb) work items from a
+ *    device queue (limb-major, so each evaluation-key limb is read once per
+ *    batch and reused from L2 by every operation with that key), then the
+ *    lanes run the ModDown tails. Rescale operations run whole on their lanes.
+ *    The persistent kernel runs an operation's items only once the operation
+ *    is admitted (ckks_batch_run_admit, ckks_batch_admit); a wait for
+ *    admission is bounded by the context's wait limit (ckks_set_wait_limit),
+ *    after which the kernel stops and the next synchronizing call returns
+ *    CKKS_ETIMEOUT.
+ * Operations follow the single-operation entry points (same checks, same
+ * results, bit for bit in every mode). */
+#define CKKS_BATCH_GRAPH 1
+#define CKKS_BATCH_PERSISTENT 2
 #define CKKS_OP_HMULT 1   /* ckks_hmult(a, b, evk, flags, out) */
 #define CKKS_OP_HROT 2    /* ckks_hrot(a, r, evk, out) */
 #define CKKS_OP_HCONJ 3   /* ckks_hconj(a, evk, out) */
@@ -285,8 +303,22 @@ typedef struct ckks_batch ckks_batch;
 /* Validates the list by running it once (synchronizes), then captures it if
  * use_graph. The batch references (does not own) the operands. */
 int ckks_batch_create(ckks_ctx* ctx, const ckks_op* ops, int count, int lanes, int use_graph, ckks_batch** out);
-/* Enqueue the whole list on the context stream (asynchronous). */
+/* Enqueue the whole list on the context stream (asynchronous); a persistent
+ * batch admits every operation. */
 int ckks_batch_run(ckks_batch* batch);
+/* Persistent batches only: enqueue the list with only operations
+ * 0 .. admitted - 1 admitted to the persistent stage (0 <= admitted <=
+ * count); the others' KeyMult / element-wise items wait, bounded, until
+ * ckks_batch_admit raises the count (the host may do so while the batch runs,
+ * which is how operations that arrive later join a running launch). A count
+ * lower than the previous run's first waits for the batch's earlier runs.
+ * The outputs of operations never admitted before the wait limit are
+ * undefined, and the next synchronizing call returns CKKS_ETIMEOUT.
+ * CKKS_EINVAL for a non-persistent batch or a count out of range. */
+int ckks_batch_run_admit(ckks_batch* batch, int admitted);
+/* Raises the admitted count of a persistent batch (never lowers it);
+ * takes effect in the running persistent kernel. */
+int ckks_batch_admit(ckks_batch* batch, int admitted);
 void ckks_batch_destroy(ckks_batch* batch);
 
 /* --- rescale without allocation (the paper has no counterpart to this entry
@@ -322,7 +354,27 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
  * wait, which can cost throughput when several lanes share the GPU. A clone
  * inherits its parent's flags when it is created. */
 #define CKKS_LAUNCH_PDL 1
+/* CKKS_TUNE_TENSOR (default off): ckks_tune also times the tensor-core
+ * shapes of the column kernels (tp in {8, 16}, below). They are slower than
+ * the CUDA-core shapes when several lanes share the GPU (their larger
+ * shared-memory blocks crowd out the other lanes' kernels), while the tuner
+ * times one kernel alone, so they are only candidates on request. */
+#define CKKS_TUNE_TENSOR 2
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
+
+/* Bounded device-side waits. The tensor-core and bulk-copy kernels wait on
+ * shared-memory barriers (for their bulk copies and matrix products); each
+ * wait gives up after `cycles` SM clock cycles (default 2^32, about two
+ * seconds), marks the context's status word, frees what the block holds and
+ * returns. The next synchronizing call on the context or any of its clones
+ * (ckks_sync, exports, decryption, the step entry points) then returns
+ * CKKS_ETIMEOUT and clears the mark; the outputs of the operations issued
+ * since the previous synchronizing call are undefined, and the context stays
+ * usable. The limit applies to kernels enqueued after the call; a clone
+ * inherits the parent's limit when it is created. CKKS_EINVAL if cycles < 1.
+ * (Not from the paper: a guard of this implementation's asynchronous
+ * kernels.) */
+int ckks_set_wait_limit(ckks_ctx* ctx, long long cycles);
 
 /* --- launch-shape fine-tuning (Sec. 4.2, "Fine-tuning"; Sec. 6) ---
  * The three BConv column kernels (ModUp conversion, ModDown conversion,
@@ -330,9 +382,15 @@ int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
  * (tc, sl, z, tp): column-tile width tc in {4, 8} columns, sl in {2, 4, 8}
  * thread slices per block sharing the tile, z in 1..4 blocks per tile
  * splitting the conversion targets, and tp in {1, 2} targets converted per
- * pass over the shared inputs. Every shape computes identical values;
- * only time changes. A context and its clones share one table of shapes per
- * (kernel, level); levels without an entry use a fixed rule. */
+ * pass over the shared inputs with CUDA-core multiply-adds. tp in {8, 16}
+ * selects the tensor-core form instead (N = 2^12 and 2^16, at most 16
+ * conversion sources, z = 1; (tc, sl) in {(8, 2), (8, 4), (4, 4), (4, 8)}):
+ * the conversion of a tile to tp targets at a time is one exact fp16 matrix
+ * product on the tensor cores (tcgen05) over byte planes of the sources and
+ * of the matrix (Eq. 2 as a matrix product, Sec. 4.2). Every shape computes
+ * identical values; only time changes. A context and its clones share one
+ * table of shapes per (kernel, level); levels without an entry use a fixed
+ * rule. */
 #define CKKS_COL_MODUP 0
 #define CKKS_COL_MODDOWN 1
 #define CKKS_COL_RS_FUSED 2
@@ -352,8 +410,10 @@ int ckks_tune(ckks_ctx* ctx, int level, int reps);
  * microseconds; *tc = 0 when the level has no entry. */
 int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us);
 /* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4, tp in
- * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps; for
- * CKKS_ROW_PASSES tc in {2, 3} at N = 2^16), or clears the entry with tc = 0.
+ * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps; the
+ * tensor-core shapes listed above; for CKKS_ROW_PASSES tc in {2, 3} at
+ * N = 2^16), or clears the entry with tc = 0. A tensor-core shape for a
+ * conversion with more than 16 sources runs the fixed CUDA-core rule.
  * Changes no value any operation computes. */
 int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, int tp);
 

@@ -124,8 +124,11 @@ _SIGS = {
     "ckks_rescale_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "ckks_batch_create": (_i, [_vp, _vp, _i, _i, _i, _P(_vp)]),
     "ckks_batch_run": (_i, [_vp]),
+    "ckks_batch_run_admit": (_i, [_vp, _i]),
+    "ckks_batch_admit": (_i, [_vp, _i]),
     "ckks_batch_destroy": (None, [_vp]),
     "ckks_set_launch_flags": (_i, [_vp, _i]),
+    "ckks_set_wait_limit": (_i, [_vp, C.c_longlong]),
     "ckks_tune": (_i, [_vp, _i, _i]),
     "ckks_tune_get": (_i, [_vp, _i, _i, _P(_i), _P(_i), _P(_i), _P(_i), _P(C.c_float)]),
     "ckks_tune_set": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
@@ -429,8 +432,12 @@ def ckks_hrot_hoisted(ctx, a, rs, evks, outs):
     check(ctx, lib.ckks_hrot_hoisted(ctx, a, cnt, r_arr, e_arr, o_arr))
 
 
-def ckks_batch_create(ctx, ops, lanes: int, use_graph: bool):
-    """ops: list of dicts with keys op, flags, r, a, b, pt, evk, out (handles)."""
+CKKS_BATCH_GRAPH, CKKS_BATCH_PERSISTENT = 1, 2
+
+
+def ckks_batch_create(ctx, ops, lanes: int, use_graph):
+    """ops: list of dicts with keys op, flags, r, a, b, pt, evk, out (handles);
+    use_graph: a bool or the mode flags CKKS_BATCH_GRAPH | CKKS_BATCH_PERSISTENT."""
     arr = (ckks_op * len(ops))()
     for i, o in enumerate(ops):
         arr[i] = ckks_op(o["op"], o.get("flags", 0), o.get("r", 0), o.get("a"), o.get("b"), o.get("pt"),
@@ -442,6 +449,16 @@ def ckks_batch_create(ctx, ops, lanes: int, use_graph: bool):
 
 def ckks_batch_run(ctx, batch):
     check(ctx, lib.ckks_batch_run(batch))
+
+
+def ckks_batch_run_admit(ctx, batch, admitted: int):
+    """Persistent batch: run with only the first `admitted` operations admitted."""
+    check(ctx, lib.ckks_batch_run_admit(batch, admitted))
+
+
+def ckks_batch_admit(ctx, batch, admitted: int):
+    """Persistent batch: raise the admitted count (takes effect in the running kernel)."""
+    check(ctx, lib.ckks_batch_admit(batch, admitted))
 
 
 def ckks_batch_destroy(batch):
@@ -459,10 +476,18 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
 
 CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED, CKKS_ROW_PASSES = 0, 1, 2, 3
 CKKS_LAUNCH_PDL = 1
+CKKS_TUNE_TENSOR = 2
 
 
 def ckks_set_launch_flags(ctx, flags: int):
     check(ctx, lib.ckks_set_launch_flags(ctx, flags))
+
+
+def ckks_set_wait_limit(ctx, cycles: int):
+    """Clock-cycle limit of the kernels' bounded device-side waits (see
+    include/ckks.h); an expired wait surfaces as CKKS_ETIMEOUT at the next
+    synchronizing call."""
+    check(ctx, lib.ckks_set_wait_limit(ctx, cycles))
 
 
 def ckks_tune(ctx, level: int, reps: int = 5):

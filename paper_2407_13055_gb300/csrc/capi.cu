@@ -31,6 +31,25 @@ int cuda_check(ckks_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, CKKS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Synchronizes the context stream, then reports a bounded device-side wait
+// that expired since the last check (status word set by the kernels).
+int sync_check(ckks_ctx* ctx, const char* what) {
+  const int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), what);
+  if (rc != CKKS_OK) return rc;
+  if (ctx->h_status) {
+    volatile uint32_t* st = ctx->h_status;
+    const uint32_t v = *st;
+    if (v) {
+      *st = 0;
+      return fail(ctx, CKKS_ETIMEOUT,
+                  "%s: a bounded device-side wait expired (wait limit %lld cycles); results of the operations "
+                  "since the last synchronizing call are undefined",
+                  what, (long long)ctx->dp.wait_limit);
+    }
+  }
+  return CKKS_OK;
+}
+
 // Status after enqueuing kernels: launch errors only (asynchronous faults
 // surface at the next synchronizing call).
 int launched(ckks_ctx* ctx, const char* what) { return cuda_check(ctx, cudaGetLastError(), what); }
@@ -141,6 +160,12 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
   ctx->seed = prm->seed;
   int rc = build_context(ctx, prm);
   if (rc != CKKS_OK) return bad(fail(ctx, rc, "building tables failed (%d)", rc));
+  rc = alloc_status(ctx);
+  if (rc != CKKS_OK) {
+    if (ctx->d_tables) cudaFree(ctx->d_tables);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    return bad(fail(ctx, rc, "status word allocation failed"));
+  }
   ctx->sc.prof = &ctx->prof;
   ctx->tune = std::make_shared<ckks::Tuning>(L);
   ctx->sc.tune = ctx->tune.get();
@@ -177,11 +202,12 @@ int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
   c->rr = parent->rr;
   c->mm = parent->mm;
   c->d_scratch = nullptr;
-  const int rc = alloc_scratch(c);
+  int rc = alloc_scratch(c);
   if (rc != CKKS_OK) {
     delete c;
     return fail(parent, rc, "clone: scratch allocation failed");
   }
+  c->h_status = parent->h_status;  // shared with the parent (dp.status copied above)
   c->sc.prof = &c->prof;
   c->tune = parent->tune;
   c->sc.tune = c->tune.get();
@@ -195,13 +221,22 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
   else cudaDeviceSynchronize();
   if (ctx->d_tables && ctx->owns_tables) cudaFree(ctx->d_tables);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+  if (ctx->owns_tables) free_status(ctx);
   for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
 }
 
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags) {
-  if (!ctx || (flags & ~CKKS_LAUNCH_PDL)) return CKKS_EINVAL;
+  if (!ctx || (flags & ~(CKKS_LAUNCH_PDL | CKKS_TUNE_TENSOR))) return CKKS_EINVAL;
   ctx->dp.pdl = (flags & CKKS_LAUNCH_PDL) ? 1 : 0;
+  ctx->dp.tune_tensor = (flags & CKKS_TUNE_TENSOR) ? 1 : 0;
+  return CKKS_OK;
+}
+
+int ckks_set_wait_limit(ckks_ctx* ctx, long long cycles) {
+  if (!ctx) return CKKS_EINVAL;
+  if (cycles < 1) return fail(ctx, CKKS_EINVAL, "wait limit %lld: must be at least one cycle", cycles);
+  ctx->dp.wait_limit = cycles;
   return CKKS_OK;
 }
 
@@ -266,7 +301,7 @@ int ckks_profile(ckks_ctx* ctx, int enable) {
 
 int ckks_profile_read(ckks_ctx* ctx, double* total_ms, uint64_t* launches) {
   if (!ctx || !total_ms || !launches) return CKKS_EINVAL;
-  int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile");
+  int rc = sync_check(ctx, "profile");
   if (rc) return rc;
   for (int i = 0; i < P_COUNT; ++i) {
     total_ms[i] = 0;
@@ -299,7 +334,7 @@ const char* ckks_last_error(ckks_ctx* ctx) { return ctx ? ctx->err.c_str() : "nu
 
 int ckks_sync(ckks_ctx* ctx) {
   if (!ctx) return CKKS_EINVAL;
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return sync_check(ctx, "stream synchronize");
 }
 
 size_t ckks_ctx_device_bytes(ckks_ctx* ctx) { return ctx ? ctx->table_bytes + ctx->scratch_bytes : 0; }
@@ -373,7 +408,7 @@ static int ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level,
   c->scale = scale;
   int rc = launched(ctx, "permute");
   if (rc || !sync) return rc;
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload");
+  return sync_check(ctx, "upload");
 }
 
 int ckks_ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level, double scale) {
@@ -410,7 +445,7 @@ static int ct_export(ckks_ctx* ctx, const ckks_ct* c, uint32_t* host, size_t wor
   rc = cuda_check(ctx, cudaMemcpyAsync(host, stage, 2 * (size_t)n * lw * 4, cudaMemcpyDeviceToHost, ctx->stream),
                   "export");
   if (rc) return rc;
-  if (sync) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "export");
+  if (sync) rc = sync_check(ctx, "export");
   if (level) *level = c->level;
   if (scale) *scale = c->scale;
   return rc;
@@ -472,7 +507,7 @@ int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
     launch_permute(ctx->dp, ctx->sc.A, (*out)->d, n, true, ctx->stream);
     rc = launched(ctx, "permute");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload");
+  if (!rc) rc = sync_check(ctx, "upload");
   if (rc) {
     ckks_free(*out);
     *out = nullptr;
@@ -494,7 +529,7 @@ int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double sc
     launch_permute(ctx->dp, ctx->sc.A, (*out)->d, n, true, ctx->stream);
     rc = launched(ctx, "permute");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload");
+  if (!rc) rc = sync_check(ctx, "upload");
   if (rc) {
     ckks_free(*out);
     *out = nullptr;
@@ -510,7 +545,7 @@ int ckks_pt_export(ckks_ctx* ctx, const ckks_pt* p, uint32_t* host, size_t words
   launch_permute(ctx->dp, p->d, ctx->sc.A, n, false, ctx->stream);
   int rc = launched(ctx, "permute");
   if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(host, ctx->sc.A, (size_t)n * lw * 4, cudaMemcpyDeviceToHost, ctx->stream), "export");
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "export");
+  if (!rc) rc = sync_check(ctx, "export");
   if (level) *level = p->level;
   if (scale) *scale = p->scale;
   return rc;
@@ -538,7 +573,7 @@ static int sk_from_coeffs(ckks_ctx* ctx, const int64_t* coeffs, ckks_sk** out) {
     launch_ntt(ctx->dp, s->d_s, np, ids, false, ctx->stream);
     rc = launched(ctx, "secret NTT");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "secret");
+  if (!rc) rc = sync_check(ctx, "secret");
   if (rc) {
     ckks_free(s);
     return rc;
@@ -602,12 +637,12 @@ static int keygen_ks(ckks_ctx* ctx, const ckks_sk* sk, const uint32_t* s_from, u
     launch_lincomb(dp, a_j, sk->d_s, -1, d_e.as<uint32_t>(), nullptr, b_j, np, ids, ctx->stream);
     launch_add_scaled(dp, s_from, d_g.as<uint2>(), b_j, b_j, np, ids, ctx->stream);
     rc = launched(ctx, "keygen");
-    if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "keygen");
+    if (!rc) rc = sync_check(ctx, "keygen");
   }
   if (!rc) {
     launch_to_mont(dp, e->d, 2 * dnum * np, ids, ctx->stream);
     rc = launched(ctx, "keygen");
-    if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "keygen");
+    if (!rc) rc = sync_check(ctx, "keygen");
   }
   if (rc) {
     ckks_free(e);
@@ -670,7 +705,7 @@ int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_e
     launch_to_mont(dp, e->d, 2 * dp.dnum * np, id_ext(dp.L, dp.L, dp.alpha), ctx->stream);
     rc = launched(ctx, "evk import");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "evk import");
+  if (!rc) rc = sync_check(ctx, "evk import");
   if (rc) {
     ckks_free(e);
     return rc;
@@ -699,7 +734,7 @@ int ckks_encode(ckks_ctx* ctx, const double* re_im, int level, double scale, ckk
     launch_ntt(ctx->dp, (*out)->d, n, id_ct(n, ctx->dp.L, base), false, ctx->stream);
     rc = launched(ctx, "encode");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encode");
+  if (!rc) rc = sync_check(ctx, "encode");
   if (rc) {
     ckks_free(*out);
     *out = nullptr;
@@ -724,7 +759,7 @@ int ckks_encode_ext(ckks_ctx* ctx, const double* re_im, int level, double scale,
     launch_ntt(ctx->dp, (*out)->d, n + alpha, ids, false, ctx->stream);
     rc = launched(ctx, "encode");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encode");
+  if (!rc) rc = sync_check(ctx, "encode");
   if (rc) {
     ckks_free(*out);
     *out = nullptr;
@@ -745,7 +780,7 @@ int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, double* re_im_out) {
   if (rc) return rc;
   std::vector<uint32_t> res((size_t)n * lw);
   rc = cuda_check(ctx, cudaMemcpyAsync(res.data(), tmp.p, res.size() * 4, cudaMemcpyDeviceToHost, ctx->stream), "download");
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "decode");
+  if (!rc) rc = sync_check(ctx, "decode");
   if (rc) return rc;
   host_decode(res.data(), n, ctx->q.data() + base, ctx->dp.log_n, pt->scale, re_im_out);
   return CKKS_OK;
@@ -779,7 +814,7 @@ int ckks_encrypt(ckks_ctx* ctx, const ckks_sk* sk, const ckks_pt* pt, uint64_t s
                    ctx->stream);
     rc = launched(ctx, "encrypt");
   }
-  if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "encrypt");
+  if (!rc) rc = sync_check(ctx, "encrypt");
   if (rc) {
     ckks_free(c);
     *out = nullptr;
@@ -877,7 +912,14 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out) {
   return launched(ctx, "rescale");
 }
 
-int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out) {
+}  // extern "C"
+
+// Validation and key-switch arguments of HMult (Sec. 2.1: tensor, then
+// relinearization by key switching, then optionally rescaling): fills k,
+// sets out's level and scale; staged = a windowed context's rational
+// rescale still has to follow the key switch (from the scratch U).
+int prepare_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out,
+                  KsArgs& k, bool& staged) {
   if (!ctx || !a || !b || !evk || !out) return CKKS_EINVAL;
   if (flags & ~(CKKS_RESCALE | CKKS_RESCALE_MERGED)) return fail(ctx, CKKS_EINVAL, "hmult: unknown flags %d", flags);
   if (evk->galois != 0) return fail(ctx, CKKS_ENOKEY, "hmult needs a relinearization key");
@@ -888,7 +930,7 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   if (rs && a->level < 1) return fail(ctx, CKKS_ELEVEL, "hmult: cannot rescale at level 0");
   if (out->cap_level < a->level - (rs ? 1 : 0)) return fail(ctx, CKKS_ELEVEL, "hmult: output capacity too small");
   const size_t lw = limb_words(ctx);
-  KsArgs k{};
+  k = KsArgs{};
   ctx->set_level(k, a->level);
   k.mode = KS_TENSOR;
   k.x0 = a->d;
@@ -903,21 +945,22 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   const bool fused = rs && (!ctx->windowed || merged);
   k.rescale = fused ? 1 : 0;
   k.mm = merged ? &ctx->mm[a->level] : nullptr;
-  const bool staged = rs && ctx->windowed && !merged;
+  staged = rs && ctx->windowed && !merged;
   k.out = staged ? ctx->sc.U : out->d;
   k.out_stride = staged ? (size_t)ctx->lvl_n(a->level) * lw : out->poly_stride();
-  launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
-  if (staged) rescale_into(ctx, a->level, ctx->sc.U, k.out_stride, out->d, out->poly_stride());
-  out->level = rs ? a->level - 1 : a->level;
-  out->scale = a->scale * b->scale * (rs ? rescale_factor(ctx, a->level) : 1.0);
-  return launched(ctx, "hmult");
+  const int level = a->level;
+  out->scale = a->scale * b->scale * (rs ? rescale_factor(ctx, level) : 1.0);
+  out->level = rs ? level - 1 : level;
+  return CKKS_OK;
 }
 
-static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_evk* evk, ckks_ct* out) {
+// Validation and key-switch arguments of an automorphism (HRot, HConj;
+// Eq. 4 then key switching), with out's level and scale set.
+int prepare_hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_evk* evk, ckks_ct* out, KsArgs& k) {
   if (evk->galois != galois) return fail(ctx, CKKS_ENOKEY, "key is for galois element %u, need %u", evk->galois, galois);
   if (out == c) return fail(ctx, CKKS_EINVAL, "output aliases the input");
   if (out->cap_level < c->level) return fail(ctx, CKKS_ELEVEL, "output capacity too small");
-  KsArgs k{};
+  k = KsArgs{};
   ctx->set_level(k, c->level);
   k.mode = KS_AUTO;
   k.x0 = c->d;
@@ -927,9 +970,31 @@ static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_ev
   k.out = out->d;
   k.out_stride = out->poly_stride();
   k.extra = 2;
-  launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
   out->level = c->level;
   out->scale = c->scale;
+  return CKKS_OK;
+}
+
+uint32_t galois_of_rotation(int r, int log_n) { return galois_rot(r, log_n); }
+
+extern "C" {
+
+int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out) {
+  KsArgs k;
+  bool staged = false;
+  const int level = a ? a->level : 0;
+  const int rc = prepare_hmult(ctx, a, b, evk, flags, out, k, staged);
+  if (rc != CKKS_OK) return rc;
+  launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
+  if (staged) rescale_into(ctx, level, ctx->sc.U, k.out_stride, out->d, out->poly_stride());
+  return launched(ctx, "hmult");
+}
+
+static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_evk* evk, ckks_ct* out) {
+  KsArgs k;
+  const int rc = prepare_hauto(ctx, c, galois, evk, out, k);
+  if (rc != CKKS_OK) return rc;
+  launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
   return launched(ctx, "hrot");
 }
 
@@ -1040,7 +1105,7 @@ static int check_ids(ckks_ctx* ctx, const int* ids, int count) {
 static int finish(ckks_ctx* ctx, const char* what) {
   int rc = launched(ctx, what);
   if (rc) return rc;
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), what);
+  return sync_check(ctx, what);
 }
 
 int ckks_step_smr(ckks_ctx* ctx, const int64_t* x, int n, int prime_id, int32_t* y) {

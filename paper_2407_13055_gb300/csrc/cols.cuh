@@ -7,6 +7,7 @@
 // separate translation units (k_cols_*.cu) so that the variants compile in
 // parallel.
 #pragma once
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -14,6 +15,7 @@
 #include "geo.cuh"
 #include "internal.h"
 #include "pdl.cuh"
+#include "tc.cuh"
 
 namespace ckks {
 
@@ -476,6 +478,10 @@ static void set_col_smem(const void* f, size_t bytes) {
 template <int V>
 using IC = std::integral_constant<int, V>;
 
+}  // namespace ckks
+#include "cols_tc.cuh"
+namespace ckks {
+
 // Calls f(IC<TC>, IC<SL>, IC<TP>) for a shape's compile-time parameters.
 template <class F>
 static bool with_shape(const ColShape& s, F f) {
@@ -512,7 +518,11 @@ static ColShape default_shape(int blocks_per_tile_column) {
 // barrier, whose thread count must be a multiple of the warp size) and the
 // parameters are among the compiled ones.
 template <class G>
+static bool tc_shape_ok(const ColShape& s);
+
+template <class G>
 static bool shape_ok(const ColShape& s) {
+  if (s.tp == 8 || s.tp == 16) return tc_shape_ok<G>(s);
   return (s.tc == 4 || s.tc == 8) && G::W % s.tc == 0 && (s.tc * G::EC) % 32 == 0 &&
          (s.sl == 2 || s.sl == 4 || s.sl == 8) && s.z >= 1 && s.z <= 4 && (s.tp == 1 || s.tp == 2);
 }
@@ -529,7 +539,26 @@ static ColShape pick_shape(const Scratch& sc, ColKernel k, int n, const ColShape
 
 template <class G>
 void launch_modup_cols(const DevParams& dp, int n, int base, int tix, int digits, const Scratch& sc,
-                       const ColShape& s, cudaStream_t st) {
+                       const ColShape& s0, cudaStream_t st) {
+  if (is_tc_shape(s0) && dp.ks.tc_img && dp.alpha <= kTcMaxSources &&
+      with_tc_shape<G>(s0, [&](auto tc, auto sl, auto nc) {
+        constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, NC = decltype(nc)::value;
+        using SH = TcShape<G, TC, SL, NC>;
+        int mmax = 0;
+        for (int j = 0; j < digits; ++j) {
+          const int g = base / dp.alpha + j;
+          const int k = std::min(n, (g + 1) * dp.alpha - base) - std::max(0, g * dp.alpha - base);
+          mmax = std::max(mmax, n + dp.alpha - k);
+        }
+        const int kr = tc_kr(dp.alpha);
+        const size_t sm = tc_smem<SH, NC>(kr, mmax).total;
+        set_col_smem((const void*)k_ks_modup_cols_tc<G, TC, SL, NC>, sm);
+        launch_pdl(dp.pdl, k_ks_modup_cols_tc<G, TC, SL, NC>, dim3(G::W / TC, digits), dim3(SH::NT), sm, st, dp, n,
+                   base, tix, kr, mmax, (const uint32_t*)sc.S, sc.T);
+        count_launch(1);
+      }))
+    return;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(digits) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
@@ -541,8 +570,21 @@ void launch_modup_cols(const DevParams& dp, int n, int base, int tix, int digits
 }
 
 template <class G>
-void launch_moddown_cols(const DevParams& dp, int n, int base, const Scratch& sc, const ColShape& s,
+void launch_moddown_cols(const DevParams& dp, int n, int base, int tix, const Scratch& sc, const ColShape& s0,
                          cudaStream_t st) {
+  if (is_tc_shape(s0) && dp.ks.tc_img && dp.alpha <= kTcMaxSources &&
+      with_tc_shape<G>(s0, [&](auto tc, auto sl, auto nc) {
+        constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, NC = decltype(nc)::value;
+        using SH = TcShape<G, TC, SL, NC>;
+        const int kr = tc_kr(dp.alpha);
+        const size_t sm = tc_smem<SH, NC>(kr, n).total;
+        set_col_smem((const void*)k_ks_moddown_cols_tc<G, TC, SL, NC>, sm);
+        launch_pdl(dp.pdl, k_ks_moddown_cols_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, base,
+                   tix, kr, (const uint32_t*)sc.S, sc.T);
+        count_launch(1);
+      }))
+    return;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
@@ -568,7 +610,20 @@ void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint
 
 template <class G>
 void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
-                                 const ColShape& s, cudaStream_t st) {
+                                 const ColShape& s0, cudaStream_t st) {
+  if (is_tc_shape(s0) && dp.ks.tc_img && dp.alpha + 1 <= kTcMaxSources &&
+      with_tc_shape<G>(s0, [&](auto tc, auto sl, auto nc) {
+        constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, NC = decltype(nc)::value;
+        using SH = TcShape<G, TC, SL, NC>;
+        const int kr = tc_kr(dp.alpha + 1);
+        const size_t sm = tc_smem<SH, NC>(kr, n - 1).total;
+        set_col_smem((const void*)k_rs_cols_fused_tc<G, TC, SL, NC>, sm);
+        launch_pdl(dp.pdl, k_rs_cols_fused_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, kr, V,
+                   Y, T3);
+        count_launch(1);
+      }))
+    return;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
@@ -580,7 +635,8 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
 }
 
 template <class G>
-void launch_mm_cols(const DevParams& dp, const MmArgs& m, const Scratch& sc, const ColShape& s, cudaStream_t st) {
+void launch_mm_cols(const DevParams& dp, const MmArgs& m, const Scratch& sc, const ColShape& s0, cudaStream_t st) {
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(m.K);

@@ -45,6 +45,59 @@ uint32_t shoup_of(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32
 uint2 shoup_pair(uint32_t w, uint32_t q) { return make_uint2(w, shoup_of(w, q)); }
 int32_t centered_h(uint32_t x, uint32_t q) { return x > q / 2 ? (int32_t)((int64_t)x - q) : (int32_t)x; }
 
+// fp16 bit pattern of an integer v with |v| <= 2048 (exact).
+uint16_t f16_bits(int v) {
+  if (v == 0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  uint32_t a = (uint32_t)(v < 0 ? -v : v);
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;
+  return (uint16_t)(sign | (uint16_t)((e + 15) << 10) | (uint16_t)((a << (10 - e)) & 0x3FFu));
+}
+
+// Byte-plane image of a conversion matrix for the tensor-core BConv (the B
+// operand of cols_tc.cuh): mat[t * K + k] (t < M targets with primes
+// prime[t]) are centered [(...) 2^32]_{prime_t} entries. For each target and
+// source, m'_a = [mat 2^(8a)]_{prime_t} centered (a < 4) is written as four
+// balanced signed bytes (m'_a = sum_b e_b 2^(8b), e_b in [-128, 128) for
+// b < 3); row 4 t + b of the image holds e_b of (k, a) at column 4 k + a, as
+// fp16. Rows are padded to a multiple of 16 (zero targets), columns to
+// kr = 16 ceil(K / 4), and the image is stored in the MMA's shared-memory
+// layout: core matrices of 8 rows x 8 columns (128 bytes), column blocks of
+// 8 adjacent (128 bytes apart), 8-row groups kr * 16 bytes apart. Returns
+// (byte offset in img, bytes).
+int2 append_planes(std::vector<uint8_t>& img, const int32_t* mat, int M, int K, const uint32_t* prime) {
+  const int kr = 16 * ((K + 3) / 4);
+  const int rows = 4 * ((M + 3) & ~3);
+  const size_t off = img.size(), bytes = (size_t)rows * kr * 2;
+  img.resize(off + bytes, 0);
+  uint8_t* base = img.data() + off;
+  for (int t = 0; t < M; ++t) {
+    const uint32_t p = prime[t];
+    for (int k = 0; k < K; ++k) {
+      const int32_t m = mat[(size_t)t * K + k];
+      const uint64_t mu = (uint64_t)(m < 0 ? (int64_t)m + p : (int64_t)m);
+      for (int a = 0; a < 4; ++a) {
+        int64_t v = centered_h((uint32_t)((mu << (8 * a)) % p), p);
+        int e[4];
+        for (int b = 0; b < 3; ++b) {
+          e[b] = (int)(((v % 256) + 256 + 128) % 256) - 128;
+          v = (v - e[b]) / 256;
+        }
+        e[3] = (int)v;
+        for (int b = 0; b < 4; ++b) {
+          const int n = 4 * t + b, c = 4 * k + a;
+          const size_t o = (size_t)(n >> 3) * kr * 16 + (size_t)(c >> 3) * 128 + (n & 7) * 16 + (c & 7) * 2;
+          const uint16_t h = f16_bits(e[b]);
+          base[o] = (uint8_t)(h & 0xFF);
+          base[o + 1] = (uint8_t)(h >> 8);
+        }
+      }
+    }
+  }
+  return make_int2((int)off, (int)bytes);
+}
+
 uint32_t brev(uint32_t v, int bits) {
   uint32_t r = 0;
   for (int i = 0; i < bits; ++i, v >>= 1) r = (r << 1) | (v & 1);
@@ -454,6 +507,38 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
     rs_mat[(size_t)i * (alpha + 1) + alpha] =
         centered_h(mulm(ctx->gadget_p[i].x, ctx->pc_host[i].mont, pr[i]), pr[i]);
   }
+  // byte-plane images of the ModUp, ModDown and fused-rescale matrices for
+  // the tensor-core BConv (at most 16 sources: K extent 64)
+  std::vector<uint8_t> tc_img;
+  std::vector<int2> up_img((size_t)(std::max(L, nlev) + 1) * dnum, make_int2(0, 0));
+  std::vector<int2> dn_img((size_t)nlev + 1, make_int2(0, 0)), rs_img((size_t)L + 1, make_int2(0, 0));
+  const bool tc_ok = alpha <= 16;
+  if (tc_ok) {
+    std::vector<int32_t> rows;
+    std::vector<uint32_t> tp;
+    for (int tix = 1; tix <= nlev; ++tix) {
+      const int s0 = ctx->lvl_first[tix - 1], nl = ctx->lvl_count[tix - 1];
+      const int ext = nl + alpha;
+      const int j0 = s0 / alpha, digits = (s0 + nl - 1) / alpha - j0 + 1;
+      for (int j = 0; j < digits; ++j) {
+        const int g = j0 + j;
+        const int lo = std::max(0, g * alpha - s0), hi = std::min(nl, (g + 1) * alpha - s0), K = hi - lo;
+        const int2 o = up_off[(size_t)tix * dnum + j];
+        rows.clear();
+        tp.clear();
+        for (int t = 0; t < ext; ++t) {
+          if (t >= lo && t < hi) continue;
+          for (int k = 0; k < K; ++k) rows.push_back(up_mat[(size_t)o.y + (size_t)t * K + k]);
+          tp.push_back(pr[t < nl ? s0 + t : L + (t - nl)]);
+        }
+        up_img[(size_t)tix * dnum + j] = append_planes(tc_img, rows.data(), ext - K, K, tp.data());
+      }
+      rows.assign(dn_mat.begin() + (size_t)s0 * alpha, dn_mat.begin() + (size_t)(s0 + nl) * alpha);
+      dn_img[tix] = append_planes(tc_img, rows.data(), nl, alpha, pr.data() + s0);
+    }
+    if (alpha + 1 <= 16)
+      for (int n = 2; n <= L; ++n) rs_img[n] = append_planes(tc_img, rs_mat.data(), n - 1, alpha + 1, pr.data());
+  }
   std::vector<uint2> dn_pqinv((size_t)L * L, make_uint2(0, 0));
   for (int l = 1; l < L; ++l)
     for (int i = 0; i < l; ++i)
@@ -628,6 +713,10 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {mm_cin.data(), mm_cin.size() * sizeof(uint2), 0},
       {mm_mat.data(), mm_mat.size() * sizeof(int32_t), 0},
       {mm_epi.data(), mm_epi.size() * sizeof(MmEpi), 0},
+      {tc_img.data(), tc_img.size(), 0},
+      {up_img.data(), up_img.size() * sizeof(int2), 0},
+      {dn_img.data(), dn_img.size() * sizeof(int2), 0},
+      {rs_img.data(), rs_img.size() * sizeof(int2), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -661,6 +750,10 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   dp.ks.up_rows = reinterpret_cast<const int2*>(base + parts[10].off);
   dp.ks.rs_mat = reinterpret_cast<const int32_t*>(base + parts[11].off);
   dp.ks.dn_pqinv = reinterpret_cast<const uint2*>(base + parts[12].off);
+  dp.ks.tc_img = tc_ok ? reinterpret_cast<const uint8_t*>(base + parts[22].off) : nullptr;
+  dp.ks.up_img = reinterpret_cast<const int2*>(base + parts[23].off);
+  dp.ks.dn_img = reinterpret_cast<const int2*>(base + parts[24].off);
+  dp.ks.rs_img = reinterpret_cast<const int2*>(base + parts[25].off);
   for (int l = 1; l < nlev && ctx->windowed; ++l) {
     RrArgs& r = ctx->rr[l];
     r.drop = reinterpret_cast<const int2*>(base + parts[13].off) + rr_off[l].drop;
@@ -684,6 +777,26 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
     ctx->d_tables = nullptr;
   }
   return rc;
+}
+
+int alloc_status(ckks_ctx* ctx) {
+  void* h = nullptr;
+  if (cudaHostAlloc(&h, sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess) return CKKS_ENOMEM;
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaFreeHost(h);
+    return CKKS_ECUDA;
+  }
+  *static_cast<volatile uint32_t*>(h) = 0;
+  ctx->h_status = static_cast<uint32_t*>(h);
+  ctx->dp.status = static_cast<uint32_t*>(d);
+  return CKKS_OK;
+}
+
+void free_status(ckks_ctx* ctx) {
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  ctx->h_status = nullptr;
+  ctx->dp.status = nullptr;
 }
 
 // Key-switching scratch of one context (one execution lane): S (row-phase

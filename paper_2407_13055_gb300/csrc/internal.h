@@ -41,6 +41,16 @@ struct KsTables {
   // [(P q_l)^-1]_{q_i}, i < l.
   const int32_t* rs_mat;
   const uint2* dn_pqinv;
+  // Tensor-core BConv (cols_tc.cuh): fp16 byte-plane images of the
+  // conversion matrices in the shared-memory layout of the MMA's B operand,
+  // one allocation tc_img; entries (byte offset, bytes) per conversion:
+  // up_img[tix * dnum + j] (ModUp digit j), dn_img[tix] (ModDown),
+  // rs_img[n] (fused ModDown + rescale at n limbs). Null tc_img: the
+  // tensor-core kernels are not available (more than 16 sources).
+  const uint8_t* tc_img;
+  const int2* up_img;
+  const int2* dn_img;
+  const int2* rs_img;
 };
 
 struct DevParams {
@@ -50,8 +60,15 @@ struct DevParams {
   const uint2* itw;      // [L + alpha][N] inverse twiddles
   KsTables ks;
   int pdl;  // host-side launch option: key-switch kernels use programmatic dependent launch
+  int tune_tensor = 0;  // host-side option: the fine-tuner also times the tensor-core column shapes
   int rows_passes = 3;  // host-side launch option at N = 2^16: row phase in 3 (16 values per
                         // thread, 64 threads per row) or 2 (32 values, 32 threads) passes
+  // Bounded device-side waits (mbarrier waits of the tensor-core and bulk-copy
+  // kernels): a wait gives up after wait_limit SM clock cycles and sets
+  // tc::kStatusTimeout in *status (host-mapped memory of the context, read
+  // back by the synchronizing calls as CKKS_ETIMEOUT).
+  uint32_t* status = nullptr;
+  long long wait_limit = 1ll << 32;
 };
 
 // Limb -> prime id. Either an explicit device array, or the extended-
@@ -291,6 +308,31 @@ bool col_shape_supported(int log_n, int tc, int sl, int z, int tp);
 int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArgs& lvl, int reps, cudaStream_t st);
 void launch_keyswitch(const DevParams& dp, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
                       cudaStream_t st);
+// The two halves of launch_keyswitch around KeyMult: ModUp into sc.T, and
+// ModDown (with its epilogue / rescaling) from accumulators A.
+void launch_ks_modup(const DevParams& dp, const Scratch& sc, const KsArgs& a, cudaStream_t st);
+void launch_ks_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A, size_t a_stride,
+                    cudaStream_t st);
+
+// Persistent streaming stage of a batch (k_keyswitch.cu): work items
+// (operation index, limb) over a table of operations.
+enum PersKind { PK_KEYMULT = 0, PK_HADD = 1, PK_PADD = 2, PK_PMULT = 3 };
+struct PersOp {
+  int kind;            // PersKind
+  int digits;          // PK_KEYMULT: active digits
+  KsArgs ks;           // PK_KEYMULT: the key switch (input, key, window)
+  const uint32_t* T;   // PK_KEYMULT: ModUp limbs [digits][n + alpha][N]
+  uint32_t* A;         // PK_KEYMULT: accumulators [2][n + alpha][N]
+  const uint32_t* x;   // element-wise: ciphertext operand [2][n] (poly stride sx words)
+  const uint32_t* y;   // second ciphertext (HAdd, poly stride sy) or plaintext [n] (PAdd, PMult)
+  uint32_t* out;       // [2][n], poly stride so
+  size_t sx, sy, so;
+  int n, base;         // limbs and window start of the element-wise operation
+};
+// q: device [head, abort] (zeroed before the launch); admitted: host-mapped
+// count of admitted operations (items of operation k run once admitted > k).
+void launch_persistent(const DevParams& dp, const PersOp* ops, const int2* items, int n_items, int* q,
+                       const int* admitted, int blocks, cudaStream_t st);
 // ModDown only: acc [2][n + alpha][N] (internal layout) -> out [2][n][N].
 void launch_hoisted_rotations(const DevParams& dp, const Scratch& sc, const KsArgs* rots, int count,
                               cudaStream_t st);
@@ -342,6 +384,8 @@ struct ckks_ctx {
   std::vector<uint2> gadget_p;  // [L + alpha] Shoup pair of [P]_{prime}
   std::string err;
   int device;
+  uint32_t* h_status = nullptr;  // host-mapped status word (dp.status is its device address), shared by
+                                 // a context and its clones; freed by the context that owns the tables
   // Levels: level l holds the primes q[lvl_first[l] .. lvl_first[l] +
   // lvl_count[l]). Single rescaling: lvl_first = 0, lvl_count = l + 1. With
   // given windows (the 25-30 prime system) rescaling is rational.
@@ -397,10 +441,22 @@ struct ckks_evk {
   uint32_t galois;
 };
 
+// capi.cu: validation and key-switch arguments of the key-switching
+// operations (out's level and scale are set), shared by the direct calls and
+// the batched forms.
+int prepare_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out,
+                  ckks::KsArgs& k, bool& staged);
+int prepare_hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_evk* evk, ckks_ct* out,
+                  ckks::KsArgs& k);
+uint32_t galois_of_rotation(int r, int log_n);
+
 // host.cu
 namespace ckks {
 int build_context(ckks_ctx* ctx, const ckks_params* p);
 int alloc_scratch(ckks_ctx* ctx);
+// Host-mapped status word of bounded device waits (dp.status); freed by free_status.
+int alloc_status(ckks_ctx* ctx);
+void free_status(ckks_ctx* ctx);
 bool host_is_prime(uint64_t n);
 uint32_t host_find_psi(uint32_t q, int log_n);
 int host_gen_primes(int log_n, int n_q, int n_p, uint32_t* q, uint32_t* p);

@@ -38,7 +38,7 @@ using G8 = Geo<4, 4>;
 #define CKKS_COL_DECL(G)                                                                                        \
   extern template void launch_modup_cols<G>(const DevParams&, int, int, int, int, const Scratch&, const ColShape&, \
                                             cudaStream_t);                                                      \
-  extern template void launch_moddown_cols<G>(const DevParams&, int, int, const Scratch&, const ColShape&,      \
+  extern template void launch_moddown_cols<G>(const DevParams&, int, int, int, const Scratch&, const ColShape&,      \
                                               cudaStream_t);                                                    \
   extern template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*,             \
                                                   cudaStream_t);                                                \
@@ -127,25 +127,27 @@ __device__ __forceinline__ void ks_input4(const DevParams& dp, const KsArgs& a, 
   }
 }
 
-// KeyMult + MAC over the D digits for extended limb t (Par. 1): the digit's
-// own limbs are the input itself (ModUp copies them), the others come from
-// the NTT'd ModUp output T[j][t]. All loads of a thread are issued before any
-// product so that one memory latency covers the whole sum. A = [2][n + alpha][N].
+// KeyMult + MAC over the D digits for extended limb t (Par. 1), positions
+// p0 .. p0 + 3: the digit's own limbs are the input itself (ModUp copies
+// them), the others come from the NTT'd ModUp output T[j][t]. All loads of a
+// thread are issued before any product so that one memory latency covers the
+// whole sum. A = [2][n + alpha][N]. With wait_dep the programmatic-dependent-
+// launch wait sits after the index arithmetic and before the first load.
 template <int D>
-__global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* A, int km_out,
-                             uint32_t* km_dst) {
-  const int t = blockIdx.y;
+__device__ __forceinline__ void keymult_quad(const DevParams& dp, const KsArgs& a, const uint32_t* T, uint32_t* A,
+                                             int t, uint32_t p0, int km_out, uint32_t* km_dst, bool wait_dep) {
   const int n = a.n, alpha = dp.alpha, L = dp.L, ext = n + alpha, ext_top = L + alpha;
   const int id = prime_of(t, n, L, a.base);
   const int key_limb = id;  // keys cover every prime: limb = global prime index
   const int g0 = a.base / alpha;  // first active digit of the window
   const PrimeConst P = dp.pc[id];
-  const uint32_t p0 = stream_pos();
   uint32_t x[D][4], e0[D][4], e1[D][4];
   // (streaming the key before the wait kept every key word live across it:
   // 86 registers and a third of the occupancy, so the wait comes first)
-  pdl_wait();
-  pdl_trigger();
+  if (wait_dep) {
+    pdl_wait();
+    pdl_trigger();
+  }
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const int lo = max(0, (g0 + j) * alpha - a.base), hi = min(n, (g0 + j + 1) * alpha - a.base);
@@ -182,6 +184,12 @@ __global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t
   uint32_t* dst = km_out == KM_ACC_ALL ? km_dst : A;
   store_vec<4>(dst + ((size_t)t << dp.log_n) + p0, acc0);
   store_vec<4>(dst + ((size_t)(ext + t) << dp.log_n) + p0, acc1);
+}
+
+template <int D>
+__global__ void k_ks_keymult(DevParams dp, KsArgs a, const uint32_t* T, uint32_t* A, int km_out,
+                             uint32_t* km_dst) {
+  keymult_quad<D>(dp, a, T, A, blockIdx.y, stream_pos(), km_out, km_dst, true);
 }
 
 static void launch_keymult(int digits, dim3 g, int th, cudaStream_t st, const DevParams& dp, const KsArgs& a,
@@ -651,7 +659,7 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
                    LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  launch_moddown_cols<G>(dp, n, a.base, sc, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
+  launch_moddown_cols<G>(dp, n, a.base, a.tix, sc, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
   prof_mark(sc, st, P_MODDOWN_COLS);
   launch_rows_fwd<G>(dp, sc.T, EpiModDown{a, A, a_stride}, 2 * n, window_map(a, dp.L), st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
@@ -668,33 +676,161 @@ static DevParams tuned_rows(const DevParams& dp, const Scratch& sc, int tix) {
   return d;
 }
 
-void launch_keyswitch(const DevParams& dp0, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
-                      cudaStream_t st) {
+// ModUp half of a key switch: input rows (d, a1 a2 or phi_k(a)), ModUp
+// columns and ModUp NTT rows; sc.T receives the ModUp limbs (own-digit limbs
+// excepted: KeyMult reads those from the input).
+void launch_ks_modup(const DevParams& dp0, const Scratch& sc, const KsArgs& a, cudaStream_t st) {
   const DevParams dp = tuned_rows(dp0, sc, a.tix);
-  const int n = a.n, alpha = dp.alpha, ext = n + alpha;
-  const int digits = active_digits(a, alpha);
-  const size_t limb = (size_t)1 << dp.log_n;
-  dim3 g;
-  int th;
+  const int digits = active_digits(a, dp.alpha);
   CKKS_DISPATCH_LOGN(dp.log_n, {
     prof_mark(sc, st, -1);
-    launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, n, window_map(a, dp.L), true, st);
+    launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, a.n, window_map(a, dp.L), true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
-    launch_modup_cols<G>(dp, n, a.base, a.tix, digits, sc,
+    launch_modup_cols<G>(dp, a.n, a.base, a.tix, digits, sc,
                          pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits)), st);
     prof_mark(sc, st, P_MODUP_COLS);
     launch_rows_g<G>(dp, false, sc.T, sc.T, a.rows_cnt, LimbMap{dp.ks.up_rows + a.rows_off, 0, 1, 0, 0}, false, st);
     prof_mark(sc, st, P_MODUP_ROWS);
-    stream_grid(dp.log_n, ext, g, th);
-    launch_keymult(digits, g, th, st, dp, a, sc.T, sc.A, km_out, km_dst);
-    count_launch(1);
-    prof_mark(sc, st, P_KEYMULT);
-    if (km_out == KM_KEYSWITCH) {
-      if (a.rescale && a.mm) merged_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
-      else if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
-      else moddown_tail<G>(dp, sc, a, sc.A, (size_t)ext * limb, st);
-    }
   });
+}
+
+// ModDown half from the accumulators A ([2][n + alpha][N], poly stride
+// a_stride words): ModDown (+ the HMult or HRot epilogue), fused with or
+// merged into the rescaling when a.rescale is set.
+void launch_ks_tail(const DevParams& dp0, const Scratch& sc, const KsArgs& a, const uint32_t* A, size_t a_stride,
+                    cudaStream_t st) {
+  const DevParams dp = tuned_rows(dp0, sc, a.tix);
+  CKKS_DISPATCH_LOGN(dp.log_n, {
+    if (a.rescale && a.mm) merged_tail<G>(dp, sc, a, A, a_stride, st);
+    else if (a.rescale) moddown_rescale_tail<G>(dp, sc, a, A, a_stride, st);
+    else moddown_tail<G>(dp, sc, a, A, a_stride, st);
+  });
+}
+
+void launch_keyswitch(const DevParams& dp0, const Scratch& sc, const KsArgs& a, int km_out, uint32_t* km_dst,
+                      cudaStream_t st) {
+  const DevParams dp = tuned_rows(dp0, sc, a.tix);
+  const int ext = a.n + dp.alpha;
+  const int digits = active_digits(a, dp.alpha);
+  const size_t limb = (size_t)1 << dp.log_n;
+  launch_ks_modup(dp0, sc, a, st);
+  dim3 g;
+  int th;
+  stream_grid(dp.log_n, ext, g, th);
+  launch_keymult(digits, g, th, st, dp, a, sc.T, sc.A, km_out, km_dst);
+  count_launch(1);
+  prof_mark(sc, st, P_KEYMULT);
+  if (km_out == KM_KEYSWITCH) launch_ks_tail(dp0, sc, a, sc.A, (size_t)ext * limb, st);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent streaming stage of a batch (stage-major form, batch.cu): one
+// launch runs the KeyMult + MAC (Par. 1) of every key-switching operation of
+// the batch and every element-wise operation (HAdd, PAdd, PMult). Its blocks
+// take work items (operation, limb) from a device queue by atomic increment
+// until the queue is empty. An item runs once its operation has been
+// admitted: the admitted-operation count lives in host-mapped memory and may
+// be raised by the host while the kernel runs. A wait for admission is
+// bounded by dp.wait_limit; when it expires the block marks the status word
+// and the queue's abort flag, and every block stops at its next item. KeyMult
+// items come limb-major (all operations' limb t, then limb t + 1), so the
+// evaluation-key rows of a limb are read from HBM once and reused from L2 by
+// every operation that uses the same key.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int load_sys_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int D>
+__device__ __forceinline__ void pers_keymult(const DevParams& dp, const PersOp& o, int t) {
+  for (uint32_t p0 = 4 * threadIdx.x; p0 < (1u << dp.log_n); p0 += 4 * blockDim.x)
+    keymult_quad<D>(dp, o.ks, o.T, o.A, t, p0, KM_KEYSWITCH, nullptr, false);
+}
+
+// Element-wise item y = u n + i of HAdd (x + y), PAdd ((x_0 + pt, x_1)) or
+// PMult (x (.) pt) at limb i of the window.
+__device__ __forceinline__ void pers_elementwise(const DevParams& dp, const PersOp& o, int y) {
+  const int u = y / o.n, i = y % o.n;
+  const PrimeConst P = dp.pc[o.base + i];
+  const size_t off = (size_t)i << dp.log_n;
+  const uint32_t* x = o.x + u * o.sx + off;
+  const uint32_t* w = o.y + (o.kind == PK_HADD ? u * o.sy : 0) + off;
+  uint32_t* out = o.out + u * o.so + off;
+  for (uint32_t p0 = 4 * threadIdx.x; p0 < (1u << dp.log_n); p0 += 4 * blockDim.x) {
+    uint32_t a[4], b[4];
+    load_vec<4>(a, x + p0);
+    if (o.kind == PK_PADD && u == 1) {
+      store_vec<4>(out + p0, a);
+      continue;
+    }
+    load_vec<4>(b, w + p0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = o.kind == PK_PMULT ? mulmod(a[k], b[k], P) : addm(a[k], b[k], P.q);
+    store_vec<4>(out + p0, a);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_persistent(DevParams dp, const PersOp* ops, const int2* items, int n_items,
+                                                    int* q, const int* admitted) {
+  __shared__ int s_it;
+  int known = 0;  // thread 0: admitted count last read
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int it = atomicAdd(&q[0], 1);
+      if (it >= n_items || *(volatile int*)&q[1]) {
+        it = -1;
+      } else {
+        const int op = items[it].x;
+        if (known <= op) known = load_sys_relaxed(admitted);
+        if (known <= op) {
+          const long long t0 = clock64();
+          for (;;) {
+            __nanosleep(200);
+            known = load_sys_relaxed(admitted);
+            if (known > op) break;
+            if (*(volatile int*)&q[1]) {
+              it = -1;
+              break;
+            }
+            if (clock64() - t0 > dp.wait_limit) {
+              tc::report_timeout(dp.status);
+              atomicExch(&q[1], 1);
+              it = -1;
+              break;
+            }
+          }
+        }
+      }
+      s_it = it;
+    }
+    __syncthreads();
+    const int it = s_it;
+    __syncthreads();
+    if (it < 0) return;
+    const int2 w = items[it];
+    const PersOp& o = ops[w.x];
+    if (o.kind == PK_KEYMULT) {
+      switch (o.digits) {
+#define CKKS_PK(D) \
+  case D: pers_keymult<D>(dp, o, w.y); break;
+        CKKS_PK(1) CKKS_PK(2) CKKS_PK(3) CKKS_PK(4) CKKS_PK(5) CKKS_PK(6) CKKS_PK(7) CKKS_PK(8)
+#undef CKKS_PK
+        default:
+          break;
+      }
+    } else {
+      pers_elementwise(dp, o, w.y);
+    }
+  }
+}
+
+void launch_persistent(const DevParams& dp, const PersOp* ops, const int2* items, int n_items, int* q,
+                       const int* admitted, int blocks, cudaStream_t st) {
+  k_persistent<<<blocks, 256, 0, st>>>(dp, ops, items, n_items, q, admitted);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -707,8 +843,15 @@ void launch_keyswitch(const DevParams& dp0, const Scratch& sc, const KsArgs& a, 
 // ---------------------------------------------------------------------------
 
 template <class G>
-static std::vector<ColShape> shape_candidates(int targets, const ColShape& def) {
+static std::vector<ColShape> shape_candidates(int targets, const ColShape& def, bool tensor) {
   std::vector<ColShape> v;
+  if (tensor)
+    for (int tc : {8, 4})
+      for (int sl : {2, 4, 8})
+        for (int nc : {8, 16}) {
+          const ColShape c{tc, sl, 1, nc};
+          if (tc_shape_ok<G>(c)) v.push_back(c);
+        }
   for (int tc : {8, 4}) {
     if (G::W % tc != 0) continue;
     for (int sl : {2, 4, 8})
@@ -741,6 +884,8 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
       if (k == CK_RS_FUSED && (n < 2 || base != 0)) continue;  // single rescaling only
       ColShape def;
       int targets;
+      const bool tensor =
+          dp.tune_tensor && dp.ks.tc_img != nullptr && dp.alpha + (k == CK_RS_FUSED ? 1 : 0) <= kTcMaxSources;
       std::function<void(const ColShape&)> run;
       if (k == CK_MODUP) {
         def = default_shape<G>(digits);
@@ -749,7 +894,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
       } else if (k == CK_MODDOWN) {
         def = default_shape<G>(2);
         targets = n;
-        run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, base, sc, s, st); };
+        run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, base, tix, sc, s, st); };
       } else {
         def = default_shape<G>(2);
         targets = n - 1;
@@ -759,7 +904,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
       }
       ColShape best = def;
       float best_ms = -1.f;
-      for (const ColShape& s : shape_candidates<G>(targets, def)) {
+      for (const ColShape& s : shape_candidates<G>(targets, def, tensor)) {
         run(s);  // first launch: attributes, instruction cache
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps; ++r) run(s);
@@ -885,7 +1030,7 @@ void launch_linear_transform(const DevParams& dp0, const Scratch& sc, const KsAr
       launch_rows_g<G>(dp, true, sc.A, down.S, 2 * alpha,
                        LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
       prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-      launch_moddown_cols<G>(dp, n, a.base, down, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
+      launch_moddown_cols<G>(dp, n, a.base, a.tix, down, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
       prof_mark(sc, st, P_MODDOWN_COLS);
       launch_rows_g<G>(dp, false, down.T, down.T, 2 * n, window_map(a, dp.L), false, st);
       prof_mark(sc, st, P_MODDOWN_ROWS);

@@ -507,7 +507,7 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
     try:
         for kern in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
             tc, sl, z, tp, us = K.ckks_tune_get(ctx, kern, n_q - 1)
-            assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and tp in (1, 2) and us > 0
+            assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and tp in (1, 2, 8, 16) and us > 0
         passes, _, _, _, us = K.ckks_tune_get(ctx, K.CKKS_ROW_PASSES, n_q - 1)
         assert passes in (2, 3) and us > 0
         # a clone shares the table
