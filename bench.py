@@ -62,40 +62,72 @@ def algorithmic_bytes(n=L, alpha=ALPHA):
     return hmult, hrot
 
 
-def kernel_models(n=L, alpha=ALPHA):
-    """Per-launch algorithmic work of each pipeline stage (dnum=3 top level):
-    compulsory HBM bytes (evaluation-key stream, the op's inputs and outputs;
-    scratch is meant to stay in L2) and modular multiplications by kind:
-    `shoup` (NTT butterflies and products by a constant: one mad.hi and two
-    mad.lo), `mac` (BConv products: one mad.wide each, reduced lazily) and
-    `smr` (variable x variable products: mad.wide, mad.lo, mad.hi).
-    modmul = shoup + mac + smr. Stages shared by HMult and HRot count HRot's
-    work (ModDown converts 2n targets for HRot, the top limb for HMult)."""
+def digit_sizes(n=L, alpha=ALPHA):
+    """alpha_j of each active digit at n limbs (the last one may be partial)."""
+    return [min(alpha, n - j * alpha) for j in range(-(-n // alpha))]
+
+
+def stage_work(op, n=L, alpha=ALPHA):
+    """Algorithmic work of each pipeline stage of one operation (op "hmult":
+    HMult + relinearize + rescale; "hrot": HRot) at n limbs: compulsory HBM
+    bytes (each input limb counted where it is first read, the evaluation-key
+    stream, the output; scratch is meant to stay in L2) and modular
+    multiplications by kind: `shoup` (NTT butterflies and products by a
+    constant: one mad.hi and two mad.lo), `mac` (BConv products: one mad.wide
+    each, reduced lazily) and `smr` (variable x variable: mad.wide, mad.lo,
+    mad.hi; a full product mod q is two). Butterflies per limb: N/2 x 10 in
+    the row phase (W = 1024), N/2 x 6 in the column phase (H = 64). BConv:
+    alpha_j (n + alpha - alpha_j) products per coefficient for ModUp digit j,
+    K per target for the ModDown (K = alpha) and fused-rescale (alpha + 1)
+    conversions."""
     N = 1 << LOG_N
-    d = -(-n // alpha)
-    ext = n + alpha
-    row, col = N // 2 * 10, N // 2 * 6      # butterflies per limb: row phase (W=1024), column phase (H=64)
-    targets = sum(ext - min(alpha, n - j * alpha) for j in range(d))
+    a_j = digit_sizes(n, alpha)
+    d, ext = len(a_j), n + alpha
+    row, col = N // 2 * 10, N // 2 * 6
+    targets = sum(ext - a for a in a_j)
     lb = LIMB_BYTES
-    m = {
-        # input preparation fused into the iNTT rows: reads the inputs (a1 a2 for HMult)
-        "ks_in_rows": dict(bytes=(2 * n + n) * lb // 2, shoup=n * row, smr=n * N // 2),
-        "modup_cols": dict(bytes=0, shoup=(n + targets) * col, mac=targets * N * alpha),
-        "modup_rows": dict(bytes=0, shoup=targets * row),
+    hm = op == "hmult"
+    w = {
+        # tensor a1 a2 (HMult) or phi(a) (HRot) formed while loading, iNTT rows
+        "ks_in_rows": dict(bytes=(2 * n if hm else n) * lb, shoup=n * row, smr=2 * n * N if hm else 0),
+        "modup_cols": dict(shoup=(n + targets) * col, mac=N * sum(a * (ext - a) for a in a_j)),
+        "modup_rows": dict(shoup=targets * row),
         "keymult": dict(bytes=2 * d * ext * lb, smr=2 * d * ext * N),
-        "moddown_in_rows": dict(bytes=0, shoup=2 * alpha * row),
-        "moddown_cols": dict(bytes=0, shoup=2 * (alpha + n) * col, mac=2 * n * N * alpha),
-        # HRot: NTT rows + ModDown epilogue writing the output (2n limbs)
-        "moddown_rows": dict(bytes=2 * n * lb // 2, shoup=2 * n * row + 2 * n * N * 2),
-        "rescale_in_rows": dict(bytes=0, shoup=2 * row),
-        "rescale_cols": dict(bytes=0, shoup=2 * col + 2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1)),
-        # HMult: NTT rows with the epilogue (A - w) (P q_l)^-1 + d q_l^-1 fused,
-        # d0/d1 re-formed, writing 2(n-1) limbs
-        "rescale_rows": dict(bytes=2 * (n - 1) * lb, shoup=2 * (n - 1) * (row + N * 2), smr=2 * (n - 1) * N * 3 // 2),
+        "moddown_in_rows": dict(shoup=2 * alpha * row),
     }
-    for v in m.values():
-        v["modmul"] = sum(v.get(k, 0) for k in ("shoup", "mac", "smr"))
-    return m
+    if hm:
+        # top limb first (ModDown of q_l, then its coefficients join the
+        # fused rescale): b1, b2 top limbs read, d0 / d1 of that limb re-formed
+        w["moddown_cols"] = dict(shoup=2 * (alpha + 1) * col, mac=2 * N * alpha)
+        w["moddown_rows"] = dict(bytes=2 * lb, shoup=2 * row + 2 * N, smr=6 * N)
+        w["rescale_in_rows"] = dict(shoup=2 * row)
+        w["rescale_cols"] = dict(shoup=2 * col + 2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1))
+        # NTT rows + (A - w)(P q_l)^-1 + d q_l^-1 with d0 / d1 re-formed from
+        # the inputs (b1, b2 read here first), output 2(n - 1) limbs
+        w["rescale_rows"] = dict(bytes=4 * (n - 1) * lb, shoup=2 * (n - 1) * (row + 2 * N),
+                                 smr=6 * (n - 1) * N)
+    else:
+        w["moddown_cols"] = dict(shoup=2 * (alpha + n) * col, mac=2 * n * N * alpha)
+        # NTT rows + (A - z) P^-1 + phi(b): b read, output 2n limbs
+        w["moddown_rows"] = dict(bytes=3 * n * lb, shoup=2 * n * row + 2 * n * N)
+    for v in w.values():
+        for k in ("bytes", "shoup", "mac", "smr"):
+            v.setdefault(k, 0)
+        v["modmul"] = v["shoup"] + v["mac"] + v["smr"]
+    return w
+
+
+def kernel_models(n=L, alpha=ALPHA):
+    """Per-launch work of each stage in the bench's one-lane profile, which
+    alternates HMult + rescale and HRot: the mean of the two operations' work
+    for the stages both run (the key-switch stages), HMult's alone for the
+    rescale stages."""
+    hm, hr = stage_work("hmult", n, alpha), stage_work("hrot", n, alpha)
+    out = {}
+    for k in hm:
+        ws = [x[k] for x in (hm, hr) if k in x]
+        out[k] = {kk: sum(x[kk] for x in ws) / len(ws) for kk in ("bytes", "shoup", "mac", "smr", "modmul")}
+    return out
 
 
 def multiply_costs(rates):
@@ -107,7 +139,7 @@ def multiply_costs(rates):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # one-lane pipeline's kernels from one `ncu --set full` capture (cold cache;
-# command in profiles/keyswitch_n16_l40_dnum3_top.md), keyed by stage. They
+# the command is recorded with the committed profile summary), keyed by stage. They
 # describe the kernel sources they were taken on: when the SHA-1 of those
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
@@ -506,6 +538,23 @@ def run_native(args, rank, world, local_rank):
     for c in up_c + dn_c:
         K.ckks_ctx_destroy(c)
 
+    # batched and served forms next to the headline (same context and keys;
+    # levels other than the top one use the default column shapes)
+    bat = batched_modes(K, ctx, sk, rk, gk, max(3, args.steps // 4), max(3, args.warmup), stream)
+    srv_runs, srv_cap, srv_res = serve_runs(K, ctx, sk, rk, stream, args.requests_default, (0.8,))
+    served = {"frac_of_capacity": 0.8, "capacity_ops_s": srv_cap, "resident_key_bytes": srv_res,
+              "requests": args.requests_default,
+              "continuous_batching_4_lanes": srv_runs["continuous_batching_4_lanes@0.8"],
+              "one_op_per_launch": srv_runs["one_op_per_launch@0.8"],
+              "note": "Poisson arrivals of HMult+rescale / HRot at 0.8 x the one-stream capacity, levels U{1..39}, "
+                      "64 resident rotation keys; latency = completion - arrival on the host clock"}
+    fusion = dict(fusion_ablation(K, ctx, sk, rk, gk, stream, pdl=args.pdl == "on"),
+                  note="one stream, median of 15 single operations (inputs rotated over 8 fresh encryptions), "
+                       "fused pipeline vs the one-step-per-launch unfused form with every intermediate in HBM")
+    batched = dict(bat, note="64 independent operations, levels U{1..39}, HMult+rescale / HRot / PMult / "
+                             "rescale; persistent = stage-major batch with one persistent KeyMult / element-wise "
+                             "kernel, replayed as a CUDA graph")
+
     # roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
     models = kernel_models()
@@ -514,30 +563,30 @@ def run_native(args, rank, world, local_rank):
     avg_s = dom_ms / 1e3 / max(dom_n, 1)
     mdl = models[dom]
     hm_bytes, hr_bytes = algorithmic_bytes()
-    # both resources of the dominant kernel: HBM (compulsory bytes) and integer
-    # ALU (modular multiplications against 152 SMs x 128 IMAD/clk at the
-    # maximum SM clock, 3 IMAD-class instructions per modular product); the
-    # bound reported is the one with the larger fraction
+    # both resources of the dominant kernel: HBM (compulsory bytes) and the
+    # integer multiply pipes; the bound reported is the one with the larger
+    # fraction
     hbm_ach = mdl["bytes"] / avg_s / 1e9
     hbm = {"bound": "hbm", "kernel": dom, "achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": f"{peak_kind} hbm_gbs",
            "algorithmic_bytes_per_launch": mdl["bytes"], "traffic": ncu_traffic(dom)}
     # integer-ALU peak of the dominant kernel: its own mix of modular products
-    # issued back to back at this GPU's measured multiply issue rates (152 SMs
-    # at the maximum SM clock)
+    # issued back to back at this GPU's measured multiply issue rates (every
+    # SM at the maximum SM clock)
     clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     rates = {}
     for op, name in ((K.CKKS_INTOP_MAD_LO, "mad_lo"), (K.CKKS_INTOP_MAD_HI, "mad_hi"),
                      (K.CKKS_INTOP_MAD_WIDE, "mad_wide")):
         n_ops, ms_op = K.ckks_bench_intop(ctx, op, 4096)
-        rates[name] = n_ops / (ms_op * 1e-3) / (152 * clk_hz)
+        rates[name] = n_ops / (ms_op * 1e-3) / (sms * clk_hz)
     cost = multiply_costs(rates)
     sm_clocks = sum(mdl.get(k, 0) * cost[k] for k in cost)
-    alu_peak = mdl["modmul"] / (sm_clocks / (152 * clk_hz)) / 1e12
+    alu_peak = mdl["modmul"] / (sm_clocks / (sms * clk_hz)) / 1e12
     alu_ach = mdl["modmul"] / avg_s / 1e12
     alu = {"bound": "alu", "kernel": dom, "achieved": alu_ach, "peak": alu_peak, "unit": "Tmodmul/s",
            "frac": alu_ach / alu_peak,
-           "peak_source": "derived: 152 SM x sm_max_mhz / (the kernel's products x SM clocks per product at "
+           "peak_source": f"derived: {sms} SM x sm_max_mhz / (the kernel's products x SM clocks per product at "
                           "the measured mad.lo / mad.hi / mad.wide issue rates)",
            "int_multiply_per_sm_clk": rates, "algorithmic_modmul_per_launch": mdl["modmul"],
            "mix": {k: mdl.get(k, 0) for k in ("shoup", "mac", "smr")}, "traffic": ncu_traffic(dom)}
@@ -568,6 +617,7 @@ def run_native(args, rank, world, local_rank):
                      "note": "same workload issued in order on one stream; stage times from its CUDA events"},
         "roofline": roof, "op_roofline": op_hbm, "stages": stage,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "batched": batched, "serve": served, "fusion": fusion,
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -587,27 +637,69 @@ def run_native(args, rank, world, local_rank):
 # lanes vs lanes captured into one CUDA graph)
 # ----------------------------------------------------------------------------
 
-def run_batched(args, local_rank):
+def fusion_ablation(K, ctx, sk, rk, gk, stream, levels=(L - 1, 20, 1), reps=15, pdl=True):
+    """Fused pipeline vs the unfused one-step-per-launch form
+    (CKKS_LAUNCH_UNFUSED) on one stream: median microseconds of HMult +
+    rescale and of HRot(1) at each level (fresh encryptions, inputs rotated
+    over 8 ciphertexts), with the launches per operation."""
     import torch
-    from paper_2407_13055_gb300 import ckks as K
     from paper_2407_13055_gb300 import inputs
-    torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
-    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
-    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
-    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
-    sk = K.ckks_keygen_secret(ctx, 11)
-    rk = K.ckks_keygen_relin(ctx, sk, 12)
-    gk = K.ckks_keygen_rot(ctx, sk, 1, 13)
-    count = 64
-    levels = inputs.level_list(7, count, L - 1)
+    base = K.CKKS_LAUNCH_PDL if pdl else 0
+    out = {}
+    for lv in levels:
+        cts = [K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(4000 + 10 * lv + i, (1 << LOG_N) // 2),
+                                                      lv, SCALE), 5000 + 10 * lv + i) for i in range(8)]
+        res = K.ckks_ct_create(ctx, lv)
+        row = {}
+        for form, flags in (("fused", base), ("unfused", base | K.CKKS_LAUNCH_UNFUSED)):
+            K.ckks_set_launch_flags(ctx, flags)
+            for op in ("hmult_rescale", "hrot"):
+                run = ((lambda i: K.ckks_hmult(ctx, cts[i % 8], cts[(i + 1) % 8], rk, K.CKKS_RESCALE, res))
+                       if op == "hmult_rescale" else (lambda i: K.ckks_hrot(ctx, cts[i % 8], 1, gk, res)))
+                for i in range(3):
+                    run(i)
+                torch.cuda.synchronize()
+                times = []
+                l0 = K.ckks_launch_count()
+                for i in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    run(i)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(1e3 * e0.elapsed_time(e1))
+                row.setdefault(op, {})[form] = {"us": statistics.median(times),
+                                                "launches": (K.ckks_launch_count() - l0) / reps}
+        for op in row:
+            row[op]["unfused_over_fused"] = row[op]["unfused"]["us"] / row[op]["fused"]["us"]
+        out[f"level_{lv}"] = row
+        K.ckks_set_launch_flags(ctx, base)
+        for h in cts + [res]:
+            K.ckks_free(h)
+    K.ckks_set_launch_flags(ctx, base)
+    return out
+
+
+BATCHED_MODES = (("one_op_per_launch", 1, 0), ("lanes4_graph", 4, 1), ("lanes4_persistent_graph", 4, 3))
+
+
+def batched_modes(K, ctx, sk, rk, gk, steps, warmup, stream, modes=BATCHED_MODES, count=64, seed=7):
+    """The batched workload: `count` independent operations on fresh
+    encryptions at levels U{1..39}, kinds uniform over HMult+rescale / HRot /
+    PMult / rescale, timed as one list per step in each mode (lanes, batch
+    mode flags: 1 = one CUDA graph, 2 = stage-major with the persistent
+    KeyMult / element-wise kernel). Returns {mode: ops/s, ms/batch, kernel
+    launches per batch}."""
+    import torch
+    from paper_2407_13055_gb300 import inputs
+    levels = inputs.level_list(seed, count, L - 1)
     kinds = ["hmult", "hrot", "pmult", "rescale"]
-    kind_ix = np.random.default_rng(8).integers(0, 4, count)
+    kind_ix = np.random.default_rng(seed + 1).integers(0, 4, count)
     handles, ops = [], []
     for i in range(count):
         lv, kind = int(levels[i]), kinds[int(kind_ix[i])]
-        enc = lambda seed: K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(seed, (1 << LOG_N) // 2), lv,
-                                                                   SCALE), seed)
+        enc = lambda sd: K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(sd, (1 << LOG_N) // 2), lv,
+                                                                 SCALE), sd)
         a = enc(1000 + i)
         out = K.ckks_ct_create(ctx, lv)
         handles += [a, out]
@@ -623,24 +715,44 @@ def run_batched(args, local_rank):
             ops.append(dict(op=K.CKKS_OP_PMULT, a=a, pt=pt, out=out))
         else:
             ops.append(dict(op=K.CKKS_OP_RESCALE, a=a, out=out))
-    tuned = tune_levels(K, ctx, levels, not args.no_tune, reps=2)
     results = {}
-    for name, lanes, graph in (("one_op_per_launch", 1, False), ("lanes4", 4, False), ("lanes4_graph", 4, True)):
-        batch = K.ckks_batch_create(ctx, ops, lanes, graph)
-        for _ in range(args.warmup):
+    for name, lanes, flags in modes:
+        batch = K.ckks_batch_create(ctx, ops, lanes, flags)
+        for _ in range(warmup):
             K.ckks_batch_run(ctx, batch)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = K.ckks_launch_count()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             K.ckks_batch_run(ctx, batch)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        results[name] = {"ops_s": count * args.steps / (ms / 1e3), "ms_per_batch": ms / args.steps,
-                         "kernel_launches_per_batch": (K.ckks_launch_count() - l0) / args.steps}
+        results[name] = {"ops_s": count * steps / (ms / 1e3), "ms_per_batch": ms / steps,
+                         "kernel_launches_per_batch": (K.ckks_launch_count() - l0) / steps}
         K.ckks_batch_destroy(batch)
+    K.ckks_sync(ctx)
+    for h in handles:
+        K.ckks_free(h)
+    return results
+
+
+def run_batched(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    from paper_2407_13055_gb300 import inputs
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
+    sk = K.ckks_keygen_secret(ctx, 11)
+    rk = K.ckks_keygen_relin(ctx, sk, 12)
+    gk = K.ckks_keygen_rot(ctx, sk, 1, 13)
+    tuned = tune_levels(K, ctx, inputs.level_list(7, 64, L - 1), not args.no_tune, reps=2)
+    modes = BATCHED_MODES + (("lanes4_direct", 4, 0), ("lanes4_persistent_direct", 4, 2))
+    results = batched_modes(K, ctx, sk, rk, gk, args.steps, args.warmup, stream, modes)
     line = {"metric": "batched mixed-level ops/sec at N=2^16 (1 GB300)", "value": results["lanes4_graph"]["ops_s"],
             "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": results["lanes4_graph"]["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
@@ -650,7 +762,7 @@ def run_batched(args, local_rank):
                        "column_shapes": "tuned per level" if tuned else "default rule"},
             "modes": results}
     print(json.dumps(line), flush=True)
-    for h in handles + [sk, rk, gk]:
+    for h in (sk, rk, gk):
         K.ckks_free(h)
     K.ckks_ctx_destroy(ctx)
 
@@ -819,9 +931,10 @@ def run_ablation(args, local_rank):
     ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
     K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     peaks, _ = measured_peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     # (1) modular multiplication methods: 8 chains per thread, enough threads
     # for many waves; every method must return the same values
-    n, rounds = 152 * 2048 * 8, 2048
+    n, rounds = sms * 2048 * 8, 2048
     rng = np.random.default_rng(1)
     mm = {}
     for pid, label in ((1, "30-bit q_1"), (0, "31-bit q_0")):
@@ -835,7 +948,7 @@ def run_ablation(args, local_rank):
             ref = out if ref is None else ref
             gmm = n * rounds / (ms * 1e-3) / 1e9
             mm.setdefault(label, {})[name] = {"gmodmul_s": gmm, "ms": ms, "agrees": bool(np.array_equal(out, ref)),
-                                              "modmul_per_sm_clk": gmm * 1e9 / (152 * peaks.get("sm_max_mhz", 2070.0)
+                                              "modmul_per_sm_clk": gmm * 1e9 / (sms * peaks.get("sm_max_mhz", 2070.0)
                                                                                 * 1e6)}
     # integer multiply issue rates per SM per clock (the unit counts behind
     # the integer-ALU roofline)
@@ -844,7 +957,7 @@ def run_ablation(args, local_rank):
     for op, name in ((K.CKKS_INTOP_MAD_LO, "mad_lo"), (K.CKKS_INTOP_MAD_HI, "mad_hi"),
                      (K.CKKS_INTOP_MAD_WIDE, "mad_wide")):
         n_ops, ms_op = K.ckks_bench_intop(ctx, op, 4096)
-        int_rates[name] = n_ops / (ms_op * 1e-3) / (152 * clk_hz)
+        int_rates[name] = n_ops / (ms_op * 1e-3) / (sms * clk_hz)
     # (2) sequential fusion: HMult with ModDown + rescale fused vs HMult then
     # a separate rescale (top level, one stream, median of 50)
     sk = K.ckks_keygen_secret(ctx, 71)
@@ -1040,28 +1153,24 @@ def run_bootstrap(args, local_rank):
 # served form: Poisson arrivals, continuous batching over lanes
 # ----------------------------------------------------------------------------
 
-def run_serve(args, local_rank):
+def serve_runs(K, ctx, sk, rk, stream, count, fracs, n_keys=64, seed=21):
+    """The served workload: `count` Poisson arrivals of single HMult+rescale /
+    HRot requests (50:50, levels U{1..39}, rotations over `n_keys` resident
+    keys) at each rate frac x the one-stream capacity, served one operation
+    at a time and by continuous batching on 4 lanes (admission by request
+    footprint next to the resident keys, in a budget of keys + 4 GB). Returns
+    ({run: latency stats}, capacity ops/s, resident key bytes)."""
     import torch
-    from paper_2407_13055_gb300 import ckks as K
     from paper_2407_13055_gb300 import inputs
     from paper_2407_13055_gb300.serve import Request, Server, latency_stats, poisson_arrivals
-    torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
-    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
-    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
-    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
-    sk = K.ckks_keygen_secret(ctx, 21)
-    rk = K.ckks_keygen_relin(ctx, sk, 22)
-    n_keys = 64
-    rots = sorted(set(int(r) for r in inputs.rotation_list(23, 4 * n_keys, (1 << LOG_N) // 2)))[:n_keys]
+    rots = sorted(set(int(r) for r in inputs.rotation_list(seed + 2, 4 * n_keys, (1 << LOG_N) // 2)))[:n_keys]
     gks = {r: K.ckks_keygen_rot(ctx, sk, r, 100 + r) for r in rots}
     pool = {}
     for lv in range(1, L):
         pool[lv] = [K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(500 + 2 * lv + t, (1 << LOG_N) // 2),
                                                            lv, SCALE), 900 + 2 * lv + t) for t in range(2)]
-    count = args.requests
-    rng = np.random.default_rng(31)
-    levels = inputs.level_list(32, count, L - 1)
+    rng = np.random.default_rng(seed + 10)
+    levels = inputs.level_list(seed + 11, count, L - 1)
     ops = ["hmult" if v < 0.5 else "hrot" for v in rng.random(count)]
     rot_ix = rng.integers(0, len(rots), count)
     reqs = [Request(i, ops[i], int(levels[i]), rots[int(rot_ix[i])] if ops[i] == "hrot" else 0) for i in range(count)]
@@ -1074,7 +1183,6 @@ def run_serve(args, local_rank):
 
     inputs_for = lambda r: (pool[r.level][0], pool[r.level][1])
     key_for = lambda r: rk if r.op == "hmult" else gks[r.rot]
-    tuned = tune_levels(K, ctx, range(1, L), not args.no_tune, reps=2)
     # capacity: the whole request list back to back on one stream
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1088,31 +1196,52 @@ def run_serve(args, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     capacity = count / (e0.elapsed_time(e1) / 1e3)
-    budget = 4 << 30
+    resident = (len(gks) + 1) * DNUM * 2 * (L + ALPHA) * (1 << LOG_N) * 4
+    budget = resident + (4 << 30)
     results = {}
-    for frac in (0.5, 0.8, 0.95):
+    for frac in fracs:
         arr = poisson_arrivals(np.random.default_rng(int(frac * 100)), count, frac * capacity)
         for r, t in zip(reqs, arr):
             r.arrival = t
         for name, lanes in (("one_op_per_launch", 1), ("continuous_batching_4_lanes", 4)):
-            srv = Server(K, ctx, lanes, budget, 1 << LOG_N)
+            srv = Server(K, ctx, lanes, budget, 1 << LOG_N, resident_bytes=resident)
             try:
                 done = srv.run(reqs, inputs_for, key_for, out_for)
             finally:
                 srv.close()
             results[f"{name}@{frac}"] = latency_stats(done)
+    K.ckks_sync(ctx)
+    for h in list(outs.values()) + [c for v in pool.values() for c in v] + list(gks.values()):
+        K.ckks_free(h)
+    return results, capacity, resident
+
+
+def run_serve(args, local_rank):
+    import torch
+    from paper_2407_13055_gb300 import ckks as K
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    q, p = K.ckks_gen_primes(LOG_N, L, ALPHA)
+    ctx = K.ckks_ctx_create(LOG_N, q, p, DNUM, scale=SCALE, secret_hw=HW, stream=stream.cuda_stream)
+    K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
+    sk = K.ckks_keygen_secret(ctx, 21)
+    rk = K.ckks_keygen_relin(ctx, sk, 22)
+    tuned = tune_levels(K, ctx, range(1, L), not args.no_tune, reps=2)
+    count = args.requests
+    results, capacity, resident = serve_runs(K, ctx, sk, rk, stream, count, (0.5, 0.8, 0.95))
     best = results["continuous_batching_4_lanes@0.95"]
     line = {"metric": "served HMult/HRot requests at N=2^16 (1 GB300): throughput and p50/p99 latency",
             "value": best["throughput_ops_s"], "unit": "requests/s", "n_gpus": 1, "steps": count, "warmup": 0,
             "ms_per_step": best["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (fresh encryptions)",
             "config": {"workload": f"{count} Poisson requests, HMult+rescale / HRot 50:50, levels U{{1..39}}, "
-                                   f"{len(rots)} resident rotation keys, arrival rate = 0.5/0.8/0.95 x one-stream "
-                                   "capacity", "capacity_ops_s": capacity, "admission_budget_bytes": budget,
+                                   "64 resident rotation keys, arrival rate = 0.5/0.8/0.95 x one-stream "
+                                   "capacity", "capacity_ops_s": capacity, "resident_key_bytes": resident,
+                       "admission_budget_bytes": resident + (4 << 30),
                        "column_shapes": "tuned per level" if tuned else "default rule"},
             "runs": results}
     print(json.dumps(line), flush=True)
-    for h in list(outs.values()) + [c for v in pool.values() for c in v] + list(gks.values()) + [sk, rk]:
+    for h in (sk, rk):
         K.ckks_free(h)
     K.ckks_ctx_destroy(ctx)
 
@@ -1127,7 +1256,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent execution lanes (streams)")
     ap.add_argument("--workload", choices=["single", "batched", "serve", "hoisted", "bootstrap", "latency", "ablation", "rns2530"], default="single")
-    ap.add_argument("--requests", type=int, default=2000, help="requests per served run")
+    ap.add_argument("--requests", type=int, default=2000, help="requests per served run (--workload serve)")
+    ap.add_argument("--requests-default", type=int, default=1000,
+                    help="requests of the served run reported in the default line")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
     ap.add_argument("--issue", choices=["graph", "direct", "python"], default="graph",
                     help="single workload: how the timed step's operations are issued")

@@ -138,6 +138,30 @@ int ckks_sync(ckks_ctx* ctx);            /* cudaStreamSynchronize on the context
 void ckks_free(void* handle);            /* any ckks_ct / ckks_pt / ckks_sk / ckks_evk */
 /* Device bytes held by the context's tables and scratch (admission control). */
 size_t ckks_ctx_device_bytes(ckks_ctx* ctx);
+/* Object memory budget (not from the paper: admission control for serving).
+ * The device memory of the objects created through a context and its clones
+ * (ciphertexts, plaintexts, secret and evaluation keys) is counted together;
+ * with a limit (bytes > 0) an allocation that would exceed it fails with
+ * CKKS_ENOMEM before the CUDA allocator is called. 0 removes the limit.
+ * ckks_memory_in_use returns the bytes those objects hold now. */
+int ckks_set_memory_limit(ckks_ctx* ctx, size_t bytes);
+size_t ckks_memory_in_use(ckks_ctx* ctx);
+/* Device bytes one request of kind `op` (CKKS_OP_*) at `level` holds while it
+ * runs on a lane: its input ciphertexts (a plaintext counted as half a
+ * ciphertext), its output ciphertext and, for the operations that use it,
+ * the lane's key-switching scratch. Resident evaluation keys are shared by
+ * requests and are not included. 0 for an unknown op or level. */
+size_t ckks_request_bytes(ckks_ctx* ctx, int op, int level);
+/* Admission pool (host-side, thread-safe): requests acquire their bytes
+ * before they start and release them when done. ckks_pool_acquire returns
+ * CKKS_EBUSY (and acquires nothing) when the bytes would exceed the budget;
+ * ckks_pool_release returns CKKS_EINVAL for more bytes than are held. */
+typedef struct ckks_pool ckks_pool;
+int ckks_pool_create(size_t budget_bytes, ckks_pool** out);
+int ckks_pool_acquire(ckks_pool* pool, size_t bytes);
+int ckks_pool_release(ckks_pool* pool, size_t bytes);
+size_t ckks_pool_in_use(const ckks_pool* pool);
+void ckks_pool_destroy(ckks_pool* pool);
 
 /* --- keys (Sec. 2.1; hybrid key switching after Han-Ki, cited by the paper) --- */
 /* Ternary secret drawn with the library's sampler (SplitMix64 stream). */
@@ -341,9 +365,11 @@ void ckks_batch_destroy(ckks_batch* batch);
  * Calls whose kernels overlap on the GPU (other streams, other threads)
  * race on that array; calls in order on one stream do not. Every scratch word
  * is written before it is read in each call, so nothing needs clearing.
- * The first call on each device looks up the array's device address with
- * that device current (cudaGetSymbolAddress); make that first call before any
- * stream capture. Asynchronous on the context stream. */
+ * The context's device must be the current device (CKKS_EINVAL otherwise,
+ * before any device work). The first call on each device looks up the
+ * array's device address with that device current (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Asynchronous on the
+ * context stream. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint32_t* out_dev);
 
 /* --- launch options ---
@@ -360,6 +386,16 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
  * shared-memory blocks crowd out the other lanes' kernels), while the tuner
  * times one kernel alone, so they are only candidates on request. */
 #define CKKS_TUNE_TENSOR 2
+/* CKKS_LAUNCH_UNFUSED (default off): HMult (with or without CKKS_RESCALE),
+ * HRot and HConj run the unfused form instead, one kernel launch per step
+ * with every intermediate in device memory (tensor or automorphism, full
+ * iNTT, one BConv per ModUp digit, full NTTs, KeyMult, iNTT of the P limbs,
+ * BConv P -> Q, NTT, ModDown epilogue, and for rescaling iNTT of the top
+ * limb, reduction, NTT, epilogue): the mechanism baseline of the fusion
+ * ablation (Sec. 5, Table 8), same residues. Single rescaling only (CKKS_EINVAL
+ * on a windowed context; CKKS_RESCALE_MERGED is refused); the first such
+ * operation allocates the form's scratch on the context. */
+#define CKKS_LAUNCH_UNFUSED 4
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
 
 /* Bounded device-side waits. The tensor-core and bulk-copy kernels wait on

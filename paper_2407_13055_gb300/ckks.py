@@ -90,6 +90,14 @@ _SIGS = {
     "ckks_sync": (_i, [_vp]),
     "ckks_free": (None, [_vp]),
     "ckks_ctx_device_bytes": (_sz, [_vp]),
+    "ckks_set_memory_limit": (_i, [_vp, _sz]),
+    "ckks_memory_in_use": (_sz, [_vp]),
+    "ckks_request_bytes": (_sz, [_vp, _i, _i]),
+    "ckks_pool_create": (_i, [_sz, _P(_vp)]),
+    "ckks_pool_acquire": (_i, [_vp, _sz]),
+    "ckks_pool_release": (_i, [_vp, _sz]),
+    "ckks_pool_in_use": (_sz, [_vp]),
+    "ckks_pool_destroy": (None, [_vp]),
     "ckks_keygen_secret": (_i, [_vp, _u64, _P(_vp)]),
     "ckks_sk_import": (_i, [_vp, _vp, _P(_vp)]),
     "ckks_keygen_relin": (_i, [_vp, _vp, _u64, _P(_vp)]),
@@ -477,10 +485,52 @@ def ckks_rescale_noalloc(ctx, in_dev: int, level: int, out_dev: int):
 CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED, CKKS_ROW_PASSES = 0, 1, 2, 3
 CKKS_LAUNCH_PDL = 1
 CKKS_TUNE_TENSOR = 2
+CKKS_LAUNCH_UNFUSED = 4
 
 
 def ckks_set_launch_flags(ctx, flags: int):
     check(ctx, lib.ckks_set_launch_flags(ctx, flags))
+
+
+def ckks_set_memory_limit(ctx, nbytes: int):
+    """Limit of the device bytes the context's objects may hold together (0 = none)."""
+    check(ctx, lib.ckks_set_memory_limit(ctx, nbytes))
+
+
+def ckks_memory_in_use(ctx) -> int:
+    return int(lib.ckks_memory_in_use(ctx))
+
+
+def ckks_request_bytes(ctx, op: int, level: int) -> int:
+    """Device bytes a request of kind op (CKKS_OP_*) at level holds while it runs."""
+    return int(lib.ckks_request_bytes(ctx, op, level))
+
+
+def ckks_pool_create(budget: int):
+    out = _vp()
+    check(None, lib.ckks_pool_create(budget, C.byref(out)))
+    return out
+
+
+def ckks_pool_acquire(pool, nbytes: int) -> bool:
+    """True when admitted; False when the budget refuses it (CKKS_EBUSY)."""
+    rc = lib.ckks_pool_acquire(pool, nbytes)
+    if rc == CKKS_EBUSY:
+        return False
+    check(None, rc)
+    return True
+
+
+def ckks_pool_release(pool, nbytes: int):
+    check(None, lib.ckks_pool_release(pool, nbytes))
+
+
+def ckks_pool_in_use(pool) -> int:
+    return int(lib.ckks_pool_in_use(pool))
+
+
+def ckks_pool_destroy(pool):
+    lib.ckks_pool_destroy(pool)
 
 
 def ckks_set_wait_limit(ctx, cycles: int):

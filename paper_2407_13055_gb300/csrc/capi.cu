@@ -1,4 +1,5 @@
 // C ABI of the library (declarations and documentation in include/ckks.h).
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,6 +80,34 @@ struct DevBuf {
     return reinterpret_cast<T*>(p);
   }
 };
+
+// Device memory of an object, charged to its context's budget: refused
+// (cudaErrorMemoryAllocation, no CUDA call) when the context's objects would
+// exceed the limit.
+cudaError_t obj_malloc(ckks_ctx* ctx, ckks_obj* o, void** p, size_t bytes) {
+  ckks::MemBudget& m = *ctx->mem;
+  const size_t lim = m.limit.load();
+  const size_t before = m.used.fetch_add(bytes);
+  if (lim && before + bytes > lim) {
+    m.used.fetch_sub(bytes);
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    m.used.fetch_sub(bytes);
+    return e;
+  }
+  o->bytes += bytes;
+  o->mem = ctx->mem;
+  return cudaSuccess;
+}
+
+void obj_release(ckks_obj* o) {
+  if (o->mem) o->mem->used.fetch_sub(o->bytes);
+  o->bytes = 0;
+  o->mem.reset();
+}
 
 uint32_t galois_rot(int r, int log_n) {
   const uint64_t two_n = 2ull << log_n;
@@ -167,6 +196,7 @@ int ckks_ctx_create(const ckks_params* prm, void* stream, ckks_ctx** out) {
     return bad(fail(ctx, rc, "status word allocation failed"));
   }
   ctx->sc.prof = &ctx->prof;
+  ctx->mem = std::make_shared<ckks::MemBudget>();
   ctx->tune = std::make_shared<ckks::Tuning>(L);
   ctx->sc.tune = ctx->tune.get();
   ctx->dp.pdl = 1;
@@ -209,6 +239,7 @@ int ckks_ctx_clone(ckks_ctx* parent, void* cuda_stream, ckks_ctx** out) {
   }
   c->h_status = parent->h_status;  // shared with the parent (dp.status copied above)
   c->sc.prof = &c->prof;
+  c->mem = parent->mem;
   c->tune = parent->tune;
   c->sc.tune = c->tune.get();
   *out = c;
@@ -221,15 +252,19 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
   else cudaDeviceSynchronize();
   if (ctx->d_tables && ctx->owns_tables) cudaFree(ctx->d_tables);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+  if (ctx->d_unfused) cudaFree(ctx->d_unfused);
   if (ctx->owns_tables) free_status(ctx);
   for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
   delete ctx;
 }
 
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags) {
-  if (!ctx || (flags & ~(CKKS_LAUNCH_PDL | CKKS_TUNE_TENSOR))) return CKKS_EINVAL;
+  if (!ctx || (flags & ~(CKKS_LAUNCH_PDL | CKKS_TUNE_TENSOR | CKKS_LAUNCH_UNFUSED))) return CKKS_EINVAL;
+  if ((flags & CKKS_LAUNCH_UNFUSED) && ctx->windowed)
+    return fail(ctx, CKKS_EINVAL, "launch flags: the unfused form supports single rescaling only");
   ctx->dp.pdl = (flags & CKKS_LAUNCH_PDL) ? 1 : 0;
   ctx->dp.tune_tensor = (flags & CKKS_TUNE_TENSOR) ? 1 : 0;
+  ctx->dp.unfused = (flags & CKKS_LAUNCH_UNFUSED) ? 1 : 0;
   return CKKS_OK;
 }
 
@@ -339,6 +374,81 @@ int ckks_sync(ckks_ctx* ctx) {
 
 size_t ckks_ctx_device_bytes(ckks_ctx* ctx) { return ctx ? ctx->table_bytes + ctx->scratch_bytes : 0; }
 
+}  // extern "C"
+
+// Admission pool of a server: a byte budget that requests acquire while
+// they hold device memory (host-side accounting, thread-safe).
+struct ckks_pool {
+  std::atomic<size_t> used{0};
+  size_t budget = 0;
+};
+
+extern "C" {
+
+int ckks_pool_create(size_t budget_bytes, ckks_pool** out) {
+  if (!out) return CKKS_EINVAL;
+  ckks_pool* p = new (std::nothrow) ckks_pool();
+  if (!p) return CKKS_ENOMEM;
+  p->budget = budget_bytes;
+  *out = p;
+  return CKKS_OK;
+}
+
+int ckks_pool_acquire(ckks_pool* pool, size_t bytes) {
+  if (!pool) return CKKS_EINVAL;
+  size_t cur = pool->used.load();
+  for (;;) {
+    if (bytes > pool->budget || cur > pool->budget - bytes) return CKKS_EBUSY;
+    if (pool->used.compare_exchange_weak(cur, cur + bytes)) return CKKS_OK;
+  }
+}
+
+int ckks_pool_release(ckks_pool* pool, size_t bytes) {
+  if (!pool) return CKKS_EINVAL;
+  size_t cur = pool->used.load();
+  for (;;) {
+    if (bytes > cur) return CKKS_EINVAL;
+    if (pool->used.compare_exchange_weak(cur, cur - bytes)) return CKKS_OK;
+  }
+}
+
+size_t ckks_pool_in_use(const ckks_pool* pool) { return pool ? pool->used.load() : 0; }
+
+void ckks_pool_destroy(ckks_pool* pool) { delete pool; }
+
+int ckks_set_memory_limit(ckks_ctx* ctx, size_t bytes) {
+  if (!ctx || !ctx->mem) return CKKS_EINVAL;
+  ctx->mem->limit.store(bytes);
+  return CKKS_OK;
+}
+
+size_t ckks_memory_in_use(ckks_ctx* ctx) { return ctx && ctx->mem ? ctx->mem->used.load() : 0; }
+
+size_t ckks_request_bytes(ckks_ctx* ctx, int op, int level) {
+  if (!ctx || level < 0 || level >= ctx->n_levels()) return 0;
+  const size_t ct = 2 * (size_t)ctx->cap_limbs(level) * limb_words(ctx) * sizeof(uint32_t);
+  size_t inputs;
+  switch (op) {
+    case CKKS_OP_HMULT:
+    case CKKS_OP_HADD:
+      inputs = 2 * ct;
+      break;
+    case CKKS_OP_HROT:
+    case CKKS_OP_HCONJ:
+    case CKKS_OP_RESCALE:
+      inputs = ct;
+      break;
+    case CKKS_OP_PMULT:
+    case CKKS_OP_PADD:
+      inputs = ct + ct / 2;
+      break;
+    default:
+      return 0;
+  }
+  const bool ks = op == CKKS_OP_HMULT || op == CKKS_OP_HROT || op == CKKS_OP_HCONJ || op == CKKS_OP_RESCALE;
+  return inputs + ct + (ks ? ctx->scratch_bytes : 0);
+}
+
 void ckks_free(void* handle) {
   if (!handle) return;
   ckks_obj* o = reinterpret_cast<ckks_obj*>(handle);
@@ -346,21 +456,25 @@ void ckks_free(void* handle) {
     case K_CT: {
       ckks_ct* c = reinterpret_cast<ckks_ct*>(handle);
       if (c->d && !c->borrowed) cudaFree(c->d);
+      obj_release(&c->h);
       delete c;
     } break;
     case K_PT: {
       ckks_pt* p = reinterpret_cast<ckks_pt*>(handle);
       if (p->d) cudaFree(p->d);
+      obj_release(&p->h);
       delete p;
     } break;
     case K_SK: {
       ckks_sk* s = reinterpret_cast<ckks_sk*>(handle);
       if (s->d_s) cudaFree(s->d_s);
+      obj_release(&s->h);
       delete s;
     } break;
     case K_EVK: {
       ckks_evk* e = reinterpret_cast<ckks_evk*>(handle);
       if (e->d) cudaFree(e->d);
+      obj_release(&e->h);
       delete e;
     } break;
     default:
@@ -382,9 +496,11 @@ int ckks_ct_create(ckks_ctx* ctx, int cap_level, ckks_ct** out) {
   c->cap_level = cap_level;
   c->scale = ctx->scale;
   c->borrowed = false;
-  if (cudaMalloc(&c->d, 2 * (size_t)ctx->cap_limbs(cap_level) * limb_words(ctx) * sizeof(uint32_t)) != cudaSuccess) {
+  const size_t cbytes = 2 * (size_t)ctx->cap_limbs(cap_level) * limb_words(ctx) * sizeof(uint32_t);
+  if (obj_malloc(ctx, &c->h, (void**)&c->d, cbytes) != cudaSuccess) {
     delete c;
-    return fail(ctx, CKKS_ENOMEM, "ciphertext allocation failed");
+    return fail(ctx, CKKS_ENOMEM, "ciphertext allocation failed (%zu bytes; objects of the context hold %zu of "
+                "a limit of %zu, 0 = none)", cbytes, ctx->mem->used.load(), ctx->mem->limit.load());
   }
   *out = c;
   return CKKS_OK;
@@ -486,7 +602,7 @@ static int pt_alloc(ckks_ctx* ctx, int level, double scale, ckks_pt** out, int e
   p->level = level;
   p->scale = scale;
   p->ext = ext;
-  if (cudaMalloc(&p->d, (size_t)(ctx->lvl_n(level) + ext) * limb_words(ctx) * 4) != cudaSuccess) {
+  if (obj_malloc(ctx, &p->h, (void**)&p->d, (size_t)(ctx->lvl_n(level) + ext) * limb_words(ctx) * 4) != cudaSuccess) {
     delete p;
     return fail(ctx, CKKS_ENOMEM, "plaintext allocation failed");
   }
@@ -562,7 +678,7 @@ static int sk_from_coeffs(ckks_ctx* ctx, const int64_t* coeffs, ckks_sk** out) {
   if (!s) return CKKS_ENOMEM;
   s->coeffs.assign(coeffs, coeffs + lw);
   DevBuf tmp;
-  if (cudaMalloc(&s->d_s, (size_t)np * lw * 4) != cudaSuccess || tmp.alloc(lw * 8) != cudaSuccess) {
+  if (obj_malloc(ctx, &s->h, (void**)&s->d_s, (size_t)np * lw * 4) != cudaSuccess || tmp.alloc(lw * 8) != cudaSuccess) {
     ckks_free(s);
     return fail(ctx, CKKS_ENOMEM, "secret allocation failed");
   }
@@ -606,7 +722,7 @@ static int keygen_ks(ckks_ctx* ctx, const ckks_sk* sk, const uint32_t* s_from, u
   ckks_evk* e = new_obj<ckks_evk>(ctx, K_EVK);
   if (!e) return CKKS_ENOMEM;
   e->galois = galois;
-  if (cudaMalloc(&e->d, (size_t)dnum * 2 * poly * 4) != cudaSuccess) {
+  if (obj_malloc(ctx, &e->h, (void**)&e->d, (size_t)dnum * 2 * poly * 4) != cudaSuccess) {
     delete e;
     return fail(ctx, CKKS_ENOMEM, "evk allocation failed");
   }
@@ -695,7 +811,7 @@ int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_e
   if (!e) return CKKS_ENOMEM;
   e->galois = galois;
   DevBuf stage;
-  if (cudaMalloc(&e->d, words * 4) != cudaSuccess || stage.alloc(words * 4)) {
+  if (obj_malloc(ctx, &e->h, (void**)&e->d, words * 4) != cudaSuccess || stage.alloc(words * 4)) {
     ckks_free(e);
     return fail(ctx, CKKS_ENOMEM, "evk allocation failed");
   }
@@ -979,12 +1095,24 @@ uint32_t galois_of_rotation(int r, int log_n) { return galois_rot(r, log_n); }
 
 extern "C" {
 
+// Key switch of an operation in the unfused form (its scratch is allocated
+// on the first use).
+static int keyswitch_unfused(ckks_ctx* ctx, const KsArgs& k, const char* what) {
+  if (k.mm) return fail(ctx, CKKS_EINVAL, "%s: the unfused form has no merged ModDown + rescale", what);
+  if (ctx->dp.alpha > 64) return fail(ctx, CKKS_EINVAL, "%s: the unfused form converts at most 64 sources", what);
+  if (!ctx->d_unfused && cudaMalloc(&ctx->d_unfused, unfused_scratch_words(ctx->dp) * sizeof(uint32_t)) != cudaSuccess)
+    return fail(ctx, CKKS_ENOMEM, "%s: unfused scratch allocation failed", what);
+  launch_keyswitch_unfused(ctx->dp, k, ctx->d_unfused, ctx->stream);
+  return launched(ctx, what);
+}
+
 int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk* evk, int flags, ckks_ct* out) {
   KsArgs k;
   bool staged = false;
   const int level = a ? a->level : 0;
   const int rc = prepare_hmult(ctx, a, b, evk, flags, out, k, staged);
   if (rc != CKKS_OK) return rc;
+  if (ctx->dp.unfused) return keyswitch_unfused(ctx, k, "hmult");
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
   if (staged) rescale_into(ctx, level, ctx->sc.U, k.out_stride, out->d, out->poly_stride());
   return launched(ctx, "hmult");
@@ -994,6 +1122,7 @@ static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_ev
   KsArgs k;
   const int rc = prepare_hauto(ctx, c, galois, evk, out, k);
   if (rc != CKKS_OK) return rc;
+  if (ctx->dp.unfused) return keyswitch_unfused(ctx, k, "hrot");
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
   return launched(ctx, "hrot");
 }

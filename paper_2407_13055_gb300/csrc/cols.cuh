@@ -504,9 +504,9 @@ static bool with_shape(const ColShape& s, F f) {
 // Default shape: 8 columns (32-byte row segments) when that already gives
 // two blocks per SM, else 4 to double the block count; four slices; no split.
 template <class G>
-static ColShape default_shape(int blocks_per_tile_column) {
+static ColShape default_shape(int blocks_per_tile_column, int sms) {
   ColShape s;
-  s.tc = ((G::W / 8) * blocks_per_tile_column >= 2 * 152 || G::W / 4 < 16) ? 8 : 4;
+  s.tc = ((G::W / 8) * blocks_per_tile_column >= 2 * sms || G::W / 4 < 16) ? 8 : 4;
   s.sl = 4;
   s.z = 1;
   s.tp = 1;
@@ -558,7 +558,7 @@ void launch_modup_cols(const DevParams& dp, int n, int base, int tix, int digits
         count_launch(1);
       }))
     return;
-  const ColShape s = is_tc_shape(s0) ? default_shape<G>(digits) : s0;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(digits, dp.sms) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
@@ -584,7 +584,7 @@ void launch_moddown_cols(const DevParams& dp, int n, int base, int tix, const Sc
         count_launch(1);
       }))
     return;
-  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2, dp.sms) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
@@ -597,7 +597,7 @@ void launch_moddown_cols(const DevParams& dp, int n, int base, int tix, const Sc
 
 template <class G>
 void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint32_t* Y, cudaStream_t st) {
-  ColShape s = default_shape<G>(2);
+  ColShape s = default_shape<G>(2, dp.sms);
   with_shape(s, [&](auto tc, auto sl, auto) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
@@ -623,7 +623,7 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
         count_launch(1);
       }))
     return;
-  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2, dp.sms) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
@@ -636,7 +636,7 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
 
 template <class G>
 void launch_mm_cols(const DevParams& dp, const MmArgs& m, const Scratch& sc, const ColShape& s0, cudaStream_t st) {
-  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2) : s0;
+  const ColShape s = is_tc_shape(s0) ? default_shape<G>(2, dp.sms) : s0;
   with_shape(s, [&](auto tc, auto sl, auto tp) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, TP = decltype(tp)::value;
     const size_t sm = col_smem_bytes<G, TC, SL>(m.K);

@@ -733,6 +733,9 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   ctx->d_tables = base;
   ctx->table_bytes = total;
   DevParams& dp = ctx->dp;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) sms = 1;
+  dp.sms = sms;
   dp.log_n = log_n;
   dp.L = L;
   dp.alpha = alpha;

@@ -59,8 +59,10 @@ struct DevParams {
   const uint2* tw;       // [L + alpha][N] forward twiddles (w, Shoup companion)
   const uint2* itw;      // [L + alpha][N] inverse twiddles
   KsTables ks;
+  int sms = 0;  // streaming multiprocessors of the context's device (grid sizing)
   int pdl;  // host-side launch option: key-switch kernels use programmatic dependent launch
   int tune_tensor = 0;  // host-side option: the fine-tuner also times the tensor-core column shapes
+  int unfused = 0;      // host-side option: key-switching operations run the unfused one-step-per-launch form
   int rows_passes = 3;  // host-side launch option at N = 2^16: row phase in 3 (16 values per
                         // thread, 64 threads per row) or 2 (32 values, 32 threads) passes
   // Bounded device-side waits (mbarrier waits of the tensor-core and bulk-copy
@@ -314,6 +316,14 @@ void launch_ks_modup(const DevParams& dp, const Scratch& sc, const KsArgs& a, cu
 void launch_ks_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A, size_t a_stride,
                     cudaStream_t st);
 
+// Unfused form (k_unfused.cu): every step of the key switch (and of the
+// rescale of HMult) as its own launch, intermediates in W
+// (unfused_scratch_words(dp) words); non-windowed levels only.
+void launch_keyswitch_keymult_only(const DevParams& dp, const KsArgs& a, const uint32_t* T, uint32_t* A,
+                                   cudaStream_t st);
+size_t unfused_scratch_words(const DevParams& dp);
+void launch_keyswitch_unfused(const DevParams& dp, const KsArgs& a, uint32_t* W, cudaStream_t st);
+
 // Persistent streaming stage of a batch (k_keyswitch.cu): work items
 // (operation index, limb) over a table of operations.
 enum PersKind { PK_KEYMULT = 0, PK_HADD = 1, PK_PADD = 2, PK_PMULT = 3 };
@@ -358,9 +368,21 @@ void launch_bconv(const DevParams& dp, const uint32_t* in, int k, const int* src
 }  // namespace ckks
 
 // ---- objects ----
+namespace ckks {
+// Device bytes held by the objects of a context and its clones, and their
+// optional limit (0 = none). Shared by a context, its clones and the objects
+// charged to it.
+struct MemBudget {
+  std::atomic<size_t> used{0};
+  std::atomic<size_t> limit{0};
+};
+}  // namespace ckks
+
 struct ckks_obj {
   int kind;  // 1 ct, 2 pt, 3 sk, 4 evk
   ckks_ctx* ctx;
+  size_t bytes = 0;                      // device bytes charged to mem
+  std::shared_ptr<ckks::MemBudget> mem;  // the budget they are charged to
 };
 
 struct ckks_ctx {
@@ -380,10 +402,12 @@ struct ckks_ctx {
   std::shared_ptr<ckks::Tuning> tune;  // shared with clones
   void* d_scratch;
   size_t scratch_bytes;
+  uint32_t* d_unfused = nullptr;  // scratch of the unfused form (allocated on its first use)
   // host-side key-switching constants needed for keygen (gadget P mod prime)
   std::vector<uint2> gadget_p;  // [L + alpha] Shoup pair of [P]_{prime}
   std::string err;
   int device;
+  std::shared_ptr<ckks::MemBudget> mem;  // object memory budget, shared with clones
   uint32_t* h_status = nullptr;  // host-mapped status word (dp.status is its device address), shared by
                                  // a context and its clones; freed by the context that owns the tables
   // Levels: level l holds the primes q[lvl_first[l] .. lvl_first[l] +

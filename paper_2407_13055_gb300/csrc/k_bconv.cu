@@ -143,7 +143,7 @@ void launch_bconv(const DevParams& dp, const uint32_t* in, int k, const int* src
     const size_t smem = (size_t)mp * kp + (size_t)TC_WARPS * mp * 8 * sizeof(int);
     cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n / 8 + TC_WARPS - 1) / TC_WARPS;
-    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks > 4 * dp.sms) blocks = 4 * dp.sms;
     k_bconv_tc<<<blocks, 32 * TC_WARPS, smem, st>>>(dp, in, k, src_ids, cin, abytes, mp, kp, out, m, dst_ids);
   }
 }

@@ -580,8 +580,8 @@ struct EpiRational {
 // Launchers
 // ---------------------------------------------------------------------------
 
-static int groups_for(int blocks_per_group, int max_groups) {
-  const int want = 2 * 152;  // aim for two blocks per SM
+static int groups_for(int blocks_per_group, int max_groups, int sms) {
+  const int want = 2 * sms;  // aim for two blocks per SM
   int g = (want + blocks_per_group - 1) / blocks_per_group;
   if (g > max_groups) g = max_groups;
   return g < 1 ? 1 : g;
@@ -626,7 +626,7 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
   prof_mark(sc, st, P_MODDOWN_ROWS);
   launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
   prof_mark(sc, st, P_RS_IN_ROWS);
-  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2)), st);
+  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_fwd<G>(dp, T3, EpiRsOut{a, A, a_stride}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, st);
   prof_mark(sc, st, P_RS_ROWS);
@@ -642,7 +642,7 @@ static void merged_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a,
   const int ext = a.n + dp.alpha;
   launch_rows_inv<G>(dp, SrcMerged{a, A, ext}, sc.S, 2 * m.K, LimbMap{m.rows, 0, 0, 0, 0}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  launch_mm_cols<G>(dp, m, sc, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2)), st);
+  launch_mm_cols<G>(dp, m, sc, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
   prof_mark(sc, st, P_RS_COLS);
   LimbMap out_map{nullptr, 0, m.n1, m.n1, dp.L};
   out_map.base = m.s1;
@@ -659,7 +659,7 @@ static void moddown_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a
   launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
                    LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  launch_moddown_cols<G>(dp, n, a.base, a.tix, sc, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
+  launch_moddown_cols<G>(dp, n, a.base, a.tix, sc, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2, dp.sms)), st);
   prof_mark(sc, st, P_MODDOWN_COLS);
   launch_rows_fwd<G>(dp, sc.T, EpiModDown{a, A, a_stride}, 2 * n, window_map(a, dp.L), st);
   prof_mark(sc, st, P_MODDOWN_ROWS);
@@ -687,7 +687,7 @@ void launch_ks_modup(const DevParams& dp0, const Scratch& sc, const KsArgs& a, c
     launch_rows_inv<G>(dp, SrcKsInput{a}, sc.S, a.n, window_map(a, dp.L), true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
     launch_modup_cols<G>(dp, a.n, a.base, a.tix, digits, sc,
-                         pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits)), st);
+                         pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits, dp.sms)), st);
     prof_mark(sc, st, P_MODUP_COLS);
     launch_rows_g<G>(dp, false, sc.T, sc.T, a.rows_cnt, LimbMap{dp.ks.up_rows + a.rows_off, 0, 1, 0, 0}, false, st);
     prof_mark(sc, st, P_MODUP_ROWS);
@@ -721,6 +721,17 @@ void launch_keyswitch(const DevParams& dp0, const Scratch& sc, const KsArgs& a, 
   count_launch(1);
   prof_mark(sc, st, P_KEYMULT);
   if (km_out == KM_KEYSWITCH) launch_ks_tail(dp0, sc, a, sc.A, (size_t)ext * limb, st);
+}
+
+// KeyMult + MAC alone (the unfused form, k_unfused.cu): T the ModUp limbs,
+// A [2][n + alpha][N] the accumulators.
+void launch_keyswitch_keymult_only(const DevParams& dp, const KsArgs& a, const uint32_t* T, uint32_t* A,
+                                   cudaStream_t st) {
+  dim3 g;
+  int th;
+  stream_grid(dp.log_n, a.n + dp.alpha, g, th);
+  launch_keymult(active_digits(a, dp.alpha), g, th, st, dp, a, T, A, KM_KEYSWITCH, nullptr);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,15 +899,15 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
           dp.tune_tensor && dp.ks.tc_img != nullptr && dp.alpha + (k == CK_RS_FUSED ? 1 : 0) <= kTcMaxSources;
       std::function<void(const ColShape&)> run;
       if (k == CK_MODUP) {
-        def = default_shape<G>(digits);
+        def = default_shape<G>(digits, dp.sms);
         targets = n;  // fewest targets of a digit: n + alpha - (digit size)
         run = [&](const ColShape& s) { launch_modup_cols<G>(dp, n, base, tix, digits, sc, s, st); };
       } else if (k == CK_MODDOWN) {
-        def = default_shape<G>(2);
+        def = default_shape<G>(2, dp.sms);
         targets = n;
         run = [&](const ColShape& s) { launch_moddown_cols<G>(dp, n, base, tix, sc, s, st); };
       } else {
-        def = default_shape<G>(2);
+        def = default_shape<G>(2, dp.sms);
         targets = n - 1;
         run = [&](const ColShape& s) {
           launch_rs_cols_fused<G>(dp, n, sc.T + 2 * limb, sc.U, sc.T + 4 * limb, s, st);
@@ -982,7 +993,7 @@ void launch_hoisted_rotations(const DevParams& dp0, const Scratch& sc, const KsA
     launch_rows_g<G>(dp, true, a0.x0 + a0.poly_stride0, sc.S, n, window_map(a0, dp.L), true, st);
     prof_mark(sc, st, P_KS_IN_ROWS);
     launch_modup_cols<G>(dp, n, a0.base, a0.tix, digits, sc,
-                         pick_shape<G>(sc, CK_MODUP, a0.tix, default_shape<G>(digits)), st);
+                         pick_shape<G>(sc, CK_MODUP, a0.tix, default_shape<G>(digits, dp.sms)), st);
     prof_mark(sc, st, P_MODUP_COLS);
     launch_rows_g<G>(dp, false, sc.T, sc.T, a0.rows_cnt, LimbMap{dp.ks.up_rows + a0.rows_off, 0, 1, 0, 0}, false,
                      st);
@@ -1017,7 +1028,7 @@ void launch_linear_transform(const DevParams& dp0, const Scratch& sc, const KsAr
       launch_rows_g<G>(dp, true, a.x0 + a.poly_stride0, sc.S, n, window_map(a, dp.L), true, st);
       prof_mark(sc, st, P_KS_IN_ROWS);
       launch_modup_cols<G>(dp, n, a.base, a.tix, digits, sc,
-                           pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits)), st);
+                           pick_shape<G>(sc, CK_MODUP, a.tix, default_shape<G>(digits, dp.sms)), st);
       prof_mark(sc, st, P_MODUP_COLS);
       launch_rows_g<G>(dp, false, sc.T, sc.T, a.rows_cnt, LimbMap{dp.ks.up_rows + a.rows_off, 0, 1, 0, 0}, false,
                        st);
@@ -1030,7 +1041,7 @@ void launch_linear_transform(const DevParams& dp0, const Scratch& sc, const KsAr
       launch_rows_g<G>(dp, true, sc.A, down.S, 2 * alpha,
                        LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
       prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-      launch_moddown_cols<G>(dp, n, a.base, a.tix, down, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2)), st);
+      launch_moddown_cols<G>(dp, n, a.base, a.tix, down, pick_shape<G>(sc, CK_MODDOWN, a.tix, default_shape<G>(2, dp.sms)), st);
       prof_mark(sc, st, P_MODDOWN_COLS);
       launch_rows_g<G>(dp, false, down.T, down.T, 2 * n, window_map(a, dp.L), false, st);
       prof_mark(sc, st, P_MODDOWN_ROWS);
@@ -1089,7 +1100,7 @@ void launch_rescale(const DevParams& dp, const Scratch& sc, const uint32_t* in, 
     launch_rows_g<G>(dp, true, in, sc.S, 2, LimbMap{nullptr, top, n, n, dp.L, 1, (int)(sin >> dp.log_n)}, true, st);
     prof_mark(sc, st, P_RS_IN_ROWS);
     const int tiles = G::W / G::TC;
-    const int gr = groups_for(tiles * 2, top);
+    const int gr = groups_for(tiles * 2, top, dp.sms);
     launch_pdl(dp.pdl, k_rs_cols<G>, dim3(tiles, 2, gr), dim3(G::CT), 0, st, dp, n, (const uint32_t*)sc.S, sc.T, gr);
     count_launch(1);
     prof_mark(sc, st, P_RS_COLS);

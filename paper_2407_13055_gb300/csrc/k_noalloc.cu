@@ -60,6 +60,14 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int l
                " scratch words exceed the fixed maximum of " + std::to_string(kScratchWords);
     return CKKS_EINVAL;
   }
+  // the array's address is per device: look it up on the context's device,
+  // which must be the current one (its stream and buffers live there)
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device) {
+    ctx->err = "rescale_noalloc: the current device (" + std::to_string(dev) + ") is not the context's device (" +
+               std::to_string(ctx->device) + "); make the context's device current first";
+    return CKKS_EINVAL;
+  }
   uint32_t* base = nullptr;
   const cudaError_t e = scratch_on_current_device(&base);
   if (e != cudaSuccess) {

@@ -3,9 +3,12 @@
 Requests arrive over time (a Poisson process in the benchmark). The host
 scheduler admits a request as soon as (1) its arrival time has passed,
 (2) an execution lane (a context clone with its own CUDA stream and scratch)
-is free, and (3) the device memory the request will hold, its output
-ciphertext, fits in the admission budget next to the requests already in
-flight. Admitted requests run on their lane's stream, so the work of several
+is free, and (3) the device memory the request holds while it runs (its
+input and output ciphertexts and its lane's key-switching scratch,
+ckks_request_bytes) fits in the admission budget next to the resident
+evaluation keys and the requests already in flight; the budget is the
+library's admission pool (ckks_pool_acquire refuses with CKKS_EBUSY).
+Admitted requests run on their lane's stream, so the work of several
 requests overlaps on the GPU; requests that arrive meanwhile are admitted as
 lanes and memory free up. Completion is detected by polling a CUDA event per
 request; latency is completion minus arrival on the host clock.
@@ -62,11 +65,18 @@ class Server:
     lanes: int
     budget_bytes: int
     n: int                       # ring degree N
+    resident_bytes: int = 0      # evaluation keys kept on the device, charged for the server's lifetime
     _streams: list = field(default_factory=list)
     _ctxs: list = field(default_factory=list)
+    _pool: object = None
 
     def __post_init__(self):
         import torch
+        self._pool = self.K.ckks_pool_create(self.budget_bytes)
+        if not self.K.ckks_pool_acquire(self._pool, self.resident_bytes):
+            self.K.ckks_pool_destroy(self._pool)
+            self._pool = None
+            raise ValueError(f"resident bytes {self.resident_bytes} exceed the admission budget {self.budget_bytes}")
         self._streams = [torch.cuda.Stream() for _ in range(self.lanes)]
         self._ctxs = [self.K.ckks_ctx_clone(self.ctx, s.cuda_stream) for s in self._streams]
 
@@ -74,9 +84,13 @@ class Server:
         for c in self._ctxs:
             self.K.ckks_ctx_destroy(c)
         self._ctxs = []
+        if self._pool is not None:
+            self.K.ckks_pool_destroy(self._pool)
+            self._pool = None
 
     def footprint(self, req: Request) -> int:
-        return 2 * (req.level + 1) * self.n * 4
+        op = self.K.CKKS_OP_HMULT if req.op == "hmult" else self.K.CKKS_OP_HROT
+        return self.K.ckks_request_bytes(self.ctx, op, req.level)
 
     def run(self, requests, inputs_for, key_for, out_for):
         """Serve `requests` (sorted by arrival). inputs_for(req) -> (a, b)
@@ -97,12 +111,16 @@ class Server:
                 if s.req is not None and s.event.query():
                     done.append(Done(s.req.rid, s.req.arrival, s.start, now, li))
                     inflight -= s.bytes
+                    K.ckks_pool_release(self._pool, s.bytes)
                     slots[li] = _Slot()
             while pending and pending[0].arrival <= now:
                 req = pending[0]
                 need = self.footprint(req)
+                if need > self.budget_bytes - self.resident_bytes:
+                    raise ValueError(f"request {req.rid} needs {need} bytes, more than the budget leaves "
+                                     f"({self.budget_bytes} - {self.resident_bytes} resident)")
                 free = [li for li, s in enumerate(slots) if s.req is None]
-                if not free or inflight + need > self.budget_bytes:
+                if not free or not K.ckks_pool_acquire(self._pool, need):
                     break
                 pending.popleft()
                 li = free[0]

@@ -24,11 +24,53 @@ def test_kernel_models_sum_their_kinds():
     m = bench.kernel_models()
     for name, v in m.items():
         assert v["modmul"] == sum(v.get(k, 0) for k in ("shoup", "mac", "smr")), name
-    # ModUp columns at dnum = 3: 122 targets, 14 products per coefficient each,
-    # and the column-phase butterflies of 40 inputs + 122 targets
+    # ModUp columns at dnum = 3, n = 40: digits of 14, 14 and 12 primes, each
+    # converted to the n + alpha - alpha_j = 40, 40, 42 limbs outside it, and
+    # the column-phase butterflies of the 40 inputs and 122 targets
     N = 1 << bench.LOG_N
-    assert m["modup_cols"]["mac"] == 122 * N * 14
+    assert bench.digit_sizes(40, 14) == [14, 14, 12]
+    assert m["modup_cols"]["mac"] == (14 * 40 + 14 * 40 + 12 * 42) * N
     assert m["modup_cols"]["shoup"] == (40 + 122) * (N // 2) * 6
+
+
+@pytest.mark.parametrize("n,alpha", [(40, 14), (21, 14), (2, 14), (40, 8), (40, 40), (9, 8)])
+def test_modup_macs_follow_the_digit_sizes(n, alpha):
+    """The ModUp BConv work is sum_j alpha_j (n + alpha - alpha_j) N products,
+    written out digit by digit from the gadget (consecutive groups of alpha
+    ciphertext primes, the last one partial)."""
+    N = 1 << bench.LOG_N
+    primes = list(range(n))
+    digits = [primes[i:i + alpha] for i in range(0, n, alpha)]
+    want = 0
+    for dg in digits:
+        others = (n + alpha) - len(dg)   # every extended limb outside the digit
+        want += len(dg) * others * N
+    for op in ("hmult", "hrot"):
+        assert bench.stage_work(op, n, alpha)["modup_cols"]["mac"] == want
+
+
+def test_moddown_stages_split_hmult_and_hrot():
+    """HRot converts all 2n limbs in ModDown; HMult with the fused rescale
+    converts only the top limb there (the rest in the rescale stages); the
+    per-launch model of a shared stage is the mean of the two."""
+    N, n, a = 1 << bench.LOG_N, 40, 14
+    hm, hr = bench.stage_work("hmult", n, a), bench.stage_work("hrot", n, a)
+    assert hr["moddown_cols"]["mac"] == 2 * n * N * a
+    assert hm["moddown_cols"]["mac"] == 2 * N * a
+    assert hm["rescale_cols"]["mac"] == 2 * (n - 1) * N * (a + 1)
+    assert "rescale_cols" not in hr
+    m = bench.kernel_models(n, a)
+    assert m["moddown_cols"]["mac"] == (hm["moddown_cols"]["mac"] + hr["moddown_cols"]["mac"]) / 2
+    assert m["rescale_cols"]["mac"] == hm["rescale_cols"]["mac"]
+
+
+@pytest.mark.parametrize("alpha", [40, 14, 8])
+def test_stage_bytes_add_up_to_the_operation_bytes(alpha):
+    """The compulsory bytes the stages charge add up to each operation's
+    algorithmic bytes (every input read once, the key stream, the output)."""
+    hm_b, hr_b = bench.algorithmic_bytes(40, alpha)
+    assert sum(v["bytes"] for v in bench.stage_work("hmult", 40, alpha).values()) == hm_b
+    assert sum(v["bytes"] for v in bench.stage_work("hrot", 40, alpha).values()) == hr_b
 
 
 def test_multiply_costs_follow_the_issue_rates():

@@ -89,4 +89,34 @@ def test_null_handles_are_rejected_without_a_gpu(K):
     assert L.ckks_tune(None, 0, 1) == E
     assert L.ckks_sync(None) == E
     assert L.ckks_batch_run(None) == E
+    assert L.ckks_batch_run_admit(None, 0) == E
+    assert L.ckks_batch_admit(None, 0) == E
+    assert L.ckks_set_wait_limit(None, 1) == E
+    assert L.ckks_rescale_noalloc(None, None, 1, None) == E
     assert L.ckks_level_limbs(None, 0) == E
+
+
+def test_admission_pool_refuses_beyond_its_budget(K):
+    """The library's admission pool (host-side): acquisitions within the
+    budget succeed, one that would exceed it returns CKKS_EBUSY and takes
+    nothing, releases return the bytes, over-release is refused."""
+    import ctypes as C
+    L = K.lib
+    h = C.c_void_p()
+    assert L.ckks_pool_create(1000, C.byref(h)) == K.CKKS_OK
+    try:
+        assert L.ckks_pool_acquire(h, 600) == K.CKKS_OK
+        assert L.ckks_pool_acquire(h, 401) == K.CKKS_EBUSY
+        assert L.ckks_pool_in_use(h) == 600
+        assert L.ckks_pool_acquire(h, 400) == K.CKKS_OK
+        assert L.ckks_pool_acquire(h, 1) == K.CKKS_EBUSY
+        assert L.ckks_pool_release(h, 1001) == K.CKKS_EINVAL
+        assert L.ckks_pool_release(h, 1000) == K.CKKS_OK
+        assert L.ckks_pool_in_use(h) == 0
+        assert L.ckks_pool_acquire(h, 1001) == K.CKKS_EBUSY
+        assert L.ckks_pool_acquire(None, 1) == K.CKKS_EINVAL
+        assert L.ckks_set_memory_limit(None, 1) == K.CKKS_EINVAL
+        assert L.ckks_memory_in_use(None) == 0
+        assert L.ckks_request_bytes(None, 1, 0) == 0
+    finally:
+        L.ckks_pool_destroy(h)

@@ -45,28 +45,31 @@ def test_results_same_alone_and_in_the_mix(K, O):
         handles += list(outs.values()) + list(alone.values())
         inputs_for = lambda r: (pool[r.level][0], pool[r.level][1])
         key_for = lambda r: rk if r.op == "hmult" else gks[r.rot]
-        # in the mix: all arrive at once on three lanes; the budget holds two
-        # top-level outputs, so the footprint check limits admission too
-        budget = 2 * 2 * L * P.n * 4
-        srv = Server(K, ctx, 3, budget, P.n)
+        # in the mix: all arrive at once on three lanes; the budget holds the
+        # resident keys and two top-level requests (inputs, output, lane
+        # scratch), so the footprint check limits admission too
+        keys = (len(gks) + 1) * P.dnum * 2 * (L + P.alpha) * P.n * 4
+        top = K.ckks_request_bytes(ctx, K.CKKS_OP_HMULT, L - 1)
+        assert top > 3 * 2 * L * P.n * 4  # more than the input and output ciphertexts: the lane scratch
+        budget = keys + 2 * top
+        srv = Server(K, ctx, 3, budget, P.n, resident_bytes=keys)
         try:
             done = srv.run(reqs, inputs_for, key_for, lambda r, lane: outs[r.rid])
+            fp = {r.rid: srv.footprint(r) for r in reqs}
         finally:
             srv.close()
         assert sorted(d.rid for d in done) == list(range(24))
         # the bytes held by admitted requests never exceeded the budget, and
         # requests did overlap (more than one in flight at some point)
-        level = {r.rid: r.level for r in reqs}
-        fp = lambda rid: 2 * (level[rid] + 1) * P.n * 4
         events = sorted([(d.start, 1, d.rid) for d in done] + [(d.end, -1, d.rid) for d in done],
                         key=lambda e: (e[0], e[1]))
         live = peak = count = max_count = 0
         for _, delta, rid in events:
-            live += delta * fp(rid)
+            live += delta * fp[rid]
             count += delta
             peak = max(peak, live)
             max_count = max(max_count, count)
-        assert peak <= budget and max_count >= 2
+        assert keys + peak <= budget and max_count >= 2
         stats = latency_stats(done)
         assert stats["completed"] == 24 and stats["p99_ms"] >= stats["p50_ms"] > 0
         # alone: one request at a time on the context itself
@@ -84,4 +87,45 @@ def test_results_same_alone_and_in_the_mix(K, O):
     finally:
         for h in handles:
             K.ckks_free(h)
+        K.ckks_ctx_destroy(ctx)
+
+
+def test_memory_limit_refuses_allocations_with_enomem(K, O):
+    """Admission by memory footprint on the device side: with a limit on the
+    bytes a context's objects may hold (shared with its clones), an
+    allocation beyond it fails with CKKS_ENOMEM before any CUDA allocation,
+    freeing an object makes room again, and the request footprint the
+    server admits by covers inputs, output and the lane's scratch."""
+    import torch
+    log_n, L, dnum = 12, 4, 4
+    P = O.make_params(log_n, L, dnum, 1)
+    ctx = K.ckks_ctx_create(log_n, P.q, P.p, dnum, scale=2.0**28)
+    lane = K.ckks_ctx_clone(ctx, torch.cuda.Stream().cuda_stream)
+    held = []
+    try:
+        base = K.ckks_memory_in_use(ctx)
+        held.append(K.ckks_ct_create(ctx, L - 1))
+        one = K.ckks_memory_in_use(ctx) - base
+        assert one == 2 * L * P.n * 4
+        K.ckks_set_memory_limit(ctx, base + one + one // 2)
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_ct_create(ctx, L - 1)
+        assert e.value.code == K.CKKS_ENOMEM
+        with pytest.raises(K.CkksError) as e:
+            K.ckks_ct_create(lane, L - 1)   # the clone shares the budget
+        assert e.value.code == K.CKKS_ENOMEM
+        assert K.ckks_memory_in_use(ctx) == base + one
+        K.ckks_free(held.pop())
+        assert K.ckks_memory_in_use(lane) == base
+        held.append(K.ckks_ct_create(lane, L - 1))
+        K.ckks_set_memory_limit(ctx, 0)
+        held.append(K.ckks_ct_create(ctx, L - 1))
+        ct = 2 * L * P.n * 4
+        assert K.ckks_request_bytes(ctx, K.CKKS_OP_HMULT, L - 1) == 3 * ct + K.lib.ckks_ctx_device_bytes(lane)
+        assert K.ckks_request_bytes(ctx, K.CKKS_OP_HADD, L - 1) == 3 * ct
+        assert K.ckks_request_bytes(ctx, 99, L - 1) == 0
+    finally:
+        for h in held:
+            K.ckks_free(h)
+        K.ckks_ctx_destroy(lane)
         K.ckks_ctx_destroy(ctx)
