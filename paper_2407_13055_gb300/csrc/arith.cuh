@@ -50,6 +50,20 @@ __device__ __forceinline__ int32_t mont_mul(uint32_t a, uint32_t bm, uint32_t q,
   return smr((int64_t)((uint64_t)a * bm), q, m);
 }
 
+// 64-bit sum folded below 2^32 q: lo + hi [2^32]_q (r32 = 2^32 mod q).
+__device__ __forceinline__ uint64_t fold64(uint64_t s, uint32_t r32) {
+  return (uint64_t)(uint32_t)s + (uint64_t)(uint32_t)(s >> 32) * r32;
+}
+
+// Unsigned Montgomery reduction (Montgomery 1985) of s < 2^32 q: s 2^-32 mod
+// q in [0, 2q]; m = q^-1 mod 2^32 (t = -lo q^-1 makes lo + t q = 0 mod 2^32,
+// with a carry exactly when lo != 0).
+__device__ __forceinline__ uint32_t redc64(uint64_t s, uint32_t q, uint32_t m) {
+  const uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32);
+  const uint32_t t = 0u - lo * m;
+  return hi + __umulhi(t, q) + (lo != 0u);
+}
+
 // (-q, q) -> [0, q)
 __device__ __forceinline__ uint32_t fix_signed(int32_t v, uint32_t q) {
   return (uint32_t)(v + ((v >> 31) & (int32_t)q));

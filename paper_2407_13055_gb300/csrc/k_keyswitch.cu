@@ -173,14 +173,28 @@ __device__ __forceinline__ void keymult_quad(const DevParams& dp, const KsArgs& 
     load_vec_stream<4>(e0[j], a.evk + ((size_t)(((g0 + j) * 2 + 0) * ext_top + key_limb) << dp.log_n) + p0);
     load_vec_stream<4>(e1[j], a.evk + ((size_t)(((g0 + j) * 2 + 1) * ext_top + key_limb) << dp.log_n) + p0);
   }
-  uint32_t acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+  // acc_u = sum_j x_j e_j[u] 2^-32 mod q with one reduction per output: the
+  // products (x < 2^31, e < q) are summed in 64 bits, three of them at most
+  // (< 3 2^62) before the sum is folded with 2^32 = mont (mod q) to below
+  // 2^32 q, and again after each further product; one unsigned Montgomery
+  // reduction of the folded sum gives a value below 2q (the key's Montgomery
+  // factor cancels the 2^-32).
+  uint32_t acc0[4], acc1[4];
 #pragma unroll
-  for (int j = 0; j < D; ++j)
+  for (int k = 0; k < 4; ++k) {
+    uint64_t s0 = 0, s1 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      acc0[k] = addm(acc0[k], fix_signed(mont_mul(x[j][k], e0[j][k], P.q, P.m), P.q), P.q);
-      acc1[k] = addm(acc1[k], fix_signed(mont_mul(x[j][k], e1[j][k], P.q, P.m), P.q), P.q);
+    for (int j = 0; j < D; ++j) {
+      s0 += (uint64_t)x[j][k] * e0[j][k];
+      s1 += (uint64_t)x[j][k] * e1[j][k];
+      if (j >= 2) {
+        s0 = fold64(s0, P.mont);
+        s1 = fold64(s1, P.mont);
+      }
     }
+    acc0[k] = csub(csub(redc64(s0, P.q, P.m), P.q), P.q);
+    acc1[k] = csub(csub(redc64(s1, P.q, P.m), P.q), P.q);
+  }
   uint32_t* dst = km_out == KM_ACC_ALL ? km_dst : A;
   store_vec<4>(dst + ((size_t)t << dp.log_n) + p0, acc0);
   store_vec<4>(dst + ((size_t)(ext + t) << dp.log_n) + p0, acc1);
@@ -671,7 +685,7 @@ static DevParams tuned_rows(const DevParams& dp, const Scratch& sc, int tix) {
   DevParams d = dp;
   if (sc.tune) {
     const ColShape s = sc.tune->get(CK_ROWS, tix);
-    if (s.tc == 2 || s.tc == 3) d.rows_passes = s.tc;
+    if (s.tc >= 2 && s.tc <= 5) d.rows_passes = s.tc;
   }
   return d;
 }
@@ -938,7 +952,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
     if constexpr (G::W == 1024) {
       int best_p = 3;
       float best_ms = -1.f;
-      for (int passes : {3, 2}) {
+      for (int passes : {3, 2, 4, 5}) {
         if (rc != CKKS_OK || lvl.rows_cnt < 1) break;
         DevParams dv = dp;
         dv.rows_passes = passes;

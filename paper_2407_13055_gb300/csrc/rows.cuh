@@ -8,6 +8,7 @@
 #include "geo.cuh"
 #include "internal.h"
 #include "pdl.cuh"
+#include "tc.cuh"
 
 namespace ckks {
 
@@ -458,13 +459,144 @@ __global__ void __launch_bounds__(128, 6) k_rows3_inv_t(DevParams dp, Src src, u
   for (int i = 0; i < 16; ++i) o[t + 64 * i] = x[i];
 }
 
+// Three-pass forward rows with the input staged by bulk copies: a block
+// takes RP consecutive row pairs of one limb; the next pairs' 8 KB of input
+// (two contiguous rows) stream into a second shared buffer with
+// cp.async.bulk (one thread issues, an mbarrier counts the bytes) while the
+// current pair is transformed, so the loads' latency overlaps the
+// arithmetic. The staging buffer of a pair also holds its transposes. Every
+// wait is bounded by dp.wait_limit (expired: status word, the block stops
+// after draining its own copies). In-place use (src == the epilogue's
+// destination) is safe: a block reads and writes only its own rows.
+template <class G, class Epi, int RP>
+__global__ void __launch_bounds__(128, 5) k_rows3_fwd_bulk(DevParams dp, const uint32_t* src, Epi epi, LimbMap map) {
+  static_assert(G::W == 1024, "three-pass rows are for W = 1024");
+  __shared__ __align__(128) uint32_t buf[2][2][1024];
+  __shared__ uint2 twa[2][15];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  const uint2* tw = dp.tw + ((size_t)lm.y << dp.log_n);
+  const uint32_t* s0 = src + ((size_t)lm.x << dp.log_n);
+  const int pair0 = blockIdx.x * RP;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&bar[1]), 1);
+    tc::mbar_init_fence();
+  }
+  uint2 tb[7], tc_[2][7];
+  row3_load_twiddles<G::H>(tb, tc_, tw, 2 * pair0 + r, t);
+  row3_stage_a<G::H>(twa[r], tw, 2 * pair0 + r, t);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  uint32_t issued = 0;  // thread 0: copies issued (pair k goes to buffer k & 1)
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2 && k < RP; ++k) {
+      const uint32_t b = tc::smem_u32(&bar[k]);
+      tc::mbar_expect_tx(b, 8192);
+      tc::bulk_g2s(tc::smem_u32(buf[k]), s0 + (size_t)(pair0 + k) * 2048, 8192, b);
+      ++issued;
+    }
+  }
+  uint32_t waited = 0;
+  for (int k = 0; k < RP; ++k) {
+    const int h = 2 * (pair0 + k) + r;
+    if (k > 0) {
+      row3_load_twiddles<G::H>(tb, tc_, tw, h, t);
+      row3_stage_a<G::H>(twa[r], tw, h, t);
+    }
+    const bool ok = tc::mbar_wait(tc::smem_u32(&bar[k & 1]), (uint32_t)((k >> 1) & 1), dp.wait_limit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) tc::report_timeout(dp.status);
+      break;
+    }
+    ++waited;
+    uint32_t* b = buf[k & 1][r];
+    uint32_t x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = b[t + 64 * i];
+    uint32_t y0[8], y1[8];
+    if (q < (1u << 30)) ct_pass_sm<16, true>(x, twa[r], q);
+    else ct_pass_sm<16, false>(x, twa[r], q);
+    __syncthreads();  // every thread read its input before the transposes overwrite it
+#pragma unroll
+    for (int i = 0; i < 16; ++i) b[row3_swz(t + 64 * i)] = x[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      y0[i] = b[row3_swz(row3_eb(t, 0, i))];
+      y1[i] = b[row3_swz(row3_eb(t, 1, i))];
+    }
+    __syncthreads();
+    if (q < (1u << 30)) {
+      ct_pass_reg<8, true>(y0, tb, q);
+      ct_pass_reg<8, true>(y1, tb, q);
+    } else {
+      ct_pass_reg<8, false>(y0, tb, q);
+      ct_pass_reg<8, false>(y1, tb, q);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      b[row3_swz(row3_eb(t, 0, i))] = y0[i];
+      b[row3_swz(row3_eb(t, 1, i))] = y1[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      y0[i] = b[row3_swz(16 * t + i)];
+      y1[i] = b[row3_swz(16 * t + 8 + i)];
+    }
+    // the buffer and the pass-A twiddles are free once every thread has read
+    // them: the next copy into this buffer may start
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0 && k + 2 < RP) {
+      const uint32_t bb = tc::smem_u32(&bar[k & 1]);
+      tc::mbar_expect_tx(bb, 8192);
+      tc::bulk_g2s(tc::smem_u32(buf[k & 1]), s0 + (size_t)(pair0 + k + 2) * 2048, 8192, bb);
+      ++issued;
+    }
+    if (q < (1u << 30)) {
+      ct_pass_reg<8, true>(y0, tc_[0], q);
+      ct_pass_reg<8, true>(y1, tc_[1], q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        x[i] = normalize<true>(y0[i], q);
+        x[8 + i] = normalize<true>(y1[i], q);
+      }
+    } else {
+      ct_pass_reg<8, false>(y0, tc_[0], q);
+      ct_pass_reg<8, false>(y1, tc_[1], q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        x[i] = normalize<false>(y0[i], q);
+        x[8 + i] = normalize<false>(y1[i], q);
+      }
+    }
+    epi(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * 1024 + 16 * t));
+  }
+  // after a timeout: let the copies still in flight land before the block's
+  // shared memory is released
+  if (threadIdx.x == 0)
+    for (uint32_t k = waited; k < issued; ++k)
+      tc::mbar_wait(tc::smem_u32(&bar[k & 1]), (k >> 1) & 1, 1ll << 32);
+}
+
 template <class G, class Epi>
 inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi& epi, int limbs, LimbMap map,
                             cudaStream_t st) {
   if (limbs <= 0) return;
   bool three = false;
   if constexpr (G::W == 1024) {
-    if (dp.rows_passes != 2) {
+    if (dp.rows_passes == 4 || dp.rows_passes == 5) {
+      if (dp.rows_passes == 4)
+        launch_pdl(dp.pdl, k_rows3_fwd_bulk<G, Epi, 2>, dim3(G::H / 4, limbs), dim3(128), 0, st, dp, src, epi, map);
+      else
+        launch_pdl(dp.pdl, k_rows3_fwd_bulk<G, Epi, 4>, dim3(G::H / 8, limbs), dim3(128), 0, st, dp, src, epi, map);
+      three = true;
+    } else if (dp.rows_passes != 2) {
       launch_pdl(dp.pdl, k_rows3_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
       three = true;
     }

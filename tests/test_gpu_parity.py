@@ -509,7 +509,7 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
             tc, sl, z, tp, us = K.ckks_tune_get(ctx, kern, n_q - 1)
             assert tc in (4, 8) and sl in (2, 4, 8) and 1 <= z <= 4 and tp in (1, 2, 8, 16) and us > 0
         passes, _, _, _, us = K.ckks_tune_get(ctx, K.CKKS_ROW_PASSES, n_q - 1)
-        assert passes in (2, 3) and us > 0
+        assert passes in (2, 3, 4, 5) and us > 0
         # a clone shares the table
         import torch
         s = torch.cuda.Stream()
@@ -529,9 +529,11 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
 
 @pytest.mark.parametrize("n_q", [40, 5])
 def test_row_phase_forms_give_identical_results(K, O, n_q):
-    """Both forms of the N = 2^16 row phase the tuner chooses between (two
-    register passes of radix 2^5, or three of 2^4 x 2^3 x 2^3) reproduce the
-    oracle bit for bit: HMult+rescale, HRot and hoisted rotations."""
+    """Every form of the N = 2^16 row phase the tuner chooses between (two
+    register passes of radix 2^5, three of 2^4 x 2^3 x 2^3, and the three-pass
+    form with its forward rows staged by bulk copies, 2 or 4 row pairs per
+    block) reproduces the oracle bit for bit: HMult+rescale, HRot and hoisted
+    rotations."""
     ctx, P = get(K, O, "n16d3")
     c1, c2 = rand_ct(P, n_q, 91), rand_ct(P, n_q, 93)
     evk = rand_evk(P, 95)
@@ -542,7 +544,7 @@ def test_row_phase_forms_give_identical_results(K, O, n_q):
     ek = K.ckks_evk_import(ctx, evk, k)
     outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in range(2)]
     try:
-        for passes in (2, 3):
+        for passes in (2, 3, 4, 5):
             K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, passes, 1, 1, 1)
             got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
             assert np.array_equal(got, want_m), passes
@@ -552,7 +554,7 @@ def test_row_phase_forms_give_identical_results(K, O, n_q):
             for o in outs:
                 assert np.array_equal(K.ckks_ct_export(ctx, o, P.n)[0], want_r), passes
         with pytest.raises(K.CkksError):
-            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 4, 1, 1, 1)
+            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 6, 1, 1, 1)
     finally:
         K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
         for h in [a, ek] + outs:
