@@ -144,9 +144,10 @@ def multiply_costs(rates):
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "044eb525937d426618e82dda000646a76bc1927e",
-    "bytes_per_launch": {"modup_cols": 10.74e6, "keymult": 137.27e6, "modup_rows": 60.94e6,
-                         "moddown_cols": 7.40e6, "moddown_rows": 76.79e6},
+    "sources_sha1": "c969e2343adaf4d20f312ae79208845cd459e89f",
+    "bytes_per_launch": {"modup_cols": 10.62e6, "keymult": 143.04e6, "modup_rows": 60.38e6,
+                         "moddown_cols": 7.40e6, "moddown_rows": 74.94e6, "rescale_cols": 7.92e6,
+                         "rescale_rows": 115.89e6, "ks_in_rows": 37.47e6},
 }
 
 
@@ -174,17 +175,30 @@ def ncu_traffic(stage):
     return NCU_TRAFFIC["bytes_per_launch"].get(stage)
 
 
+FORCED = {"col_shape": None, "row_passes": None}   # set from --col-shape / --row-passes
+
+
 def tune_levels(K, ctx, levels, enabled, reps=3):
     """Run the fine-tuner at each level (outside any timed region) and return
     the chosen column shapes and row-phase passes {level: {kernel: (tc, sl, z,
-    tp, us)}} (row_passes: tc = passes)."""
-    if not enabled:
-        return None
+    tp, us)}} (row_passes: tc = passes). A shape or row form given on the
+    command line replaces the tuner's choice for every level."""
     names = {K.CKKS_COL_MODUP: "modup_cols", K.CKKS_COL_MODDOWN: "moddown_cols", K.CKKS_COL_RS_FUSED: "rescale_cols",
              K.CKKS_ROW_PASSES: "row_passes"}
+    forced = FORCED["col_shape"] is not None or FORCED["row_passes"] is not None
+    if not enabled and not forced:
+        return None
     out = {}
     for lv in sorted(set(int(x) for x in levels)):
-        K.ckks_tune(ctx, lv, reps)
+        if enabled:
+            K.ckks_tune(ctx, lv, reps)
+        if FORCED["col_shape"] is not None:
+            for k in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
+                if k == K.CKKS_COL_RS_FUSED and lv < 1:
+                    continue
+                K.ckks_tune_set(ctx, k, lv, *FORCED["col_shape"])
+        if FORCED["row_passes"] is not None:
+            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, lv, FORCED["row_passes"], 1, 1, 1)
         out[lv] = {nm: K.ckks_tune_get(ctx, k, lv) for k, nm in names.items()}
     return out
 
@@ -478,7 +492,7 @@ def run_native(args, rank, world, local_rank):
     # events ordering the stages, so copies overlap the computation.
     n = 1 << LOG_N
     nl = args.lanes
-    NS = 2
+    NS = args.e2e_slots
     pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     host_in = [pinned((2, L, n)) for _ in range(E2E_HOST)]
     for i in range(E2E_HOST):
@@ -529,8 +543,8 @@ def run_native(args, rank, world, local_rank):
            "h2d_bytes_per_step": e2e_pairs * 2 * ct_bytes,
            "d2h_bytes_per_step": e2e_pairs * (ct_bytes * (L - 1) // L + ct_bytes),
            "ops_per_step": 2 * e2e_pairs,
-           "note": f"{nl} lanes, each pair's inputs uploaded from and results read back to pinned host "
-                   "memory; upload / compute / export pipelined on separate streams, wall clock"}
+           "note": f"{nl} lanes x {NS} buffer slots, each pair's inputs uploaded from and results read back to "
+                   "pinned host memory; upload / compute / export pipelined on separate streams, wall clock"}
     for grp in (dev_a, dev_b, dev_m, dev_r):
         for row in grp:
             for h in row:
@@ -1264,10 +1278,20 @@ def main():
                     help="single workload: how the timed step's operations are issued")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="resident ciphertexts per step of the single-op workload (smaller only for profiling)")
+    ap.add_argument("--col-shape", default=None,
+                    help="tc,sl,z,tp: use this launch shape for the three column kernels at every level instead "
+                         "of the tuner's (tp 8/16: tensor-core BConv)")
+    ap.add_argument("--row-passes", type=int, default=None, choices=[2, 3, 4, 5],
+                    help="N=2^16 row-phase form instead of the tuner's (4, 5: forward rows staged by bulk copies)")
+    ap.add_argument("--e2e-slots", type=int, default=2,
+                    help="buffer slots per lane of the end-to-end upload / compute / export pipeline")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",
                     help="programmatic dependent launch for the key-switch kernels")
     args = ap.parse_args()
     BATCH = args.batch
+    if args.col_shape:
+        FORCED["col_shape"] = tuple(int(x) for x in args.col_shape.split(","))
+    FORCED["row_passes"] = args.row_passes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
