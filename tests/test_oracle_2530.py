@@ -199,3 +199,126 @@ def _decrypt_window(O, P, s, ct, base, n, scale):
     coef = O.intt(m.astype(np.uint32), primes)
     big = O.crt_centered(coef, primes)
     return O.decode_coeffs(np.array([float(b) for b in big]), scale, P.log_n)
+
+
+# ---------------------------------------------------------------------------
+# Hybrid key switching on a window q[s .. s+n) that does not start at prime 0
+# (the levels of the 25-30 system, Table 2). The digits are the fixed groups of
+# alpha consecutive primes of the whole list (Sec. 2.3 with the level's window
+# cut out of them), so a window starting inside a group opens with a partial
+# digit; the evaluation key of a digit is the one of its global group. These
+# pins recompute the cut from the global prime index and check each step with
+# big-integer CRT arithmetic.
+
+def _prod(ps):
+    r = 1
+    for v in ps:
+        r *= int(v)
+    return r
+
+
+def _crt(res, primes):
+    Q = _prod(primes)
+    x = 0
+    for r, qi in zip(res, primes):
+        qi = int(qi)
+        qh = Q // qi
+        x += int(r) * qh * pow(qh % qi, -1, qi)
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+def _cent(v, m):
+    v %= m
+    return v - m if v > m // 2 else v
+
+
+def _groups(P, s, n):
+    """Global digit index of each window limb, and the active digits in order."""
+    g = [(s + t) // P.alpha for t in range(n)]
+    return g, sorted(set(g))
+
+
+# (alpha, level window): windows opening inside a group, on a group boundary,
+# and with a first global digit above 0 (alpha = 2, 3, 4), so that a cut taken
+# relative to the window or a key indexed by the window's digit number differs.
+WINDOWS = [(5, (2, 2)), (5, (4, 7)), (5, (1, 13)), (4, (4, 3)), (3, (4, 7)), (3, (2, 11)), (2, (3, 9))]
+
+
+@pytest.mark.parametrize("alpha,lv", WINDOWS)
+def test_windowed_modup_cuts_digits_at_global_groups(O, alpha, lv):
+    """ModUp on a window: digit j copies the window limbs of global group g_j
+    and converts them (Eq. 2, centered) to every other window prime and P; the
+    converted value is X + u*Q_j with |u| <= |group|/2."""
+    P, _ = O.prime_system_2530(5, alpha)
+    s, n = lv
+    g, active = _groups(P, s, n)
+    assert P.digits(n, s) == len(active)
+    rng = np.random.default_rng(60 + alpha * 256 + s * 16 + n)
+    win = [int(v) for v in P.q[s:s + n]]
+    ext = win + [int(v) for v in P.p]
+    d = np.stack([rng.integers(0, q, P.n) for q in win]).astype(np.uint32)
+    up = O.modup(P, d, n, base=s)
+    assert up.shape == (len(active), n + P.alpha, P.n)
+    coef = O.intt(d, win)
+    for j, gj in enumerate(active):
+        own = [t for t in range(n) if g[t] == gj]
+        assert (up[j, own] == d[own]).all()
+        others = [t for t in range(n + P.alpha) if t not in own]
+        src = [win[t] for t in own]
+        dst = [ext[t] for t in others]
+        Qs = _prod(src)
+        out = O.intt(up[j][others], np.array(dst, np.uint32))
+        for c in range(0, P.n, 3):
+            X = _crt([int(coef[t, c]) for t in own], src)
+            us = {_cent((int(out[i, c]) - X) * pow(Qs % dt, -1, dt), dt) for i, dt in enumerate(dst)}
+            assert len(us) == 1
+            assert abs(us.pop()) <= len(own) / 2
+
+
+@pytest.mark.parametrize("alpha,lv", WINDOWS)
+def test_windowed_keymult_uses_the_global_digit_key(O, alpha, lv):
+    """KeyMult on a window: limb t of the window takes key limb s+t, limb k of
+    P takes key limb L+k, and digit j multiplies the key of global group g_j."""
+    P, _ = O.prime_system_2530(5, alpha)
+    s, n = lv
+    _, active = _groups(P, s, n)
+    rng = np.random.default_rng(80 + alpha * 256 + s * 16 + n)
+    ext = [int(v) for v in P.q[s:s + n]] + [int(v) for v in P.p]
+    up = np.stack([np.stack([rng.integers(0, q, P.n) for q in ext]) for _ in active]).astype(np.uint32)
+    allp = [int(v) for v in P.all_primes()]
+    evk = np.stack([np.stack([np.stack([rng.integers(0, q, P.n) for q in allp]) for _ in range(2)])
+                    for _ in range(P.dnum)]).astype(np.uint32)
+    acc = O.keymult(P, up, n, evk, base=s)
+    key = [s + t for t in range(n)] + [P.L + k for k in range(P.alpha)]
+    for t in range(2):
+        for li, kl in enumerate(key):
+            tot = np.zeros(P.n, dtype=object)
+            for j, gj in enumerate(active):
+                tot = tot + up[j, li].astype(object) * evk[gj, t, kl].astype(object)
+            assert [int(v) % ext[li] for v in tot] == acc[t, li].tolist()
+
+
+@pytest.mark.parametrize("alpha,lv", WINDOWS)
+def test_windowed_moddown_is_division_by_p(O, alpha, lv):
+    """ModDown on a window: out = (A - BConv(A mod P)) / P over the window's
+    primes, i.e. round(A / P) up to the conversion's |u| <= alpha/2 multiples
+    of the window modulus."""
+    P, _ = O.prime_system_2530(5, alpha)
+    s, n = lv
+    rng = np.random.default_rng(100 + alpha * 256 + s * 16 + n)
+    win = [int(v) for v in P.q[s:s + n]]
+    pp = [int(v) for v in P.p]
+    ext = win + pp
+    acc = np.stack([np.stack([rng.integers(0, q, P.n) for q in ext]) for _ in range(2)]).astype(np.uint32)
+    out = O.moddown(P, acc, n, base=s)
+    Pp, Q = _prod(pp), _prod(win)
+    for t in range(2):
+        ca = O.intt(acc[t], np.array(ext, np.uint32))
+        co = O.intt(out[t], np.array(win, np.uint32))
+        for c in range(0, P.n, 3):
+            A = _crt([int(v) for v in ca[:, c]], ext)
+            XP = _crt([int(v) for v in ca[n:, c]], pp)
+            assert (A - XP) % Pp == 0
+            o = _crt([int(v) for v in co[:, c]], win)
+            assert abs(_cent((A - XP) // Pp - o, Q)) <= P.alpha / 2
