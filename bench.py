@@ -31,6 +31,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2407_13055_gb300 import tune_cache  # noqa: E402  (host-side file of tuned shapes)
+
 LOG_N, L, DNUM, ALPHA, HW, SCALE = 16, 40, 3, 14, 192, 2.0**30
 LEVEL = L - 1
 BATCH = 256          # distinct resident ciphertexts per timed step (5.4 GB, far above L2)
@@ -176,22 +178,31 @@ def ncu_traffic(stage):
 
 
 FORCED = {"col_shape": None, "row_passes": None}   # set from --col-shape / --row-passes
+# per-GPU file of tuned shapes (tune_cache.TuneStore) and what tune_levels did with it
+TUNE = {"store": None, "retune": False, "loaded": 0, "tuned": 0}
 
 
-def tune_levels(K, ctx, levels, enabled, reps=3):
-    """Run the fine-tuner at each level (outside any timed region) and return
-    the chosen column shapes and row-phase passes {level: {kernel: (tc, sl, z,
-    tp, us)}} (row_passes: tc = passes). A shape or row form given on the
-    command line replaces the tuner's choice for every level."""
+def tune_levels(K, ctx, levels, enabled, reps=3, pkey=None):
+    """Set the fine-tuner's shapes at each level (outside any timed region) and
+    return the chosen column shapes and row-phase passes {level: {kernel: (tc,
+    sl, z, tp, us)}} (row_passes: tc = passes). Levels found in the per-GPU
+    tune file under the parameter key `pkey` are set from it; the others are
+    tuned and written to it. A shape or row form given on the command line
+    replaces the tuner's choice for every level."""
     names = {K.CKKS_COL_MODUP: "modup_cols", K.CKKS_COL_MODDOWN: "moddown_cols", K.CKKS_COL_RS_FUSED: "rescale_cols",
              K.CKKS_ROW_PASSES: "row_passes"}
     forced = FORCED["col_shape"] is not None or FORCED["row_passes"] is not None
     if not enabled and not forced:
         return None
+    levels = sorted(set(int(x) for x in levels))
+    stored = {}
+    if enabled:
+        store = TUNE["store"] if pkey is not None else None
+        stored, loaded, tuned = tune_cache.tune_or_load(K, ctx, levels, pkey, store, reps, TUNE["retune"])
+        TUNE["loaded"] += len(loaded)
+        TUNE["tuned"] += len(tuned)
     out = {}
-    for lv in sorted(set(int(x) for x in levels)):
-        if enabled:
-            K.ckks_tune(ctx, lv, reps)
+    for lv in levels:
         if FORCED["col_shape"] is not None:
             for k in (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED):
                 if k == K.CKKS_COL_RS_FUSED and lv < 1:
@@ -200,7 +211,28 @@ def tune_levels(K, ctx, levels, enabled, reps=3):
         if FORCED["row_passes"] is not None:
             K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, lv, FORCED["row_passes"], 1, 1, 1)
         out[lv] = {nm: K.ckks_tune_get(ctx, k, lv) for k, nm in names.items()}
+        if not forced and lv in stored:
+            out[lv] = stored[lv]
     return out
+
+
+def open_tune_store(args, device):
+    """The per-GPU file of tuned shapes (--tune-file, else $CKKS_TUNE_CACHE,
+    else one file per GPU in the user's cache folder); none with --no-tune or
+    --tune-file none."""
+    if args.no_tune or (args.tune_file or "").lower() == "none":
+        return
+    gpu = tune_cache.gpu_identity(device)
+    TUNE["store"] = tune_cache.TuneStore(args.tune_file or tune_cache.default_path(gpu), gpu)
+    TUNE["retune"] = bool(args.retune)
+
+
+def tune_file_summary():
+    st = TUNE["store"]
+    if st is None:
+        return None
+    return {"path": st.path, "levels_loaded": TUNE["loaded"], "levels_tuned": TUNE["tuned"],
+            "kernels_digest": st.digest}
 
 
 def measured_peaks():
@@ -402,7 +434,7 @@ def run_native(args, rank, world, local_rank):
     lanes = [ctx] + [K.ckks_ctx_clone(ctx, s_.cuda_stream) for s_ in streams[1:]]
     outs_m = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
     outs_r = [K.ckks_ct_create(ctx, LEVEL) for _ in lanes]
-    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune)
+    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune, pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
 
     def step(n_lanes):
         for i in range(BATCH):
@@ -626,7 +658,8 @@ def run_native(args, rank, world, local_rank):
                                              "python": "one binding call per operation"}[args.issue],
                                    "programmatic_dependent_launch": args.pdl,
                                    "column_shapes": ({k: list(v) for k, v in tuned[LEVEL].items()} if tuned
-                                                     else "default rule")}),
+                                                     else "default rule"),
+                                   "tune_file": tune_file_summary()}),
         "one_lane": {"value": seq_ops_per_s, "unit": UNIT, "hmult_rescale_us": hmult_us, "hrot_us": hrot_us,
                      "note": "same workload issued in order on one stream; stage times from its CUDA events"},
         "roofline": roof, "op_roofline": op_hbm, "stages": stage,
@@ -764,7 +797,8 @@ def run_batched(args, local_rank):
     sk = K.ckks_keygen_secret(ctx, 11)
     rk = K.ckks_keygen_relin(ctx, sk, 12)
     gk = K.ckks_keygen_rot(ctx, sk, 1, 13)
-    tuned = tune_levels(K, ctx, inputs.level_list(7, 64, L - 1), not args.no_tune, reps=2)
+    tuned = tune_levels(K, ctx, inputs.level_list(7, 64, L - 1), not args.no_tune, reps=2,
+                        pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
     modes = BATCHED_MODES + (("lanes4_direct", 4, 0), ("lanes4_persistent_direct", 4, 2))
     results = batched_modes(K, ctx, sk, rk, gk, args.steps, args.warmup, stream, modes)
     line = {"metric": "batched mixed-level ops/sec at N=2^16 (1 GB300)", "value": results["lanes4_graph"]["ops_s"],
@@ -805,8 +839,7 @@ def run_latency(args, local_rank):
         rk = K.ckks_keygen_relin(ctx, sk, 62)
         gks = {r: K.ckks_keygen_rot(ctx, sk, r, 63 + r % 1000) for r in (1, 5, r_rand)}
         for level in (L - 1, 20, 1):
-            if not args.no_tune:
-                K.ckks_tune(ctx, level, 3)
+            tune_levels(K, ctx, [level], not args.no_tune, 3, tune_cache.params_key(LOG_N, q, p, dnum))
             a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(64, (1 << LOG_N) // 2), level, SCALE), 65)
             b = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(66, (1 << LOG_N) // 2), level, SCALE), 67)
             out = K.ckks_ct_create(ctx, level)
@@ -894,8 +927,7 @@ def run_rns2530(args, local_rank):
         return float(np.median(ts))
 
     for lv in range(len(levels)):
-        if not args.no_tune:
-            K.ckks_tune(ctx, lv, 3)
+        tune_levels(K, ctx, [lv], not args.no_tune, 3, tune_cache.params_key(LOG_N, q, p, dnum, levels))
         delta = 2.0 ** (55 if lv >= 5 else 40)
         a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(84, (1 << LOG_N) // 2), lv, delta), 85)
         out = K.ckks_ct_create(ctx, lv)
@@ -976,8 +1008,7 @@ def run_ablation(args, local_rank):
     # a separate rescale (top level, one stream, median of 50)
     sk = K.ckks_keygen_secret(ctx, 71)
     rk = K.ckks_keygen_relin(ctx, sk, 72)
-    if not args.no_tune:
-        K.ckks_tune(ctx, LEVEL, 3)
+    tune_levels(K, ctx, [LEVEL], not args.no_tune, 3, pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
     a = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(73, (1 << LOG_N) // 2), LEVEL, SCALE), 74)
     b = K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(75, (1 << LOG_N) // 2), LEVEL, SCALE), 76)
     mid, out = K.ckks_ct_create(ctx, LEVEL), K.ckks_ct_create(ctx, LEVEL)
@@ -1042,7 +1073,7 @@ def run_hoisted(args, local_rank):
     cts = [K.ckks_encrypt(ctx, sk, K.ckks_encode(ctx, inputs.messages(600 + i, (1 << LOG_N) // 2), LEVEL, SCALE),
                           700 + i) for i in range(4)]
     outs = [K.ckks_ct_create(ctx, LEVEL) for _ in rots]
-    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune)
+    tuned = tune_levels(K, ctx, [LEVEL], not args.no_tune, pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
     # linear transform sum_{r=0..32} d_r (.) HRot(ct, r): extended diagonals
     lt_rots = [0] + rots
     lt_keys = [None] + gks
@@ -1123,7 +1154,8 @@ def run_bootstrap(args, local_rank):
     u = inputs.messages(52, slots)
     pt = K.ckks_encode(ctx, u, LEVEL, SCALE)
     ct = K.ckks_encrypt(ctx, sk, pt, 53)
-    tuned = tune_levels(K, ctx, range(LEVEL - spec.levels_used(), LEVEL + 1), not args.no_tune, reps=2)
+    tuned = tune_levels(K, ctx, range(LEVEL - spec.levels_used(), LEVEL + 1), not args.no_tune, reps=2,
+                         pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
     tr = Trace(K, ctx, spec, LEVEL, q, slots, sk=sk)
     want = expected(spec, u)
     res = {}
@@ -1240,7 +1272,8 @@ def run_serve(args, local_rank):
     K.ckks_set_launch_flags(ctx, K.CKKS_LAUNCH_PDL if args.pdl == "on" else 0)
     sk = K.ckks_keygen_secret(ctx, 21)
     rk = K.ckks_keygen_relin(ctx, sk, 22)
-    tuned = tune_levels(K, ctx, range(1, L), not args.no_tune, reps=2)
+    tuned = tune_levels(K, ctx, range(1, L), not args.no_tune, reps=2,
+                        pkey=tune_cache.params_key(LOG_N, q, p, DNUM))
     count = args.requests
     results, capacity, resident = serve_runs(K, ctx, sk, rk, stream, count, (0.5, 0.8, 0.95))
     best = results["continuous_batching_4_lanes@0.95"]
@@ -1274,6 +1307,11 @@ def main():
     ap.add_argument("--requests-default", type=int, default=1000,
                     help="requests of the served run reported in the default line")
     ap.add_argument("--no-tune", action="store_true", help="use the default column-kernel launch shapes")
+    ap.add_argument("--tune-file", default=None,
+                    help="JSON file of tuned launch shapes for this GPU (default: $CKKS_TUNE_CACHE, else one file "
+                         "per GPU under ~/.cache/paper_2407_13055_gb300; 'none': tune every run, keep nothing)")
+    ap.add_argument("--retune", action="store_true",
+                    help="tune every level again and overwrite its entries in the tune file")
     ap.add_argument("--issue", choices=["graph", "direct", "python"], default="graph",
                     help="single workload: how the timed step's operations are issued")
     ap.add_argument("--batch", type=int, default=BATCH,
@@ -1298,6 +1336,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    open_tune_store(args, local_rank)
     if args.workload == "batched":
         run_batched(args, local_rank)
         return

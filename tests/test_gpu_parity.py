@@ -527,6 +527,37 @@ def test_tune_records_a_shape_and_keeps_results(K, O):
         K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
 
 
+def test_tune_file_round_trip(K, O, tmp_path):
+    """Shapes tuned on one context and written to the GPU's tune file are set
+    on the next context from the file, without timing, and keep the results."""
+    import torch
+    from paper_2407_13055_gb300 import tune_cache
+    ctx, P = get(K, O, "n16d3")
+    n_q = 21
+    gpu = tune_cache.gpu_identity(torch.cuda.current_device())
+    assert gpu["sms"] > 0 and gpu["cc"]
+    path = str(tmp_path / "tune.json")
+    pkey = tune_cache.params_key(P.log_n, P.q, P.p, P.dnum)
+    levels = [n_q - 1]
+    try:
+        first, loaded, tuned = tune_cache.tune_or_load(K, ctx, levels, pkey, tune_cache.TuneStore(path, gpu), reps=2)
+        assert loaded == [] and tuned == levels
+        for kid in tune_cache.kernel_names(K).values():
+            K.ckks_tune_set(ctx, kid, n_q - 1, 0, 1, 1, 1)
+        again, loaded, tuned = tune_cache.tune_or_load(K, ctx, levels, pkey, tune_cache.TuneStore(path, gpu), reps=2)
+        assert loaded == levels and tuned == []
+        for name, kid in tune_cache.kernel_names(K).items():
+            assert K.ckks_tune_get(ctx, kid, n_q - 1)[:4] == first[n_q - 1][name][:4], name
+        assert again[n_q - 1]["modup_cols"][4] == pytest.approx(first[n_q - 1]["modup_cols"][4], abs=1e-3)
+        c1, c2 = rand_ct(P, n_q, 91), rand_ct(P, n_q, 93)
+        evk = rand_evk(P, 95)
+        got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
+        assert np.array_equal(got, O.hmult(P, c1, c2, evk, rescale=True))
+    finally:
+        _set_all(K, ctx, n_q - 1, (0, 4, 1, 1))
+        K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
+
+
 @pytest.mark.parametrize("n_q", [40, 5])
 def test_row_phase_forms_give_identical_results(K, O, n_q):
     """Every form of the N = 2^16 row phase the tuner chooses between (two
