@@ -516,15 +516,20 @@ def run_native(args, rank, world, local_rank):
     hmult_us = 1e3 * sum(per_launch[k] for k in hm_stages)
     hrot_us = 1e3 * sum(per_launch[k] for k in hm_stages[:9])
 
-    # end to end through the C ABI with host buffers: every pair's two input
-    # ciphertexts are copied from pinned host memory and its two results read
-    # back to pinned host memory, as a three-stage pipeline per lane: uploads
-    # on a transfer-only clone context, HMult + HRot on the lane, exports on a
-    # second transfer-only clone, with two buffer slots per lane and CUDA
-    # events ordering the stages, so copies overlap the computation.
+    # end to end through the C ABI with host buffers. A step is e2e_pairs pairs
+    # over e2e_pairs + 1 input ciphertexts (pair i: HMult(ct_i, ct_i+1) + rescale,
+    # HRot(ct_i), as in the device-resident step); each input is copied once from
+    # pinned host memory into a ring of device buffers, and both results of every
+    # pair are read back to pinned host memory. Uploads (on transfer-only clone
+    # contexts), the pairs (on the lanes) and the exports (on a second set of
+    # transfer-only clones) form a pipeline ordered by CUDA events, so copies
+    # overlap the computation: an upload waits for the two pairs that read its
+    # buffer's previous ciphertext, a pair for its two uploads and for the export
+    # of its output slot's previous results.
     n = 1 << LOG_N
     nl = args.lanes
     NS = args.e2e_slots
+    R = NS * nl + 2                       # device input buffers (ring)
     pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     host_in = [pinned((2, L, n)) for _ in range(E2E_HOST)]
     for i in range(E2E_HOST):
@@ -533,29 +538,47 @@ def run_native(args, rank, world, local_rank):
     dn_s = [torch.cuda.Stream() for _ in range(nl)]
     up_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in up_s]
     dn_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in dn_s]
+    dev_in = [K.ckks_ct_create(ctx, LEVEL) for _ in range(R)]
     slot = lambda: [[K.ckks_ct_create(ctx, LEVEL) for _ in range(NS)] for _ in range(nl)]
-    dev_a, dev_b, dev_m, dev_r = slot(), slot(), slot(), slot()
+    dev_m, dev_r = slot(), slot()
     host_m = [[pinned((2, L - 1, n)) for _ in range(NS)] for _ in range(nl)]
     host_r = [[pinned((2, L, n)) for _ in range(NS)] for _ in range(nl)]
     ev = lambda: [[torch.cuda.Event() for _ in range(NS)] for _ in range(nl)]
-    ev_up, ev_comp, ev_dn = ev(), ev(), ev()
+    ev_comp, ev_dn = ev(), ev()
+    ev_in = [torch.cuda.Event() for _ in range(R)]        # upload into the buffer done
+    ev_use = [[torch.cuda.Event() for _ in range(R)] for _ in range(2)]   # read as a / as b done
     for l in range(nl):
         for k in range(NS):
-            ev_comp[l][k].record(stream)
             ev_dn[l][k].record(stream)
+    for b in range(R):
+        ev_use[0][b].record(stream)
+        ev_use[1][b].record(stream)
     e2e_pairs = 4 * E2E_HOST
+    uploads = [0]                          # next upload's global index
+
+    def upload():
+        u = uploads[0]
+        uploads[0] += 1
+        b, l = u % R, u % nl
+        up_s[l].wait_event(ev_use[0][b])
+        up_s[l].wait_event(ev_use[1][b])
+        K.ckks_ct_upload_async(up_c[l], dev_in[b], host_in[u % E2E_HOST], LEVEL, SCALE)
+        ev_in[b].record(up_s[l])
+        return b
 
     def e2e_step():
+        nxt = upload()
         for i in range(e2e_pairs):
             l, k = i % nl, (i // nl) % NS
-            up_s[l].wait_event(ev_comp[l][k])
-            K.ckks_ct_upload_async(up_c[l], dev_a[l][k], host_in[i % E2E_HOST], LEVEL, SCALE)
-            K.ckks_ct_upload_async(up_c[l], dev_b[l][k], host_in[(i + 1) % E2E_HOST], LEVEL, SCALE)
-            ev_up[l][k].record(up_s[l])
-            streams[l].wait_event(ev_up[l][k])
+            ba, bb = nxt, upload()
+            nxt = bb
+            streams[l].wait_event(ev_in[ba])
+            streams[l].wait_event(ev_in[bb])
             streams[l].wait_event(ev_dn[l][k])
-            K.ckks_hmult(lanes[l], dev_a[l][k], dev_b[l][k], rk, K.CKKS_RESCALE, dev_m[l][k])
-            K.ckks_hrot(lanes[l], dev_a[l][k], 1, gk, dev_r[l][k])
+            K.ckks_hmult(lanes[l], dev_in[ba], dev_in[bb], rk, K.CKKS_RESCALE, dev_m[l][k])
+            K.ckks_hrot(lanes[l], dev_in[ba], 1, gk, dev_r[l][k])
+            ev_use[0][ba].record(streams[l])
+            ev_use[1][bb].record(streams[l])
             ev_comp[l][k].record(streams[l])
             dn_s[l].wait_event(ev_comp[l][k])
             K.ckks_ct_export_async(dn_c[l], dev_m[l][k], host_m[l][k])
@@ -572,12 +595,15 @@ def run_native(args, rank, world, local_rank):
     e2e_dt = replicas.max_over_ranks(time.perf_counter() - t0)
     ct_bytes = 2 * L * n * 4
     e2e = {"value": replicas.job_throughput(2 * e2e_pairs * e2e_steps, 1e3 * e2e_dt, world), "unit": UNIT,
-           "h2d_bytes_per_step": e2e_pairs * 2 * ct_bytes,
+           "h2d_bytes_per_step": (e2e_pairs + 1) * ct_bytes,
            "d2h_bytes_per_step": e2e_pairs * (ct_bytes * (L - 1) // L + ct_bytes),
            "ops_per_step": 2 * e2e_pairs,
-           "note": f"{nl} lanes x {NS} buffer slots, each pair's inputs uploaded from and results read back to "
+           "note": f"{nl} lanes x {NS} output slots, {R} input buffers; each step's {e2e_pairs + 1} input "
+                   "ciphertexts uploaded once from pinned host memory, both results of every pair read back to "
                    "pinned host memory; upload / compute / export pipelined on separate streams, wall clock"}
-    for grp in (dev_a, dev_b, dev_m, dev_r):
+    for h in dev_in:
+        K.ckks_free(h)
+    for grp in (dev_m, dev_r):
         for row in grp:
             for h in row:
                 K.ckks_free(h)
@@ -1319,8 +1345,9 @@ def main():
     ap.add_argument("--col-shape", default=None,
                     help="tc,sl,z,tp: use this launch shape for the three column kernels at every level instead "
                          "of the tuner's (tp 8/16: tensor-core BConv)")
-    ap.add_argument("--row-passes", type=int, default=None, choices=[2, 3, 4, 5],
-                    help="N=2^16 row-phase form instead of the tuner's (4, 5: forward rows staged by bulk copies)")
+    ap.add_argument("--row-passes", type=int, default=None, choices=[2, 3, 4, 5, 6],
+                    help="N=2^16 row-phase form instead of the tuner's (4, 5: forward rows staged by bulk copies; "
+                         "6: twiddles in shared memory)")
     ap.add_argument("--e2e-slots", type=int, default=2,
                     help="buffer slots per lane of the end-to-end upload / compute / export pipeline")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",

@@ -437,7 +437,13 @@ int ckks_set_wait_limit(ckks_ctx* ctx, long long cycles);
  * switches. tc = 4 and 5 select the three-pass form whose forward rows take
  * 2 (4) and 4 (5) row pairs per block and stage each pair's input in shared
  * memory with bulk copies (cp.async.bulk) that overlap the previous pair's
- * arithmetic (bounded waits, see ckks_set_wait_limit). Without an entry: 3. */
+ * arithmetic (bounded waits, see ckks_set_wait_limit). tc = 6 selects the
+ * three-pass form with the second and third passes' twiddles copied into
+ * shared memory by asynchronous copies (cp.async) instead of held in
+ * registers (64 registers, 8 blocks of 4 warps per SM), forward and inverse
+ * rows; ckks_tune does not time it (slower than form 3 on GB300, most of all
+ * for the rows with fused epilogues), it is set by hand only. Without an
+ * entry: 3. */
 #define CKKS_ROW_PASSES 3
 /* Times every candidate shape of the three kernels at `level` (reps launches
  * each, CUDA events on the context stream, on the context's scratch), and at
@@ -450,7 +456,7 @@ int ckks_tune(ckks_ctx* ctx, int level, int reps);
 int ckks_tune_get(ckks_ctx* ctx, int kernel, int level, int* tc, int* sl, int* z, int* tp, float* us);
 /* Sets a shape by hand (tc in {4, 8}, sl in {2, 4, 8}, z in 1..4, tp in
  * {1, 2}; at N = 2^8 only tc = 8, since a slice must be whole warps; the
- * tensor-core shapes listed above; for CKKS_ROW_PASSES tc in 2 .. 5 at
+ * tensor-core shapes listed above; for CKKS_ROW_PASSES tc in 2 .. 6 at
  * N = 2^16), or clears the entry with tc = 0. A tensor-core shape for a
  * conversion with more than 16 sources runs the fixed CUDA-core rule.
  * Changes no value any operation computes. */

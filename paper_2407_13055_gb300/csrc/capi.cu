@@ -305,7 +305,7 @@ int ckks_tune_set(ckks_ctx* ctx, int kernel, int level, int tc, int sl, int z, i
   if (level < 0 || level >= ctx->n_levels()) return fail(ctx, CKKS_ELEVEL, "tune: level %d out of range", level);
   ckks::ColShape s;
   if (tc != 0 && kernel == ckks::CK_ROWS) {
-    if (ctx->dp.log_n != 16 || tc < 2 || tc > 5)
+    if (ctx->dp.log_n != 16 || tc < 2 || tc > 6)
       return fail(ctx, CKKS_EINVAL, "tune: row passes %d not supported at N = 2^%d", tc, ctx->dp.log_n);
     s = ckks::ColShape{tc, 1, 1, 1};
   } else if (tc != 0) {

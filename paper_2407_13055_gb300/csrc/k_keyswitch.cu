@@ -685,7 +685,7 @@ static DevParams tuned_rows(const DevParams& dp, const Scratch& sc, int tix) {
   DevParams d = dp;
   if (sc.tune) {
     const ColShape s = sc.tune->get(CK_ROWS, tix);
-    if (s.tc >= 2 && s.tc <= 5) d.rows_passes = s.tc;
+    if (s.tc >= 2 && s.tc <= 6) d.rows_passes = s.tc;
   }
   return d;
 }
@@ -952,7 +952,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
     if constexpr (G::W == 1024) {
       int best_p = 3;
       float best_ms = -1.f;
-      for (int passes : {3, 2, 4, 5}) {
+      for (int passes : {3, 2, 4, 5}) {  // form 6 (twiddles in shared memory): by hand only
         if (rc != CKKS_OK || lvl.rows_cnt < 1) break;
         DevParams dv = dp;
         dv.rows_passes = passes;

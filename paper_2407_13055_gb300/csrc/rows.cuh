@@ -459,6 +459,291 @@ __global__ void __launch_bounds__(128, 6) k_rows3_inv_t(DevParams dp, Src src, u
   for (int i = 0; i < 16; ++i) o[t + 64 * i] = x[i];
 }
 
+// ---------------------------------------------------------------------------
+// Three-pass rows with the twiddles in shared memory. The same passes, layouts
+// and twiddle indices as k_rows3_fwd_t / k_rows3_inv_t, but the pass-B and
+// pass-C twiddles (21 pairs per thread, 42 registers there) are copied into
+// shared memory with asynchronous copies (cp.async: no registers, the copies
+// land while the thread loads its row and runs its first pass) and read from
+// there at each stage. A thread then keeps little more than its 16 values, so
+// the kernel fits 8 blocks of 4 warps per SM (64 registers, 25 KB of shared
+// memory per block): 32 resident warps against 24.
+// Layouts per row: pass A as before (15 pairs, entry (2^s - 1) + b); pass B per
+// group o = t >> 2, entry (1 << s) + b (entry 0 unused), 10 entries per group
+// so that the 8 groups of a warp fall in distinct banks; pass C per thread as
+// 7 16-byte pairs in pair-major order (pair p of thread t at [p][t]): pair 0 =
+// stage 0 of groups 0 and 1, pairs 1 + g = stage 1 of group g, pairs 3 + 2g and
+// 4 + 2g = stage 2 of group g (blocks 0-1 and 2-3), each read as one 16-byte
+// word by the thread, conflict-free across the warp.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+struct Row3Tw {
+  uint2 a[2][15];        // pass A, per row
+  uint2 b[2][16][10];    // pass B, per row and group o
+  uint4 c[2][7][64];     // pass C, per row, pair, thread
+};
+
+// Copies of thread t of row r (row h of the limb's table t): pass A by the
+// first 15 threads, pass B by the four threads of each group (one stage part
+// each), pass C by every thread (its own 7 pairs). Two commit groups: pass A,
+// then passes B and C (order `a_first`), or pass C then passes B and A.
+template <int H>
+__device__ __forceinline__ void row3s_copy_twiddles(Row3Tw& sw, const uint2* __restrict__ tw, int r, int h, int t,
+                                                    bool a_first) {
+  auto copy_a = [&]() {
+    if (t < 15) {
+      const int s = 31 - __clz(t + 1);
+      const int b = t + 1 - (1 << s);
+      cp_async8(&sw.a[r][t], tw + ((uint32_t)(H + h) << s) + b);
+    }
+  };
+  auto copy_b = [&]() {
+    const int o = t >> 2, part = t & 3;
+    const uint32_t bb = (uint32_t)(H + h) * 16 + o;
+    if (part == 0) cp_async8(&sw.b[r][o][1], tw + bb);
+    else if (part == 1) cp_async16(&sw.b[r][o][2], tw + 2 * bb);
+    else cp_async16(&sw.b[r][o][4 + 2 * (part - 2)], tw + 4 * bb + 2 * (part - 2));
+  };
+  auto copy_c = [&]() {
+    const uint32_t bc = (uint32_t)(H + h) * 128 + 2 * t;
+    cp_async16(&sw.c[r][0][t], tw + bc);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) cp_async16(&sw.c[r][1 + k][t], tw + 2 * bc + 2 * k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async16(&sw.c[r][3 + k][t], tw + 4 * bc + 2 * k);
+  };
+  if (a_first) {
+    copy_a();
+    cp_async_commit();
+    copy_b();
+    copy_c();
+  } else {
+    copy_c();
+    cp_async_commit();
+    copy_b();
+    copy_a();
+  }
+  cp_async_commit();
+}
+
+// Pass B on both groups, twiddle of stage s, block b at w[(1 << s) + b].
+template <bool LAZY>
+__device__ __forceinline__ void row3s_ct_b(uint32_t (&y0)[8], uint32_t (&y1)[8], const uint2* w, uint32_t q) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int half = 8 >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 tw = w[(1 << s) + b];
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        ct_bfly<LAZY>(y0[i0], y0[i0 + half], tw.x, tw.y, q);
+        ct_bfly<LAZY>(y1[i0], y1[i0 + half], tw.x, tw.y, q);
+      }
+    }
+  }
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void row3s_gs_b(uint32_t (&y0)[8], uint32_t (&y1)[8], const uint2* w, uint32_t q) {
+#pragma unroll
+  for (int s = 2; s >= 0; --s) {
+    const int half = 8 >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 tw = w[(1 << s) + b];
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        gs_bfly<LAZY>(y0[i0], y0[i0 + half], tw.x, tw.y, q);
+        gs_bfly<LAZY>(y1[i0], y1[i0 + half], tw.x, tw.y, q);
+      }
+    }
+  }
+}
+
+// Twiddle pair of group g, stage s, block b from the thread's pass-C pairs
+// (c[p * 64] = pair p).
+__device__ __forceinline__ uint2 row3s_c_tw(const uint4* c, int g, int s, int b) {
+  const uint4 v = s == 0 ? c[0] : s == 1 ? c[(1 + g) * 64] : c[(3 + 2 * g + (b >> 1)) * 64];
+  const bool hi = s == 0 ? g == 1 : (b & 1) == 1;
+  return hi ? make_uint2(v.z, v.w) : make_uint2(v.x, v.y);
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void row3s_ct_c(uint32_t (&y0)[8], uint32_t (&y1)[8], const uint4* c, uint32_t q) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int half = 8 >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w0 = row3s_c_tw(c, 0, s, b), w1 = row3s_c_tw(c, 1, s, b);
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        ct_bfly<LAZY>(y0[i0], y0[i0 + half], w0.x, w0.y, q);
+        ct_bfly<LAZY>(y1[i0], y1[i0 + half], w1.x, w1.y, q);
+      }
+    }
+  }
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void row3s_gs_c(uint32_t (&y0)[8], uint32_t (&y1)[8], const uint4* c, uint32_t q) {
+#pragma unroll
+  for (int s = 2; s >= 0; --s) {
+    const int half = 8 >> (s + 1);
+#pragma unroll
+    for (int b = 0; b < (1 << s); ++b) {
+      const uint2 w0 = row3s_c_tw(c, 0, s, b), w1 = row3s_c_tw(c, 1, s, b);
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = b * 2 * half + k;
+        gs_bfly<LAZY>(y0[i0], y0[i0 + half], w0.x, w0.y, q);
+        gs_bfly<LAZY>(y1[i0], y1[i0 + half], w1.x, w1.y, q);
+      }
+    }
+  }
+}
+
+template <class G, class Epi>
+__global__ void __launch_bounds__(128, 8) k_rows3s_fwd_t(DevParams dp, const uint32_t* src, Epi epi, LimbMap map) {
+  static_assert(G::W == 1024, "three-pass rows are for W = 1024");
+  __shared__ uint32_t buf[2][1024];
+  __shared__ __align__(16) Row3Tw sw;
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int h = blockIdx.x * 2 + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  row3s_copy_twiddles<G::H>(sw, dp.tw + ((size_t)lm.y << dp.log_n), r, h, t, true);
+  pdl_wait();
+  pdl_trigger();
+  const uint32_t* s = src + ((size_t)lm.x << dp.log_n) + (size_t)h * 1024;
+  uint32_t x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = s[t + 64 * i];
+  cp_async_wait<1>();
+  __syncthreads();
+  uint32_t* b = buf[r];
+  uint32_t y0[8], y1[8];
+  const bool lazy = q < (1u << 30);
+  if (lazy) ct_pass_sm<16, true>(x, sw.a[r], q);
+  else ct_pass_sm<16, false>(x, sw.a[r], q);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) b[row3_swz(t + 64 * i)] = x[i];
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(row3_eb(t, 0, i))];
+    y1[i] = b[row3_swz(row3_eb(t, 1, i))];
+  }
+  __syncthreads();
+  const uint2* wb = sw.b[r][t >> 2];
+  if (lazy) row3s_ct_b<true>(y0, y1, wb, q);
+  else row3s_ct_b<false>(y0, y1, wb, q);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(row3_eb(t, 0, i))] = y0[i];
+    b[row3_swz(row3_eb(t, 1, i))] = y1[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(16 * t + i)];
+    y1[i] = b[row3_swz(16 * t + 8 + i)];
+  }
+  const uint4* wc = &sw.c[r][0][t];
+  if (lazy) {
+    row3s_ct_c<true>(y0, y1, wc, q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = normalize<true>(y0[i], q);
+      x[8 + i] = normalize<true>(y1[i], q);
+    }
+  } else {
+    row3s_ct_c<false>(y0, y1, wc, q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = normalize<false>(y0[i], q);
+      x[8 + i] = normalize<false>(y1[i], q);
+    }
+  }
+  epi(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * 1024 + 16 * t));
+}
+
+template <class G, class Src>
+__global__ void __launch_bounds__(128, 8) k_rows3s_inv_t(DevParams dp, Src src, uint32_t* dst, LimbMap map,
+                                                      int dst_compact) {
+  static_assert(G::W == 1024, "three-pass rows are for W = 1024");
+  __shared__ uint32_t buf[2][1024];
+  __shared__ __align__(16) Row3Tw sw;
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int h = blockIdx.x * 2 + r;
+  const int2 lm = map(blockIdx.y);
+  const uint32_t q = dp.pc[lm.y].q;
+  row3s_copy_twiddles<G::H>(sw, dp.itw + ((size_t)lm.y << dp.log_n), r, h, t, false);
+  pdl_wait();
+  pdl_trigger();
+  uint32_t x[16];
+  src(dp, x, (int)blockIdx.y, lm, (uint32_t)(h * 1024 + 16 * t));
+  uint32_t* b = buf[r];
+  uint32_t y0[8], y1[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = x[i];
+    y1[i] = x[8 + i];
+  }
+  const bool lazy = q < (1u << 30);
+  cp_async_wait<1>();  // own pass-C pairs (read by this thread only)
+  const uint4* wc = &sw.c[r][0][t];
+  if (lazy) row3s_gs_c<true>(y0, y1, wc, q);
+  else row3s_gs_c<false>(y0, y1, wc, q);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(16 * t + i)] = y0[i];
+    b[row3_swz(16 * t + 8 + i)] = y1[i];
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    y0[i] = b[row3_swz(row3_eb(t, 0, i))];
+    y1[i] = b[row3_swz(row3_eb(t, 1, i))];
+  }
+  __syncthreads();
+  const uint2* wb = sw.b[r][t >> 2];
+  if (lazy) row3s_gs_b<true>(y0, y1, wb, q);
+  else row3s_gs_b<false>(y0, y1, wb, q);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[row3_swz(row3_eb(t, 0, i))] = y0[i];
+    b[row3_swz(row3_eb(t, 1, i))] = y1[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = b[row3_swz(t + 64 * i)];
+  if (lazy) gs_pass_sm<16, true>(x, sw.a[r], q);
+  else gs_pass_sm<16, false>(x, sw.a[r], q);
+  const size_t dl = dst_compact ? (size_t)blockIdx.y : (size_t)lm.x;
+  uint32_t* o = dst + (dl << dp.log_n) + (size_t)h * 1024;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) o[t + 64 * i] = x[i];
+}
+
 // Three-pass forward rows with the input staged by bulk copies: a block
 // takes RP consecutive row pairs of one limb; the next pairs' 8 KB of input
 // (two contiguous rows) stream into a second shared buffer with
@@ -596,6 +881,9 @@ inline void launch_rows_fwd(const DevParams& dp, const uint32_t* src, const Epi&
       else
         launch_pdl(dp.pdl, k_rows3_fwd_bulk<G, Epi, 4>, dim3(G::H / 8, limbs), dim3(128), 0, st, dp, src, epi, map);
       three = true;
+    } else if (dp.rows_passes == 6) {
+      launch_pdl(dp.pdl, k_rows3s_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
+      three = true;
     } else if (dp.rows_passes != 2) {
       launch_pdl(dp.pdl, k_rows3_fwd_t<G, Epi>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, src, epi, map);
       three = true;
@@ -612,7 +900,11 @@ inline void launch_rows_inv(const DevParams& dp, const Src& srcf, uint32_t* dst,
   if (limbs <= 0) return;
   bool three = false;
   if constexpr (G::W == 1024) {
-    if (dp.rows_passes != 2) {
+    if (dp.rows_passes == 6) {
+      launch_pdl(dp.pdl, k_rows3s_inv_t<G, Src>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, srcf, dst, map,
+                 dst_compact ? 1 : 0);
+      three = true;
+    } else if (dp.rows_passes != 2) {
       launch_pdl(dp.pdl, k_rows3_inv_t<G, Src>, dim3(G::H / 2, limbs), dim3(128), 0, st, dp, srcf, dst, map,
                  dst_compact ? 1 : 0);
       three = true;

@@ -71,6 +71,24 @@ def test_rational_rescale_matches_oracle(K, O, log_n, level):
 @pytest.mark.parametrize("log_n", [12, 16])
 @pytest.mark.parametrize("level", [0, 1, 2, 3, 4, 6, 8])
 def test_hmult_hrot_at_windows_match_oracle(K, O, log_n, level):
+    _check_hmult_hrot(K, O, log_n, level)
+
+
+@pytest.mark.parametrize("level", [4, 8])
+@pytest.mark.parametrize("passes", [2, 4, 6])
+def test_row_forms_at_windows_match_oracle(K, O, level, passes):
+    """The row-phase forms other than the default one (two passes, bulk-staged
+    forward rows, twiddles in shared memory) at windows of the 25-30 system:
+    the rational rescale's and the merged form's row epilogues included."""
+    ctx, P, levels = system(K, O, 16)
+    K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, level, passes, 1, 1, 1)
+    try:
+        _check_hmult_hrot(K, O, 16, level)
+    finally:
+        K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, level, 0, 1, 1, 1)
+
+
+def _check_hmult_hrot(K, O, log_n, level):
     ctx, P, levels = system(K, O, log_n)
     s0, n0 = levels[level]
     c1, c2 = rand_ct(P, levels[level], 310 + level), rand_ct(P, levels[level], 320 + level)

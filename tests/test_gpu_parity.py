@@ -561,31 +561,35 @@ def test_tune_file_round_trip(K, O, tmp_path):
 @pytest.mark.parametrize("n_q", [40, 5])
 def test_row_phase_forms_give_identical_results(K, O, n_q):
     """Every form of the N = 2^16 row phase the tuner chooses between (two
-    register passes of radix 2^5, three of 2^4 x 2^3 x 2^3, and the three-pass
+    register passes of radix 2^5, three of 2^4 x 2^3 x 2^3, the three-pass
     form with its forward rows staged by bulk copies, 2 or 4 row pairs per
-    block) reproduces the oracle bit for bit: HMult+rescale, HRot and hoisted
-    rotations."""
+    block, and the three-pass form with its twiddles staged in shared memory)
+    reproduces the oracle bit for bit: HMult+rescale, HMult with the merged
+    ModDown + rescale, HRot and hoisted rotations."""
     ctx, P = get(K, O, "n16d3")
     c1, c2 = rand_ct(P, n_q, 91), rand_ct(P, n_q, 93)
     evk = rand_evk(P, 95)
     want_m = O.hmult(P, c1, c2, evk, rescale=True)
+    want_mm = O.hmult_merged(P, c1, c2, evk)
     k = O.rot_k(1, P.log_n)
     want_r = O.hrot(P, c1, k, evk)
     a = K.ckks_ct_import(ctx, c1, n_q - 1, 2.0**30)
     ek = K.ckks_evk_import(ctx, evk, k)
     outs = [K.ckks_ct_create(ctx, n_q - 1) for _ in range(2)]
     try:
-        for passes in (2, 3, 4, 5):
+        for passes in (2, 3, 4, 5, 6):
             K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, passes, 1, 1, 1)
             got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True)
             assert np.array_equal(got, want_m), passes
+            got, _, _ = _run_hmult(K, ctx, P, c1, c2, evk, True, K.CKKS_RESCALE_MERGED)
+            assert np.array_equal(got, want_mm), passes
             got, _ = _run_hrot(K, O, ctx, P, c1, evk, 1)
             assert np.array_equal(got, want_r), passes
             K.ckks_hrot_hoisted(ctx, a, [1, 1], [ek, ek], outs)
             for o in outs:
                 assert np.array_equal(K.ckks_ct_export(ctx, o, P.n)[0], want_r), passes
         with pytest.raises(K.CkksError):
-            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 6, 1, 1, 1)
+            K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 7, 1, 1, 1)
     finally:
         K.ckks_tune_set(ctx, K.CKKS_ROW_PASSES, n_q - 1, 0, 1, 1, 1)
         for h in [a, ek] + outs:
