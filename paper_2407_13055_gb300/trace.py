@@ -30,8 +30,10 @@ import numpy as np
 
 @dataclass
 class TraceSpec:
-    n1: int = 8          # baby steps
-    n2: int = 4          # giant steps
+    # 32 baby x 2 giant steps: 64 diagonals per transform over 32 rotation
+    # indices (1 .. 31 hoisted, 32 for the giant step)
+    n1: int = 32         # baby steps
+    n2: int = 2          # giant steps
     lt_levels: int = 2   # linear-transform levels on each side
     depth: int = 6       # product-tree depth: polynomial degree 2^depth
     seed: int = 1234
