@@ -95,20 +95,22 @@ def stage_work(op, n=L, alpha=ALPHA):
         "modup_cols": dict(shoup=(n + targets) * col, mac=N * sum(a * (ext - a) for a in a_j)),
         "modup_rows": dict(shoup=targets * row),
         "keymult": dict(bytes=2 * d * ext * lb, smr=2 * d * ext * N),
-        "moddown_in_rows": dict(shoup=2 * alpha * row),
     }
     if hm:
-        # top limb first (ModDown of q_l, then its coefficients join the
-        # fused rescale): b1, b2 top limbs read, d0 / d1 of that limb re-formed
-        w["moddown_cols"] = dict(shoup=2 * (alpha + 1) * col, mac=2 * N * alpha)
-        w["moddown_rows"] = dict(bytes=2 * lb, shoup=2 * row + 2 * N, smr=6 * N)
-        w["rescale_in_rows"] = dict(shoup=2 * row)
-        w["rescale_cols"] = dict(shoup=2 * col + 2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1))
+        # top limb first (ModDown of q_l in the coefficient domain, then its
+        # coefficients join the fused rescale): the iNTT rows also take
+        # E = acc_l P^-1 + d_l (b1, b2 top limbs read, d0 / d1 of that limb
+        # re-formed); the first column kernel iNTTs E, converts P -> q_l and
+        # forms V = E - z P^-1
+        w["moddown_in_rows"] = dict(bytes=2 * lb, shoup=2 * (alpha + 1) * row + 2 * N, smr=6 * N)
+        w["moddown_cols"] = dict(shoup=2 * (alpha + 1) * col + 2 * N, mac=2 * N * alpha)
+        w["rescale_cols"] = dict(shoup=2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1))
         # NTT rows + (A - w)(P q_l)^-1 + d q_l^-1 with d0 / d1 re-formed from
         # the inputs (b1, b2 read here first), output 2(n - 1) limbs
         w["rescale_rows"] = dict(bytes=4 * (n - 1) * lb, shoup=2 * (n - 1) * (row + 2 * N),
                                  smr=6 * (n - 1) * N)
     else:
+        w["moddown_in_rows"] = dict(shoup=2 * alpha * row)
         w["moddown_cols"] = dict(shoup=2 * (alpha + n) * col, mac=2 * n * N * alpha)
         # NTT rows + (A - z) P^-1 + phi(b): b read, output 2n limbs
         w["moddown_rows"] = dict(bytes=3 * n * lb, shoup=2 * n * row + 2 * n * N)
@@ -123,10 +125,10 @@ def kernel_models(n=L, alpha=ALPHA):
     """Per-launch work of each stage in the bench's one-lane profile, which
     alternates HMult + rescale and HRot: the mean of the two operations' work
     for the stages both run (the key-switch stages), HMult's alone for the
-    rescale stages."""
+    rescale stages and HRot's alone for the ModDown NTT rows."""
     hm, hr = stage_work("hmult", n, alpha), stage_work("hrot", n, alpha)
     out = {}
-    for k in hm:
+    for k in list(hm) + [k for k in hr if k not in hm]:
         ws = [x[k] for x in (hm, hr) if k in x]
         out[k] = {kk: sum(x[kk] for x in ws) / len(ws) for kk in ("bytes", "shoup", "mac", "smr", "modmul")}
     return out
@@ -509,12 +511,11 @@ def run_native(args, rank, world, local_rank):
     K.ckks_profile(ctx, False)
     prof = K.ckks_profile_read(ctx)
     seq_ops_per_s = 2 * BATCH * seq_steps / (ms_seq / 1e3)
-    hm_stages = ("ks_prep", "ks_in_rows", "modup_cols", "modup_rows", "keymult", "moddown_in_rows",
-                 "moddown_cols", "moddown_rows", "ks_epilogue", "rescale_in_rows", "rescale_cols",
-                 "rescale_rows", "rescale_epilogue")   # ks_prep, ks_epilogue, rescale_epilogue: fused, no launches
+    ks_stages = ("ks_in_rows", "modup_cols", "modup_rows", "keymult", "moddown_in_rows", "moddown_cols")
     per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
-    hmult_us = 1e3 * sum(per_launch[k] for k in hm_stages)
-    hrot_us = 1e3 * sum(per_launch[k] for k in hm_stages[:9])
+    # stages both operations run are averaged over both in the profile
+    hmult_us = 1e3 * sum(per_launch[k] for k in ks_stages + ("rescale_cols", "rescale_rows"))
+    hrot_us = 1e3 * sum(per_launch[k] for k in ks_stages + ("moddown_rows",))
 
     # end to end through the C ABI with host buffers. A step is e2e_pairs pairs
     # over e2e_pairs + 1 input ciphertexts (pair i: HMult(ct_i, ct_i+1) + rescale,

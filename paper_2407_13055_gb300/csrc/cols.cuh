@@ -330,12 +330,16 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevP
 
 // ModDown fused with rescaling, first column kernel: the P limbs' iNTT
 // columns give the centered coefficients y (kept in Y for the second
-// kernel); only the top limb q_l is converted here (its ModDown output is
-// needed in the coefficient domain before the others). grid (W/TC, 2 polys).
+// kernel); only the top limb q_l is converted here, and its ModDown output is
+// finished in the coefficient domain: S holds, after the P limbs of both
+// polynomials, E_u = A_u[l] P^-1 + extra_u[l] through its iNTT rows, so that
+// V_u = E_u - z P^-1 (z = BConv(P -> q_l)) comes out of this kernel as
+// coefficients; its centered value c_l joins Y as source alpha of the fused
+// rescale conversion. Y = [2][alpha + 1][N]. grid (W/TC, 2 polys).
 template <class G, int TC, int SL>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
                                                                                         const uint32_t* S,
-                                                                                        uint32_t* T, uint32_t* Y) {
+                                                                                        uint32_t* Y) {
   pdl_wait();
   pdl_trigger();
   using CTL = ColTile<G, TC>;
@@ -346,26 +350,56 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(
   const int u = blockIdx.y;
   const int alpha = dp.alpha, top = n - 1;
   int4* y4 = smem4;
-  uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)alpha * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  uint32_t* colbuf =
+      reinterpret_cast<uint32_t*>(smem4 + (size_t)(alpha + 1) * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  uint32_t* Yu = Y + ((size_t)(u * (alpha + 1)) << dp.log_n);
   col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
-                    y4, colbuf, l, jj, c, pos, slice, SL, Y + ((size_t)(u * alpha) << dp.log_n));
+                    y4, colbuf, l, jj, c, pos, slice, SL, Yu);
+  const PrimeConst Pt = dp.pc[top];
+  if (slice == SL - 1) {
+    // E_u: iNTT columns, times N^-1, kept in [0, q_l) in source slot alpha
+    const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
+    const uint32_t* s = S + ((size_t)(2 * alpha + u) << dp.log_n);
+    uint32_t x[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
+    if (Pt.q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
+    int32_t e[G::EC];
+#pragma unroll
+    for (int i = 0; i < G::EC; ++i) e[i] = (int32_t)csub(shoup(x[i], Pt.ninv, Pt.ninv_sh, Pt.q), Pt.q);
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4)
+      y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(e[4 * i4], e[4 * i4 + 1], e[4 * i4 + 2], e[4 * i4 + 3]);
+  }
   __syncthreads();
-  auto tgt = [&](int, const int32_t*& row, int& id, uint32_t*& dst) {
-    row = dp.ks.dn_mat + top * alpha;
-    id = top;
-    dst = T + ((size_t)u << dp.log_n);
-  };
-  col_targets<G, TC, 1>(dp, y4, alpha, 1, slice, SL, tgt, colbuf, l, jj, c, pos, slice, src_bound(dp, alpha, dp.L));
+  if (slice == 0) {
+    uint32_t z[G::EC];
+    bconv_accumulate<G::EC, CTL::CT>(y4, pos, alpha, dp.ks.dn_mat + top * alpha, Pt, z,
+                                     no_fold(src_bound(dp, alpha, dp.L), Pt.q));
+    const uint2 pinv = dp.ks.dn_pinv[top];
+    uint32_t* yc = Yu + ((size_t)alpha << dp.log_n);
+#pragma unroll
+    for (int i4 = 0; i4 < G::EC / 4; ++i4) {
+      const int4 e = y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos];
+      const uint32_t ev[4] = {(uint32_t)e.x, (uint32_t)e.y, (uint32_t)e.z, (uint32_t)e.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = 4 * i4 + k;
+        const uint32_t zp = csub(shoup(z[i], pinv.x, pinv.y, Pt.q), Pt.q);
+        const uint32_t v = csub(ev[k] + Pt.q - zp, Pt.q);
+        yc[(jj + G::EC * i) * G::W + l] = (uint32_t)centered(v, Pt.q);
+      }
+    }
+  }
 }
 
-// ModDown fused with rescaling, second column kernel: iNTT columns of the top
-// limb's ModDown output (row phase already applied) give c_l, centered; with
-// the stored y it forms K = alpha + 1 inputs whose conversion to q_i (matrix
-// rs_mat: the ModDown row plus [P]_{q_i}) is w_i = z_i + P [c_l]_{q_i}; then
-// the NTT columns. grid (W/TC, 2 polys, Z); targets i < l.
+// ModDown fused with rescaling, second column kernel: the K = alpha + 1
+// stored centered coefficients of polynomial u (P limbs and c_l) convert to
+// q_i (matrix rs_mat: the ModDown row plus [P]_{q_i}) as w_i = z_i + P [c_l]_{q_i};
+// then the NTT columns. grid (W/TC, 2 polys, Z); targets i < l.
 template <class G, int TC, int SL, int TP>
 __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
-                                                                                  const uint32_t* V,
                                                                                   const uint32_t* Y, uint32_t* T) {
   pdl_wait();
   pdl_trigger();
@@ -378,32 +412,15 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevPar
   const int alpha = dp.alpha, top = n - 1, K = alpha + 1;
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
-  // stored centered P-limb coefficients, A layout along h
-  for (int k = slice; k < alpha; k += SL) {
-    const uint32_t* yk = Y + ((size_t)(u * alpha + k) << dp.log_n);
+  // stored centered coefficients, A layout along h
+  for (int k = slice; k < K; k += SL) {
+    const uint32_t* yk = Y + ((size_t)(u * K + k) << dp.log_n);
     int32_t y[G::EC];
 #pragma unroll
     for (int i = 0; i < G::EC; ++i) y[i] = (int32_t)yk[(jj + G::EC * i) * G::W + l];
 #pragma unroll
     for (int i4 = 0; i4 < G::EC / 4; ++i4)
       y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
-  }
-  if (slice == SL - 1) {
-    const PrimeConst Pt = dp.pc[top];
-    const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
-    const uint32_t* s = V + ((size_t)u << dp.log_n);
-    uint32_t x[G::EC];
-#pragma unroll
-    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
-    if (Pt.q < (1u << 30)) col_inv<G::EC, TC, true>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
-    else col_inv<G::EC, TC, false>(x, colbuf, itw, jj, c, Pt.q, slice + 1, CTL::CT);
-    int32_t y[G::EC];
-#pragma unroll
-    for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], Pt.ninv, Pt.ninv_sh, Pt.q), Pt.q), Pt.q);
-#pragma unroll
-    for (int i4 = 0; i4 < G::EC / 4; ++i4)
-      y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos] =
-          make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
   }
   __syncthreads();
   auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
@@ -600,17 +617,17 @@ void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint
   ColShape s = default_shape<G>(2, dp.sms);
   with_shape(s, [&](auto tc, auto sl, auto) {
     constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value;
-    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha);
+    const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
     set_col_smem((const void*)k_ks_moddown_cols_top<G, TC, SL>, sm);
     launch_pdl(dp.pdl, k_ks_moddown_cols_top<G, TC, SL>, dim3(G::W / TC, 2), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
-               n, (const uint32_t*)sc.S, sc.T, Y);
+               n, (const uint32_t*)sc.S, Y);
     count_launch(1);
   });
 }
 
 template <class G>
-void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const uint32_t* Y, uint32_t* T3,
-                                 const ColShape& s0, cudaStream_t st) {
+void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* Y, uint32_t* T3, const ColShape& s0,
+                          cudaStream_t st) {
   if (is_tc_shape(s0) && dp.ks.tc_img && dp.alpha + 1 <= kTcMaxSources &&
       with_tc_shape<G>(s0, [&](auto tc, auto sl, auto nc) {
         constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, NC = decltype(nc)::value;
@@ -618,8 +635,8 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
         const int kr = tc_kr(dp.alpha + 1);
         const size_t sm = tc_smem<SH, NC>(kr, n - 1).total;
         set_col_smem((const void*)k_rs_cols_fused_tc<G, TC, SL, NC>, sm);
-        launch_pdl(dp.pdl, k_rs_cols_fused_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, kr, V,
-                   Y, T3);
+        launch_pdl(dp.pdl, k_rs_cols_fused_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, kr, Y,
+                   T3);
         count_launch(1);
       }))
     return;
@@ -629,7 +646,7 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* V, const u
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
     set_col_smem((const void*)k_rs_cols_fused<G, TC, SL, TP>, sm);
     launch_pdl(dp.pdl, k_rs_cols_fused<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
-               n, V, Y, T3);
+               n, Y, T3);
     count_launch(1);
   });
 }

@@ -341,11 +341,11 @@ __global__ void __launch_bounds__(TcShape<G, TC, SL, NC>::NT, 1)
 }
 
 // ModDown fused with rescaling, second column kernel, tensor-core form of
-// k_rs_cols_fused: K = alpha + 1 sources (the stored centered P-limb
-// coefficients and the top limb's c_l), targets i < l.
+// k_rs_cols_fused: K = alpha + 1 stored sources (the centered P-limb
+// coefficients and the top limb's c_l, Y = [2][alpha + 1][N]), targets i < l.
 template <class G, int TC, int SL, int NC>
 __global__ void __launch_bounds__(TcShape<G, TC, SL, NC>::NT, 1)
-    k_rs_cols_fused_tc(DevParams dp, int n, int kr_max, const uint32_t* V, const uint32_t* Y, uint32_t* T) {
+    k_rs_cols_fused_tc(DevParams dp, int n, int kr_max, const uint32_t* Y, uint32_t* T) {
   using SH = TcShape<G, TC, SL, NC>;
   extern __shared__ __align__(128) uint8_t tc_sm[];
   const int tid = threadIdx.x, slice = tid / SH::CT, pos = tid % SH::CT;
@@ -360,26 +360,12 @@ __global__ void __launch_bounds__(TcShape<G, TC, SL, NC>::NT, 1)
   blk.begin(dp, dp.ks.tc_img + img.x, (uint32_t)img.y, K, top, target);
   pdl_wait();
   pdl_trigger();
-  for (int k = slice; k < alpha; k += SL) {
-    const uint32_t* yk = Y + ((size_t)(u * alpha + k) << dp.log_n);
+  for (int k = slice; k < K; k += SL) {
+    const uint32_t* yk = Y + ((size_t)(u * K + k) << dp.log_n);
     int32_t y[G::EC];
 #pragma unroll
     for (int i = 0; i < G::EC; ++i) y[i] = (int32_t)yk[(jj + G::EC * i) * G::W + l];
     blk.put(k, y, jj, c);
-  }
-  if (slice == SL - 1) {
-    const PrimeConst Pt = dp.pc[top];
-    const uint2* itw = dp.itw + ((size_t)top << dp.log_n);
-    const uint32_t* s = V + ((size_t)u << dp.log_n);
-    uint32_t x[G::EC];
-#pragma unroll
-    for (int i = 0; i < G::EC; ++i) x[i] = s[(G::EC * jj + i) * G::W + l];
-    if (Pt.q < (1u << 30)) col_inv<G::EC, TC, true>(x, blk.colbuf(slice), itw, jj, c, Pt.q, slice + 1, SH::CT);
-    else col_inv<G::EC, TC, false>(x, blk.colbuf(slice), itw, jj, c, Pt.q, slice + 1, SH::CT);
-    int32_t y[G::EC];
-#pragma unroll
-    for (int i = 0; i < G::EC; ++i) y[i] = centered(csub(shoup(x[i], Pt.ninv, Pt.ninv_sh, Pt.q), Pt.q), Pt.q);
-    blk.put(alpha, y, jj, c);
   }
   blk.convert(dp, top, target, l, jj, c, slice);
 }

@@ -809,14 +809,15 @@ int alloc_scratch(ckks_ctx* ctx) {
   const DevParams& dp = ctx->dp;
   const int L = dp.L, np = dp.L + dp.alpha;
   const size_t limb = (size_t)1 << dp.log_n;
-  // windows are at most L primes; the merged ModDown + rescaling takes 2K limbs
-  size_t s_limbs = std::max(L, 2 * dp.alpha);
+  // windows are at most L primes; the fused ModDown + rescaling takes the 2
+  // alpha P limbs and two top limbs, the merged one 2K limbs
+  size_t s_limbs = std::max(L, 2 * dp.alpha + 2);
   for (const MmArgs& m : ctx->mm) s_limbs = std::max(s_limbs, 2 * (size_t)m.K);
   // T: the ModUp limbs (dnum (L + alpha)) followed by room for the ModDown
   // conversions (2L), so that hoisted rotations keep the ModUp limbs
   const size_t t_limbs = std::max((size_t)dp.dnum * np + 2 * (size_t)L, (size_t)2 * L + 4);
-  // U holds the [2][alpha] centered P-limb coefficients of the fused rescale
-  const size_t a_limbs = 2 * (size_t)np, u_limbs = 2 * (size_t)std::max(L, dp.alpha);
+  // U holds the [2][alpha + 1] centered coefficients of the fused rescale
+  const size_t a_limbs = 2 * (size_t)np, u_limbs = 2 * (size_t)std::max(L, dp.alpha + 1);
   const size_t words = (s_limbs + t_limbs + a_limbs + u_limbs) * limb;
   uint32_t* sc = nullptr;
   if (cudaMalloc(&sc, words * sizeof(uint32_t)) != cudaSuccess) return CKKS_ENOMEM;

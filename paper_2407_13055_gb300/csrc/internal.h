@@ -268,7 +268,7 @@ struct Scratch {
   uint32_t* S;  // row-phase iNTT outputs (ModUp input, ModDown P-limbs)
   uint32_t* T;  // column-phase outputs [dnum][L + alpha][N] (ModUp), then [2][L][N] (ModDown)
   uint32_t* A;  // accumulators [2][n + alpha][N]
-  uint32_t* U;  // centered P-limb coefficients of the fused ModDown + rescale [2][alpha][N]
+  uint32_t* U;  // centered coefficients of the fused ModDown + rescale [2][alpha + 1][N]; staged HMult output
   Prof* prof;   // optional stage timing (null or off: no events)
   const Tuning* tune = nullptr;  // tuned column-kernel shapes (null: default rule)
 };

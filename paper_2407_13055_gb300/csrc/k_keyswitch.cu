@@ -14,6 +14,13 @@
 //   rows    (rows)  : NTT row phase of T, then the epilogue
 //                     (acc - z) P^-1 + (d0, d1) or (phi(b), 0)               -> out
 //
+// HMult with rescaling by q_l fuses the ModDown into the rescale: the P limbs'
+// iNTT rows also take E = acc_l P^-1 + d_l of the top limb; one column kernel
+// finishes the top limb's ModDown output V = E - BConv(P -> q_l) P^-1 in the
+// coefficient domain; the second converts the P limbs and V's centered
+// coefficients to every q_i, i < l, and the NTT rows' epilogue forms
+// (acc_i - w_i)(P q_l)^-1 + d_i q_l^-1.
+//
 // Row kernels (rows.cuh) hold W-word rows in registers with their twiddles
 // loaded up front, and take the element-wise step before (input preparation)
 // or after (ModDown and rescale epilogues) the transform as a functor, so
@@ -42,8 +49,8 @@ using G8 = Geo<4, 4>;
                                               cudaStream_t);                                                    \
   extern template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*,             \
                                                   cudaStream_t);                                                \
-  extern template void launch_rs_cols_fused<G>(const DevParams&, int, const uint32_t*, const uint32_t*,         \
-                                               uint32_t*, const ColShape&, cudaStream_t);                       \
+  extern template void launch_rs_cols_fused<G>(const DevParams&, int, const uint32_t*, uint32_t*,               \
+                                               const ColShape&, cudaStream_t);                                  \
   extern template void launch_mm_cols<G>(const DevParams&, const MmArgs&, const Scratch&, const ColShape&,     \
                                          cudaStream_t);
 CKKS_COL_DECL(G16)
@@ -399,29 +406,35 @@ struct EpiModDown {
   }
 };
 
-// Top limb of the fused ModDown + rescale (launch limb y = u):
-// V_u = (A_u[l] - z) P^-1 + extra_u[l].
-struct EpiModDownTop {
+// Inputs of the fused ModDown + rescale's iNTT rows: launch limbs y < 2 alpha
+// are the P limbs of the two accumulators (data limb lm.x of A); limb
+// 2 alpha + u is the top limb's E_u = A_u[l] P^-1 + extra_u[l] (l = n - 1, NTT
+// domain, formed while loading), so that the top limb's ModDown output
+// V_u = (A_u[l] - z) P^-1 + extra_u[l] = E_u - z P^-1 can be finished in the
+// coefficient domain by the column kernel that converts z = BConv(P -> q_l).
+struct SrcModDownTop {
   KsArgs a;
   const uint32_t* A;
   size_t a_stride;
-  uint32_t* V;
   template <int E>
-  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
+  __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2 lm,
                                              uint32_t pos0) const {
-    const int u = y, top = a.n - 1;
+    const int two_alpha = 2 * dp.alpha;
+    if (y < two_alpha) {
+      load_vec<E>(x, A + ((size_t)lm.x << dp.log_n) + pos0);
+      return;
+    }
+    const int u = y - two_alpha, top = a.n - 1;
     const PrimeConst P = dp.pc[top];
     const uint2 pinv = dp.ks.dn_pinv[top];
 #pragma unroll
     for (int c = 0; c < E / 4; ++c) {
       const uint32_t p = pos0 + 4 * c;
-      uint32_t acc[4], e[4], z[4];
+      uint32_t acc[4], e[4];
       load_vec<4>(acc, A + u * a_stride + ((size_t)top << dp.log_n) + p);
       ks_extra4(dp, a, u, top, p, P, e);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pinv.x, pinv.y, P.q), P.q), e[k], P.q);
-      store_vec<4>(V + ((size_t)u << dp.log_n) + p, z);
+      for (int k = 0; k < 4; ++k) x[4 * c + k] = addm(csub(shoup(acc[k], pinv.x, pinv.y, P.q), P.q), e[k], P.q);
     }
   }
 };
@@ -624,23 +637,17 @@ template <class G>
 static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const KsArgs& a, const uint32_t* A,
                                  size_t a_stride, cudaStream_t st) {
   const int n = a.n, alpha = dp.alpha, top = n - 1;
-  const size_t limb = (size_t)1 << dp.log_n;
-  uint32_t* T2 = sc.T;              // [2] converted top limb (NTT cols, then rows)
-  uint32_t* V = sc.T + 2 * limb;    // [2] ModDown output of the top limb
-  uint32_t* T3 = sc.T + 4 * limb;   // [2][top] fused conversions
-  uint32_t* Y = sc.U;               // [2][alpha] centered P-limb coefficients
-  launch_rows_g<G>(dp, true, A, sc.S, 2 * alpha,
-                   LimbMap{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)}, true, st);
+  uint32_t* T3 = sc.T;   // [2][top] fused conversions
+  uint32_t* Y = sc.U;    // [2][alpha + 1] centered coefficients: P limbs, then the top limb's ModDown output
+  // iNTT rows of the P limbs and of E_u (SrcModDownTop), compact in S
+  LimbMap in_map{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)};
+  in_map.tail = 2 * alpha;
+  in_map.tail_prime = top;
+  launch_rows_inv<G>(dp, SrcModDownTop{a, A, a_stride}, sc.S, 2 * alpha + 2, in_map, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
   launch_moddown_cols_top<G>(dp, n, sc, Y, st);
   prof_mark(sc, st, P_MODDOWN_COLS);
-  LimbMap top_map{nullptr, 0, 1, 1, dp.L};
-  top_map.fixed = top;
-  launch_rows_fwd<G>(dp, T2, EpiModDownTop{a, A, a_stride, V}, 2, top_map, st);
-  prof_mark(sc, st, P_MODDOWN_ROWS);
-  launch_rows_g<G>(dp, true, V, V, 2, top_map, false, st);
-  prof_mark(sc, st, P_RS_IN_ROWS);
-  launch_rs_cols_fused<G>(dp, n, V, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
+  launch_rs_cols_fused<G>(dp, n, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_fwd<G>(dp, T3, EpiRsOut{a, A, a_stride}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, st);
   prof_mark(sc, st, P_RS_ROWS);
@@ -924,7 +931,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
         def = default_shape<G>(2, dp.sms);
         targets = n - 1;
         run = [&](const ColShape& s) {
-          launch_rs_cols_fused<G>(dp, n, sc.T + 2 * limb, sc.U, sc.T + 4 * limb, s, st);
+          launch_rs_cols_fused<G>(dp, n, sc.U, sc.T, s, st);
         };
       }
       ColShape best = def;

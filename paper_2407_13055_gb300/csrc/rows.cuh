@@ -24,7 +24,9 @@ struct LimbMap {
   int pl = 1 << 30, ps = 0;
   int fixed = -1;   // >= 0: every limb uses this prime id
   int base = 0;
+  int tail = 1 << 30, tail_prime = 0;  // launch limbs y >= tail: (y, tail_prime)
   __device__ __forceinline__ int2 operator()(int y) const {
+    if (y >= tail) return make_int2(y, tail_prime);
     if (tab) return tab[y];
     const int u = y / pl, r = y % pl;
     const int t = (first + r) % per;

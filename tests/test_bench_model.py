@@ -59,9 +59,14 @@ def test_moddown_stages_split_hmult_and_hrot():
     assert hm["moddown_cols"]["mac"] == 2 * N * a
     assert hm["rescale_cols"]["mac"] == 2 * (n - 1) * N * (a + 1)
     assert "rescale_cols" not in hr
+    # HMult finishes the top limb's ModDown in the coefficient domain: no
+    # ModDown NTT rows and no separate iNTT rows before the rescale columns
+    assert "moddown_rows" not in hm and "rescale_in_rows" not in hm
+    assert hm["moddown_in_rows"]["shoup"] > hr["moddown_in_rows"]["shoup"]
     m = bench.kernel_models(n, a)
     assert m["moddown_cols"]["mac"] == (hm["moddown_cols"]["mac"] + hr["moddown_cols"]["mac"]) / 2
     assert m["rescale_cols"]["mac"] == hm["rescale_cols"]["mac"]
+    assert m["moddown_rows"]["shoup"] == hr["moddown_rows"]["shoup"]
 
 
 @pytest.mark.parametrize("alpha", [40, 14, 8])
