@@ -97,14 +97,14 @@ def stage_work(op, n=L, alpha=ALPHA):
         "keymult": dict(bytes=2 * d * ext * lb, smr=2 * d * ext * N),
     }
     if hm:
-        # top limb first (ModDown of q_l in the coefficient domain, then its
-        # coefficients join the fused rescale): the iNTT rows also take
-        # E = acc_l P^-1 + d_l (b1, b2 top limbs read, d0 / d1 of that limb
-        # re-formed); the first column kernel iNTTs E, converts P -> q_l and
-        # forms V = E - z P^-1
+        # the iNTT rows also take E = acc_l P^-1 + d_l of the top limb (b1, b2
+        # top limbs read, d0 / d1 of that limb re-formed); one column kernel
+        # per tile iNTTs the P limbs and E, converts P -> q_l, forms the top
+        # limb's ModDown output V = E - z P^-1 and converts the P limbs and V
+        # to the n - 1 lower primes (the rescale), then their NTT columns
         w["moddown_in_rows"] = dict(bytes=2 * lb, shoup=2 * (alpha + 1) * row + 2 * N, smr=6 * N)
-        w["moddown_cols"] = dict(shoup=2 * (alpha + 1) * col + 2 * N, mac=2 * N * alpha)
-        w["rescale_cols"] = dict(shoup=2 * (n - 1) * col, mac=2 * (n - 1) * N * (alpha + 1))
+        w["rescale_cols"] = dict(shoup=2 * (alpha + 1) * col + 2 * N + 2 * (n - 1) * col,
+                                 mac=2 * N * alpha + 2 * (n - 1) * N * (alpha + 1))
         # NTT rows + (A - w)(P q_l)^-1 + d q_l^-1 with d0 / d1 re-formed from
         # the inputs (b1, b2 read here first), output 2(n - 1) limbs
         w["rescale_rows"] = dict(bytes=4 * (n - 1) * lb, shoup=2 * (n - 1) * (row + 2 * N),
@@ -514,7 +514,7 @@ def run_native(args, rank, world, local_rank):
     ks_stages = ("ks_in_rows", "modup_cols", "modup_rows", "keymult", "moddown_in_rows", "moddown_cols")
     per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
     # stages both operations run are averaged over both in the profile
-    hmult_us = 1e3 * sum(per_launch[k] for k in ks_stages + ("rescale_cols", "rescale_rows"))
+    hmult_us = 1e3 * sum(per_launch[k] for k in ks_stages[:5] + ("rescale_cols", "rescale_rows"))
     hrot_us = 1e3 * sum(per_launch[k] for k in ks_stages + ("moddown_rows",))
 
     # end to end through the C ABI with host buffers. A step is e2e_pairs pairs

@@ -328,31 +328,21 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols(DevP
 }
 
 
-// ModDown fused with rescaling, first column kernel: the P limbs' iNTT
-// columns give the centered coefficients y (kept in Y for the second
-// kernel); only the top limb q_l is converted here, and its ModDown output is
-// finished in the coefficient domain: S holds, after the P limbs of both
-// polynomials, E_u = A_u[l] P^-1 + extra_u[l] through its iNTT rows, so that
-// V_u = E_u - z P^-1 (z = BConv(P -> q_l)) comes out of this kernel as
-// coefficients; its centered value c_l joins Y as source alpha of the fused
-// rescale conversion. Y = [2][alpha + 1][N]. grid (W/TC, 2 polys).
-template <class G, int TC, int SL>
-__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
-                                                                                        const uint32_t* S,
-                                                                                        uint32_t* Y) {
-  pdl_wait();
-  pdl_trigger();
+// Top limb of the ModDown fused with rescaling, on one column tile of
+// polynomial u (every thread of the block calls it). S holds the P limbs of
+// both polynomials through their iNTT rows and, after them, E_u = A_u[l] P^-1
+// + extra_u[l] (l = n - 1) through its iNTT rows. The P limbs' iNTT columns
+// give their centered coefficients y (sources 0 .. alpha - 1 in y4); E's iNTT
+// columns and the conversion z = BConv(P -> q_l) give the top limb's ModDown
+// output V = E - z P^-1 = iNTT((A_l - z_l) P^-1 + d_l) in the coefficient
+// domain, whose centered value c_l becomes source alpha. With Yu the y and
+// c_l are also stored ([alpha + 1][N], A layout along h).
+template <class G, int TC>
+__device__ __forceinline__ void top_limb_sources(const DevParams& dp, int n, const uint32_t* S, int4* y4,
+                                                 uint32_t* colbuf, int l, int jj, int c, int pos, int slice, int SL,
+                                                 int u, uint32_t* Yu) {
   using CTL = ColTile<G, TC>;
-  extern __shared__ int4 smem4[];
-  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
-  const int c = pos % TC, jj = pos / TC;
-  const int l = blockIdx.x * TC + c;
-  const int u = blockIdx.y;
   const int alpha = dp.alpha, top = n - 1;
-  int4* y4 = smem4;
-  uint32_t* colbuf =
-      reinterpret_cast<uint32_t*>(smem4 + (size_t)(alpha + 1) * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
-  uint32_t* Yu = Y + ((size_t)(u * (alpha + 1)) << dp.log_n);
   col_inputs<G, TC>(dp, S + ((size_t)(u * alpha) << dp.log_n), (size_t)1 << dp.log_n, alpha, dp.L, dp.ks.dn_cin,
                     y4, colbuf, l, jj, c, pos, slice, SL, Yu);
   const PrimeConst Pt = dp.pc[top];
@@ -378,29 +368,58 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(
     bconv_accumulate<G::EC, CTL::CT>(y4, pos, alpha, dp.ks.dn_mat + top * alpha, Pt, z,
                                      no_fold(src_bound(dp, alpha, dp.L), Pt.q));
     const uint2 pinv = dp.ks.dn_pinv[top];
-    uint32_t* yc = Yu + ((size_t)alpha << dp.log_n);
 #pragma unroll
     for (int i4 = 0; i4 < G::EC / 4; ++i4) {
-      const int4 e = y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos];
+      int4& slot = y4[(alpha * (G::EC / 4) + i4) * CTL::CT + pos];
+      const int4 e = slot;
       const uint32_t ev[4] = {(uint32_t)e.x, (uint32_t)e.y, (uint32_t)e.z, (uint32_t)e.w};
+      int32_t cl[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int i = 4 * i4 + k;
-        const uint32_t zp = csub(shoup(z[i], pinv.x, pinv.y, Pt.q), Pt.q);
-        const uint32_t v = csub(ev[k] + Pt.q - zp, Pt.q);
-        yc[(jj + G::EC * i) * G::W + l] = (uint32_t)centered(v, Pt.q);
+        const uint32_t zp = csub(shoup(z[4 * i4 + k], pinv.x, pinv.y, Pt.q), Pt.q);
+        cl[k] = centered(csub(ev[k] + Pt.q - zp, Pt.q), Pt.q);
+      }
+      slot = make_int4(cl[0], cl[1], cl[2], cl[3]);
+      if (Yu) {
+        uint32_t* yc = Yu + ((size_t)alpha << dp.log_n);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) yc[(jj + G::EC * (4 * i4 + k)) * G::W + l] = (uint32_t)cl[k];
       }
     }
   }
+  __syncthreads();
 }
 
-// ModDown fused with rescaling, second column kernel: the K = alpha + 1
-// stored centered coefficients of polynomial u (P limbs and c_l) convert to
-// q_i (matrix rs_mat: the ModDown row plus [P]_{q_i}) as w_i = z_i + P [c_l]_{q_i};
-// then the NTT columns. grid (W/TC, 2 polys, Z); targets i < l.
+// Top limb of the fused ModDown + rescale alone (the tensor-core form of the
+// rescale conversion takes its sources from Y = [2][alpha + 1][N]).
+// grid (W/TC, 2 polys).
+template <class G, int TC, int SL>
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_ks_moddown_cols_top(DevParams dp, int n,
+                                                                                        const uint32_t* S,
+                                                                                        uint32_t* Y) {
+  pdl_wait();
+  pdl_trigger();
+  using CTL = ColTile<G, TC>;
+  extern __shared__ int4 smem4[];
+  const int slice = threadIdx.x / CTL::CT, pos = threadIdx.x % CTL::CT;
+  const int c = pos % TC, jj = pos / TC;
+  const int l = blockIdx.x * TC + c;
+  const int u = blockIdx.y, alpha = dp.alpha;
+  uint32_t* colbuf =
+      reinterpret_cast<uint32_t*>(smem4 + (size_t)(alpha + 1) * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
+  top_limb_sources<G, TC>(dp, n, S, smem4, colbuf, l, jj, c, pos, slice, SL, u,
+                          Y + ((size_t)(u * (alpha + 1)) << dp.log_n));
+}
+
+// ModDown fused with rescaling, one column kernel per tile: the top limb's
+// sources (top_limb_sources: the P limbs' centered coefficients and c_l, K =
+// alpha + 1) convert to every q_i, i < l (matrix rs_mat: the ModDown row plus
+// [P]_{q_i}) as w_i = z_i + P [c_l]_{q_i}; then the NTT columns. The top
+// limb's ModDown needs only the coefficients of its own column positions, so
+// it happens inside the tile. grid (W/TC, 2 polys, Z).
 template <class G, int TC, int SL, int TP>
-__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n,
-                                                                                  const uint32_t* Y, uint32_t* T) {
+__global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevParams dp, int n, const uint32_t* S,
+                                                                                  uint32_t* T) {
   pdl_wait();
   pdl_trigger();
   using CTL = ColTile<G, TC>;
@@ -412,17 +431,7 @@ __global__ void __launch_bounds__(SL* ColTile<G, TC>::CT) k_rs_cols_fused(DevPar
   const int alpha = dp.alpha, top = n - 1, K = alpha + 1;
   int4* y4 = smem4;
   uint32_t* colbuf = reinterpret_cast<uint32_t*>(smem4 + (size_t)K * (G::EC / 4) * CTL::CT) + slice * CTL::BUF;
-  // stored centered coefficients, A layout along h
-  for (int k = slice; k < K; k += SL) {
-    const uint32_t* yk = Y + ((size_t)(u * K + k) << dp.log_n);
-    int32_t y[G::EC];
-#pragma unroll
-    for (int i = 0; i < G::EC; ++i) y[i] = (int32_t)yk[(jj + G::EC * i) * G::W + l];
-#pragma unroll
-    for (int i4 = 0; i4 < G::EC / 4; ++i4)
-      y4[(k * (G::EC / 4) + i4) * CTL::CT + pos] = make_int4(y[4 * i4], y[4 * i4 + 1], y[4 * i4 + 2], y[4 * i4 + 3]);
-  }
-  __syncthreads();
+  top_limb_sources<G, TC>(dp, n, S, y4, colbuf, l, jj, c, pos, slice, SL, u, nullptr);
   auto tgt = [&](int i, const int32_t*& row, int& id, uint32_t*& dst) {
     row = dp.ks.rs_mat + i * K;
     id = i;
@@ -626,17 +635,20 @@ void launch_moddown_cols_top(const DevParams& dp, int n, const Scratch& sc, uint
 }
 
 template <class G>
-void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* Y, uint32_t* T3, const ColShape& s0,
+void launch_rs_cols_fused(const DevParams& dp, int n, const Scratch& sc, uint32_t* T3, const ColShape& s0,
                           cudaStream_t st) {
   if (is_tc_shape(s0) && dp.ks.tc_img && dp.alpha + 1 <= kTcMaxSources &&
       with_tc_shape<G>(s0, [&](auto tc, auto sl, auto nc) {
         constexpr int TC = decltype(tc)::value, SL = decltype(sl)::value, NC = decltype(nc)::value;
         using SH = TcShape<G, TC, SL, NC>;
+        // top limb first (its sources go through Y), then the conversion on
+        // the tensor cores
+        launch_moddown_cols_top<G>(dp, n, sc, sc.U, st);
         const int kr = tc_kr(dp.alpha + 1);
         const size_t sm = tc_smem<SH, NC>(kr, n - 1).total;
         set_col_smem((const void*)k_rs_cols_fused_tc<G, TC, SL, NC>, sm);
-        launch_pdl(dp.pdl, k_rs_cols_fused_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, kr, Y,
-                   T3);
+        launch_pdl(dp.pdl, k_rs_cols_fused_tc<G, TC, SL, NC>, dim3(G::W / TC, 2), dim3(SH::NT), sm, st, dp, n, kr,
+                   (const uint32_t*)sc.U, T3);
         count_launch(1);
       }))
     return;
@@ -646,7 +658,7 @@ void launch_rs_cols_fused(const DevParams& dp, int n, const uint32_t* Y, uint32_
     const size_t sm = col_smem_bytes<G, TC, SL>(dp.alpha + 1);
     set_col_smem((const void*)k_rs_cols_fused<G, TC, SL, TP>, sm);
     launch_pdl(dp.pdl, k_rs_cols_fused<G, TC, SL, TP>, dim3(G::W / TC, 2, s.z), dim3(SL * ColTile<G, TC>::CT), sm, st, dp,
-               n, Y, T3);
+               n, (const uint32_t*)sc.S, T3);
     count_launch(1);
   });
 }

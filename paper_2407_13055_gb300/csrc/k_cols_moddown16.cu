@@ -4,6 +4,5 @@
 namespace ckks {
 
 template void launch_moddown_cols<Geo<8, 32>>(const DevParams&, int, int, int, const Scratch&, const ColShape&, cudaStream_t);
-template void launch_moddown_cols_top<Geo<8, 32>>(const DevParams&, int, const Scratch&, uint32_t*, cudaStream_t);
 
 }  // namespace ckks

@@ -7,8 +7,7 @@ namespace ckks {
   template void launch_modup_cols<G>(const DevParams&, int, int, int, int, const Scratch&, const ColShape&,     \
                                      cudaStream_t);                                                           \
   template void launch_moddown_cols<G>(const DevParams&, int, int, int, const Scratch&, const ColShape&, cudaStream_t); \
-  template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*, cudaStream_t);      \
-  template void launch_rs_cols_fused<G>(const DevParams&, int, const uint32_t*, uint32_t*, const ColShape&,      \
+  template void launch_rs_cols_fused<G>(const DevParams&, int, const Scratch&, uint32_t*, const ColShape&,       \
                                         cudaStream_t);                                                        \
   template void launch_mm_cols<G>(const DevParams&, const MmArgs&, const Scratch&, const ColShape&, cudaStream_t);
 using G12 = Geo<8, 8>;

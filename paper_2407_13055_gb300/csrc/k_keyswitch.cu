@@ -16,9 +16,9 @@
 //
 // HMult with rescaling by q_l fuses the ModDown into the rescale: the P limbs'
 // iNTT rows also take E = acc_l P^-1 + d_l of the top limb; one column kernel
-// finishes the top limb's ModDown output V = E - BConv(P -> q_l) P^-1 in the
-// coefficient domain; the second converts the P limbs and V's centered
-// coefficients to every q_i, i < l, and the NTT rows' epilogue forms
+// finishes, per column tile, the top limb's ModDown output V = E - BConv(P ->
+// q_l) P^-1 in the coefficient domain and converts the P limbs' and V's
+// centered coefficients to every q_i, i < l; the NTT rows' epilogue forms
 // (acc_i - w_i)(P q_l)^-1 + d_i q_l^-1.
 //
 // Row kernels (rows.cuh) hold W-word rows in registers with their twiddles
@@ -47,9 +47,7 @@ using G8 = Geo<4, 4>;
                                             cudaStream_t);                                                      \
   extern template void launch_moddown_cols<G>(const DevParams&, int, int, int, const Scratch&, const ColShape&,      \
                                               cudaStream_t);                                                    \
-  extern template void launch_moddown_cols_top<G>(const DevParams&, int, const Scratch&, uint32_t*,             \
-                                                  cudaStream_t);                                                \
-  extern template void launch_rs_cols_fused<G>(const DevParams&, int, const uint32_t*, uint32_t*,               \
+  extern template void launch_rs_cols_fused<G>(const DevParams&, int, const Scratch&, uint32_t*,                \
                                                const ColShape&, cudaStream_t);                                  \
   extern template void launch_mm_cols<G>(const DevParams&, const MmArgs&, const Scratch&, const ColShape&,     \
                                          cudaStream_t);
@@ -638,16 +636,13 @@ static void moddown_rescale_tail(const DevParams& dp, const Scratch& sc, const K
                                  size_t a_stride, cudaStream_t st) {
   const int n = a.n, alpha = dp.alpha, top = n - 1;
   uint32_t* T3 = sc.T;   // [2][top] fused conversions
-  uint32_t* Y = sc.U;    // [2][alpha + 1] centered coefficients: P limbs, then the top limb's ModDown output
   // iNTT rows of the P limbs and of E_u (SrcModDownTop), compact in S
   LimbMap in_map{nullptr, n, n + alpha, n, dp.L, alpha, (int)(a_stride >> dp.log_n)};
   in_map.tail = 2 * alpha;
   in_map.tail_prime = top;
   launch_rows_inv<G>(dp, SrcModDownTop{a, A, a_stride}, sc.S, 2 * alpha + 2, in_map, true, st);
   prof_mark(sc, st, P_MODDOWN_IN_ROWS);
-  launch_moddown_cols_top<G>(dp, n, sc, Y, st);
-  prof_mark(sc, st, P_MODDOWN_COLS);
-  launch_rs_cols_fused<G>(dp, n, Y, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
+  launch_rs_cols_fused<G>(dp, n, sc, T3, pick_shape<G>(sc, CK_RS_FUSED, a.tix, default_shape<G>(2, dp.sms)), st);
   prof_mark(sc, st, P_RS_COLS);
   launch_rows_fwd<G>(dp, T3, EpiRsOut{a, A, a_stride}, 2 * top, LimbMap{nullptr, 0, top, top, dp.L}, st);
   prof_mark(sc, st, P_RS_ROWS);
@@ -931,7 +926,7 @@ int tune_columns(const DevParams& dp, const Scratch& sc, Tuning& tu, const KsArg
         def = default_shape<G>(2, dp.sms);
         targets = n - 1;
         run = [&](const ColShape& s) {
-          launch_rs_cols_fused<G>(dp, n, sc.U, sc.T, s, st);
+          launch_rs_cols_fused<G>(dp, n, sc, sc.T, s, st);
         };
       }
       ColShape best = def;

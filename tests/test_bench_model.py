@@ -56,15 +56,17 @@ def test_moddown_stages_split_hmult_and_hrot():
     N, n, a = 1 << bench.LOG_N, 40, 14
     hm, hr = bench.stage_work("hmult", n, a), bench.stage_work("hrot", n, a)
     assert hr["moddown_cols"]["mac"] == 2 * n * N * a
-    assert hm["moddown_cols"]["mac"] == 2 * N * a
-    assert hm["rescale_cols"]["mac"] == 2 * (n - 1) * N * (a + 1)
+    # HMult: the top limb's ModDown (P -> q_l, alpha products per coefficient
+    # and polynomial) and the rescale conversion (alpha + 1 sources to the
+    # n - 1 lower primes) in one column stage; no ModDown NTT rows and no
+    # separate iNTT rows before the rescale columns
+    assert hm["rescale_cols"]["mac"] == 2 * N * a + 2 * (n - 1) * N * (a + 1)
     assert "rescale_cols" not in hr
-    # HMult finishes the top limb's ModDown in the coefficient domain: no
-    # ModDown NTT rows and no separate iNTT rows before the rescale columns
-    assert "moddown_rows" not in hm and "rescale_in_rows" not in hm
+    assert not {"moddown_cols", "moddown_rows", "rescale_in_rows"} & set(hm)
     assert hm["moddown_in_rows"]["shoup"] > hr["moddown_in_rows"]["shoup"]
     m = bench.kernel_models(n, a)
-    assert m["moddown_cols"]["mac"] == (hm["moddown_cols"]["mac"] + hr["moddown_cols"]["mac"]) / 2
+    assert m["moddown_in_rows"]["shoup"] == (hm["moddown_in_rows"]["shoup"] + hr["moddown_in_rows"]["shoup"]) / 2
+    assert m["moddown_cols"]["mac"] == hr["moddown_cols"]["mac"]
     assert m["rescale_cols"]["mac"] == hm["rescale_cols"]["mac"]
     assert m["moddown_rows"]["shoup"] == hr["moddown_rows"]["shoup"]
 
