@@ -543,9 +543,13 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   for (int l = 1; l < L; ++l)
     for (int i = 0; i < l; ++i)
       dn_pqinv[(size_t)l * L + i] = shoup_pair(invm(mulm(ctx->gadget_p[i].x, pr[l] % pr[i], pr[i]), pr[i]), pr[i]);
-  std::vector<uint2> rs_qinv((size_t)L * L, make_uint2(0, 0));
+  std::vector<uint2> rs_qinv((size_t)L * L, make_uint2(0, 0)), rs_qinv_r((size_t)L * L, make_uint2(0, 0));
   for (int l = 1; l < L; ++l)
-    for (int i = 0; i < l; ++i) rs_qinv[(size_t)l * L + i] = shoup_pair(invm(pr[l] % pr[i], pr[i]), pr[i]);
+    for (int i = 0; i < l; ++i) {
+      const uint32_t inv = invm(pr[l] % pr[i], pr[i]);
+      rs_qinv[(size_t)l * L + i] = shoup_pair(inv, pr[i]);
+      rs_qinv_r[(size_t)l * L + i] = shoup_pair(mulm(inv, (uint32_t)((1ull << 32) % pr[i]), pr[i]), pr[i]);
+    }
 
   // rational rescaling transitions l -> l - 1 (windowed levels only)
   std::vector<int2> rr_drop, rr_rows;
@@ -717,6 +721,7 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
       {up_img.data(), up_img.size() * sizeof(int2), 0},
       {dn_img.data(), dn_img.size() * sizeof(int2), 0},
       {rs_img.data(), rs_img.size() * sizeof(int2), 0},
+      {rs_qinv_r.data(), rs_qinv_r.size() * sizeof(uint2), 0},
   };
   size_t total = 0;
   for (auto& p : parts) {
@@ -757,6 +762,7 @@ int build_context(ckks_ctx* ctx, const ckks_params* prm) {
   dp.ks.up_img = reinterpret_cast<const int2*>(base + parts[23].off);
   dp.ks.dn_img = reinterpret_cast<const int2*>(base + parts[24].off);
   dp.ks.rs_img = reinterpret_cast<const int2*>(base + parts[25].off);
+  dp.ks.rs_qinv_r = reinterpret_cast<const uint2*>(base + parts[26].off);
   for (int l = 1; l < nlev && ctx->windowed; ++l) {
     RrArgs& r = ctx->rr[l];
     r.drop = reinterpret_cast<const int2*>(base + parts[13].off) + rr_off[l].drop;

@@ -30,8 +30,11 @@ struct KsTables {
   const uint2* dn_cin;
   const int32_t* dn_mat;
   const uint2* dn_pinv;
-  // Rescale: rs_qinv[l * L + i] = Shoup pair of [q_l^-1]_{q_i}, i < l.
+  // Rescale: rs_qinv[l * L + i] = Shoup pair of [q_l^-1]_{q_i}, i < l;
+  // rs_qinv_r the same for [q_l^-1 2^32]_{q_i} (applied to a Montgomery-reduced
+  // product, which carries 2^-32).
   const uint2* rs_qinv;
+  const uint2* rs_qinv_r;
   // ModUp output limbs that need the NTT row phase, per level n (in order of
   // n = 1 .. L): (limb index j (n + alpha) + t in the scratch, prime id) for
   // every digit j and every extended limb t outside the digit.

@@ -437,11 +437,34 @@ struct SrcModDownTop {
   }
 };
 
+// HMult's d0 = b1 b2 (u = 0) or d1 = a1 b2 + a2 b1 (u = 1) at limb i, times
+// 2^-32: the 64-bit product (or sum of two, below 2 q^2 < 2^32 q) through one
+// unsigned Montgomery reduction, in [0, 2q]; the caller's constant carries
+// the 2^32 back.
+__device__ __forceinline__ void tensor_d4_mont(const DevParams& dp, const KsArgs& a, int u, int i, uint32_t p0,
+                                               const PrimeConst& P, uint32_t (&e)[4]) {
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  uint32_t b1[4], b2[4];
+  load_vec<4>(b1, a.x0 + off);
+  load_vec<4>(b2, a.x1 + off);
+  if (u == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = redc64((uint64_t)b1[k] * b2[k], P.q, P.m);
+  } else {
+    uint32_t a1[4], a2[4];
+    load_vec<4>(a1, a.x0 + a.poly_stride0 + off);
+    load_vec<4>(a2, a.x1 + a.poly_stride1 + off);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = redc64((uint64_t)a1[k] * b2[k] + (uint64_t)a2[k] * b1[k], P.q, P.m);
+  }
+}
+
 // Output of the fused ModDown + rescale after the NTT rows of the conversion
 // w (launch limb y = u top + i, top = l): out_u[i] = (A_u[i] - w)(P q_l)^-1 +
 // extra_u[i] q_l^-1, d0/d1 re-formed from the four input limbs (at the
 // three-pass rows' 24 warps per SM their loads hide: 39 us against 23 + 23
-// us as rows then a streaming kernel).
+// us as rows then a streaming kernel). For HMult (extra = 1) the products are
+// reduced once (tensor_d4_mont) and q_l^-1 2^32 restores their scale.
 struct EpiRsOut {
   KsArgs a;
   const uint32_t* A;
@@ -451,14 +474,17 @@ struct EpiRsOut {
                                              uint32_t pos0) const {
     const int top = a.n - 1, u = y / top, i = y % top;
     const PrimeConst P = dp.pc[i];
-    const uint2 pq = dp.ks.dn_pqinv[top * dp.L + i], qi = dp.ks.rs_qinv[top * dp.L + i];
+    const bool mont = a.extra == 1;
+    const uint2 pq = dp.ks.dn_pqinv[top * dp.L + i],
+                qi = mont ? dp.ks.rs_qinv_r[top * dp.L + i] : dp.ks.rs_qinv[top * dp.L + i];
     const size_t limb = (size_t)i << dp.log_n;
 #pragma unroll
     for (int c = 0; c < E / 4; ++c) {
       const uint32_t p = pos0 + 4 * c;
       uint32_t acc[4], e[4], z[4];
       load_vec<4>(acc, A + u * a_stride + limb + p);
-      ks_extra4(dp, a, u, i, p, P, e);
+      if (mont) tensor_d4_mont(dp, a, u, i, p, P, e);
+      else ks_extra4(dp, a, u, i, p, P, e);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         z[k] = addm(csub(shoup(acc[k] - x[4 * c + k] + P.q, pq.x, pq.y, P.q), P.q),
