@@ -142,16 +142,17 @@ def multiply_costs(rates):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# one-lane pipeline's kernels from one `ncu --set full` capture (cold cache;
-# the command is recorded with the committed profile summary), keyed by stage. They
+# one-lane pipeline's kernels from one ncu launch list with those two metrics
+# (cold cache; the command is recorded with the committed profile summary;
+# stages that two kernels share: the mean of the two), keyed by stage. They
 # describe the kernel sources they were taken on: when the SHA-1 of those
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "c969e2343adaf4d20f312ae79208845cd459e89f",
-    "bytes_per_launch": {"modup_cols": 10.62e6, "keymult": 143.04e6, "modup_rows": 60.38e6,
-                         "moddown_cols": 7.40e6, "moddown_rows": 74.94e6, "rescale_cols": 7.92e6,
-                         "rescale_rows": 115.89e6, "ks_in_rows": 37.47e6},
+    "sources_sha1": "e9785912a6f59e170c52d57b54eb693d0e0846c0",
+    "bytes_per_launch": {"modup_cols": 10.58e6, "keymult": 136.21e6, "modup_rows": 60.33e6,
+                         "moddown_in_rows": 15.76e6, "moddown_cols": 7.40e6, "moddown_rows": 74.26e6,
+                         "rescale_cols": 7.95e6, "rescale_rows": 115.48e6, "ks_in_rows": 37.31e6},
 }
 
 
