@@ -135,19 +135,37 @@ void launch_rows_inv_only(const DevParams& dp, uint32_t* data, int limbs, IdMap 
 // bit reversal is an involution, so one kernel serves both directions.
 // ---------------------------------------------------------------------------
 
-__global__ void k_permute(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int log_n) {
-  const uint32_t n = 1u << log_n;
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+// Bit-reversal permutation of each limb (an involution): out[p] = in[brev(p)].
+// A position of log_n = 2K + m bits is p = (a, b, c) with a the top K bits, b
+// the middle m and c the low K; brev(p) = (brev(c), brev(b), brev(a)). A block
+// takes one b: it reads the 2^K x 2^K tile in[(a, b, c)] row by row (c runs
+// over consecutive words) into shared memory and writes out[(r, brev(b), j)] =
+// tile[brev(j)][brev(r)] row by row (j consecutive), so both sides move whole
+// 2^K-word runs; the padded row makes the column reads conflict-free.
+template <int K>
+__global__ void __launch_bounds__(256) k_permute(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                 int log_n) {
+  constexpr int T = 1 << K;
+  __shared__ uint32_t tile[T][T + 1];
+  const int m = log_n - 2 * K;
+  const uint32_t b = blockIdx.x;
+  const uint32_t bb = m > 0 ? brev_n(b, m) : 0u;
   const size_t base = (size_t)blockIdx.y << log_n;
-  out[base + p] = in[base + brev_n(p, log_n)];
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int a = idx >> K, c = idx & (T - 1);
+    tile[a][c] = in[base + ((size_t)a << (K + m)) + ((size_t)b << K) + c];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = idx >> K, j = idx & (T - 1);
+    out[base + ((size_t)r << (K + m)) + ((size_t)bb << K) + j] = tile[brev_n(j, K)][brev_n(r, K)];
+  }
 }
 
 void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int limbs, bool, cudaStream_t st) {
   if (limbs <= 0) return;
-  const int n = 1 << dp.log_n;
-  dim3 g((n + 255) / 256, limbs);
-  k_permute<<<g, 256, 0, st>>>(in, out, dp.log_n);
+  if (dp.log_n >= 10) k_permute<5><<<dim3(1u << (dp.log_n - 10), limbs), 256, 0, st>>>(in, out, dp.log_n);
+  else k_permute<4><<<dim3(1u << (dp.log_n - 8), limbs), 256, 0, st>>>(in, out, dp.log_n);  // N = 2^8
 }
 
 // ---------------------------------------------------------------------------
