@@ -379,10 +379,29 @@ struct SrcKsInput {
 
 // ModDown epilogue after the NTT rows of z (launch limb y = u n + i):
 // out_u[i] = (A_u[i] - z) P^-1 + extra_u[i].
+// L2 prefetch of the operands an HMult epilogue reads at limb i (poly u,
+// positions p0 ..): the tensor inputs d0 / d1 are formed from.
+__device__ __forceinline__ void prefetch_tensor_inputs(const DevParams& dp, const KsArgs& a, int u, int i,
+                                                       uint32_t p0) {
+  if (a.extra != 1) return;
+  const size_t off = ((size_t)i << dp.log_n) + p0;
+  prefetch_l2(a.x0 + off);
+  prefetch_l2(a.x1 + off);
+  if (u == 1) {
+    prefetch_l2(a.x0 + a.poly_stride0 + off);
+    prefetch_l2(a.x1 + a.poly_stride1 + off);
+  }
+}
+
 struct EpiModDown {
   KsArgs a;
   const uint32_t* A;
   size_t a_stride;
+  __device__ __forceinline__ void prefetch(const DevParams& dp, int y, uint32_t pos0) const {
+    const int u = y / a.n, i = y % a.n;
+    prefetch_l2(A + u * a_stride + ((size_t)i << dp.log_n) + pos0);
+    prefetch_tensor_inputs(dp, a, u, i, pos0);
+  }
   template <int E>
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {
@@ -469,6 +488,11 @@ struct EpiRsOut {
   KsArgs a;
   const uint32_t* A;
   size_t a_stride;
+  __device__ __forceinline__ void prefetch(const DevParams& dp, int y, uint32_t pos0) const {
+    const int top = a.n - 1, u = y / top, i = y % top;
+    prefetch_l2(A + u * a_stride + ((size_t)i << dp.log_n) + pos0);
+    prefetch_tensor_inputs(dp, a, u, i, pos0);
+  }
   template <int E>
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {

@@ -5,6 +5,8 @@
 // register pass, which are specific to the thread) are issued before the
 // first butterfly, so a warp waits for memory once instead of once per stage.
 #pragma once
+#include <type_traits>
+
 #include "geo.cuh"
 #include "internal.h"
 #include "pdl.cuh"
@@ -33,6 +35,18 @@ struct LimbMap {
     return make_int2(u * ps + first + r, fixed >= 0 ? fixed : (t < n ? base + t : L + (t - n)));
   }
 };
+
+// Epilogues that read operands after the transform may name them up front
+// (a method prefetch(dp, y, pos0)): the row kernel asks for them to be moved
+// into L2 before it starts its passes, so the epilogue's loads find them there.
+template <class Epi, class = void>
+struct HasPrefetch : std::false_type {};
+template <class Epi>
+struct HasPrefetch<Epi, std::void_t<decltype(&Epi::prefetch)>> : std::true_type {};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // Register-resident twiddles of one pass: tw[(1 << s) - 1 + b] for local
 // stage s and block b (2^s blocks).
@@ -338,6 +352,7 @@ __global__ void __launch_bounds__(128, 6) k_rows3_fwd_t(DevParams dp, const uint
   __syncthreads();
   pdl_wait();
   pdl_trigger();
+  if constexpr (HasPrefetch<Epi>::value) epi.prefetch(dp, (int)blockIdx.y, (uint32_t)(h * 1024 + 16 * t));
   const uint32_t* s = src + ((size_t)lm.x << dp.log_n) + (size_t)h * 1024;
   uint32_t x[16];
 #pragma unroll
