@@ -149,10 +149,10 @@ def multiply_costs(rates):
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "e9785912a6f59e170c52d57b54eb693d0e0846c0",
-    "bytes_per_launch": {"modup_cols": 10.58e6, "keymult": 136.21e6, "modup_rows": 60.33e6,
-                         "moddown_in_rows": 15.76e6, "moddown_cols": 7.40e6, "moddown_rows": 74.26e6,
-                         "rescale_cols": 7.95e6, "rescale_rows": 115.48e6, "ks_in_rows": 37.31e6},
+    "sources_sha1": "a2f9442f396f431ff567e9830ec716c691b62f2f",
+    "bytes_per_launch": {"modup_cols": 10.58e6, "keymult": 136.12e6, "modup_rows": 60.33e6,
+                         "moddown_in_rows": 15.77e6, "moddown_cols": 7.40e6, "moddown_rows": 74.31e6,
+                         "rescale_cols": 7.95e6, "rescale_rows": 117.81e6, "ks_in_rows": 37.31e6},
 }
 
 

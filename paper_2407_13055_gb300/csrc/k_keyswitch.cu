@@ -525,6 +525,13 @@ struct EpiMmOut {
   MmArgs m;
   const uint32_t* A;
   size_t a_stride;
+  __device__ __forceinline__ void prefetch(const DevParams& dp, int y, uint32_t pos0) const {
+    const int u = y / m.n1, t = y % m.n1;
+    const int old_limb = m.epi[t].old_limb;
+    if (old_limb < 0) return;
+    prefetch_l2(A + u * a_stride + ((size_t)old_limb << dp.log_n) + pos0);
+    prefetch_tensor_inputs(dp, a, u, old_limb, pos0);
+  }
   template <int E>
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {
@@ -560,6 +567,9 @@ struct EpiRescale {
   int top;
   uint32_t* out;
   size_t sout;
+  __device__ __forceinline__ void prefetch(const DevParams& dp, int y, uint32_t pos0) const {
+    prefetch_l2(in + (y / top) * sin + ((size_t)(y % top) << dp.log_n) + pos0);
+  }
   template <int E>
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {
@@ -627,6 +637,10 @@ struct EpiRational {
   size_t sin;
   uint32_t* out;
   size_t sout;
+  __device__ __forceinline__ void prefetch(const DevParams& dp, int y, uint32_t pos0) const {
+    const int old_limb = r.epi[y % r.n1].old_limb;
+    if (old_limb >= 0) prefetch_l2(in + (y / r.n1) * sin + ((size_t)old_limb << dp.log_n) + pos0);
+  }
   template <int E>
   __device__ __forceinline__ void operator()(const DevParams& dp, uint32_t (&x)[E], int y, int2,
                                              uint32_t pos0) const {
