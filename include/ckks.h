@@ -54,6 +54,7 @@ extern "C" {
 #define CKKS_ECUDA (-6)    /* a CUDA call failed (message in ckks_last_error) */
 #define CKKS_ETIMEOUT (-7) /* a bounded device-side wait expired */
 #define CKKS_EBUSY (-8)    /* admission refused (memory footprint) */
+#define CKKS_ERANGE (-9)   /* checked launch mode: a residue was not below its prime */
 
 #define CKKS_RESCALE 1     /* ckks_hmult flag: rescale the product (Sec. 2.1) */
 #define CKKS_RESCALE_MERGED 2 /* ckks_hmult flag: rescale with ModDown merged into it (Sec. 6) */
@@ -396,6 +397,21 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint32_t* in_dev, int level, uint3
  * on a windowed context; CKKS_RESCALE_MERGED is refused); the first such
  * operation allocates the form's scratch on the context. */
 #define CKKS_LAUNCH_UNFUSED 4
+/* CKKS_LAUNCH_CHECKED (default off): checked mode. Every homomorphic
+ * operation first checks, on the device, that each residue of its ciphertext
+ * and plaintext operands is below its prime (q_i of the level's window, p_k of
+ * the auxiliary limbs), and checks its output the same way after it ran;
+ * uploads and imports of ciphertexts, plaintexts and evaluation keys check
+ * what they wrote. A violation marks the context's status word: the next
+ * synchronizing call on the context or a clone (ckks_sync, exports, imports,
+ * decryption) returns CKKS_ERANGE and clears the mark; the results of the
+ * operations since the previous synchronizing call are then undefined, and
+ * the context stays usable. The checks cost one extra read of every operand
+ * and result. No kernel indexes memory by a residue, so residues out of range
+ * give wrong values, never out-of-bounds accesses; the kernels' indices follow
+ * from the launch geometry and host-checked arguments only. Operations of a
+ * persistent stage-major batch (CKKS_BATCH_PERSISTENT) are not checked. */
+#define CKKS_LAUNCH_CHECKED 8
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags);
 
 /* Bounded device-side waits. The tensor-core and bulk-copy kernels wait on

@@ -28,6 +28,7 @@ CKKS_ENOMEM = -5
 CKKS_ECUDA = -6
 CKKS_ETIMEOUT = -7
 CKKS_EBUSY = -8
+CKKS_ERANGE = -9
 CKKS_RESCALE = 1
 CKKS_RESCALE_MERGED = 2
 
@@ -486,6 +487,7 @@ CKKS_COL_MODUP, CKKS_COL_MODDOWN, CKKS_COL_RS_FUSED, CKKS_ROW_PASSES = 0, 1, 2, 
 CKKS_LAUNCH_PDL = 1
 CKKS_TUNE_TENSOR = 2
 CKKS_LAUNCH_UNFUSED = 4
+CKKS_LAUNCH_CHECKED = 8
 
 
 def ckks_set_launch_flags(ctx, flags: int):

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "internal.h"
+#include "tc.cuh"
 
 using namespace ckks;
 
@@ -40,6 +41,13 @@ int sync_check(ckks_ctx* ctx, const char* what) {
   if (ctx->h_status) {
     volatile uint32_t* st = ctx->h_status;
     const uint32_t v = *st;
+    if (v & ckks::tc::kStatusRange) {
+      *st = 0;
+      return fail(ctx, CKKS_ERANGE,
+                  "%s: checked mode found a residue not below its prime; results of the operations since the "
+                  "last synchronizing call are undefined",
+                  what);
+    }
     if (v) {
       *st = 0;
       return fail(ctx, CKKS_ETIMEOUT,
@@ -54,6 +62,19 @@ int sync_check(ckks_ctx* ctx, const char* what) {
 // Status after enqueuing kernels: launch errors only (asynchronous faults
 // surface at the next synchronizing call).
 int launched(ckks_ctx* ctx, const char* what) { return cuda_check(ctx, cudaGetLastError(), what); }
+
+// Checked launch mode (CKKS_LAUNCH_CHECKED): device-side range checks of a
+// ciphertext's or plaintext's residues at its level, enqueued on the context
+// stream; a violation surfaces as CKKS_ERANGE at the next synchronizing call.
+static void check_ct(ckks_ctx* ctx, const ckks_ct* c) {
+  if (ctx->dp.checked && c)
+    launch_check_range(ctx->dp, c->d, c->poly_stride(), 2, ctx->lvl_n(c->level), 0, ctx->lvl_base(c->level),
+                       ctx->stream);
+}
+static void check_pt(ckks_ctx* ctx, const ckks_pt* p) {
+  if (ctx->dp.checked && p)
+    launch_check_range(ctx->dp, p->d, 0, 1, ctx->lvl_n(p->level), p->ext, ctx->lvl_base(p->level), ctx->stream);
+}
 
 size_t limb_words(const ckks_ctx* ctx) { return (size_t)ctx->N; }
 
@@ -259,12 +280,14 @@ void ckks_ctx_destroy(ckks_ctx* ctx) {
 }
 
 int ckks_set_launch_flags(ckks_ctx* ctx, int flags) {
-  if (!ctx || (flags & ~(CKKS_LAUNCH_PDL | CKKS_TUNE_TENSOR | CKKS_LAUNCH_UNFUSED))) return CKKS_EINVAL;
+  if (!ctx || (flags & ~(CKKS_LAUNCH_PDL | CKKS_TUNE_TENSOR | CKKS_LAUNCH_UNFUSED | CKKS_LAUNCH_CHECKED)))
+    return CKKS_EINVAL;
   if ((flags & CKKS_LAUNCH_UNFUSED) && ctx->windowed)
     return fail(ctx, CKKS_EINVAL, "launch flags: the unfused form supports single rescaling only");
   ctx->dp.pdl = (flags & CKKS_LAUNCH_PDL) ? 1 : 0;
   ctx->dp.tune_tensor = (flags & CKKS_TUNE_TENSOR) ? 1 : 0;
   ctx->dp.unfused = (flags & CKKS_LAUNCH_UNFUSED) ? 1 : 0;
+  ctx->dp.checked = (flags & CKKS_LAUNCH_CHECKED) ? 1 : 0;
   return CKKS_OK;
 }
 
@@ -522,6 +545,7 @@ static int ct_upload(ckks_ctx* ctx, ckks_ct* c, const uint32_t* host, int level,
   }
   c->level = level;
   c->scale = scale;
+  check_ct(ctx, c);
   int rc = launched(ctx, "permute");
   if (rc || !sync) return rc;
   return sync_check(ctx, "upload");
@@ -621,6 +645,7 @@ int ckks_pt_import(ckks_ctx* ctx, const uint32_t* host, int level, double scale,
                   "upload");
   if (!rc) {
     launch_permute(ctx->dp, ctx->sc.A, (*out)->d, n, true, ctx->stream);
+    check_pt(ctx, *out);
     rc = launched(ctx, "permute");
   }
   if (!rc) rc = sync_check(ctx, "upload");
@@ -643,6 +668,7 @@ int ckks_pt_import_ext(ckks_ctx* ctx, const uint32_t* host, int level, double sc
                   "upload");
   if (!rc) {
     launch_permute(ctx->dp, ctx->sc.A, (*out)->d, n, true, ctx->stream);
+    check_pt(ctx, *out);
     rc = launched(ctx, "permute");
   }
   if (!rc) rc = sync_check(ctx, "upload");
@@ -818,6 +844,8 @@ int ckks_evk_import(ckks_ctx* ctx, const uint32_t* host, uint32_t galois, ckks_e
   int rc = cuda_check(ctx, cudaMemcpyAsync(stage.p, host, words * 4, cudaMemcpyHostToDevice, ctx->stream), "upload");
   if (!rc) {
     launch_permute(dp, stage.as<uint32_t>(), e->d, 2 * dp.dnum * np, true, ctx->stream);
+    // checked mode: the imported key in [dnum][2][L + alpha] before its Montgomery form
+    if (dp.checked) launch_check_range(dp, e->d, (size_t)np << dp.log_n, 2 * dp.dnum, dp.L, dp.alpha, 0, ctx->stream);
     launch_to_mont(dp, e->d, 2 * dp.dnum * np, id_ext(dp.L, dp.L, dp.alpha), ctx->stream);
     rc = launched(ctx, "evk import");
   }
@@ -962,11 +990,14 @@ int ckks_hadd(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
   if (a->level != b->level) return fail(ctx, CKKS_ELEVEL, "hadd: levels %d and %d differ", a->level, b->level);
   if (!scales_match(a->scale, b->scale)) return fail(ctx, CKKS_ESCALE, "hadd: scales differ");
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "hadd: output capacity too small");
+  check_ct(ctx, a);
+  check_ct(ctx, b);
   launch_hadd(ctx->dp, a->d, b->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
               b->poly_stride(), out->poly_stride(),
               ctx->stream);
   out->level = a->level;
   out->scale = a->scale;
+  check_ct(ctx, out);
   return launched(ctx, "hadd");
 }
 
@@ -976,10 +1007,13 @@ int ckks_pmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out)
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "pmult: output capacity too small");
   if (ctx->windowed && pt->level != a->level)
     return fail(ctx, CKKS_ELEVEL, "pmult: plaintext level %d differs from %d (level windows)", pt->level, a->level);
+  check_ct(ctx, a);
+  check_pt(ctx, pt);
   launch_pmult(ctx->dp, a->d, pt->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
                out->poly_stride(), ctx->stream);
   out->level = a->level;
   out->scale = a->scale * pt->scale;
+  check_ct(ctx, out);
   return launched(ctx, "pmult");
 }
 
@@ -990,10 +1024,13 @@ int ckks_padd(ckks_ctx* ctx, const ckks_ct* a, const ckks_pt* pt, ckks_ct* out) 
   if (out->cap_level < a->level) return fail(ctx, CKKS_ELEVEL, "padd: output capacity too small");
   if (ctx->windowed && pt->level != a->level)
     return fail(ctx, CKKS_ELEVEL, "padd: plaintext level %d differs from %d (level windows)", pt->level, a->level);
+  check_ct(ctx, a);
+  check_pt(ctx, pt);
   launch_padd(ctx->dp, a->d, pt->d, out->d, ctx->lvl_n(a->level), ctx->lvl_base(a->level), a->poly_stride(),
               out->poly_stride(), ctx->stream);
   out->level = a->level;
   out->scale = a->scale;
+  check_ct(ctx, out);
   return launched(ctx, "padd");
 }
 
@@ -1022,9 +1059,11 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct* out) {
   if (in->level < 1) return fail(ctx, CKKS_ELEVEL, "rescale at level 0");
   if (out == in || out->d == in->d) return fail(ctx, CKKS_EINVAL, "rescale: output aliases input");
   if (out->cap_level < in->level - 1) return fail(ctx, CKKS_ELEVEL, "rescale: output capacity too small");
+  check_ct(ctx, in);
   rescale_into(ctx, in->level, in->d, in->poly_stride(), out->d, out->poly_stride());
   out->level = in->level - 1;
   out->scale = in->scale * rescale_factor(ctx, in->level);
+  check_ct(ctx, out);
   return launched(ctx, "rescale");
 }
 
@@ -1110,20 +1149,35 @@ int ckks_hmult(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, const ckks_evk
   KsArgs k;
   bool staged = false;
   const int level = a ? a->level : 0;
+  if (ctx && a && b && out) {
+    check_ct(ctx, a);
+    check_ct(ctx, b);
+  }
   const int rc = prepare_hmult(ctx, a, b, evk, flags, out, k, staged);
   if (rc != CKKS_OK) return rc;
-  if (ctx->dp.unfused) return keyswitch_unfused(ctx, k, "hmult");
+  if (ctx->dp.unfused) {
+    const int ru = keyswitch_unfused(ctx, k, "hmult");
+    check_ct(ctx, out);
+    return ru;
+  }
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
   if (staged) rescale_into(ctx, level, ctx->sc.U, k.out_stride, out->d, out->poly_stride());
+  check_ct(ctx, out);
   return launched(ctx, "hmult");
 }
 
 static int hauto(ckks_ctx* ctx, const ckks_ct* c, uint32_t galois, const ckks_evk* evk, ckks_ct* out) {
   KsArgs k;
+  if (out) check_ct(ctx, c);
   const int rc = prepare_hauto(ctx, c, galois, evk, out, k);
   if (rc != CKKS_OK) return rc;
-  if (ctx->dp.unfused) return keyswitch_unfused(ctx, k, "hrot");
+  if (ctx->dp.unfused) {
+    const int ru = keyswitch_unfused(ctx, k, "hrot");
+    check_ct(ctx, out);
+    return ru;
+  }
   launch_keyswitch(ctx->dp, ctx->sc, k, KM_KEYSWITCH, nullptr, ctx->stream);
+  check_ct(ctx, out);
   return launched(ctx, "hrot");
 }
 
@@ -1166,10 +1220,12 @@ int ckks_hrot_hoisted(ckks_ctx* ctx, const ckks_ct* c, int count, const int* r, 
     k.extra = 2;
     k.hoisted = 1;
   }
+  check_ct(ctx, c);
   launch_hoisted_rotations(ctx->dp, ctx->sc, ks.data(), count, ctx->stream);
   for (int i = 0; i < count; ++i) {
     outs[i]->level = c->level;
     outs[i]->scale = c->scale;
+    check_ct(ctx, outs[i]);
   }
   return launched(ctx, "hrot_hoisted");
 }
@@ -1215,9 +1271,12 @@ int ckks_linear_transform(ckks_ctx* ctx, const ckks_ct* c, int count, const int*
   k.poly_stride0 = c->poly_stride();
   k.out = out->d;
   k.out_stride = out->poly_stride();
+  check_ct(ctx, c);
+  for (int i = 0; i < count; ++i) check_pt(ctx, pts[i]);
   launch_linear_transform(ctx->dp, ctx->sc, k, lt, ctx->stream);
   out->level = c->level;
   out->scale = c->scale * pscale;
+  check_ct(ctx, out);
   return launched(ctx, "linear_transform");
 }
 

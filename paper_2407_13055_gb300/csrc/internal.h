@@ -66,6 +66,7 @@ struct DevParams {
   int pdl;  // host-side launch option: key-switch kernels use programmatic dependent launch
   int tune_tensor = 0;  // host-side option: the fine-tuner also times the tensor-core column shapes
   int unfused = 0;      // host-side option: key-switching operations run the unfused one-step-per-launch form
+  int checked = 0;      // host-side option: range checks of operands and results (CKKS_LAUNCH_CHECKED)
   int rows_passes = 3;  // host-side launch option at N = 2^16: row phase in 3 (16 values per
                         // thread, 64 threads per row) or 2 (32 values, 32 threads) passes
   // Bounded device-side waits (mbarrier waits of the tensor-core and bulk-copy
@@ -286,6 +287,12 @@ void launch_ntt(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, bool 
 void launch_rows_inv_only(const DevParams& dp, uint32_t* data, int limbs, IdMap ids, cudaStream_t st);
 void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int limbs, bool to_internal,
                     cudaStream_t st);
+// Range check (checked launch mode): every residue of `polys` polynomials
+// (poly_stride words apart) of n_q window limbs (primes q[base ..]) followed
+// by n_ext auxiliary limbs (p[0 ..]) must be below its prime; a violation sets
+// tc::kStatusRange in dp.status.
+void launch_check_range(const DevParams& dp, const uint32_t* d, size_t poly_stride, int polys, int n_q, int n_ext,
+                        int base, cudaStream_t st);
 void launch_hadd(const DevParams& dp, const uint32_t* a, const uint32_t* b, uint32_t* out, int n, int base, size_t sa,
                  size_t sb, size_t so, cudaStream_t st);
 void launch_padd(const DevParams& dp, const uint32_t* a, const uint32_t* pt, uint32_t* out, int n, int base, size_t sa,

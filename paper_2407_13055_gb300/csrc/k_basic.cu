@@ -2,6 +2,7 @@
 // operations, Eq. 4 automorphism; Alg. 2 SMR).
 #include "geo.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 #include <atomic>
 
@@ -166,6 +167,28 @@ void launch_permute(const DevParams& dp, const uint32_t* in, uint32_t* out, int 
   if (limbs <= 0) return;
   if (dp.log_n >= 10) k_permute<5><<<dim3(1u << (dp.log_n - 10), limbs), 256, 0, st>>>(in, out, dp.log_n);
   else k_permute<4><<<dim3(1u << (dp.log_n - 8), limbs), 256, 0, st>>>(in, out, dp.log_n);  // N = 2^8
+}
+
+// Range check of the checked launch mode: grid (N / 1024, polys * limbs),
+// four residues per thread; one flag write per block that saw a violation.
+__global__ void __launch_bounds__(256) k_check_range(DevParams dp, const uint32_t* __restrict__ d, size_t poly_stride,
+                                                     int n_q, int n_ext, int base) {
+  const int limbs = n_q + n_ext;
+  const int u = blockIdx.y / limbs, t = blockIdx.y % limbs;
+  const uint32_t q = dp.pc[t < n_q ? base + t : dp.L + (t - n_q)].q;
+  const size_t off = u * poly_stride + ((size_t)t << dp.log_n) + 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const uint4 v = *reinterpret_cast<const uint4*>(d + off);
+  const bool bad = v.x >= q || v.y >= q || v.z >= q || v.w >= q;
+  if (__syncthreads_or(bad) && threadIdx.x == 0 && dp.status) atomicOr(dp.status, tc::kStatusRange);
+}
+
+void launch_check_range(const DevParams& dp, const uint32_t* d, size_t poly_stride, int polys, int n_q, int n_ext,
+                        int base, cudaStream_t st) {
+  const int limbs = n_q + n_ext;
+  if (!d || polys <= 0 || limbs <= 0) return;
+  const int quads = (1 << dp.log_n) / 4, threads = quads < 256 ? quads : 256;
+  k_check_range<<<dim3(quads / threads, polys * limbs), threads, 0, st>>>(dp, d, poly_stride, n_q, n_ext, base);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------------------

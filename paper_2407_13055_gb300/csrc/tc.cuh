@@ -151,6 +151,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // Status word bits written by bounded waits that expired (read back by the
 // host as CKKS_ETIMEOUT).
 constexpr uint32_t kStatusTimeout = 1u;
+// Set by the range checks of the checked launch mode (a residue >= its prime).
+constexpr uint32_t kStatusRange = 2u;
 
 __device__ __forceinline__ void report_timeout(uint32_t* status) {
   if (status) atomicOr(status, kStatusTimeout);

@@ -74,6 +74,18 @@ def test_prime_system_2530_matches_oracle(K, O, log_n):
     assert levels == [tuple(x) for x in lv]
 
 
+def test_status_codes_and_flags_match_the_header(K):
+    """The binding's error codes and launch flags are the header's."""
+    src = open(os.path.join(ROOT, "include", "ckks.h")).read()
+    defs = dict(re.findall(r"#define (CKKS_[A-Z0-9_]+) \(?(-?\d+)\)?", src))
+    for name in ("CKKS_EINVAL", "CKKS_ETIMEOUT", "CKKS_EBUSY", "CKKS_ERANGE", "CKKS_LAUNCH_PDL", "CKKS_TUNE_TENSOR",
+                 "CKKS_LAUNCH_UNFUSED", "CKKS_LAUNCH_CHECKED"):
+        assert int(defs[name]) == getattr(K, name), name
+    assert len({int(v) for k, v in defs.items() if k.startswith("CKKS_E")}) == \
+        len([k for k in defs if k.startswith("CKKS_E")])
+    assert K.lib.ckks_set_launch_flags(None, K.CKKS_LAUNCH_CHECKED) == K.CKKS_EINVAL
+
+
 def test_null_handles_are_rejected_without_a_gpu(K):
     """Every operation validates its handles before touching the device:
     null context, operands or outputs give CKKS_EINVAL."""
