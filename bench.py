@@ -149,10 +149,10 @@ def multiply_costs(rates):
 # sources (kernel_sources) differs, the figures are stale and the bench
 # reports null.
 NCU_TRAFFIC = {
-    "sources_sha1": "a2f9442f396f431ff567e9830ec716c691b62f2f",
-    "bytes_per_launch": {"modup_cols": 10.58e6, "keymult": 136.12e6, "modup_rows": 60.33e6,
-                         "moddown_in_rows": 15.77e6, "moddown_cols": 7.40e6, "moddown_rows": 74.31e6,
-                         "rescale_cols": 7.95e6, "rescale_rows": 117.81e6, "ks_in_rows": 37.31e6},
+    "sources_sha1": "7752ec4617116707750c987e104ac7492e35ba55",
+    "bytes_per_launch": {"modup_cols": 10.58e6, "keymult": 135.59e6, "modup_rows": 60.32e6,
+                         "moddown_in_rows": 15.76e6, "moddown_cols": 7.40e6, "moddown_rows": 74.29e6,
+                         "rescale_cols": 7.95e6, "rescale_rows": 118.13e6, "ks_in_rows": 37.31e6},
 }
 
 
