@@ -545,99 +545,8 @@ def run_native(args, rank, world, local_rank):
     hmult_us = 1e3 * sum(per_launch[k] for k in ks_stages[:5] + ("rescale_cols", "rescale_rows"))
     hrot_us = 1e3 * sum(per_launch[k] for k in ks_stages + ("moddown_rows",))
 
-    # end to end through the C ABI with host buffers. A step is e2e_pairs pairs
-    # over e2e_pairs + 1 input ciphertexts (pair i: HMult(ct_i, ct_i+1) + rescale,
-    # HRot(ct_i), as in the device-resident step); each input is copied once from
-    # pinned host memory into a ring of device buffers, and both results of every
-    # pair are read back to pinned host memory. Uploads (on transfer-only clone
-    # contexts), the pairs (on the lanes) and the exports (on a second set of
-    # transfer-only clones) form a pipeline ordered by CUDA events, so copies
-    # overlap the computation: an upload waits for the two pairs that read its
-    # buffer's previous ciphertext, a pair for its two uploads and for the export
-    # of its output slot's previous results.
-    n = 1 << LOG_N
-    nl = args.lanes
-    NS = args.e2e_slots
-    R = NS * nl + 2                       # device input buffers (ring)
-    pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
-    host_in = [pinned((2, L, n)) for _ in range(E2E_HOST)]
-    for i in range(E2E_HOST):
-        K.ckks_ct_export(ctx, cts[i], n, out=host_in[i])
-    up_s = [torch.cuda.Stream() for _ in range(nl)]
-    dn_s = [torch.cuda.Stream() for _ in range(nl)]
-    up_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in up_s]
-    dn_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in dn_s]
-    dev_in = [K.ckks_ct_create(ctx, LEVEL) for _ in range(R)]
-    slot = lambda: [[K.ckks_ct_create(ctx, LEVEL) for _ in range(NS)] for _ in range(nl)]
-    dev_m, dev_r = slot(), slot()
-    host_m = [[pinned((2, L - 1, n)) for _ in range(NS)] for _ in range(nl)]
-    host_r = [[pinned((2, L, n)) for _ in range(NS)] for _ in range(nl)]
-    ev = lambda: [[torch.cuda.Event() for _ in range(NS)] for _ in range(nl)]
-    ev_comp, ev_dn = ev(), ev()
-    ev_in = [torch.cuda.Event() for _ in range(R)]        # upload into the buffer done
-    ev_use = [[torch.cuda.Event() for _ in range(R)] for _ in range(2)]   # read as a / as b done
-    for l in range(nl):
-        for k in range(NS):
-            ev_dn[l][k].record(stream)
-    for b in range(R):
-        ev_use[0][b].record(stream)
-        ev_use[1][b].record(stream)
-    e2e_pairs = 4 * E2E_HOST
-    uploads = [0]                          # next upload's global index
-
-    def upload():
-        u = uploads[0]
-        uploads[0] += 1
-        b, l = u % R, u % nl
-        up_s[l].wait_event(ev_use[0][b])
-        up_s[l].wait_event(ev_use[1][b])
-        K.ckks_ct_upload_async(up_c[l], dev_in[b], host_in[u % E2E_HOST], LEVEL, SCALE)
-        ev_in[b].record(up_s[l])
-        return b
-
-    def e2e_step():
-        nxt = upload()
-        for i in range(e2e_pairs):
-            l, k = i % nl, (i // nl) % NS
-            ba, bb = nxt, upload()
-            nxt = bb
-            streams[l].wait_event(ev_in[ba])
-            streams[l].wait_event(ev_in[bb])
-            streams[l].wait_event(ev_dn[l][k])
-            K.ckks_hmult(lanes[l], dev_in[ba], dev_in[bb], rk, K.CKKS_RESCALE, dev_m[l][k])
-            K.ckks_hrot(lanes[l], dev_in[ba], 1, gk, dev_r[l][k])
-            ev_use[0][ba].record(streams[l])
-            ev_use[1][bb].record(streams[l])
-            ev_comp[l][k].record(streams[l])
-            dn_s[l].wait_event(ev_comp[l][k])
-            K.ckks_ct_export_async(dn_c[l], dev_m[l][k], host_m[l][k])
-            K.ckks_ct_export_async(dn_c[l], dev_r[l][k], host_r[l][k])
-            ev_dn[l][k].record(dn_s[l])
-
-    e2e_step()
-    barrier()
-    e2e_steps = max(10, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    barrier()
-    e2e_dt = replicas.max_over_ranks(time.perf_counter() - t0)
-    ct_bytes = 2 * L * n * 4
-    e2e = {"value": replicas.job_throughput(2 * e2e_pairs * e2e_steps, 1e3 * e2e_dt, world), "unit": UNIT,
-           "h2d_bytes_per_step": (e2e_pairs + 1) * ct_bytes,
-           "d2h_bytes_per_step": e2e_pairs * (ct_bytes * (L - 1) // L + ct_bytes),
-           "ops_per_step": 2 * e2e_pairs,
-           "note": f"{nl} lanes x {NS} output slots, {R} input buffers; each step's {e2e_pairs + 1} input "
-                   "ciphertexts uploaded once from pinned host memory, both results of every pair read back to "
-                   "pinned host memory; upload / compute / export pipelined on separate streams, wall clock"}
-    for h in dev_in:
-        K.ckks_free(h)
-    for grp in (dev_m, dev_r):
-        for row in grp:
-            for h in row:
-                K.ckks_free(h)
-    for c in up_c + dn_c:
-        K.ckks_ctx_destroy(c)
+    e2e = e2e_leg(K, ctx, lanes, streams, stream, cts, rk, gk, args.lanes, args.e2e_slots, args.steps,
+                  args.e2e_priority, barrier, world)
 
     # batched and served forms next to the headline (same context and keys;
     # levels other than the top one use the default column shapes)
@@ -738,6 +647,115 @@ def run_native(args, rank, world, local_rank):
 # batched form: independent operations at mixed levels (one op per launch vs
 # lanes vs lanes captured into one CUDA graph)
 # ----------------------------------------------------------------------------
+
+def e2e_leg(K, ctx, lanes, streams, stream, cts, rk, gk, n_lanes, slots, steps, priority, barrier, world):
+    """End-to-end throughput (key-switch ops/s) through the C ABI with host
+    buffers: inputs uploaded from and results read back to pinned host memory
+    inside the timed region, on n_lanes compute lanes (lanes / streams) with
+    `slots` output slots per lane; `priority` ("high" or "normal") is the
+    priority of the transfer streams."""
+    import torch
+    from paper_2407_13055_gb300 import replicas
+    # end to end through the C ABI with host buffers. A step is e2e_pairs pairs
+    # over e2e_pairs + 1 input ciphertexts (pair i: HMult(ct_i, ct_i+1) + rescale,
+    # HRot(ct_i), as in the device-resident step); each input is copied once from
+    # pinned host memory into a ring of device buffers, and both results of every
+    # pair are read back to pinned host memory. Uploads (on transfer-only clone
+    # contexts), the pairs (on the lanes) and the exports (on a second set of
+    # transfer-only clones) form a pipeline ordered by CUDA events, so copies
+    # overlap the computation: an upload waits for the two pairs that read its
+    # buffer's previous ciphertext, a pair for its two uploads and for the export
+    # of its output slot's previous results.
+    n = 1 << LOG_N
+    nl = n_lanes
+    NS = slots
+    R = NS * nl + 2                       # device input buffers (ring)
+    pinned = lambda shape: torch.empty(shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    host_in = [pinned((2, L, n)) for _ in range(E2E_HOST)]
+    for i in range(E2E_HOST):
+        K.ckks_ct_export(ctx, cts[i], n, out=host_in[i])
+    # transfer streams: with high priority their layout permutations are
+    # scheduled ahead of the compute lanes' pending blocks, so the copies
+    # behind them start as soon as their data is ready
+    prio = -1 if priority == "high" else 0
+    up_s = [torch.cuda.Stream(priority=prio) for _ in range(nl)]
+    dn_s = [torch.cuda.Stream(priority=prio) for _ in range(nl)]
+    up_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in up_s]
+    dn_c = [K.ckks_ctx_clone(ctx, x.cuda_stream) for x in dn_s]
+    dev_in = [K.ckks_ct_create(ctx, LEVEL) for _ in range(R)]
+    slot = lambda: [[K.ckks_ct_create(ctx, LEVEL) for _ in range(NS)] for _ in range(nl)]
+    dev_m, dev_r = slot(), slot()
+    host_m = [[pinned((2, L - 1, n)) for _ in range(NS)] for _ in range(nl)]
+    host_r = [[pinned((2, L, n)) for _ in range(NS)] for _ in range(nl)]
+    ev = lambda: [[torch.cuda.Event() for _ in range(NS)] for _ in range(nl)]
+    ev_comp, ev_dn = ev(), ev()
+    ev_in = [torch.cuda.Event() for _ in range(R)]        # upload into the buffer done
+    ev_use = [[torch.cuda.Event() for _ in range(R)] for _ in range(2)]   # read as a / as b done
+    for l in range(nl):
+        for k in range(NS):
+            ev_dn[l][k].record(stream)
+    for b in range(R):
+        ev_use[0][b].record(stream)
+        ev_use[1][b].record(stream)
+    e2e_pairs = 4 * E2E_HOST
+    uploads = [0]                          # next upload's global index
+
+    def upload():
+        u = uploads[0]
+        uploads[0] += 1
+        b, l = u % R, u % nl
+        up_s[l].wait_event(ev_use[0][b])
+        up_s[l].wait_event(ev_use[1][b])
+        K.ckks_ct_upload_async(up_c[l], dev_in[b], host_in[u % E2E_HOST], LEVEL, SCALE)
+        ev_in[b].record(up_s[l])
+        return b
+
+    def e2e_step():
+        nxt = upload()
+        for i in range(e2e_pairs):
+            l, k = i % nl, (i // nl) % NS
+            ba, bb = nxt, upload()
+            nxt = bb
+            streams[l].wait_event(ev_in[ba])
+            streams[l].wait_event(ev_in[bb])
+            streams[l].wait_event(ev_dn[l][k])
+            K.ckks_hmult(lanes[l], dev_in[ba], dev_in[bb], rk, K.CKKS_RESCALE, dev_m[l][k])
+            K.ckks_hrot(lanes[l], dev_in[ba], 1, gk, dev_r[l][k])
+            ev_use[0][ba].record(streams[l])
+            ev_use[1][bb].record(streams[l])
+            ev_comp[l][k].record(streams[l])
+            dn_s[l].wait_event(ev_comp[l][k])
+            K.ckks_ct_export_async(dn_c[l], dev_m[l][k], host_m[l][k])
+            K.ckks_ct_export_async(dn_c[l], dev_r[l][k], host_r[l][k])
+            ev_dn[l][k].record(dn_s[l])
+
+    e2e_step()
+    barrier()
+    e2e_steps = max(10, steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_dt = replicas.max_over_ranks(time.perf_counter() - t0)
+    ct_bytes = 2 * L * n * 4
+    e2e = {"value": replicas.job_throughput(2 * e2e_pairs * e2e_steps, 1e3 * e2e_dt, world), "unit": UNIT,
+           "h2d_bytes_per_step": (e2e_pairs + 1) * ct_bytes,
+           "d2h_bytes_per_step": e2e_pairs * (ct_bytes * (L - 1) // L + ct_bytes),
+           "ops_per_step": 2 * e2e_pairs,
+           "note": f"{nl} lanes x {NS} output slots, {R} input buffers; each step's {e2e_pairs + 1} input "
+                   "ciphertexts uploaded once from pinned host memory, both results of every pair read back to "
+                   "pinned host memory; upload / compute / export pipelined on separate streams, wall clock"}
+    for h in dev_in:
+        K.ckks_free(h)
+    for grp in (dev_m, dev_r):
+        for row in grp:
+            for h in row:
+                K.ckks_free(h)
+    for c in up_c + dn_c:
+        K.ckks_ctx_destroy(c)
+
+    return e2e
+
 
 def fusion_ablation(K, ctx, sk, rk, gk, stream, levels=(L - 1, 20, 1), reps=15, pdl=True):
     """Fused pipeline vs the unfused one-step-per-launch form
@@ -1379,6 +1397,8 @@ def main():
                          "6: twiddles in shared memory)")
     ap.add_argument("--e2e-slots", type=int, default=2,
                     help="buffer slots per lane of the end-to-end upload / compute / export pipeline")
+    ap.add_argument("--e2e-priority", choices=["high", "normal"], default="high",
+                    help="priority of the end-to-end leg's transfer streams")
     ap.add_argument("--pdl", choices=["on", "off"], default="on",
                     help="programmatic dependent launch for the key-switch kernels")
     args = ap.parse_args()
