@@ -480,13 +480,13 @@ def run_native(args, rank, world, local_rank):
     if args.issue != "python":
         nl = args.lanes
         outs_b = [K.ckks_ct_create(ctx, LEVEL) for _ in range(2 * BATCH)]
-        ops = []
+        batch_ops = []
         for g0 in range(0, BATCH, nl):
             grp = range(g0, min(g0 + nl, BATCH))
-            ops += [dict(op=K.CKKS_OP_HMULT, a=cts[i], b=cts[(i + 1) % BATCH], evk=rk, flags=K.CKKS_RESCALE,
-                         out=outs_b[2 * i]) for i in grp]
-            ops += [dict(op=K.CKKS_OP_HROT, a=cts[i], r=1, evk=gk, out=outs_b[2 * i + 1]) for i in grp]
-        batch = K.ckks_batch_create(ctx, ops, nl, args.issue == "graph")
+            batch_ops += [dict(op=K.CKKS_OP_HMULT, a=cts[i], b=cts[(i + 1) % BATCH], evk=rk,
+                               flags=K.CKKS_RESCALE, out=outs_b[2 * i]) for i in grp]
+            batch_ops += [dict(op=K.CKKS_OP_HROT, a=cts[i], r=1, evk=gk, out=outs_b[2 * i + 1]) for i in grp]
+        batch = K.ckks_batch_create(ctx, batch_ops, nl, args.issue == "graph")
 
     def barrier():
         replicas.barrier()
@@ -561,6 +561,10 @@ def run_native(args, rank, world, local_rank):
     fusion = dict(fusion_ablation(K, ctx, sk, rk, gk, stream, pdl=args.pdl == "on"),
                   note="one stream, median of 15 single operations (inputs rotated over 8 fresh encryptions), "
                        "fused pipeline vs the one-step-per-launch unfused form with every intermediate in HBM")
+    tc_bconv = None
+    if batch is not None and args.issue == "graph":
+        tc_bconv = tensor_core_leg(K, ctx, batch_ops, args.lanes, stream, max(5, args.steps // 2),
+                                   max(3, args.warmup), value)
     batched = dict(bat, note="64 independent operations, levels U{1..39}, HMult+rescale / HRot / PMult / "
                              "rescale; persistent = stage-major batch with one persistent KeyMult / element-wise "
                              "kernel, replayed as a CUDA graph")
@@ -628,7 +632,7 @@ def run_native(args, rank, world, local_rank):
                      "note": "same workload issued in order on one stream; stage times from its CUDA events"},
         "roofline": roof, "op_roofline": op_hbm, "stages": stage,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-        "batched": batched, "serve": served, "fusion": fusion,
+        "batched": batched, "serve": served, "fusion": fusion, "tensor_core_bconv": tc_bconv,
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -755,6 +759,47 @@ def e2e_leg(K, ctx, lanes, streams, stream, cts, rk, gk, n_lanes, slots, steps, 
         K.ckks_ctx_destroy(c)
 
     return e2e
+
+
+def tensor_core_leg(K, ctx, ops, n_lanes, stream, steps, warmup, cuda_core_ops_s, shape=(4, 8, 1, 16)):
+    """The headline's operations (one CUDA graph per step over n_lanes lanes)
+    with the BConv of every column kernel on the tensor cores (tcgen05, exact
+    fp16 byte planes; launch shape tc, sl, z, targets per chunk) instead of
+    CUDA cores, on the same context and inputs; the tuned shapes are put back
+    afterwards. Returns ops/s beside the CUDA-core figure and the operations'
+    HBM fraction."""
+    import torch
+    kernels = (K.CKKS_COL_MODUP, K.CKKS_COL_MODDOWN, K.CKKS_COL_RS_FUSED)
+    saved = {k: K.ckks_tune_get(ctx, k, LEVEL) for k in kernels}
+    try:
+        for k in kernels:
+            K.ckks_tune_set(ctx, k, LEVEL, *shape)
+        b = K.ckks_batch_create(ctx, ops, n_lanes, True)
+        try:
+            for _ in range(warmup):
+                K.ckks_batch_run(ctx, b)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                K.ckks_batch_run(ctx, b)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+        finally:
+            K.ckks_batch_destroy(b)
+    finally:
+        for k, v in saved.items():   # tc = 0 clears an untuned entry
+            K.ckks_tune_set(ctx, k, LEVEL, *v[:4])
+    ops_s = len(ops) * steps / (ms / 1e3)
+    mean_bytes = (algorithmic_bytes()[0] + algorithmic_bytes()[1]) / 2
+    peaks, kind = measured_peaks()
+    return {"ops_s": ops_s, "cuda_core_ops_s": cuda_core_ops_s, "col_shape": list(shape),
+            "op_frac_of_hbm": ops_s * mean_bytes / 1e9 / peaks["hbm_gbs"],
+            "cuda_core_op_frac_of_hbm": cuda_core_ops_s * mean_bytes / 1e9 / peaks["hbm_gbs"],
+            "note": f"{steps} graph replays of the same {len(ops)} operations, every column kernel's BConv on "
+                    f"the tensor cores (shape {shape}), against the headline's tuned CUDA-core shapes; "
+                    f"HBM fraction of {kind} hbm_gbs"}
 
 
 def fusion_ablation(K, ctx, sk, rk, gk, stream, levels=(L - 1, 20, 1), reps=15, pdl=True):
