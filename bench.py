@@ -557,7 +557,8 @@ def run_native(args, rank, world, local_rank):
               "continuous_batching_4_lanes": srv_runs["continuous_batching_4_lanes@0.8"],
               "one_op_per_launch": srv_runs["one_op_per_launch@0.8"],
               "note": "Poisson arrivals of HMult+rescale / HRot at 0.8 x the one-stream capacity, levels U{1..39}, "
-                      "64 resident rotation keys; latency = completion - arrival on the host clock"}
+                      "64 resident rotation keys; the library's native serving loop (ckks_serve_run); latency = "
+                      "completion - arrival on the host's steady clock"}
     fusion = dict(fusion_ablation(K, ctx, sk, rk, gk, stream, pdl=args.pdl == "on"),
                   note="one stream, median of 15 single operations (inputs rotated over 8 fresh encryptions), "
                        "fused pipeline vs the one-step-per-launch unfused form with every intermediate in HBM")
@@ -1338,12 +1339,7 @@ def serve_runs(K, ctx, sk, rk, stream, count, fracs, n_keys=64, seed=21):
     ops = ["hmult" if v < 0.5 else "hrot" for v in rng.random(count)]
     rot_ix = rng.integers(0, len(rots), count)
     reqs = [Request(i, ops[i], int(levels[i]), rots[int(rot_ix[i])] if ops[i] == "hrot" else 0) for i in range(count)]
-    outs = {}
-
-    def out_for(req, lane):
-        if lane not in outs:
-            outs[lane] = K.ckks_ct_create(ctx, L - 1)
-        return outs[lane]
+    lane_outs = [K.ckks_ct_create(ctx, L - 1) for _ in range(4)]   # one output per lane, reused
 
     inputs_for = lambda r: (pool[r.level][0], pool[r.level][1])
     key_for = lambda r: rk if r.op == "hmult" else gks[r.rot]
@@ -1354,9 +1350,9 @@ def serve_runs(K, ctx, sk, rk, stream, count, fracs, n_keys=64, seed=21):
     for r in reqs:
         a, b = inputs_for(r)
         if r.op == "hmult":
-            K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, out_for(r, -1))
+            K.ckks_hmult(ctx, a, b, rk, K.CKKS_RESCALE, lane_outs[0])
         else:
-            K.ckks_hrot(ctx, a, r.rot, gks[r.rot], out_for(r, -1))
+            K.ckks_hrot(ctx, a, r.rot, gks[r.rot], lane_outs[0])
     e1.record(stream)
     torch.cuda.synchronize()
     capacity = count / (e0.elapsed_time(e1) / 1e3)
@@ -1370,12 +1366,12 @@ def serve_runs(K, ctx, sk, rk, stream, count, fracs, n_keys=64, seed=21):
         for name, lanes in (("one_op_per_launch", 1), ("continuous_batching_4_lanes", 4)):
             srv = Server(K, ctx, lanes, budget, 1 << LOG_N, resident_bytes=resident)
             try:
-                done = srv.run(reqs, inputs_for, key_for, out_for)
+                done = srv.run(reqs, inputs_for, key_for, lane_outs=lane_outs[:lanes])
             finally:
                 srv.close()
             results[f"{name}@{frac}"] = latency_stats(done)
     K.ckks_sync(ctx)
-    for h in list(outs.values()) + [c for v in pool.values() for c in v] + list(gks.values()):
+    for h in lane_outs + [c for v in pool.values() for c in v] + list(gks.values()):
         K.ckks_free(h)
     return results, capacity, resident
 

@@ -346,6 +346,65 @@ int ckks_batch_run_admit(ckks_batch* batch, int admitted);
 int ckks_batch_admit(ckks_batch* batch, int admitted);
 void ckks_batch_destroy(ckks_batch* batch);
 
+/* --- served form: continuous batching of single requests (not in the paper,
+ * which runs one operation at a time; Sec. 5.2 names multi-query batching as
+ * a different model) ---
+ * A request is one HMult with rescaling (CKKS_OP_HMULT, flags CKKS_RESCALE)
+ * or one HRot by r (CKKS_OP_HROT) that arrives arrival_s seconds after the
+ * run starts. ckks_serve_run serves a list of them on n_lanes execution lanes
+ * (contexts on their own streams, e.g. clones): a request is admitted, in
+ * arrival order, once its arrival time has passed, a lane is idle and the
+ * pool grants its `bytes` (its device footprint, ckks_request_bytes); it then
+ * runs on that lane, so admitted requests overlap on the GPU, and requests
+ * that arrive meanwhile are admitted as lanes and bytes free up. Completion
+ * is a CUDA event recorded after the request on its lane; its bytes go back
+ * to the pool. The loop runs on the calling thread (polling; it returns once
+ * every request has completed). Times are host steady-clock seconds since
+ * the start of the run. The lanes' device must be the current device; the
+ * loop allocates no device memory (one CUDA event per lane).
+ *  lanes:     n_lanes contexts (1 <= n_lanes <= 64), all of the same
+ *             parameters; lane l's requests are enqueued on lanes[l]'s stream.
+ *  pool:      admission pool; it may already hold bytes (resident keys).
+ *  reqs:      n requests, sorted by arrival_s (CKKS_EINVAL otherwise); a
+ *             request whose out is NULL writes to lane_outs[lane].
+ *  lane_outs: n_lanes output ciphertexts, or NULL when every request has its
+ *             own out.
+ *  hooks:     NULL for the library's own issue and completion; non-NULL
+ *             replaces both (host tests of the scheduling: issue(user, i,
+ *             lane) starts request i on the lane and returns CKKS_OK or an
+ *             error, query(user, lane) returns 1 once the lane's request has
+ *             completed, 0 while it runs, a negative code on failure; lanes
+ *             may then be NULL).
+ *  done:      n records, filled by request index: admission and completion
+ *             times, the lane.
+ *  order:     NULL or n request indices in completion order.
+ * Errors: CKKS_EINVAL for bad arguments, or a request whose bytes exceed
+ * what the pool can ever grant it (its budget less the bytes it held at the
+ * start); the first failing issue or completion ends the run with that code
+ * after waiting for the requests already running. */
+typedef struct {
+  int op;
+  int r;
+  double arrival_s;
+  const ckks_ct* a;
+  const ckks_ct* b;
+  const ckks_evk* evk;
+  ckks_ct* out;
+  size_t bytes;
+} ckks_request;
+typedef struct {
+  double start_s;
+  double end_s;
+  int lane;
+} ckks_request_done;
+typedef struct {
+  int (*issue)(void* user, int request, int lane);
+  int (*query)(void* user, int lane);
+  void* user;
+} ckks_serve_hooks;
+int ckks_serve_run(ckks_ctx* const* lanes, int n_lanes, ckks_pool* pool, const ckks_request* reqs, int n,
+                   ckks_ct* const* lane_outs, const ckks_serve_hooks* hooks, ckks_request_done* done, int* order);
+
 /* --- rescale without allocation (the paper has no counterpart to this entry
  * point; it exists for callers that must not allocate device memory while
  * they run, such as a serving loop with a latency budget, where cudaMalloc can

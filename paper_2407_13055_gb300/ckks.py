@@ -73,6 +73,31 @@ class ckks_op(C.Structure):
 CKKS_OP_HMULT, CKKS_OP_HROT, CKKS_OP_HCONJ, CKKS_OP_PMULT, CKKS_OP_RESCALE, CKKS_OP_HADD, CKKS_OP_PADD = 1, 2, 3, 4, 5, 6, 7
 
 
+class ckks_request(C.Structure):
+    _fields_ = [
+        ("op", C.c_int),
+        ("r", C.c_int),
+        ("arrival_s", C.c_double),
+        ("a", C.c_void_p),
+        ("b", C.c_void_p),
+        ("evk", C.c_void_p),
+        ("out", C.c_void_p),
+        ("bytes", C.c_size_t),
+    ]
+
+
+class ckks_request_done(C.Structure):
+    _fields_ = [("start_s", C.c_double), ("end_s", C.c_double), ("lane", C.c_int)]
+
+
+_ISSUE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int)
+_QUERY_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int)
+
+
+class ckks_serve_hooks(C.Structure):
+    _fields_ = [("issue", _ISSUE_FN), ("query", _QUERY_FN), ("user", C.c_void_p)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
 
@@ -136,6 +161,7 @@ _SIGS = {
     "ckks_batch_run_admit": (_i, [_vp, _i]),
     "ckks_batch_admit": (_i, [_vp, _i]),
     "ckks_batch_destroy": (None, [_vp]),
+    "ckks_serve_run": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "ckks_set_launch_flags": (_i, [_vp, _i]),
     "ckks_set_wait_limit": (_i, [_vp, C.c_longlong]),
     "ckks_tune": (_i, [_vp, _i, _i]),
@@ -506,6 +532,46 @@ def ckks_memory_in_use(ctx) -> int:
 def ckks_request_bytes(ctx, op: int, level: int) -> int:
     """Device bytes a request of kind op (CKKS_OP_*) at level holds while it runs."""
     return int(lib.ckks_request_bytes(ctx, op, level))
+
+
+def ckks_serve_run(lanes, pool, reqs, lane_outs=None, hooks=None, n_lanes=None):
+    """Serve `reqs` (dicts op, r, arrival (seconds), a, b, evk, out (or None:
+    the lane's output from lane_outs), bytes; sorted by arrival) on the lane
+    contexts `lanes`. hooks = (issue(i, lane) -> status, query(lane) -> 1 / 0 /
+    negative) replaces the device work (then lanes may be None and n_lanes
+    gives their count). Returns ([(start_s, end_s, lane) per request],
+    [request indices in completion order])."""
+    n = len(reqs)
+    nl = n_lanes if n_lanes is not None else len(lanes)
+    arr = (ckks_request * max(n, 1))()
+    for i, q in enumerate(reqs):
+        arr[i] = ckks_request(q["op"], q.get("r", 0), q["arrival"], q.get("a"), q.get("b"), q.get("evk"),
+                              q.get("out"), q["bytes"])
+    lanes_arr = (_vp * nl)(*lanes) if lanes is not None else None
+    outs_arr = (_vp * nl)(*lane_outs) if lane_outs is not None else None
+    done = (ckks_request_done * max(n, 1))()
+    order = (C.c_int * max(n, 1))()
+    hk = None
+    if hooks is not None:
+        issue_py, query_py = hooks
+
+        def _issue(_user, i, lane):
+            try:
+                return int(issue_py(i, lane))
+            except Exception:  # a failing hook ends the run instead of unwinding through C
+                return CKKS_EINVAL
+
+        def _query(_user, lane):
+            try:
+                return int(query_py(lane))
+            except Exception:
+                return CKKS_EINVAL
+
+        hk = ckks_serve_hooks(_ISSUE_FN(_issue), _QUERY_FN(_query), None)
+    rc = lib.ckks_serve_run(lanes_arr, nl, pool, arr, n, outs_arr, C.byref(hk) if hk is not None else None, done,
+                            order)
+    check(lanes[0] if lanes is not None and hooks is None else None, rc)
+    return [(done[i].start_s, done[i].end_s, done[i].lane) for i in range(n)], [order[i] for i in range(n)]
 
 
 def ckks_pool_create(budget: int):

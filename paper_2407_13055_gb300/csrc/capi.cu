@@ -401,11 +401,6 @@ size_t ckks_ctx_device_bytes(ckks_ctx* ctx) { return ctx ? ctx->table_bytes + ct
 
 // Admission pool of a server: a byte budget that requests acquire while
 // they hold device memory (host-side accounting, thread-safe).
-struct ckks_pool {
-  std::atomic<size_t> used{0};
-  size_t budget = 0;
-};
-
 extern "C" {
 
 int ckks_pool_create(size_t budget_bytes, ckks_pool** out) {

@@ -446,6 +446,13 @@ struct ckks_ctx {
   }
 };
 
+// Admission pool (ckks_pool_*): bytes granted to running requests, against
+// a fixed budget.
+struct ckks_pool {
+  std::atomic<size_t> used{0};
+  size_t budget = 0;
+};
+
 struct ckks_ct {
   ckks_obj h;
   uint32_t* d;

@@ -1,24 +1,22 @@
 """Served form: continuous batching of single HMult / HRot requests.
 
-Requests arrive over time (a Poisson process in the benchmark). The host
-scheduler admits a request as soon as (1) its arrival time has passed,
-(2) an execution lane (a context clone with its own CUDA stream and scratch)
-is free, and (3) the device memory the request holds while it runs (its
-input and output ciphertexts and its lane's key-switching scratch,
-ckks_request_bytes) fits in the admission budget next to the resident
-evaluation keys and the requests already in flight; the budget is the
-library's admission pool (ckks_pool_acquire refuses with CKKS_EBUSY).
-Admitted requests run on their lane's stream, so the work of several
-requests overlaps on the GPU; requests that arrive meanwhile are admitted as
-lanes and memory free up. Completion is detected by polling a CUDA event per
-request; latency is completion minus arrival on the host clock.
+Requests arrive over time (a Poisson process in the benchmark). The
+library's serving loop (ckks_serve_run, native, on the calling thread)
+admits a request as soon as (1) its arrival time has passed, (2) an
+execution lane (a context clone with its own CUDA stream and scratch) is
+idle, and (3) the device memory the request holds while it runs (its input
+and output ciphertexts and its lane's key-switching scratch,
+ckks_request_bytes) fits in the admission pool next to the resident
+evaluation keys and the requests already in flight. Admitted requests run on
+their lane's stream, so the work of several requests overlaps on the GPU;
+requests that arrive meanwhile are admitted as lanes and memory free up.
+Completion is a CUDA event per request polled by the loop; latency is
+completion minus arrival on the host's steady clock.
 
 With one lane this is the plain one-operation-at-a-time server.
 """
 from __future__ import annotations
 
-import collections
-import time
 from dataclasses import dataclass, field
 
 
@@ -38,14 +36,6 @@ class Done:
     start: float
     end: float
     lane: int
-
-
-@dataclass
-class _Slot:
-    req: Request | None = None
-    event: object = None
-    start: float = 0.0
-    bytes: int = 0
 
 
 def poisson_arrivals(rng, count: int, rate: float):
@@ -92,50 +82,24 @@ class Server:
         op = self.K.CKKS_OP_HMULT if req.op == "hmult" else self.K.CKKS_OP_HROT
         return self.K.ckks_request_bytes(self.ctx, op, req.level)
 
-    def run(self, requests, inputs_for, key_for, out_for):
-        """Serve `requests` (sorted by arrival). inputs_for(req) -> (a, b)
+    def run(self, requests, inputs_for, key_for, out_for=None, lane_outs=None):
+        """Serve `requests` in arrival order. inputs_for(req) -> (a, b)
         ciphertext handles (b ignored for hrot); key_for(req) -> evk handle;
-        out_for(req, lane) -> output ciphertext handle. Returns Done records
-        in completion order."""
+        out_for(req) -> the request's output ciphertext, or lane_outs: one
+        output ciphertext per lane that every request on that lane writes.
+        Returns Done records in completion order."""
         import torch
         K = self.K
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        slots = [_Slot() for _ in range(self.lanes)]
-        inflight = 0
-        done = []
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        native = []
+        for r in reqs:   # a request larger than the budget leaves is refused (CKKS_EINVAL)
+            a, b = inputs_for(r)
+            native.append(dict(op=K.CKKS_OP_HMULT if r.op == "hmult" else K.CKKS_OP_HROT, r=r.rot,
+                               arrival=r.arrival, a=a, b=b if r.op == "hmult" else None, evk=key_for(r),
+                               out=out_for(r) if out_for is not None else None, bytes=self.footprint(r)))
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        while pending or any(s.req for s in slots):
-            now = time.perf_counter() - t0
-            for li, s in enumerate(slots):
-                if s.req is not None and s.event.query():
-                    done.append(Done(s.req.rid, s.req.arrival, s.start, now, li))
-                    inflight -= s.bytes
-                    K.ckks_pool_release(self._pool, s.bytes)
-                    slots[li] = _Slot()
-            while pending and pending[0].arrival <= now:
-                req = pending[0]
-                need = self.footprint(req)
-                if need > self.budget_bytes - self.resident_bytes:
-                    raise ValueError(f"request {req.rid} needs {need} bytes, more than the budget leaves "
-                                     f"({self.budget_bytes} - {self.resident_bytes} resident)")
-                free = [li for li, s in enumerate(slots) if s.req is None]
-                if not free or not K.ckks_pool_acquire(self._pool, need):
-                    break
-                pending.popleft()
-                li = free[0]
-                lane = self._ctxs[li]
-                a, b = inputs_for(req)
-                out = out_for(req, li)
-                if req.op == "hmult":
-                    K.ckks_hmult(lane, a, b, key_for(req), K.CKKS_RESCALE, out)
-                else:
-                    K.ckks_hrot(lane, a, req.rot, key_for(req), out)
-                ev = torch.cuda.Event()
-                ev.record(self._streams[li])
-                slots[li] = _Slot(req, ev, now, need)
-                inflight += need
-        return done
+        times, order = K.ckks_serve_run(self._ctxs, self._pool, native, lane_outs=lane_outs)
+        return [Done(reqs[i].rid, reqs[i].arrival, times[i][0], times[i][1], times[i][2]) for i in order]
 
 
 def latency_stats(done):

@@ -106,6 +106,14 @@ def test_null_handles_are_rejected_without_a_gpu(K):
     assert L.ckks_set_wait_limit(None, 1) == E
     assert L.ckks_rescale_noalloc(None, None, 1, None) == E
     assert L.ckks_level_limbs(None, 0) == E
+    assert L.ckks_serve_run(None, 1, None, None, 0, None, None, None, None) == E   # no pool
+    pool = K.ckks_pool_create(100)
+    try:
+        assert L.ckks_serve_run(None, 1, pool, None, 0, None, None, None, None) == E   # no lanes, no hooks
+        assert L.ckks_serve_run(None, 0, pool, None, 0, None, None, None, None) == E   # no lane
+        assert L.ckks_serve_run(None, 1, pool, None, 1, None, None, None, None) == E   # no requests
+    finally:
+        K.ckks_pool_destroy(pool)
 
 
 def test_admission_pool_refuses_beyond_its_budget(K):

@@ -54,7 +54,7 @@ def test_results_same_alone_and_in_the_mix(K, O):
         budget = keys + 2 * top
         srv = Server(K, ctx, 3, budget, P.n, resident_bytes=keys)
         try:
-            done = srv.run(reqs, inputs_for, key_for, lambda r, lane: outs[r.rid])
+            done = srv.run(reqs, inputs_for, key_for, out_for=lambda r: outs[r.rid])
             fp = {r.rid: srv.footprint(r) for r in reqs}
         finally:
             srv.close()
