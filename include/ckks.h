@@ -376,8 +376,9 @@ void ckks_batch_destroy(ckks_batch* batch);
  *             completed, 0 while it runs, a negative code on failure; lanes
  *             may then be NULL).
  *  done:      n records, filled by request index: admission and completion
- *             times, the lane.
- *  order:     NULL or n request indices in completion order.
+ *             times, the lane (-1 for a request that was never admitted).
+ *  order:     NULL or n request indices in completion order (after a
+ *             failure only the completed requests' entries are written).
  * Errors: CKKS_EINVAL for bad arguments, or a request whose bytes exceed
  * what the pool can ever grant it (its budget less the bytes it held at the
  * start); the first failing issue or completion ends the run with that code
